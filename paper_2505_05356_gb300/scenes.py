@@ -1,0 +1,225 @@
+"""Seeded synthetic scenes shaped like the paper's C-ToF workloads.
+
+This module only DRAWS inputs (random Gaussian parameters, cameras, times,
+backgrounds); it holds none of the method's arithmetic.  Both the CUDA path's
+tests and the FP64 oracle take their inputs from here.  Every array is drawn
+in single precision and kept as float32, so the single-precision CUDA path and
+the double-precision oracle see exactly the same numbers (the oracle widens
+them losslessly).
+
+Scene shapes (the paper's datasets are not available; these stand in for
+their shape: a static monocular camera, fast lateral/axial motion, depths
+within about one unambiguous range, raw quartets; Sec. 6 "Datasets"):
+
+* ``static_1k``   -- 1,000 static Gaussians, 64x64, 30 MHz, 4 offsets.
+* ``dynamic_100k`` -- 100,000 Gaussians on cubic trajectories, 640x480.
+* ``batch_300k``  -- 300,000 dynamic Gaussians, 640x480, 16 timesteps t=b/15,
+  per-frame visible fraction U[0.3, 1] (the rest displaced 10 m sideways
+  for that frame through the per-frame displacement input).
+* ``twofreq_500k`` -- 500,000 dynamic Gaussians, 640x576, 30 and 80 MHz
+  (phase wrapping), depths 0.5-6 m, 8 timesteps.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+F32 = np.float32
+
+
+@dataclasses.dataclass
+class Camera:
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    world_to_cam: np.ndarray  # (3, 4) float32, [R | t], R orthonormal
+    near: float = 0.2
+
+
+@dataclasses.dataclass
+class Sensor:
+    freqs_hz: List[float]
+    offsets_rad: List[float]
+    source_intensity: float = 1.0
+
+    @property
+    def n_channels(self) -> int:
+        return len(self.freqs_hz) * len(self.offsets_rad) + 1
+
+
+@dataclasses.dataclass
+class Consts:
+    dilation: float = 0.3
+    alpha_max: float = 0.99
+    alpha_min: float = 1.0 / 255.0
+    t_min: float = 1e-4
+    guard: float = 1.3
+    sigma_cut: float = 3.0
+    tile_w: int = 16
+    tile_h: int = 16
+
+    def rounded(self) -> "Consts":
+        """The same constants rounded to float32 (what a single-precision
+        implementation actually uses)."""
+        r = lambda v: float(np.float32(v))
+        return Consts(r(self.dilation), r(self.alpha_max), r(self.alpha_min),
+                      r(self.t_min), r(self.guard), r(self.sigma_cut),
+                      self.tile_w, self.tile_h)
+
+
+@dataclasses.dataclass
+class Scene:
+    means: np.ndarray       # (N, 3)
+    coeffs: Optional[np.ndarray]  # (N, 3, 3): c1, c2, c3 (each xyz)
+    scales: np.ndarray      # (N, 3) linear scales
+    quats: np.ndarray       # (N, 4) w, x, y, z (unnormalised)
+    opacity: np.ndarray     # (N,) in (0, 1)
+    amplitude: np.ndarray   # (N,) reflectivity r_k
+    times: np.ndarray       # (B,)
+    cameras: List[Camera]   # B cameras
+    delta: Optional[np.ndarray]  # (B, N, 3) per-frame displacement or None
+    sensor: Sensor
+    consts: Consts
+    bg: np.ndarray          # (B, C) background per channel
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @property
+    def frames(self) -> int:
+        return len(self.cameras)
+
+    @property
+    def width(self) -> int:
+        return self.cameras[0].width
+
+    @property
+    def height(self) -> int:
+        return self.cameras[0].height
+
+
+def pinhole(width: int, height: int, fov_x_deg: float = 60.0,
+            near: float = 0.2) -> Camera:
+    """Camera at the origin looking down +z, square pixels, principal point
+    at the image centre (fx from the horizontal field of view)."""
+    fx = float(F32(width / (2.0 * math.tan(math.radians(fov_x_deg) / 2.0))))
+    rt = np.zeros((3, 4), F32)
+    rt[:3, :3] = np.eye(3, dtype=F32)
+    return Camera(width, height, fx, fx, width / 2.0, height / 2.0, rt, near)
+
+
+def _unit_quats(rng: np.random.Generator, n: int) -> np.ndarray:
+    q = rng.standard_normal((n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return q.astype(F32)
+
+
+def _sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def random_gaussians(rng, n, cam: Camera, z_range=(1.0, 3.0), box=False,
+                     log_scale=(-3.5, 0.3), coeff_std=0.0):
+    """Random Gaussians: depth uniform in z_range, lateral position uniform
+    inside the camera frustum at that depth (or in a 1 m box when box=True)."""
+    z = rng.uniform(z_range[0], z_range[1], n)
+    if box:
+        x = rng.uniform(-0.5, 0.5, n)
+        y = rng.uniform(-0.5, 0.5, n)
+    else:
+        hx = (cam.width / 2.0) / cam.fx
+        hy = (cam.height / 2.0) / cam.fy
+        x = rng.uniform(-1.0, 1.0, n) * hx * z
+        y = rng.uniform(-1.0, 1.0, n) * hy * z
+    means = np.stack([x, y, z], 1).astype(F32)
+    scales = np.exp(rng.normal(log_scale[0], log_scale[1], (n, 3))).astype(F32)
+    quats = _unit_quats(rng, n)
+    opacity = _sigmoid(rng.standard_normal(n)).astype(F32)
+    amplitude = rng.uniform(0.1, 1.0, n).astype(F32)
+    coeffs = None
+    if coeff_std > 0:
+        coeffs = rng.normal(0.0, coeff_std, (n, 3, 3)).astype(F32)
+    return means, coeffs, scales, quats, opacity, amplitude
+
+
+def make_scene(name: str, seed: int = 0, **over) -> Scene:
+    """Build one of the named synthetic workloads (see module docstring).
+
+    Overrides: n, width, height, frames, freqs_hz, offsets_rad, tile, bg
+    ('zero' | 'random'), z_range, coeff_std, visible_min, consts.
+    """
+    rng = np.random.default_rng(seed)
+    if name == "static_1k":
+        d = dict(n=1000, width=64, height=64, frames=1, freqs_hz=[30e6],
+                 z_range=(1.0, 3.0), coeff_std=0.0, box=True, visible_min=1.0)
+    elif name == "dynamic_100k":
+        d = dict(n=100_000, width=640, height=480, frames=1, freqs_hz=[30e6],
+                 z_range=(1.0, 3.0), coeff_std=0.05, box=False, visible_min=1.0)
+    elif name == "batch_300k":
+        d = dict(n=300_000, width=640, height=480, frames=16, freqs_hz=[30e6],
+                 z_range=(1.0, 3.0), coeff_std=0.05, box=False, visible_min=0.3)
+    elif name == "twofreq_500k":
+        d = dict(n=500_000, width=640, height=576, frames=8,
+                 freqs_hz=[30e6, 80e6], z_range=(0.5, 6.0), coeff_std=0.05,
+                 box=False, visible_min=0.3)
+    else:
+        raise ValueError("unknown scene %r" % name)
+    d.update(dict(offsets_rad=[0.0, math.pi / 2, math.pi, 3 * math.pi / 2],
+                  tile=(16, 16), bg="random", log_scale=(-3.5, 0.3)))
+    d.update(over)
+
+    cam = pinhole(d["width"], d["height"])
+    means, coeffs, scales, quats, opacity, amplitude = random_gaussians(
+        rng, d["n"], cam, d["z_range"], d["box"], d["log_scale"], d["coeff_std"])
+    frames = d["frames"]
+    times = (np.arange(frames) / max(frames - 1, 1)).astype(F32)
+    if frames == 1 and d["coeff_std"] > 0:
+        times = np.array([rng.uniform(0.0, 1.0)], F32)
+    delta = None
+    if d["visible_min"] < 1.0:
+        delta = np.zeros((frames, d["n"], 3), F32)
+        for b in range(frames):
+            v = rng.uniform(d["visible_min"], 1.0)
+            hide = rng.random(d["n"]) >= v
+            delta[b, hide, 0] = 10.0
+    sensor = Sensor([float(F32(f)) for f in d["freqs_hz"]],
+                    [float(F32(o)) for o in d["offsets_rad"]], 1.0)
+    consts = d.get("consts") or Consts(tile_w=d["tile"][0], tile_h=d["tile"][1])
+    consts = consts.rounded()
+    C = sensor.n_channels
+    if d["bg"] == "random":
+        bg = rng.uniform(-1.0, 1.0, (frames, C)).astype(F32)
+    else:
+        bg = np.zeros((frames, C), F32)
+    return Scene(means, coeffs, scales, quats, opacity, amplitude, times,
+                 [cam] * frames, delta, sensor, consts, bg)
+
+
+def random_dout(scene: Scene, seed: int = 1, density: float = 1.0) -> np.ndarray:
+    """A seeded loss gradient dL/d(out), shape (B, C, H, W), float32.
+    density < 1 keeps only that fraction of pixels (the rest exactly 0)."""
+    rng = np.random.default_rng(seed)
+    B, C, H, W = scene.frames, scene.sensor.n_channels, scene.height, scene.width
+    g = rng.standard_normal((B, C, H, W)).astype(F32)
+    if density < 1.0:
+        keep = rng.random((B, 1, H, W)) < density
+        g = g * keep
+    return g
+
+
+def sample_pixels(scene: Scene, k: int, seed: int = 2) -> np.ndarray:
+    """k distinct pixel positions (x, y) per frame, int32, shape (B, k, 2)."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((scene.frames, k, 2), np.int32)
+    for b in range(scene.frames):
+        idx = rng.choice(scene.width * scene.height, size=k, replace=False)
+        out[b, :, 0] = idx % scene.width
+        out[b, :, 1] = idx // scene.width
+    return out
