@@ -1,0 +1,499 @@
+"""Benchmark: fwd+bwd raw C-ToF frames/s at 640x480 with 300k Gaussians.
+
+One step = one batch of 16 timesteps of the 300k-Gaussian dynamic scene
+(cubic trajectories, 30-100 % of the Gaussians visible per frame): deform +
+project, bin + sort, composite (Eq. 4), then the backward (Eq. S3 re-walk,
+chain rule to every Gaussian parameter), all in libgftorf's kernels,
+replayed as one captured CUDA graph.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the baseline this path is compared with).
+Multi-GPU (torchrun): every rank renders its own batch (independent
+problems, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd raw C-ToF frames/sec at 640x480, 300k Gaussians; % HBM/FP32 roofline"
+UNIT = "frames/s"
+WORKLOAD = "batch_300k"
+
+# Algorithmic work per unit ("Roofline"): FP32 lane operations per
+# evaluated (pixel, Gaussian) pair of the compositing kernels, and bytes per
+# Gaussian-frame / per instance of the memory-bound stages.
+OPS_PER_PAIR_FWD = 20
+OPS_PER_PAIR_BWD = 60
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_05356_gb300 import gftorf, scenes
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    sc = scenes.make_scene(args.workload, seed=rank)
+    B, N, W, H = sc.frames, sc.n, sc.width, sc.height
+    tile = tuple(int(v) for v in args.tile.split("x"))
+    sc.consts.tile_w, sc.consts.tile_h = tile
+    r = gftorf.Renderer(N, B, W, H, len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad),
+                        tile=tile, render_mode=args.mode)
+    p = gftorf.params_from_scene(sc)
+    fr = gftorf.frames_from_scene(sc)
+    se = gftorf.sensor_from_scene(sc)
+    co = gftorf.consts_from_scene(sc)
+    bg = torch.as_tensor(sc.bg, device="cuda")
+    dout = torch.as_tensor(scenes.random_dout(sc, 100 + rank), device="cuda")
+    r.fit_capacity(p, fr, se, co, bg)
+    out = torch.empty((B, sc.sensor.n_channels, H, W), device="cuda")
+    grads = r.alloc_grads(p, bg)
+
+    def step():
+        r.preprocess(p, fr, se, co)
+        r.bin()
+        r.composite_fwd(bg, out)
+        r.zero_grad_buffers(grads)
+        r.composite_bwd(bg, dout, grads)
+        r.preprocess_bwd(p, grads)
+
+    # eager warm-up + kernels per step
+    step()
+    torch.cuda.synchronize()
+    r.check()
+    k0 = gftorf.kernel_launches()
+    step()
+    torch.cuda.synchronize()
+    kernels_per_step = gftorf.kernel_launches() - k0
+
+    use_graph = not args.no_graph
+    if use_graph:
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step()
+        torch.cuda.current_stream().wait_stream(s)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        run = graph.replay
+    else:
+        run = step
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    code, count = r.read_status()
+    if code != gftorf.OK:
+        raise RuntimeError("device status %s" % gftorf.STATUS.get(code))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * B * args.steps / (ms / 1e3)
+
+    # --- per-stage timing (same stream, CUDA events, eager) ---
+    stages = ["preprocess", "bin", "composite_fwd", "zero_grad_buffers", "composite_bwd",
+              "preprocess_bwd"]
+    calls = [lambda: r.preprocess(p, fr, se, co), r.bin, lambda: r.composite_fwd(bg, out),
+             lambda: r.zero_grad_buffers(grads), lambda: r.composite_bwd(bg, dout, grads),
+             lambda: r.preprocess_bwd(p, grads)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        ev[k][0].record()
+        for i, c in enumerate(calls):
+            c()
+            ev[k][i + 1].record()
+    torch.cuda.synchronize()
+    stage_ms = {s_: sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
+                for i, s_ in enumerate(stages)}
+
+    # --- algorithmic work of this batch ---
+    keys, vals, ranges, cnt = r.tile_lists(with_keys=False)
+    tf, nl = r.pixel_state()
+    rg = ranges.to(torch.int64)
+    lens = (rg[:, 1] - rg[:, 0]).reshape(B, r.tiles_y, r.tiles_x)
+    lens_px = lens.repeat_interleave(tile[1], 1).repeat_interleave(tile[0], 2)[:, :H, :W]
+    pairs = int(torch.minimum(nl.to(torch.int64) + 1, lens_px).sum().item())
+    instances = int(cnt.item())
+    peaks, peak_kind = _peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e9  # G FP32 lane-ops/s
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    vis = B * N  # upper bound of Gaussian-frames
+    work = {
+        "composite_bwd": ("alu", pairs * OPS_PER_PAIR_BWD / 1e9, "Gop/s", alu_peak),
+        "composite_fwd": ("alu", pairs * OPS_PER_PAIR_FWD / 1e9, "Gop/s", alu_peak),
+        # read 84 B of parameters + write a 48 B record, 8 B rect, 4 B key
+        "preprocess": ("hbm", vis * (84 + 60) / 1e9, "GB/s", hbm_peak),
+        # instance values written once; depth keys 4 passes x 16 B
+        "bin": ("hbm", (instances * 4 + vis * 16 * 4) / 1e9, "GB/s", hbm_peak),
+        "preprocess_bwd": ("hbm", vis * (84 + 36 + 12) / 1e9, "GB/s", hbm_peak),
+        "zero_grad_buffers": ("hbm", vis * 36 / 1e9, "GB/s", hbm_peak),
+    }
+    dom = max(stage_ms, key=stage_ms.get)
+    bound, amount, unit, peak = work[dom]
+    achieved = amount / (stage_ms[dom] / 1e3)
+    roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 2),
+                "peak": round(peak, 2), "unit": unit, "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_source": peak_kind}
+    stage_rows = {}
+    for s_ in stages:
+        b_, a_, u_, pk_ = work[s_]
+        ach = a_ / (stage_ms[s_] / 1e3) if stage_ms[s_] > 0 else 0.0
+        stage_rows[s_] = {"ms": round(stage_ms[s_], 4), "bound": b_, "achieved": round(ach, 1),
+                          "unit": u_, "frac": round(ach / pk_, 4)}
+
+    # --- end to end through the public API with host buffers ---
+    e2e = None
+    if not args.skip_e2e:
+        host = {k: v.cpu().pin_memory() for k, v in p.items() if v is not None}
+        hbg = bg.cpu().pin_memory()
+        hdout = dout.cpu().pin_memory()
+        hgr = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in grads.items()}
+        h2d = sum(t.numel() * t.element_size() for t in host.values()) + \
+            hbg.numel() * 4 + hdout.numel() * 4
+        d2h = sum(t.numel() * t.element_size() for t in hgr.values())
+
+        def e2e_step():
+            for k, t in host.items():
+                p[k].copy_(t, non_blocking=True)
+            bg.copy_(hbg, non_blocking=True)
+            dout.copy_(hdout, non_blocking=True)
+            run()
+            for k, t in hgr.items():
+                t.copy_(grads[k], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(args.steps):
+            e2e_step()
+        a1.record()
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": round(world * B * args.steps / (ems / 1e3), 2), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # --- per-frame plain launches (no batching, no graph), same work ---
+    plain = None
+    if not args.skip_plain and rank == 0:
+        r1 = gftorf.Renderer(N, 1, W, H, len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad),
+                             tile=tile, render_mode=0,
+                             max_instances=max(1024, int(r.capacity / B * 1.6)))
+        gacc = {k: torch.zeros_like(v) for k, v in grads.items() if k not in ("bg", "delta")}
+        p1s = []
+        for b in range(B):
+            p1 = dict(p)
+            p1["delta"] = p["delta"][b:b + 1].contiguous() if p["delta"] is not None else None
+            p1s.append(p1)
+        bgs = [bg[b:b + 1].contiguous() for b in range(B)]
+        douts = [dout[b:b + 1].contiguous() for b in range(B)]
+        out1 = torch.empty((1,) + tuple(out.shape[1:]), device="cuda")
+        g1 = r1.alloc_grads(p1s[0], bgs[0])
+
+        def plain_step():
+            for v in gacc.values():
+                v.zero_()
+            for b in range(B):
+                r1.preprocess(p1s[b], [fr[b]], se, co)
+                r1.render_fwd(bgs[b], out1)
+                r1.render_bwd(p1s[b], bgs[b], douts[b], grads=g1)
+                for k, v in gacc.items():
+                    v.add_(g1[k])
+
+        for _ in range(max(2, args.warmup)):
+            plain_step()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record()
+        for _ in range(args.steps):
+            plain_step()
+        q1.record()
+        torch.cuda.synchronize()
+        pms = q0.elapsed_time(q1) / args.steps
+        code1, _ = r1.read_status()
+        plain = {"value": round(B / (pms / 1e3), 2), "unit": UNIT, "ms_per_step": round(pms, 3),
+                 "status": gftorf.STATUS.get(code1)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(sc, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded; shaped like the paper's C-ToF scenes)",
+            "config": {"workload": "%s: %d dynamic Gaussians (cubic trajectories), %dx%d, "
+                                   "%d timesteps per batch, 30 MHz x 4 offsets + ambient, "
+                                   "30-100%% visible per frame" % (WORKLOAD, N, W, H, B),
+                       "frames_per_step": B, "tile": args.tile,
+                       "render_mode": "persistent" if args.mode == 1 else "grid",
+                       "cuda_graph": use_graph, "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (%.0f MB workspace per step)" % (r.ws_bytes / 1e6),
+                       "instances_per_step": instances, "pairs_per_step": pairs},
+            "gpu_launches": int(kernels_per_step * args.steps),
+            "kernels_per_step": int(kernels_per_step),
+            "roofline": roofline,
+            "stages": stage_rows,
+            "e2e": e2e,
+            "per_frame_plain": plain,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline; bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def oracle_sample(sc, n_pix, frame=0, seed=5):
+    """Time the FP64 oracle's fwd+bwd on n_pix random pixels of one frame and
+    extrapolate to frames/s.  Returns (frames_per_s, seconds_spent, detail)."""
+    from oracle import oracle as ora
+    from paper_2505_05356_gb300 import scenes
+
+    one = scenes.Scene(sc.means, sc.coeffs, sc.scales, sc.quats, sc.opacity, sc.amplitude,
+                       sc.times[frame:frame + 1], sc.cameras[frame:frame + 1],
+                       None if sc.delta is None else sc.delta[frame:frame + 1],
+                       sc.sensor, sc.consts, sc.bg[frame:frame + 1])
+    HW = sc.width * sc.height
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(HW, n_pix, replace=False)
+    pix = np.stack([idx % sc.width, idx // sc.width], 1).astype(np.int32)
+    P = ora.Params(one)
+    t0 = time.perf_counter()
+    sp = ora.project(one, 0, ora.EPS_NONE, P)
+    t1 = time.perf_counter()
+    ora.render_pixels(one, 0, pix, sp)
+    t2 = time.perf_counter()
+    dout = np.zeros((sc.sensor.n_channels, sc.height, sc.width))
+    dout[:, pix[:, 1], pix[:, 0]] = 1.0
+    nf = 2 * len(sc.sensor.freqs_hz) + 1
+    g2d = np.zeros((sc.n, 6 + nf))
+    lib = ora.lib()
+    fr, se, co = ora.pack_frame(one, 0), ora.pack_sensor(one), ora.pack_consts(one)
+    lib.ora_backward_2d(sc.n, ora._p(sp), ora._p(fr), ora._p(se), ora._p(co),
+                        ora._p(np.ascontiguousarray(one.bg[0], np.float64)), ora._p(dout),
+                        ora._p(g2d), None)
+    t3 = time.perf_counter()
+    grads = np.zeros((sc.n, ora.NPARAM))
+    lib.ora_backward_params(sc.n, ora._p(P.means), ora._p(P.coeffs), ora._p(P.scales),
+                            ora._p(P.quats), ora._p(P.opacity), ora._p(P.amplitude),
+                            ora._p(P.delta_of(0)), ora._p(fr), ora._p(se), ora._p(co),
+                            ora._p(sp), ora._p(g2d), ora._p(grads))
+    t4 = time.perf_counter()
+    touched = int(np.count_nonzero(np.any(g2d != 0, axis=1)))
+    visible = int(np.count_nonzero(sp[:, ora.SP["VIS"]]))
+    per_frame = ((t1 - t0) + ((t2 - t1) + (t3 - t2)) * HW / n_pix +
+                 (t4 - t3) * (visible / max(touched, 1)))
+    detail = dict(project_s=t1 - t0, fwd_pixels_s=t2 - t1, bwd_pixels_s=t3 - t2,
+                  chain_s=t4 - t3, touched=touched, visible=visible)
+    return 1.0 / per_frame, t4 - t0, detail
+
+
+def cpu_baseline(sc, seconds):
+    from oracle import oracle as ora
+    # calibrate the pixel sample so the run takes about `seconds`
+    fps, spent, _ = oracle_sample(sc, 16)
+    per_px = max(spent, 1e-3) / 16
+    n_pix = int(min(sc.width * sc.height, max(16, seconds / per_px)))
+    fps, spent, det = oracle_sample(sc, n_pix, seed=6)
+    return {"value": round(fps, 6), "unit": UNIT, "cores": ora.num_threads(), "kind": "oracle",
+            "sample": "frame 0 of the batch: projection of all %d Gaussians + fwd/bwd of %d "
+                      "random pixels (of %d) + chain rule of the %d touched Gaussians, "
+                      "extrapolated to a full frame (%.1f s of CPU work)"
+                      % (sc.n, n_pix, sc.width * sc.height, det["touched"], spent)}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as ora
+    from paper_2505_05356_gb300 import scenes
+
+    sc = scenes.make_scene(args.workload, seed=0)
+    fps, spent, _ = oracle_sample(sc, 16)
+    per_px = max(spent, 1e-3) / 16
+    budget = max(5.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
+    n_pix = int(min(sc.width * sc.height, max(16, budget / per_px)))
+    for w in range(args.warmup):
+        oracle_sample(sc, max(16, n_pix // 8), frame=w % sc.frames, seed=w)
+    rates, total = [], 0.0
+    for k in range(args.steps):
+        fps, spent, det = oracle_sample(sc, n_pix, frame=k % sc.frames, seed=100 + k)
+        rates.append(fps)
+        total += spent
+    value = len(rates) / sum(1.0 / x for x in rates)  # frames per second over the steps
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sc.frames / value, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded; shaped like the paper's C-ToF scenes)",
+        "config": {"workload": "%s: %d dynamic Gaussians, %dx%d, %d timesteps per batch"
+                               % (WORKLOAD, sc.n, sc.width, sc.height, sc.frames)},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": ora.num_threads(),
+                         "kind": "oracle",
+                         "sample": "per step one frame: projection of all Gaussians + fwd/bwd of "
+                                   "%d random pixels + chain rule of the touched Gaussians, "
+                                   "extrapolated to the full frame" % n_pix},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--mode", type=int, default=0, help="0 grid, 1 persistent")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * gftorf.h -- C ABI of the GB300 (sm_103a) raw C-ToF Gaussian splatting path
+ * of "Time of the Flight of the Gaussians" (arXiv 2505.05356).
+ *
+ * The library renders time-varying 3D Gaussians into raw continuous-wave
+ * time-of-flight samples (Eq. 4: each Gaussian contributes
+ * (s r_k / d_k^2) sin(psi_k + phi_j) o_k G2D_k T_k^2, psi_k = 4 pi d_k f / c,
+ * with T_k squared for the round trip, plus q_bg T_N) at every modulation
+ * frequency f and phase offset phi_j, plus one ambient channel
+ * (sum_k (s r_k / d_k^2) o_k G2D_k T_k^2 + bg T_N), and differentiates it
+ * (Eq. S3 opacity recursion with squared transmittance).
+ *
+ * Pipeline per batch of frames (three calls):
+ *   gftorf_preprocess  -- deform each Gaussian to the frame's time
+ *                         x(t) = mu + c1 t + c2 t^2 + c3 t^3 (+ delta_b),
+ *                         project (EWA, 3DGS convention), depth, tile bounds,
+ *                         C-ToF features (Sec. 4, Eq. 3/4 terms).
+ *   gftorf_render_fwd  -- depth radix sort, tile-key duplication, stable tile
+ *                         sort, per-tile ranges, then front-to-back
+ *                         compositing of Eq. 4 per pixel.
+ *   gftorf_render_bwd  -- back-to-front re-walk (Eq. S3), 2D gradients with
+ *                         warp-reduced atomics, chain rule to the Gaussian
+ *                         parameters, summed over frames.
+ *
+ * Conventions shared by every entry point:
+ *   - All array arguments are DEVICE pointers unless stated otherwise, owned
+ *     by the caller.  The library never allocates or frees memory; all its
+ *     scratch lives in a caller-allocated workspace (see
+ *     gftorf_workspace_size).  Nothing synchronises the stream unless stated.
+ *   - `stream` is a cudaStream_t passed as void*.  All work is enqueued on it
+ *     in order, so the calls can be captured in a CUDA graph.
+ *   - Scalar type of all parameter, output and gradient arrays is
+ *     dims->dtype: GFTORF_F32 (float) or GFTORF_F64 (double).
+ *   - Errors: invalid arguments return immediately with GFTORF_ERR_ARG (no
+ *     work enqueued).  Errors found on the device (tile-instance capacity
+ *     exceeded) are recorded in a status word inside the workspace; the
+ *     affected work is skipped without out-of-bounds access; read the word
+ *     with gftorf_read_device_status.  No entry point aborts or traps.
+ *   - Pixel (x, y) samples the image plane at (x + 0.5, y + 0.5); a point
+ *     p (camera frame) projects to (fx p_x / p_z + cx, fy p_y / p_z + cy).
+ *   - Outputs are channel-major: out[frame][channel][y][x]; channels are the
+ *     F*P raw samples, frequency-major (f0 phi0, f0 phi1, ..., f1 phi0, ...),
+ *     then the ambient channel; C = F*P + 1.
+ */
+#ifndef GFTORF_H
+#define GFTORF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GFTORF_MAX_FREQ 4
+#define GFTORF_MAX_OFFSETS 8
+#define GFTORF_MAX_FRAMES 64
+
+typedef enum {
+  GFTORF_OK = 0,
+  GFTORF_ERR_ARG = 1,         /* invalid argument (host-side check)          */
+  GFTORF_ERR_CAPACITY = 2,    /* more tile instances than dims.max_instances */
+  GFTORF_ERR_TIMEOUT = 3,     /* a bounded device wait gave up               */
+  GFTORF_ERR_CUDA = 4,        /* a CUDA launch or runtime call failed        */
+  GFTORF_ERR_UNSUPPORTED = 5, /* valid but unsupported configuration         */
+  GFTORF_ERR_WORKSPACE = 6    /* workspace missing, misaligned or too small  */
+} gftorf_status;
+
+typedef enum { GFTORF_F32 = 0, GFTORF_F64 = 1 } gftorf_dtype;
+
+/* Static problem shape.  One workspace serves one dims value. */
+typedef struct {
+  int32_t n_gaussians;   /* N >= 0                                          */
+  int32_t n_frames;      /* B in [1, GFTORF_MAX_FRAMES]                     */
+  int32_t width, height; /* image size in pixels, >= 1                      */
+  int32_t tile_w, tile_h;/* one of 8x8, 16x16, 16x32 (w x h)                */
+  int32_t n_freq;        /* F in [1, GFTORF_MAX_FREQ]                       */
+  int32_t n_offsets;     /* P in [1, GFTORF_MAX_OFFSETS]                    */
+  int32_t dtype;         /* gftorf_dtype                                    */
+  int32_t render_mode;   /* 0: one CTA per (frame, tile);
+                            1: persistent CTAs over a (frame, tile) queue   */
+  int64_t max_instances; /* capacity of the (Gaussian, tile) instance list,
+                            summed over the batch                           */
+} gftorf_dims;
+
+/* One frame (host struct): pinhole camera with a rigid world->camera
+ * transform [R | t] (R orthonormal, row-major 3x4), near-plane cull distance (> 0)
+ * on the view depth, and the frame's time t for the deformation.  Sec. 4:
+ * emitter co-located with the camera, so d_k is the distance from the
+ * Gaussian centre to the optical centre o = -R^T t. */
+typedef struct {
+  float fx, fy, cx, cy;
+  float world_to_cam[12];
+  float near_plane;
+  float time;
+} gftorf_frame;
+
+/* C-ToF sensor (Sec. 3): modulation frequencies f (Hz), phase offsets phi_j
+ * of the reference signal (rad, shared by all frequencies), source
+ * intensity s.  Raw sample j of frequency f is A sin(psi_f + phi_j). */
+typedef struct {
+  float freq_hz[GFTORF_MAX_FREQ];
+  float offset_rad[GFTORF_MAX_OFFSETS];
+  float source_intensity;
+} gftorf_sensor;
+
+/* Screen-space constants of the 3DGS rasterizer the paper builds on
+ * (Sec. 5, implementation details).  Defaults: dilation 0.3 (added to the 2D
+ * covariance diagonal), alpha_max 0.99 (alpha = min(alpha_max, o G)),
+ * alpha_min 1/255 (smaller alphas are skipped), t_min 1e-4 (the walk stops
+ * before a Gaussian that would take the one-way T below it), guard 1.3
+ * (lateral clamp of the EWA Jacobian, in units of the half field of view),
+ * sigma_cut 3 (footprint radius in standard deviations). */
+typedef struct {
+  float dilation, alpha_max, alpha_min, t_min, guard, sigma_cut;
+} gftorf_consts;
+
+/* Gaussian parameters (device pointers, dims.dtype, N rows):
+ *   means[N][3]; coeffs[N][3][3] = (c1, c2, c3) each xyz, or NULL (static);
+ *   scales[N][3] (linear, > 0); quats[N][4] (w, x, y, z; normalised inside);
+ *   opacity[N] in (0, 1]; amplitude[N] = reflectivity r_k;
+ *   delta[B][N][3] per-frame displacement added to x(t), or NULL. */
+typedef struct {
+  const void *means, *coeffs, *scales, *quats, *opacity, *amplitude, *delta;
+} gftorf_gaussians;
+
+/* Gradient outputs (device pointers, dims.dtype; each may be NULL to skip),
+ * same layouts as the inputs; bg[B][C].  They are OVERWRITTEN, not
+ * accumulated. */
+typedef struct {
+  void *means, *coeffs, *scales, *quats, *opacity, *amplitude, *delta, *bg;
+} gftorf_gradients;
+
+/* Bytes of workspace needed for `dims` (0 if dims is invalid).  The
+ * workspace must be 256-byte aligned device memory owned by the caller; the
+ * library keeps everything between gftorf_preprocess and gftorf_render_bwd
+ * there (projected records, sort buffers, tile ranges, per-pixel final
+ * transmittance and last-contributor index, 2D gradients). */
+size_t gftorf_workspace_size(const gftorf_dims* dims);
+
+/* Deformation + projection + C-ToF features for all frames (Sec. 4, Eq. 3/4
+ * terms; deformation x(t) = mu + c1 t + c2 t^2 + c3 t^3 + delta_b).
+ * frames: HOST array of dims->n_frames entries; sensor, consts: HOST.
+ * Resets the device status word. */
+gftorf_status gftorf_preprocess(const gftorf_dims* dims,
+                                const gftorf_gaussians* gaussians,
+                                const gftorf_frame* frames,
+                                const gftorf_sensor* sensor,
+                                const gftorf_consts* consts, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* Binning and compositing (Eq. 4).  bg[B][C] device; out[B][C][H][W] device.
+ * Needs a preceding gftorf_preprocess on the same workspace. */
+gftorf_status gftorf_render_fwd(const gftorf_dims* dims, const void* bg,
+                                void* out, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* Backward of gftorf_render_fwd (Eq. S3 recursion; chain rule through the
+ * projection and deformation, summed over frames in a fixed order).
+ * gaussians: the same parameters the batch was preprocessed with (re-read
+ * to recompute the projection instead of storing it); dL_dout[B][C][H][W]
+ * and bg[B][C] device.  Needs the gftorf_render_fwd of the same batch to be
+ * the last render on this workspace. */
+gftorf_status gftorf_render_bwd(const gftorf_dims* dims,
+                                const gftorf_gaussians* gaussians,
+                                const void* bg, const void* dL_dout,
+                                const gftorf_gradients* grads, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* The stages of gftorf_render_fwd and gftorf_render_bwd, callable one by
+ * one (same arguments and requirements as the combined calls):
+ *   gftorf_render_fwd = gftorf_bin + gftorf_composite_fwd
+ *   gftorf_render_bwd = gftorf_zero_grad_buffers + gftorf_composite_bwd
+ *                       + gftorf_preprocess_bwd
+ * gftorf_bin: depth radix sort, tile-key duplication, stable tile sort and
+ *   per-(frame, tile) ranges of the preprocessed batch.
+ * gftorf_composite_fwd: Eq. 4 compositing over the binned lists.
+ * gftorf_zero_grad_buffers: clears the workspace's per-(frame, Gaussian) 2D
+ *   gradient rows and grads->bg (if non-NULL) before a backward.
+ * gftorf_composite_bwd: Eq. S3 re-walk; accumulates 2D gradients in the
+ *   workspace and dL/dbg into grads->bg (if non-NULL).
+ * gftorf_preprocess_bwd: chain rule from the 2D gradients to the parameter
+ *   gradients of `grads` (except bg), overwriting them. */
+gftorf_status gftorf_bin(const gftorf_dims* dims, void* workspace,
+                         size_t workspace_bytes, void* stream);
+gftorf_status gftorf_composite_fwd(const gftorf_dims* dims, const void* bg,
+                                   void* out, void* workspace,
+                                   size_t workspace_bytes, void* stream);
+gftorf_status gftorf_zero_grad_buffers(const gftorf_dims* dims,
+                                       const gftorf_gradients* grads,
+                                       void* workspace, size_t workspace_bytes,
+                                       void* stream);
+gftorf_status gftorf_composite_bwd(const gftorf_dims* dims, const void* bg,
+                                   const void* dL_dout,
+                                   const gftorf_gradients* grads,
+                                   void* workspace, size_t workspace_bytes,
+                                   void* stream);
+gftorf_status gftorf_preprocess_bwd(const gftorf_dims* dims,
+                                    const gftorf_gaussians* gaussians,
+                                    const gftorf_gradients* grads,
+                                    void* workspace, size_t workspace_bytes,
+                                    void* stream);
+
+/* Binning alone, from caller-given screen-space footprints (device arrays
+ * [B][N]: u, v float32 centre, radius int32 (<= 0: not visible), z float32
+ * view depth > 0).  Tile rectangle, in single precision:
+ *   [floor((u-r)/tw), floor((u+r)/tw)+1) x [floor((v-r)/th), floor((v+r)/th)+1)
+ * clamped to the grid.  Every covered tile emits the 64-bit key
+ * ((b*tiles + tile) << 32) | bits(z) with value g; the pairs are sorted by
+ * key, equal keys by g.  Writes keys[M], values[M] (device, capacity
+ * dims->max_instances), ranges[B*tiles][2] = [start, end) (empty tiles get
+ * [k, k), k the count in the tiles before), and *count (device int64).
+ * Uses dims->n_gaussians, n_frames, width, height, tile_w, tile_h,
+ * max_instances. */
+gftorf_status gftorf_sort_footprints(const gftorf_dims* dims, const float* u,
+                                     const float* v, const int32_t* radius,
+                                     const float* z, uint64_t* keys,
+                                     uint32_t* values, uint32_t* ranges,
+                                     int64_t* count, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+
+/* Copy the current batch's sorted tile instances out of the workspace:
+ * keys[M] (as in gftorf_sort_footprints), values[M], ranges[B*tiles][2],
+ * *count (all device; keys may be NULL).  For inspection and tests. */
+gftorf_status gftorf_export_tile_lists(const gftorf_dims* dims, uint64_t* keys,
+                                       uint32_t* values, uint32_t* ranges,
+                                       int64_t* count, void* workspace,
+                                       size_t workspace_bytes, void* stream);
+
+/* Copy per-pixel state of the last forward: t_final[B][H][W] (dims.dtype),
+ * n_last[B][H][W] (uint32: index within the tile list of the last composited
+ * Gaussian, plus one).  Device pointers; either may be NULL. */
+gftorf_status gftorf_export_pixel_state(const gftorf_dims* dims, void* t_final,
+                                        uint32_t* n_last, void* workspace,
+                                        size_t workspace_bytes, void* stream);
+
+/* Synchronises `stream`, then returns the device status word written since
+ * the last gftorf_preprocess (GFTORF_OK or GFTORF_ERR_CAPACITY /
+ * GFTORF_ERR_TIMEOUT) and, if count is non-NULL, the batch's instance count
+ * (host int64). */
+gftorf_status gftorf_read_device_status(const gftorf_dims* dims,
+                                        void* workspace, size_t workspace_bytes,
+                                        int64_t* count, void* stream);
+
+/* Number of CUDA kernels this library has enqueued so far in this process
+ * (host-side counter; a captured graph's replays are not counted again). */
+int64_t gftorf_kernel_launches(void);
+
+/* Static description of a status code. */
+const char* gftorf_status_string(gftorf_status status);
+
+/* ABI version (major * 100 + minor). */
+int32_t gftorf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFTORF_H */

@@ -1,0 +1,415 @@
+// binning.cu -- tile-key duplication and sorting of (Gaussian, tile)
+// instances, per frame of a batch.
+//
+// The instance order is that of a stable sort of the 64-bit keys
+// (frame * tiles + tile) << 32 | bits(z), with instances emitted in Gaussian
+// order (so equal keys stay in index order).  It is computed as an LSD radix
+// sort whose low digits (the 32 depth bits) are applied to the Gaussians
+// BEFORE duplication -- they are a per-Gaussian key -- and whose high digit
+// (frame, tile) is one stable counting pass over the duplicated instances:
+//   1. depth sort: 4 passes of 8 bits over the per-frame depth keys
+//      (culled Gaussians carry 0xFFFFFFFF and end up last);
+//   2. per chunk of 4096 depth-ordered Gaussians, count covered tiles;
+//   3. exclusive scan over (frame, tile, chunk) -> tile ranges and bases;
+//   4. scatter: each warp walks its Gaussians in depth order and writes the
+//      Gaussian index at its tile's running cursor (stable by construction).
+// The 64-bit keys themselves are never needed by the compositing kernels;
+// gftorf_export_tile_lists materialises them from the ranges.
+#include "gftorf_internal.cuh"
+
+namespace gftorf {
+namespace {
+
+// Exclusive scan in place of a[0..S) by one CTA; returns the total through
+// *total (if non-null).  Each thread scans a contiguous segment.
+__device__ void cta_exclusive_scan(uint32_t* a, int64_t S, uint64_t* total) {
+  __shared__ uint64_t s_warp[32];
+  const int nt = blockDim.x, tid = threadIdx.x;
+  const int64_t seg = (S + nt - 1) / nt;
+  const int64_t lo = min((int64_t)tid * seg, S), hi = min(lo + seg, S);
+  uint64_t sum = 0;
+  for (int64_t i = lo; i < hi; ++i) sum += a[i];
+  // block exclusive scan of the segment sums
+  const int lane = tid & 31, wid = tid >> 5;
+  uint64_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (nt + 31) / 32;
+    uint64_t v = lane < nw ? s_warp[lane] : 0;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < nw) s_warp[lane] = x - v;  // exclusive warp offsets
+  }
+  __syncthreads();
+  uint64_t run = s_warp[wid] + incl - sum;
+  for (int64_t i = lo; i < hi; ++i) {
+    uint32_t v = a[i];
+    a[i] = (uint32_t)run;
+    run += v;
+  }
+  if (total && tid == nt - 1) *total = run;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// footprints given by the caller (binning-only entry point)
+// ---------------------------------------------------------------------------
+__global__ void footprint_kernel(const float* __restrict__ u,
+                                 const float* __restrict__ v,
+                                 const int32_t* __restrict__ radius,
+                                 const float* __restrict__ z,
+                                 Header* __restrict__ hdr,
+                                 uint2* __restrict__ rect,
+                                 uint32_t* __restrict__ zkey, int N, int TW,
+                                 int TH, int tiles_x, int tiles_y) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  bool visible = false;
+  if (g < N) {
+    const size_t i = (size_t)b * N + g;
+    uint2 rr = make_uint2(0, 0);
+    uint32_t key = kCulledKey;
+    const int r = radius[i];
+    if (r > 0) {
+      int x0, y0, x1, y1;
+      tile_rect(u[i], v[i], r, TW, TH, tiles_x, tiles_y, x0, y0, x1, y1);
+      if (x0 < x1 && y0 < y1) {
+        visible = true;
+        rr = pack_rect(x0, y0, x1, y1);
+        key = __float_as_uint(z[i]);
+      }
+    }
+    rect[i] = rr;
+    zkey[i] = key;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, visible);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(&hdr->vis[b], (uint32_t)__popc(m));
+}
+
+// ---------------------------------------------------------------------------
+// depth sort: stable LSD radix sort, 8-bit digits, one segment per frame
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads)
+    dsort_hist_kernel(const uint32_t* __restrict__ kin, int N, int shift,
+                      uint32_t* __restrict__ dh, int n_dblk) {
+  __shared__ uint32_t h[256];
+  const int blk = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+  h[tid] = 0;
+  __syncthreads();
+  const uint32_t* k = kin + (size_t)b * N;
+#pragma unroll 4
+  for (int it = 0; it < kSortItems; ++it) {
+    const int pos = blk * kSortTile + it * kSortThreads + tid;
+    const bool valid = pos < N;
+    const uint32_t d = valid ? (k[pos] >> shift) & 255u : 256u + (tid & 31);
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (valid && __popc(peers & lanemask_lt()) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  dh[((size_t)b * 256 + tid) * n_dblk + blk] = h[tid];
+}
+
+__global__ void __launch_bounds__(1024)
+    dsort_scan_kernel(uint32_t* __restrict__ dh, int n_dblk) {
+  cta_exclusive_scan(dh + (size_t)blockIdx.x * 256 * n_dblk, (int64_t)256 * n_dblk,
+                     nullptr);
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    dsort_scatter_kernel(const uint32_t* __restrict__ kin,
+                         const uint32_t* __restrict__ iin,
+                         uint32_t* __restrict__ kout, uint32_t* __restrict__ iout,
+                         int N, int shift, const uint32_t* __restrict__ dh,
+                         int n_dblk) {
+  __shared__ uint32_t wc[kSortWarps][256];
+  const int blk = blockIdx.x, b = blockIdx.y;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&wc[0][0])[i] = 0;
+  __syncthreads();
+  const size_t fb = (size_t)b * N;
+  const int start = blk * kSortTile + w * (kSortTile / kSortWarps);
+  uint32_t key[kSortItems], id[kSortItems], loc[kSortItems];
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const int pos = start + it * 32 + lane;
+    const bool valid = pos < N;
+    const uint32_t k = valid ? kin[fb + pos] : 0u;
+    const uint32_t ident = valid ? (iin ? iin[fb + pos] : (uint32_t)pos) : 0u;
+    const uint32_t d = valid ? (k >> shift) & 255u : 256u + lane;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lanemask_lt());
+    const uint32_t before = valid ? wc[w][d] : 0u;
+    __syncwarp();
+    if (valid && rank == 0) wc[w][d] = before + __popc(peers);
+    __syncwarp();
+    key[it] = k;
+    id[it] = ident;
+    loc[it] = before + rank;
+  }
+  __syncthreads();
+  {
+    const int d = tid;  // 256 threads, one digit each
+    uint32_t run = dh[((size_t)b * 256 + d) * n_dblk + blk];
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ++ww) {
+      const uint32_t t = wc[ww][d];
+      wc[ww][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const int pos = start + it * 32 + lane;
+    if (pos < N) {
+      const uint32_t d = (key[it] >> shift) & 255u;
+      const uint32_t dst = wc[w][d] + loc[it];
+      kout[fb + dst] = key[it];
+      iout[fb + dst] = id[it];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tile counting pass
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    tile_count_kernel(const uint32_t* __restrict__ sorted_ids,
+                      const uint2* __restrict__ rect,
+                      const Header* __restrict__ hdr,
+                      uint32_t* __restrict__ tcnt, int N, int NT, int tiles_x,
+                      int n_chunk) {
+  extern __shared__ uint32_t cnt[];  // NT
+  const int c = blockIdx.x, b = blockIdx.y;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) cnt[t] = 0;
+  __syncthreads();
+  const int vis = (int)hdr->vis[b];
+  const int lo = c * kChunk, hi = min(lo + kChunk, vis);
+  for (int pos = lo + threadIdx.x; pos < hi; pos += blockDim.x) {
+    const uint32_t g = sorted_ids[(size_t)b * N + pos];
+    int x0, y0, x1, y1;
+    unpack_rect(rect[(size_t)b * N + g], x0, y0, x1, y1);
+    for (int ty = y0; ty < y1; ++ty)
+      for (int tx = x0; tx < x1; ++tx) atomicAdd(&cnt[ty * tiles_x + tx], 1u);
+  }
+  __syncthreads();
+  uint32_t* out = tcnt + ((size_t)b * n_chunk + c) * NT;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) out[t] = cnt[t];
+}
+
+// column scan over chunks for each (frame, tile): tcnt becomes the exclusive
+// prefix over chunks, ttot the tile's total
+__global__ void tile_colscan_kernel(uint32_t* __restrict__ tcnt,
+                                    uint32_t* __restrict__ ttot, int NT,
+                                    int n_chunk) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (t >= NT) return;
+  uint32_t run = 0;
+  uint32_t* col = tcnt + (size_t)b * n_chunk * NT + t;
+  for (int c = 0; c < n_chunk; ++c) {
+    const uint32_t v = col[(size_t)c * NT];
+    col[(size_t)c * NT] = run;
+    run += v;
+  }
+  ttot[(size_t)b * NT + t] = run;
+}
+
+// exclusive scan of the tile totals over (frame, tile); ranges; capacity
+__global__ void __launch_bounds__(1024)
+    tile_scan_kernel(uint32_t* __restrict__ ttot, uint2* __restrict__ ranges,
+                     Header* __restrict__ hdr, int64_t S, int64_t cap) {
+  __shared__ uint64_t s_total;
+  // keep the totals: the scan runs in place on a copy held in `ranges.x`
+  for (int64_t i = threadIdx.x; i < S; i += blockDim.x) ranges[i].y = ttot[i];
+  __syncthreads();
+  cta_exclusive_scan(ttot, S, &s_total);
+  __syncthreads();
+  const uint64_t total = s_total;
+  for (int64_t i = threadIdx.x; i < S; i += blockDim.x) {
+    const uint64_t s = ttot[i], e = s + ranges[i].y;
+    ranges[i] = make_uint2((uint32_t)min(s, (uint64_t)cap), (uint32_t)min(e, (uint64_t)cap));
+  }
+  if (threadIdx.x == 0) {
+    hdr->count = (int64_t)total;
+    if (total > (uint64_t)cap) set_status(hdr, GFTORF_ERR_CAPACITY);
+  }
+}
+
+// stable scatter of the instances: warp w of chunk c walks its Gaussians in
+// depth order, one Gaussian at a time, lanes spread over its tiles
+__global__ void __launch_bounds__(256)
+    tile_scatter_kernel(const uint32_t* __restrict__ sorted_ids,
+                        const uint2* __restrict__ rect,
+                        const Header* __restrict__ hdr,
+                        const uint32_t* __restrict__ tcnt,
+                        const uint32_t* __restrict__ toff,
+                        uint32_t* __restrict__ values, int N, int NT,
+                        int tiles_x, int n_chunk, int64_t cap) {
+  extern __shared__ uint32_t cur[];  // [warps][NT]
+  const int c = blockIdx.x, b = blockIdx.y;
+  const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int vis = (int)hdr->vis[b];
+  const int lo = c * kChunk;
+  if (lo >= vis) return;
+  for (int i = threadIdx.x; i < nw * NT; i += blockDim.x) cur[i] = 0;
+  __syncthreads();
+  const int per = kChunk / nw;
+  const int wlo = lo + w * per, whi = min(wlo + per, vis);
+  const uint32_t* ids = sorted_ids + (size_t)b * N;
+  const uint2* rc = rect + (size_t)b * N;
+  uint32_t* my = cur + (size_t)w * NT;
+  // phase 1: per-warp tile counts
+  for (int pos = wlo + lane; pos < whi; pos += 32) {
+    int x0, y0, x1, y1;
+    unpack_rect(rc[ids[pos]], x0, y0, x1, y1);
+    for (int ty = y0; ty < y1; ++ty)
+      for (int tx = x0; tx < x1; ++tx) atomicAdd(&my[ty * tiles_x + tx], 1u);
+  }
+  __syncthreads();
+  // phase 2: cursors = tile base + chunk prefix + earlier warps of the chunk
+  const uint32_t* cc = tcnt + ((size_t)b * n_chunk + c) * NT;
+  const uint32_t* to = toff + (size_t)b * NT;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    uint32_t run = to[t] + cc[t];
+    for (int ww = 0; ww < nw; ++ww) {
+      const uint32_t v = cur[(size_t)ww * NT + t];
+      cur[(size_t)ww * NT + t] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  // phase 3: ordered writes
+  for (int base = wlo; base < whi; base += 32) {
+    const int pos = base + lane;
+    uint32_t g = 0;
+    uint2 pr = make_uint2(0, 0);
+    if (pos < whi) {
+      g = ids[pos];
+      pr = rc[g];
+    }
+    const int cnt = min(32, whi - base);
+    for (int j = 0; j < cnt; ++j) {
+      const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
+      uint2 rj;
+      rj.x = __shfl_sync(0xffffffffu, pr.x, j);
+      rj.y = __shfl_sync(0xffffffffu, pr.y, j);
+      int x0, y0, x1, y1;
+      unpack_rect(rj, x0, y0, x1, y1);
+      const int wd = x1 - x0, area = wd * (y1 - y0);
+      for (int k = lane; k < area; k += 32) {
+        const int ty = y0 + k / wd, tx = x0 + k % wd;
+        const int t = ty * tiles_x + tx;
+        const uint32_t p = my[t];
+        my[t] = p + 1;
+        if ((int64_t)p < cap) values[p] = gj;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void export_keys_kernel(const uint2* __restrict__ ranges,
+                                   const uint32_t* __restrict__ values,
+                                   const uint32_t* __restrict__ zkey,
+                                   uint64_t* __restrict__ keys, int N, int NT) {
+  const int t = blockIdx.x, b = blockIdx.y;
+  const uint2 r = ranges[(size_t)b * NT + t];
+  const uint64_t hi = ((uint64_t)b * NT + t) << 32;
+  for (uint32_t i = r.x + threadIdx.x; i < r.y; i += blockDim.x)
+    keys[i] = hi | zkey[(size_t)b * N + values[i]];
+}
+
+}  // namespace
+
+void launch_footprints(const Layout& L, const float* u, const float* v,
+                       const int32_t* radius, const float* z,
+                       unsigned char* ws, cudaStream_t st) {
+  if (L.N == 0) return;
+  dim3 grid((L.N + 255) / 256, L.B);
+  footprint_kernel<<<grid, 256, 0, st>>>(
+      u, v, radius, z, at<Header>(ws, L.off_header), at<uint2>(ws, L.off_rect),
+      at<uint32_t>(ws, L.off_zkey), L.N, L.TW, L.TH, L.tiles_x, L.tiles_y);
+  count_launches(1);
+}
+
+void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {  // per-CTA tile counters may exceed the default 48 KB
+    cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(tile_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr_set = true;
+  }
+  auto* hdr = at<Header>(ws, L.off_header);
+  auto* zkey = at<uint32_t>(ws, L.off_zkey);
+  auto* k0 = at<uint32_t>(ws, L.off_zkey2);
+  auto* k1 = k0 + (size_t)L.B * L.N;
+  auto* i0 = at<uint32_t>(ws, L.off_ids);
+  auto* i1 = at<uint32_t>(ws, L.off_ids2);
+  auto* dh = at<uint32_t>(ws, L.off_dhist);
+  auto* rect = at<const uint2>(ws, L.off_rect);
+  auto* tcnt = at<uint32_t>(ws, L.off_tcnt);
+  auto* ttot = at<uint32_t>(ws, L.off_toff);
+  auto* ranges = at<uint2>(ws, L.off_ranges);
+  auto* values = at<uint32_t>(ws, L.off_values);
+  const uint32_t* sorted = i1;
+  if (L.N > 0) {
+    // depth sort: zkey -> (k0,i0) -> (k1,i1) -> (k0,i0) -> (k1,i1)
+    const uint32_t* kin = zkey;
+    const uint32_t* iin = nullptr;
+    uint32_t* kout[2] = {k0, k1};
+    uint32_t* iout[2] = {i0, i1};
+    dim3 g(L.n_dblk, L.B);
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 8 * pass;
+      dsort_hist_kernel<<<g, kSortThreads, 0, st>>>(kin, L.N, shift, dh, L.n_dblk);
+      dsort_scan_kernel<<<L.B, 1024, 0, st>>>(dh, L.n_dblk);
+      dsort_scatter_kernel<<<g, kSortThreads, 0, st>>>(kin, iin, kout[pass & 1],
+                                                       iout[pass & 1], L.N, shift,
+                                                       dh, L.n_dblk);
+      kin = kout[pass & 1];
+      iin = iout[pass & 1];
+    }
+    dim3 gc(L.n_chunk, L.B);
+    tile_count_kernel<<<gc, 256, (size_t)L.NT * 4, st>>>(sorted, rect, hdr, tcnt, L.N,
+                                                         L.NT, L.tiles_x, L.n_chunk);
+    count_launches(13);
+  } else {
+    cudaMemsetAsync(tcnt, 0, (size_t)L.B * L.n_chunk * L.NT * 4, st);
+  }
+  dim3 gs((L.NT + 255) / 256, L.B);
+  tile_colscan_kernel<<<gs, 256, 0, st>>>(tcnt, ttot, L.NT, L.n_chunk);
+  tile_scan_kernel<<<1, 1024, 0, st>>>(ttot, ranges, hdr, (int64_t)L.B * L.NT, L.cap);
+  count_launches(2);
+  if (L.N > 0) {
+    dim3 gc(L.n_chunk, L.B);
+    const int nw = L.scatter_warps;
+    tile_scatter_kernel<<<gc, nw * 32, (size_t)nw * L.NT * 4, st>>>(
+        sorted, rect, hdr, tcnt, ttot, values, L.N, L.NT, L.tiles_x, L.n_chunk,
+        L.cap);
+    count_launches(1);
+  }
+}
+
+void launch_export_keys(const Layout& L, uint64_t* keys, unsigned char* ws,
+                        cudaStream_t st) {
+  dim3 g(L.NT, L.B);
+  export_keys_kernel<<<g, 128, 0, st>>>(
+      at<const uint2>(ws, L.off_ranges), at<const uint32_t>(ws, L.off_values),
+      at<const uint32_t>(ws, L.off_zkey), keys, L.N, L.NT);
+  count_launches(1);
+}
+
+}  // namespace gftorf

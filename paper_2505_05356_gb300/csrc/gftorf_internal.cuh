@@ -1,0 +1,153 @@
+// gftorf_internal.cuh -- device-side layout and helpers shared by the CUDA
+// translation units of libgftorf (sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gftorf.h"
+
+namespace gftorf {
+
+constexpr int kMaxF = GFTORF_MAX_FREQ;
+constexpr int kMaxP = GFTORF_MAX_OFFSETS;
+constexpr int kMaxFrames = GFTORF_MAX_FRAMES;
+constexpr uint32_t kCulledKey = 0xFFFFFFFFu;
+
+// Depth sort geometry: 256 threads, 16 keys each, one tile of 4096 keys.
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+// Tile binning: a chunk of depth-ordered Gaussians per CTA.
+constexpr int kChunk = 4096;
+
+// Per-frame camera in device memory (double; kernels round to their type).
+struct FrameDev {
+  double fx, fy, cx, cy;
+  double R[9];
+  double t[3];
+  double near_plane, time;
+  double limx, limy;  // guard * half field of view (tan), x and y
+};
+
+// Everything a batch needs besides the arrays: written into the workspace by
+// gftorf_preprocess, read by the later kernels.
+struct Table {
+  FrameDev fr[kMaxFrames];
+  double kf[kMaxF];  // 4 f / c: psi / pi per metre of distance
+  double cos_off[kMaxP], sin_off[kMaxP];
+  double source;
+  double dilation, alpha_max, alpha_min, t_min, sigma_cut;
+};
+
+// Device-side status block at the start of the workspace.
+struct Header {
+  int32_t status;
+  int32_t pad0;
+  int64_t count;           // tile instances of the batch
+  uint32_t queue[4];       // persistent work-queue heads (fwd, bwd)
+  uint32_t vis[kMaxFrames];  // visible Gaussians per frame
+};
+
+// Host-computed byte layout of the workspace for one gftorf_dims.
+struct Layout {
+  int B, N, W, H, TW, TH, F, P, C, NF, dtype, real_size, mode;
+  int tiles_x, tiles_y, NT;
+  int rec_stride;  // Reals per projected record (16-byte multiple)
+  int g2d_stride;  // Reals per 2D-gradient row
+  int n_dblk;      // depth-sort tiles per frame
+  int n_chunk;     // binning chunks per frame
+  int scatter_warps;
+  int64_t cap;
+  size_t off_header, off_table, off_rec, off_rect, off_zkey, off_zkey2,
+      off_ids, off_ids2, off_dhist, off_tcnt, off_toff, off_ranges,
+      off_values, off_tfinal, off_nlast, off_g2d, total;
+};
+
+// Host-side count of kernels enqueued by the library (gftorf_kernel_launches).
+void count_launches(int n);
+int64_t launches_so_far();
+
+// Launch entry points implemented in the .cu files (all on `st`).
+template <typename Real>
+void launch_preprocess(const Layout& L, const gftorf_gaussians& g,
+                       unsigned char* ws, cudaStream_t st);
+template <typename Real>
+void launch_preprocess_bwd(const Layout& L, const gftorf_gaussians& g,
+                           const gftorf_gradients& gr, unsigned char* ws,
+                           cudaStream_t st);
+void launch_footprints(const Layout& L, const float* u, const float* v,
+                       const int32_t* radius, const float* z,
+                       unsigned char* ws, cudaStream_t st);
+void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st);
+void launch_export_keys(const Layout& L, uint64_t* keys, unsigned char* ws,
+                        cudaStream_t st);
+template <typename Real>
+void launch_render_fwd(const Layout& L, const Real* bg, Real* out,
+                       unsigned char* ws, cudaStream_t st);
+template <typename Real>
+void launch_render_bwd(const Layout& L, const Real* bg, const Real* dout,
+                       Real* dbg, unsigned char* ws, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__host__ __device__ inline T* at(unsigned char* ws, size_t off) {
+  return reinterpret_cast<T*>(ws + off);
+}
+
+__device__ __forceinline__ void set_status(Header* h, int32_t code) {
+  atomicCAS(&h->status, 0, code);
+}
+
+// 2^x with the hardware approximation (PTX ex2.approx.ftz.f32); used on the
+// compositing hot path with the conic pre-scaled by log2(e).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double ex2_approx(double x) { return exp2(x); }
+
+// Tile rectangle [x0,x1) x [y0,y1) of the disc of radius r around (u, v),
+// every step in single precision with one rounding each (the binning
+// contract); clamps are done in float so NaN and huge values are safe.
+__device__ __forceinline__ int clamp_tile(float v, int hi) {
+  if (!(v > 0.0f)) return 0;
+  if (v > (float)hi) return hi;
+  return (int)v;
+}
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int tw,
+                                          int th, int tiles_x, int tiles_y,
+                                          int& x0, int& y0, int& x1, int& y1) {
+  const float rf = (float)r, twf = (float)tw, thf = (float)th;
+  x0 = clamp_tile(floorf(__fdiv_rn(__fsub_rn(u, rf), twf)), tiles_x);
+  x1 = clamp_tile(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(u, rf), twf)), 1.0f), tiles_x);
+  y0 = clamp_tile(floorf(__fdiv_rn(__fsub_rn(v, rf), thf)), tiles_y);
+  y1 = clamp_tile(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(v, rf), thf)), 1.0f), tiles_y);
+}
+
+// packed rectangle: 4 x uint16 (x0, y0, x1, y1) in one uint2
+__device__ __forceinline__ uint2 pack_rect(int x0, int y0, int x1, int y1) {
+  return make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16),
+                    (uint32_t)x1 | ((uint32_t)y1 << 16));
+}
+__device__ __forceinline__ void unpack_rect(uint2 r, int& x0, int& y0, int& x1,
+                                            int& y1) {
+  x0 = r.x & 0xFFFF;
+  y0 = r.x >> 16;
+  x1 = r.y & 0xFFFF;
+  y1 = r.y >> 16;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+}  // namespace gftorf

@@ -1,0 +1,505 @@
+// render.cu -- per-tile compositing of raw C-ToF samples (Eq. 4) and its
+// backward re-walk (Eq. S3), one thread per pixel, one CTA per (frame, tile)
+// or persistent CTAs pulling (frame, tile) items from a queue.
+//
+// Forward, per pixel, front to back over the tile's depth-ordered list:
+//   alpha = min(alpha_max, o 2^(power2)), power2 = log2(e) * power
+//   skip if power2 > 0 or alpha < alpha_min
+//   stop (without compositing) if T (1 - alpha) < t_min
+//   w = alpha T^2;  acc_f += w feature_f  (A sin psi_f, A cos psi_f, A)
+//   T <- T (1 - alpha)
+// Epilogue: Q_fj = cos(phi_j) S_f + sin(phi_j) C_f + bg_fj T,
+//           ambient = I + bg_amb T   (sum_k A_k sin(psi_k + phi_j) w_k + bg T)
+// Backward, per pixel, back to front from its last composited Gaussian:
+//   T_k = T_{k+1} / (1 - alpha_k)   (one-way transmittance recovered)
+//   dL/dalpha_k = sum_c g_c T_k^2 (q_kc - 2 (1 - alpha_k) acc_c)
+//                 - g_T T_N / (1 - alpha_k)
+//   acc_c <- alpha_k q_kc + (1 - alpha_k)^2 acc_c          (Eq. S3)
+// with g_c the gradient of the accumulators (the raw samples are linear in
+// them) and g_T = sum_c bg_c dL/dQ_c.  Per-Gaussian sums over the CTA's
+// pixels: warp shuffle reduction, shared-memory accumulation, then one
+// global atomic per value per CTA.
+#include "gftorf_internal.cuh"
+
+namespace gftorf {
+namespace {
+
+constexpr double kLn2 = 0.69314718055994530942;
+
+template <typename Real>
+struct RecStride;  // Reals per record: 6 + 2F + 1, padded to 16 bytes
+template <int F>
+struct RecStrideF {
+  static constexpr int value = ((6 + 2 * F + 1) + 3) / 4 * 4;
+};
+template <int F>
+struct RecStrideD {
+  static constexpr int value = ((6 + 2 * F + 1) + 1) / 2 * 2;
+};
+template <typename Real, int F>
+constexpr int rec_stride() {
+  return sizeof(Real) == 4 ? RecStrideF<F>::value : RecStrideD<F>::value;
+}
+
+// one rounding per operation, so forward and backward evaluate alpha with
+// bit-identical results (the backward replays the forward's decisions)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+// exponent (log2 domain) and alpha of one Gaussian at one pixel
+template <typename Real>
+__device__ __forceinline__ void eval_alpha(const Real* r, Real fpx, Real fpy,
+                                           Real amax, Real& dx, Real& dy,
+                                           Real& pw, Real& G, Real& oG,
+                                           Real& alpha) {
+  dx = sub_rn(r[0], fpx);
+  dy = sub_rn(r[1], fpy);
+  const Real t1 = mul_rn(r[3], dy);
+  const Real t2 = fma_rn(r[2], dx, t1);
+  const Real t3 = mul_rn(mul_rn(r[4], dy), dy);
+  pw = fma_rn(dx, t2, t3);
+  G = ex2_approx(pw);
+  oG = mul_rn(r[5], G);
+  alpha = oG < amax ? oG : amax;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real warp_sum(Real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct TileCtx {
+  int b, tile, tx, ty;
+};
+
+__device__ __forceinline__ TileCtx tile_of(uint32_t item, int NT, int tiles_x) {
+  TileCtx c;
+  c.b = item / NT;
+  c.tile = item - c.b * NT;
+  c.ty = c.tile / tiles_x;
+  c.tx = c.tile - c.ty * tiles_x;
+  return c;
+}
+
+struct RenderGeom {
+  int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B;
+};
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+template <typename Real, int F>
+__device__ __forceinline__ void render_tile_fwd(
+    const TileCtx& tc, const RenderGeom& rg, const Table* __restrict__ tab,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
+    const Real* __restrict__ rec, const Real* __restrict__ bg,
+    Real* __restrict__ out, Real* __restrict__ tfinal,
+    uint32_t* __restrict__ nlast, Real* s_rec) {
+  constexpr int NF = 2 * F + 1;
+  constexpr int RS = rec_stride<Real, F>();
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  const int lx = tid % rg.TW, ly = tid / rg.TW;
+  const int px = tc.tx * rg.TW + lx, py = tc.ty * rg.TH + ly;
+  const bool inside = px < rg.W && py < rg.H;
+  const Real fpx = (Real)px + Real(0.5), fpy = (Real)py + Real(0.5);
+  const Real amax = (Real)tab->alpha_max, amin = (Real)tab->alpha_min;
+  const Real tmin = (Real)tab->t_min;
+  const uint2 range = ranges[(size_t)tc.b * rg.NT + tc.tile];
+  const Real* frec = rec + (size_t)tc.b * rg.N * RS;
+
+  Real T = 1;
+  Real acc[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) acc[f] = 0;
+  uint32_t last = range.x;
+  bool done = !inside;
+
+  for (uint32_t base = range.x; base < range.y; base += nthr) {
+    if (__syncthreads_count(done) == nthr) break;
+    const uint32_t i = base + tid;
+    if (i < range.y) {
+      const uint32_t g = values[i];
+      const float4* src = reinterpret_cast<const float4*>(frec + (size_t)g * RS);
+      float4* dst = reinterpret_cast<float4*>(s_rec + tid * RS);
+#pragma unroll
+      for (int k = 0; k < RS * (int)sizeof(Real) / 16; ++k) dst[k] = __ldg(src + k);
+    }
+    __syncthreads();
+    const int cnt = min((uint32_t)nthr, range.y - base);
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        const Real* r = s_rec + j * RS;
+        Real dx, dy, pw, G, oG, alpha;
+        eval_alpha<Real>(r, fpx, fpy, amax, dx, dy, pw, G, oG, alpha);
+        if (pw > Real(0) || alpha < amin) continue;
+        const Real tn = T * (Real(1) - alpha);
+        if (tn < tmin) {
+          done = true;
+          break;
+        }
+        const Real w = alpha * T * T;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] += w * r[6 + f];
+        T = tn;
+        last = base + j + 1;
+      }
+    }
+  }
+  if (inside) {
+    const size_t HW = (size_t)rg.W * rg.H;
+    const size_t pix = (size_t)py * rg.W + px;
+    Real* o = out + (size_t)tc.b * rg.C * HW + pix;
+    const Real* bgb = bg + (size_t)tc.b * rg.C;
+    for (int f = 0; f < F; ++f)
+      for (int j = 0; j < rg.P; ++j)
+        o[(size_t)(f * rg.P + j) * HW] = (Real)tab->cos_off[j] * acc[2 * f] +
+                                         (Real)tab->sin_off[j] * acc[2 * f + 1] +
+                                         bgb[f * rg.P + j] * T;
+    o[(size_t)(F * rg.P) * HW] = acc[2 * F] + bgb[F * rg.P] * T;
+    tfinal[(size_t)tc.b * HW + pix] = T;
+    nlast[(size_t)tc.b * HW + pix] = last - range.x;
+  }
+}
+
+template <typename Real, int F>
+__global__ void __launch_bounds__(512)
+    render_fwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
+                      Header* __restrict__ hdr,
+                      const uint2* __restrict__ ranges,
+                      const uint32_t* __restrict__ values,
+                      const Real* __restrict__ rec, const Real* __restrict__ bg,
+                      Real* __restrict__ out, Real* __restrict__ tfinal,
+                      uint32_t* __restrict__ nlast, int persistent) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* s_rec = reinterpret_cast<Real*>(smem_raw);
+  const uint32_t items = (uint32_t)rg.B * rg.NT;
+  if (!persistent) {
+    const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
+    render_tile_fwd<Real, F>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                             values, rec, bg, out, tfinal, nlast, s_rec);
+    return;
+  }
+  __shared__ uint32_t s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&hdr->queue[0], 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= items) break;
+    render_tile_fwd<Real, F>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                             values, rec, bg, out, tfinal, nlast, s_rec);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+template <typename Real, int F>
+__device__ __forceinline__ void render_tile_bwd(
+    const TileCtx& tc, const RenderGeom& rg, const Table* __restrict__ tab,
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
+    const Real* __restrict__ rec, const Real* __restrict__ bg,
+    const Real* __restrict__ dout, const Real* __restrict__ tfinal,
+    const uint32_t* __restrict__ nlast, Real* __restrict__ g2d, int g2d_stride,
+    Real* __restrict__ dbg, Real* s_rec, Real* s_grad, uint32_t* s_id,
+    Real* s_red) {
+  constexpr int NF = 2 * F + 1;
+  constexpr int GS = 6 + NF;
+  constexpr int RS = rec_stride<Real, F>();
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
+  const int lx = tid % rg.TW, ly = tid / rg.TW;
+  const int px = tc.tx * rg.TW + lx, py = tc.ty * rg.TH + ly;
+  const bool inside = px < rg.W && py < rg.H;
+  const Real fpx = (Real)px + Real(0.5), fpy = (Real)py + Real(0.5);
+  const Real amax = (Real)tab->alpha_max, amin = (Real)tab->alpha_min;
+  const uint2 range = ranges[(size_t)tc.b * rg.NT + tc.tile];
+  const Real* frec = rec + (size_t)tc.b * rg.N * RS;
+  const size_t HW = (size_t)rg.W * rg.H;
+  const size_t pix = (size_t)py * rg.W + px;
+
+  // fold dL/dQ into accumulator gradients
+  Real gacc[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) gacc[f] = 0;
+  Real gT = 0, Tf = 1;
+  int nl = 0;
+  const Real* bgb = bg + (size_t)tc.b * rg.C;
+  if (inside) {
+    const Real* go = dout + (size_t)tc.b * rg.C * HW + pix;
+    Tf = tfinal[(size_t)tc.b * HW + pix];
+    nl = (int)nlast[(size_t)tc.b * HW + pix];
+    for (int f = 0; f < F; ++f)
+      for (int j = 0; j < rg.P; ++j) {
+        const Real gq = go[(size_t)(f * rg.P + j) * HW];
+        gacc[2 * f] += (Real)tab->cos_off[j] * gq;
+        gacc[2 * f + 1] += (Real)tab->sin_off[j] * gq;
+        gT += bgb[f * rg.P + j] * gq;
+      }
+    gacc[2 * F] = go[(size_t)(F * rg.P) * HW];
+    gT += bgb[F * rg.P] * gacc[2 * F];
+  }
+  // dL/dbg_c = sum over pixels of T_N dL/dQ_c (block reduce, one atomic each)
+  if (dbg) {
+    for (int c = 0; c < rg.C; ++c) {
+      Real v = inside ? Tf * dout[((size_t)tc.b * rg.C + c) * HW + pix] : Real(0);
+      v = warp_sum(v);
+      if (lane == 0) s_red[wid] = v;
+      __syncthreads();
+      if (tid == 0) {
+        Real s = 0;
+        for (int w = 0; w < nwarps; ++w) s += s_red[w];
+        if (s != Real(0)) atomicAdd(&dbg[(size_t)tc.b * rg.C + c], s);
+      }
+      __syncthreads();
+    }
+  }
+  // longest list any pixel of the tile needs
+  int maxn = nl;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
+  if (lane == 0) reinterpret_cast<int*>(s_red)[wid] = maxn;
+  __syncthreads();
+  maxn = 0;
+  for (int w = 0; w < nwarps; ++w) maxn = max(maxn, reinterpret_cast<int*>(s_red)[w]);
+  __syncthreads();
+
+  Real T = Tf;
+  Real acc[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) acc[f] = 0;
+  const Real ln2 = Real(kLn2);
+  Real* gbase = g2d + (size_t)tc.b * rg.N * g2d_stride;
+
+  for (int hi = maxn; hi > 0; hi -= nthr) {
+    const int lo = max(0, hi - nthr);
+    const int cnt = hi - lo;
+    if (tid < cnt) {
+      const uint32_t g = values[range.x + lo + tid];
+      s_id[tid] = g;
+      const float4* src = reinterpret_cast<const float4*>(frec + (size_t)g * RS);
+      float4* dst = reinterpret_cast<float4*>(s_rec + tid * RS);
+#pragma unroll
+      for (int k = 0; k < RS * (int)sizeof(Real) / 16; ++k) dst[k] = __ldg(src + k);
+    }
+    for (int k = tid; k < cnt * GS; k += nthr) s_grad[k] = Real(0);
+    __syncthreads();
+    // warps whose pixels all stop before this batch skip it entirely
+    const int my_hi = min(nl, hi) - lo;  // entries [0, my_hi) are mine
+    int warp_hi = my_hi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) warp_hi = max(warp_hi, __shfl_xor_sync(0xffffffffu, warp_hi, o));
+    for (int j = warp_hi - 1; j >= 0; --j) {
+      const Real* r = s_rec + j * RS;
+      Real c[GS];
+#pragma unroll
+      for (int k = 0; k < GS; ++k) c[k] = 0;
+      bool has = false;
+      if (j < my_hi) {
+        Real dx, dy, pw, G, oG, alpha;
+        eval_alpha<Real>(r, fpx, fpy, amax, dx, dy, pw, G, oG, alpha);
+        if (!(pw > Real(0) || alpha < amin)) {
+          has = true;
+          const Real oma = Real(1) - alpha;
+          const Real Tk = T / oma;
+          const Real T2 = Tk * Tk;
+          Real dLda = -gT * Tf / oma;
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const Real q = r[6 + f];
+            dLda += gacc[f] * T2 * (q - Real(2) * oma * acc[f]);
+            c[6 + f] = gacc[f] * alpha * T2;
+            acc[f] = alpha * q + oma * oma * acc[f];
+          }
+          T = Tk;
+          if (oG < amax) {
+            c[5] = dLda * G;
+            const Real dLdp = dLda * alpha;  // d alpha / d power = alpha
+            c[0] = dLdp * ln2 * (Real(2) * r[2] * dx + r[3] * dy);
+            c[1] = dLdp * ln2 * (Real(2) * r[4] * dy + r[3] * dx);
+            c[2] = Real(-0.5) * dLdp * dx * dx;
+            c[3] = -dLdp * dx * dy;
+            c[4] = Real(-0.5) * dLdp * dy * dy;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, has)) {
+#pragma unroll
+        for (int k = 0; k < GS; ++k) {
+          const Real v = warp_sum(c[k]);
+          if (lane == 0 && v != Real(0)) atomicAdd(&s_grad[j * GS + k], v);
+        }
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < cnt * GS; k += nthr) {
+      const Real v = s_grad[k];
+      if (v != Real(0)) {
+        const int j = k / GS, comp = k - j * GS;
+        atomicAdd(&gbase[(size_t)s_id[j] * g2d_stride + comp], v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename Real, int F>
+__global__ void __launch_bounds__(512)
+    render_bwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
+                      Header* __restrict__ hdr,
+                      const uint2* __restrict__ ranges,
+                      const uint32_t* __restrict__ values,
+                      const Real* __restrict__ rec, const Real* __restrict__ bg,
+                      const Real* __restrict__ dout,
+                      const Real* __restrict__ tfinal,
+                      const uint32_t* __restrict__ nlast, Real* __restrict__ g2d,
+                      int g2d_stride, Real* __restrict__ dbg, int persistent) {
+  constexpr int NF = 2 * F + 1;
+  constexpr int GS = 6 + NF;
+  constexpr int RS = rec_stride<Real, F>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nthr = blockDim.x;
+  Real* s_rec = reinterpret_cast<Real*>(smem_raw);
+  Real* s_grad = s_rec + (size_t)nthr * RS;
+  Real* s_red = s_grad + (size_t)nthr * GS;
+  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_red + 32);
+  const uint32_t items = (uint32_t)rg.B * rg.NT;
+  if (!persistent) {
+    const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
+    render_tile_bwd<Real, F>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                             values, rec, bg, dout, tfinal, nlast, g2d,
+                             g2d_stride, dbg, s_rec, s_grad, s_id, s_red);
+    return;
+  }
+  __shared__ uint32_t s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&hdr->queue[1], 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= items) break;
+    render_tile_bwd<Real, F>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                             values, rec, bg, dout, tfinal, nlast, g2d,
+                             g2d_stride, dbg, s_rec, s_grad, s_id, s_red);
+  }
+}
+
+RenderGeom geom_of(const Layout& L) {
+  RenderGeom g;
+  g.N = L.N, g.W = L.W, g.H = L.H, g.TW = L.TW, g.TH = L.TH;
+  g.tiles_x = L.tiles_x, g.NT = L.NT, g.P = L.P, g.C = L.C;
+  g.rec_stride = L.rec_stride, g.B = L.B;
+  return g;
+}
+
+template <typename KernelT>
+int persistent_grid(KernelT kernel, int threads, size_t smem) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+template <typename Real, int F>
+void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
+                cudaStream_t st) {
+  constexpr int RS = rec_stride<Real, F>();
+  const int threads = L.TW * L.TH;
+  const size_t smem = (size_t)threads * RS * sizeof(Real);
+  auto kernel = render_fwd_kernel<Real, F>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr_set = true;
+  }
+  auto* hdr = at<Header>(ws, L.off_header);
+  dim3 grid(L.NT, L.B);
+  if (L.mode == 1) {
+    const int n = persistent_grid(kernel, threads, smem);
+    grid = dim3(min(n, L.B * L.NT), 1);
+    cudaMemsetAsync(&hdr->queue[0], 0, sizeof(uint32_t), st);
+  }
+  kernel<<<grid, threads, smem, st>>>(
+      geom_of(L), at<const Table>(ws, L.off_table), hdr,
+      at<const uint2>(ws, L.off_ranges), at<const uint32_t>(ws, L.off_values),
+      at<const Real>(ws, L.off_rec), bg, out, at<Real>(ws, L.off_tfinal),
+      at<uint32_t>(ws, L.off_nlast), L.mode == 1);
+  count_launches(1);
+}
+
+template <typename Real, int F>
+void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
+                unsigned char* ws, cudaStream_t st) {
+  constexpr int NF = 2 * F + 1;
+  constexpr int RS = rec_stride<Real, F>();
+  const int threads = L.TW * L.TH;
+  const size_t smem = (size_t)threads * (RS + 6 + NF) * sizeof(Real) +
+                      32 * sizeof(Real) + (size_t)threads * sizeof(uint32_t);
+  auto kernel = render_bwd_kernel<Real, F>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr_set = true;
+  }
+  auto* hdr = at<Header>(ws, L.off_header);
+  dim3 grid(L.NT, L.B);
+  if (L.mode == 1) {
+    const int n = persistent_grid(kernel, threads, smem);
+    grid = dim3(min(n, L.B * L.NT), 1);
+    cudaMemsetAsync(&hdr->queue[1], 0, sizeof(uint32_t), st);
+  }
+  kernel<<<grid, threads, smem, st>>>(
+      geom_of(L), at<const Table>(ws, L.off_table), hdr,
+      at<const uint2>(ws, L.off_ranges), at<const uint32_t>(ws, L.off_values),
+      at<const Real>(ws, L.off_rec), bg, dout, at<const Real>(ws, L.off_tfinal),
+      at<const uint32_t>(ws, L.off_nlast), at<Real>(ws, L.off_g2d),
+      L.g2d_stride, dbg, L.mode == 1);
+  count_launches(1);
+}
+
+}  // namespace
+
+template <typename Real>
+void launch_render_fwd(const Layout& L, const Real* bg, Real* out,
+                       unsigned char* ws, cudaStream_t st) {
+  switch (L.F) {
+    case 1: fwd_launch<Real, 1>(L, bg, out, ws, st); break;
+    case 2: fwd_launch<Real, 2>(L, bg, out, ws, st); break;
+    case 3: fwd_launch<Real, 3>(L, bg, out, ws, st); break;
+    default: fwd_launch<Real, 4>(L, bg, out, ws, st); break;
+  }
+}
+
+template <typename Real>
+void launch_render_bwd(const Layout& L, const Real* bg, const Real* dout,
+                       Real* dbg, unsigned char* ws, cudaStream_t st) {
+  switch (L.F) {
+    case 1: bwd_launch<Real, 1>(L, bg, dout, dbg, ws, st); break;
+    case 2: bwd_launch<Real, 2>(L, bg, dout, dbg, ws, st); break;
+    case 3: bwd_launch<Real, 3>(L, bg, dout, dbg, ws, st); break;
+    default: bwd_launch<Real, 4>(L, bg, dout, dbg, ws, st); break;
+  }
+}
+
+template void launch_render_fwd<float>(const Layout&, const float*, float*,
+                                       unsigned char*, cudaStream_t);
+template void launch_render_fwd<double>(const Layout&, const double*, double*,
+                                        unsigned char*, cudaStream_t);
+template void launch_render_bwd<float>(const Layout&, const float*, const float*,
+                                       float*, unsigned char*, cudaStream_t);
+template void launch_render_bwd<double>(const Layout&, const double*,
+                                        const double*, double*, unsigned char*,
+                                        cudaStream_t);
+
+}  // namespace gftorf

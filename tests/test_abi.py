@@ -1,0 +1,110 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every
+symbol include/gftorf.h declares, sizes workspaces and rejects invalid
+arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2505_05356_gb300 import gftorf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "gftorf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gftorf_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return gftorf.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_status_strings(lib):
+    assert lib.gftorf_version() == 100
+    for code, text in gftorf.STATUS.items():
+        assert lib.gftorf_status_string(code).decode() == text
+
+
+def _dims(**kw):
+    d = dict(n_gaussians=1000, n_frames=2, width=64, height=48, tile_w=16, tile_h=16,
+             n_freq=1, n_offsets=4, dtype=0, render_mode=0, max_instances=10000)
+    d.update(kw)
+    return gftorf.Dims(*[d[k] for k, _ in gftorf.Dims._fields_])
+
+
+def test_workspace_size_validates_dims(lib):
+    ok = lib.gftorf_workspace_size(ctypes.byref(_dims()))
+    assert ok > 0 and ok % 256 == 0
+    # more capacity, frames or precision never shrink the workspace
+    assert lib.gftorf_workspace_size(ctypes.byref(_dims(max_instances=20000))) >= ok + 40000 - 256
+    assert lib.gftorf_workspace_size(ctypes.byref(_dims(dtype=1))) > ok
+    assert lib.gftorf_workspace_size(ctypes.byref(_dims(n_frames=4))) > ok
+    for bad in (dict(n_frames=0), dict(n_frames=65), dict(width=0), dict(tile_w=12),
+                dict(tile_w=32, tile_h=16), dict(n_freq=0), dict(n_freq=5),
+                dict(n_offsets=9), dict(dtype=2), dict(render_mode=2),
+                dict(n_gaussians=-1), dict(max_instances=-1),
+                dict(max_instances=1 << 33)):
+        assert lib.gftorf_workspace_size(ctypes.byref(_dims(**bad))) == 0, bad
+    assert lib.gftorf_workspace_size(None) == 0
+    # the empty scene is a valid problem
+    assert lib.gftorf_workspace_size(ctypes.byref(_dims(n_gaussians=0))) > 0
+
+
+def test_host_side_argument_errors(lib):
+    d = _dims()
+    g = gftorf.Gaussians()
+    fr = (gftorf.Frame * 2)(*[gftorf.make_frame(50, 50, 32, 24, [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0],
+                                                0.2, 0.0) for _ in range(2)])
+    se = gftorf.make_sensor([30e6], [0, 1.57, 3.14, 4.71])
+    co = gftorf.make_consts()
+    # null parameter pointers with N > 0
+    assert lib.gftorf_preprocess(ctypes.byref(d), ctypes.byref(g), fr, ctypes.byref(se),
+                                 ctypes.byref(co), None, 0, None) == gftorf.ERR_ARG
+    # invalid dims
+    bad = _dims(tile_w=3)
+    assert lib.gftorf_render_fwd(ctypes.byref(bad), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                 None, 0, None) == gftorf.ERR_ARG
+    # missing / misaligned / short workspace (checked before any device call)
+    assert lib.gftorf_render_fwd(ctypes.byref(d), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                 None, 0, None) == gftorf.ERR_WORKSPACE
+    need = lib.gftorf_workspace_size(ctypes.byref(d))
+    assert lib.gftorf_render_fwd(ctypes.byref(d), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                 ctypes.c_void_p(4096 + 8), need, None) == gftorf.ERR_WORKSPACE
+    assert lib.gftorf_render_fwd(ctypes.byref(d), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                 ctypes.c_void_p(4096), need - 1, None) == gftorf.ERR_WORKSPACE
+    # non-finite camera values are rejected on the host
+    pg = gftorf.Gaussians(*([ctypes.c_void_p(256)] * 7))
+    fr[1].fx = float("nan")
+    assert lib.gftorf_preprocess(ctypes.byref(d), ctypes.byref(pg), fr, ctypes.byref(se),
+                                 ctypes.byref(co), ctypes.c_void_p(4096), need,
+                                 None) == gftorf.ERR_ARG
+    fr[1].fx = 50.0
+    co.alpha_max = 1.5
+    assert lib.gftorf_preprocess(ctypes.byref(d), ctypes.byref(pg), fr, ctypes.byref(se),
+                                 ctypes.byref(co), ctypes.c_void_p(4096), need,
+                                 None) == gftorf.ERR_ARG
+    # backward needs its gradient struct
+    assert lib.gftorf_render_bwd(ctypes.byref(d), ctypes.byref(pg), ctypes.c_void_p(16),
+                                 ctypes.c_void_p(16), None, ctypes.c_void_p(4096), need,
+                                 None) == gftorf.ERR_ARG
+
+
+def test_struct_layouts_match_header():
+    # sizes fixed by the header's field lists (C layout, no hidden padding)
+    assert ctypes.sizeof(gftorf.Dims) == 10 * 4 + 8
+    assert ctypes.sizeof(gftorf.Frame) == 18 * 4
+    assert ctypes.sizeof(gftorf.Sensor) == (4 + 8 + 1) * 4
+    assert ctypes.sizeof(gftorf.Consts) == 6 * 4
+    assert ctypes.sizeof(gftorf.Gaussians) == 7 * ctypes.sizeof(ctypes.c_void_p)
+    assert ctypes.sizeof(gftorf.Gradients) == 8 * ctypes.sizeof(ctypes.c_void_p)
