@@ -109,6 +109,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _overrides(args):
+    """Smaller variants of the workload (profiling captures only)."""
+    o = {}
+    if args.frames:
+        o["frames"] = args.frames
+    if args.n:
+        o["n"] = args.n
+    return o
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -130,7 +140,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    sc = scenes.make_scene(args.workload, seed=rank)
+    sc = scenes.make_scene(args.workload, seed=rank, **_overrides(args))
     B, N, W, H = sc.frames, sc.n, sc.width, sc.height
     tile = tuple(int(v) for v in args.tile.split("x"))
     sc.consts.tile_w, sc.consts.tile_h = tile
@@ -353,7 +363,7 @@ def run_ours(args):
             "data": "synthetic (seeded; shaped like the paper's C-ToF scenes)",
             "config": {"workload": "%s: %d dynamic Gaussians (cubic trajectories), %dx%d, "
                                    "%d timesteps per batch, 30 MHz x 4 offsets + ambient, "
-                                   "30-100%% visible per frame" % (WORKLOAD, N, W, H, B),
+                                   "30-100%% visible per frame" % (args.workload, N, W, H, B),
                        "frames_per_step": B, "tile": args.tile,
                        "render_mode": "persistent" if args.mode == 1 else "grid",
                        "cuda_graph": use_graph, "parallelism": "replicas" if world > 1 else "1 GPU",
@@ -421,12 +431,17 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
     return 1.0 / per_frame, t4 - t0, detail
 
 
+def _calibrate(sc, seconds):
+    """Pixels per sample so that one oracle sample takes about `seconds`."""
+    _, spent, det = oracle_sample(sc, 64)
+    per_px = max(det["fwd_pixels_s"] + det["bwd_pixels_s"], 1e-4) / 64
+    fixed = det["project_s"] + det["chain_s"]
+    return int(min(sc.width * sc.height, max(64, (seconds - fixed) / per_px)))
+
+
 def cpu_baseline(sc, seconds):
     from oracle import oracle as ora
-    # calibrate the pixel sample so the run takes about `seconds`
-    fps, spent, _ = oracle_sample(sc, 16)
-    per_px = max(spent, 1e-3) / 16
-    n_pix = int(min(sc.width * sc.height, max(16, seconds / per_px)))
+    n_pix = _calibrate(sc, seconds)
     fps, spent, det = oracle_sample(sc, n_pix, seed=6)
     return {"value": round(fps, 6), "unit": UNIT, "cores": ora.num_threads(), "kind": "oracle",
             "sample": "frame 0 of the batch: projection of all %d Gaussians + fwd/bwd of %d "
@@ -442,11 +457,9 @@ def run_reference(args):
     from oracle import oracle as ora
     from paper_2505_05356_gb300 import scenes
 
-    sc = scenes.make_scene(args.workload, seed=0)
-    fps, spent, _ = oracle_sample(sc, 16)
-    per_px = max(spent, 1e-3) / 16
+    sc = scenes.make_scene(args.workload, seed=0, **_overrides(args))
     budget = max(5.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
-    n_pix = int(min(sc.width * sc.height, max(16, budget / per_px)))
+    n_pix = _calibrate(sc, budget)
     for w in range(args.warmup):
         oracle_sample(sc, max(16, n_pix // 8), frame=w % sc.frames, seed=w)
     rates, total = [], 0.0
@@ -488,6 +501,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--frames", type=int, default=0, help="override frames per batch")
+    ap.add_argument("--n", type=int, default=0, help="override the Gaussian count")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
