@@ -67,11 +67,60 @@ __device__ __forceinline__ void eval_alpha(const Real* r, Real fpx, Real fpy,
   alpha = oG < amax ? oG : amax;
 }
 
+__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
+
 template <typename Real>
 __device__ __forceinline__ Real warp_sum(Real v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Reduce GS values over the 32 lanes of a warp by recursive halving: at
+// each step a lane keeps one half of its values and trades the other half
+// with its partner, so the warp spends ceil(GS/2) + ceil(GS/4) + ... shuffles
+// instead of 5 GS.  Afterwards lane L holds the full sum of value index
+// `slot_of_lane` (computed once per thread by butterfly_slot).
+template <int LEN, int OFF>
+struct Fold {
+  template <typename Real>
+  static __device__ __forceinline__ void run(Real* v, int lane) {
+    constexpr int H = (LEN + 1) / 2;
+    const bool up = (lane & OFF) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const Real lo = v[i];
+      const Real hi = (i + H < LEN) ? v[i + H] : Real(0);
+      const Real keep = up ? hi : lo;
+      const Real send = up ? lo : hi;
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+    }
+    Fold<H, OFF / 2>::run(v, lane);
+  }
+};
+template <int LEN>
+struct Fold<LEN, 0> {
+  template <typename Real>
+  static __device__ __forceinline__ void run(Real*, int) {}
+};
+
+// value index whose warp total lane `lane` ends with after Fold<GS, 16>;
+// -1 for lanes that end with padding only
+template <int GS>
+__device__ __forceinline__ int butterfly_slot(int lane) {
+  int start = 0, end = GS, len = GS;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const int h = (len + 1) / 2;
+    if (lane & off) {
+      start += h;
+    } else {
+      end = min(end, start + h);
+    }
+    len = h;
+  }
+  return start < end ? start : -1;
 }
 
 struct TileCtx {
@@ -271,6 +320,8 @@ __device__ __forceinline__ void render_tile_bwd(
   __syncthreads();
 
   Real T = Tf;
+  const Real gTf = gT * Tf;
+  const int slot = butterfly_slot<GS>(lane);
   Real acc[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) acc[f] = 0;
@@ -307,34 +358,35 @@ __device__ __forceinline__ void render_tile_bwd(
         if (!(pw > Real(0) || alpha < amin)) {
           has = true;
           const Real oma = Real(1) - alpha;
-          const Real Tk = T / oma;
+          const Real rcp = div_fast(Real(1), oma);
+          const Real Tk = T * rcp;
           const Real T2 = Tk * Tk;
-          Real dLda = -gT * Tf / oma;
+          const Real two_oma = oma + oma, oma2 = oma * oma, aT2 = alpha * T2;
+          Real dLda = -gTf * rcp;
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             const Real q = r[6 + f];
-            dLda += gacc[f] * T2 * (q - Real(2) * oma * acc[f]);
-            c[6 + f] = gacc[f] * alpha * T2;
-            acc[f] = alpha * q + oma * oma * acc[f];
+            dLda += gacc[f] * T2 * (q - two_oma * acc[f]);
+            c[6 + f] = gacc[f] * aT2;
+            acc[f] = alpha * q + oma2 * acc[f];
           }
           T = Tk;
           if (oG < amax) {
             c[5] = dLda * G;
             const Real dLdp = dLda * alpha;  // d alpha / d power = alpha
-            c[0] = dLdp * ln2 * (Real(2) * r[2] * dx + r[3] * dy);
-            c[1] = dLdp * ln2 * (Real(2) * r[4] * dy + r[3] * dx);
-            c[2] = Real(-0.5) * dLdp * dx * dx;
+            const Real e = dLdp * ln2;
+            c[0] = e * (Real(2) * r[2] * dx + r[3] * dy);
+            c[1] = e * (Real(2) * r[4] * dy + r[3] * dx);
+            const Real h = Real(-0.5) * dLdp;
+            c[2] = h * dx * dx;
             c[3] = -dLdp * dx * dy;
-            c[4] = Real(-0.5) * dLdp * dy * dy;
+            c[4] = h * dy * dy;
           }
         }
       }
       if (__any_sync(0xffffffffu, has)) {
-#pragma unroll
-        for (int k = 0; k < GS; ++k) {
-          const Real v = warp_sum(c[k]);
-          if (lane == 0 && v != Real(0)) atomicAdd(&s_grad[j * GS + k], v);
-        }
+        Fold<GS, 16>::run(c, lane);
+        if (slot >= 0 && c[0] != Real(0)) atomicAdd(&s_grad[j * GS + slot], c[0]);
       }
     }
     __syncthreads();
