@@ -55,8 +55,8 @@ Layout make_layout(const gftorf_dims* d) {
   L.rec_stride = (6 + L.NF + per16 - 1) / per16 * per16;
   L.g2d_stride = 6 + L.NF;
   L.n_dblk = (L.N + kSortTile - 1) / kSortTile;
-  L.n_chunk = (L.N + kChunk - 1) / kChunk;
-  if (L.n_chunk < 1) L.n_chunk = 1;
+  L.n_chunk = (int)((d->max_instances + kChunk - 1) / kChunk) + L.B;
+  L.n_scan = (int)(((size_t)L.B * L.N + kScanTile - 1) / kScanTile);
   int nw = 8;
   while (nw > 1 && (size_t)nw * L.NT * 4 > 96 * 1024) nw >>= 1;
   L.scatter_warps = nw;
@@ -77,7 +77,9 @@ Layout make_layout(const gftorf_dims* d) {
   L.off_ids = take(BN * 4);
   L.off_ids2 = take(BN * 4);
   L.off_dhist = take((size_t)L.B * 256 * (L.n_dblk > 0 ? L.n_dblk : 1) * 4);
-  L.off_tcnt = take((size_t)L.B * L.n_chunk * L.NT * 4);
+  L.off_ecnt = take((size_t)L.B * L.N * 4 + 4);
+  L.off_bsum = take((size_t)(L.n_scan + 1) * 8);
+  L.off_tcnt = take((size_t)L.n_chunk * L.NT * 4);
   L.off_toff = take((size_t)L.B * L.NT * 4);
   L.off_ranges = take((size_t)L.B * L.NT * sizeof(uint2));
   L.off_values = take((size_t)(L.cap > 0 ? L.cap : 1) * 4);

@@ -22,7 +22,8 @@ namespace {
 
 // Exclusive scan in place of a[0..S) by one CTA; returns the total through
 // *total (if non-null).  Each thread scans a contiguous segment.
-__device__ void cta_exclusive_scan(uint32_t* a, int64_t S, uint64_t* total) {
+template <typename T>
+__device__ void cta_exclusive_scan(T* a, int64_t S, uint64_t* total) {
   __shared__ uint64_t s_warp[32];
   const int nt = blockDim.x, tid = threadIdx.x;
   const int64_t seg = (S + nt - 1) / nt;
@@ -53,12 +54,29 @@ __device__ void cta_exclusive_scan(uint32_t* a, int64_t S, uint64_t* total) {
   __syncthreads();
   uint64_t run = s_warp[wid] + incl - sum;
   for (int64_t i = lo; i < hi; ++i) {
-    uint32_t v = a[i];
-    a[i] = (uint32_t)run;
+    const uint64_t v = a[i];
+    a[i] = (T)run;
     run += v;
   }
   if (total && tid == nt - 1) *total = run;
   __syncthreads();
+}
+
+// Largest r in [0, n) with e[r] <= s, for e strictly increasing and
+// e[0] <= s; one 32-way probe per step by the calling warp.
+__device__ __forceinline__ int warp_upper_rank(const uint32_t* __restrict__ e, int n,
+                                               uint32_t s, int lane) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) / 32;
+    const int probe = lo + lane * step;
+    const bool ok = probe < hi && e[probe] <= s;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    const int last = 31 - __clz(m);
+    lo += last * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -121,8 +139,8 @@ __global__ void __launch_bounds__(kSortThreads)
 
 __global__ void __launch_bounds__(1024)
     dsort_scan_kernel(uint32_t* __restrict__ dh, int n_dblk) {
-  cta_exclusive_scan(dh + (size_t)blockIdx.x * 256 * n_dblk, (int64_t)256 * n_dblk,
-                     nullptr);
+  cta_exclusive_scan<uint32_t>(dh + (size_t)blockIdx.x * 256 * n_dblk,
+                               (int64_t)256 * n_dblk, nullptr);
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -181,45 +199,179 @@ __global__ void __launch_bounds__(kSortThreads)
 }
 
 // ---------------------------------------------------------------------------
-// tile counting pass
+// emission offsets: tiles covered by each depth-ordered Gaussian, scanned
+// over the whole batch (frame-major), so instance k of the batch is tile
+// (k - e[g]) of Gaussian g's rectangle (row-major) for the g with
+// e[g] <= k < e[g + 1]
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    inst_count_kernel(const uint32_t* __restrict__ sorted_ids,
+                      const uint2* __restrict__ rect,
+                      const Header* __restrict__ hdr,
+                      uint32_t* __restrict__ ecnt, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i >= N) return;
+  uint32_t c = 0;
+  if (i < (int)hdr->vis[b]) {
+    int x0, y0, x1, y1;
+    unpack_rect(rect[(size_t)b * N + sorted_ids[(size_t)b * N + i]], x0, y0, x1, y1);
+    c = (uint32_t)((x1 - x0) * (y1 - y0));
+  }
+  ecnt[(size_t)b * N + i] = c;
+}
+
+// device-wide exclusive scan: tile sums, scan of the sums, tile scans
+__global__ void __launch_bounds__(256)
+    scan_reduce_kernel(const uint32_t* __restrict__ a, int64_t S,
+                       uint64_t* __restrict__ bsum) {
+  __shared__ uint64_t s_w[8];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint64_t sum = 0;
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    const int64_t i = base + k;
+    if (i < S) sum += a[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+    scan_top_kernel(uint64_t* __restrict__ bsum, int nblk) {
+  __shared__ uint64_t s_total;
+  cta_exclusive_scan<uint64_t>(bsum, nblk, &s_total);
+  if (threadIdx.x == 0) bsum[nblk] = s_total;
+}
+
+__global__ void __launch_bounds__(256)
+    scan_down_kernel(uint32_t* __restrict__ a, int64_t S,
+                     const uint64_t* __restrict__ bsum) {
+  constexpr int kItems = kScanTile / 256;
+  __shared__ uint64_t s_w[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kItems;
+  uint32_t v[kItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    v[k] = base + k < S ? a[base + k] : 0u;
+    sum += v[k];
+  }
+  uint64_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_w[wid] = incl;
+  __syncthreads();
+  uint64_t run = bsum[blockIdx.x] + incl - sum;
+  for (int w = 0; w < wid; ++w) run += s_w[w];
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    if (base + k < S) a[base + k] = (uint32_t)run;
+    run += v[k];
+  }
+}
+
+// per frame: first instance and first chunk (chunks never straddle frames)
+__global__ void chunk_table_kernel(const uint32_t* __restrict__ eoff,
+                                   const uint64_t* __restrict__ bsum, int nblk,
+                                   Header* __restrict__ hdr, int B, int N,
+                                   int64_t cap, int n_chunk) {
+  if (threadIdx.x != 0) return;
+  const uint64_t total = bsum[nblk];
+  const bool over = total > (uint64_t)cap;
+  hdr->count = (int64_t)total;
+  if (over) set_status(hdr, GFTORF_ERR_CAPACITY);
+  uint32_t c = 0;
+  for (int b = 0; b < B; ++b) {
+    const uint64_t fs = eoff[(size_t)b * N];
+    const uint64_t fe = b + 1 < B ? (uint64_t)eoff[(size_t)(b + 1) * N] : total;
+    hdr->fstart[b] = (uint32_t)fs;
+    hdr->coff[b] = c;
+    if (!over) c += (uint32_t)((fe - fs + kChunk - 1) / kChunk);
+  }
+  hdr->fstart[B] = (uint32_t)total;
+  hdr->coff[B] = c <= (uint32_t)n_chunk ? c : (uint32_t)n_chunk;
+}
+
+struct ChunkPos {
+  int b;
+  uint32_t s, e;  // instance range of the chunk
+};
+
+__device__ __forceinline__ ChunkPos chunk_pos(const Header* hdr, int c) {
+  ChunkPos p;
+  int b = 0;
+  while ((uint32_t)c >= hdr->coff[b + 1]) ++b;
+  p.b = b;
+  p.s = hdr->fstart[b] + (uint32_t)(c - (int)hdr->coff[b]) * kChunk;
+  p.e = min(p.s + (uint32_t)kChunk, hdr->fstart[b + 1]);
+  return p;
+}
+
+// count the tiles hit by the instances [s, e) of one chunk
 __global__ void __launch_bounds__(256)
     tile_count_kernel(const uint32_t* __restrict__ sorted_ids,
                       const uint2* __restrict__ rect,
                       const Header* __restrict__ hdr,
+                      const uint32_t* __restrict__ eoff,
                       uint32_t* __restrict__ tcnt, int N, int NT, int tiles_x,
-                      int n_chunk) {
-  extern __shared__ uint32_t cnt[];  // NT
-  const int c = blockIdx.x, b = blockIdx.y;
-  for (int t = threadIdx.x; t < NT; t += blockDim.x) cnt[t] = 0;
-  __syncthreads();
-  const int vis = (int)hdr->vis[b];
-  const int lo = c * kChunk, hi = min(lo + kChunk, vis);
-  for (int pos = lo + threadIdx.x; pos < hi; pos += blockDim.x) {
-    const uint32_t g = sorted_ids[(size_t)b * N + pos];
-    int x0, y0, x1, y1;
-    unpack_rect(rect[(size_t)b * N + g], x0, y0, x1, y1);
-    for (int ty = y0; ty < y1; ++ty)
-      for (int tx = x0; tx < x1; ++tx) atomicAdd(&cnt[ty * tiles_x + tx], 1u);
+                      int B) {
+  extern __shared__ uint32_t hist[];  // NT
+  __shared__ int s_r0;
+  const int c = blockIdx.x;
+  if ((uint32_t)c >= hdr->coff[B]) return;
+  const ChunkPos cp = chunk_pos(hdr, c);
+  const int vis = (int)hdr->vis[cp.b];
+  const uint32_t* eb = eoff + (size_t)cp.b * N;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) hist[t] = 0;
+  if (threadIdx.x < 32) {
+    const int r0 = warp_upper_rank(eb, vis, cp.s, threadIdx.x);
+    if (threadIdx.x == 0) s_r0 = r0;
   }
   __syncthreads();
-  uint32_t* out = tcnt + ((size_t)b * n_chunk + c) * NT;
-  for (int t = threadIdx.x; t < NT; t += blockDim.x) out[t] = cnt[t];
+  const uint32_t* ids = sorted_ids + (size_t)cp.b * N;
+  const uint2* rc = rect + (size_t)cp.b * N;
+  for (int r = s_r0 + threadIdx.x; r < vis; r += blockDim.x) {
+    const uint32_t eo = eb[r];
+    if (eo >= cp.e) break;
+    int x0, y0, x1, y1;
+    unpack_rect(rc[ids[r]], x0, y0, x1, y1);
+    const int w = x1 - x0;
+    const uint32_t n = (uint32_t)(w * (y1 - y0));
+    const uint32_t lo = max(cp.s, eo) - eo, hi = min(cp.e, eo + n) - eo;
+    int ky = (int)(lo / (uint32_t)w), kx = (int)(lo - (uint32_t)ky * w);
+    for (uint32_t k = lo; k < hi; ++k) {
+      atomicAdd(&hist[(y0 + ky) * tiles_x + x0 + kx], 1u);
+      if (++kx == w) kx = 0, ++ky;
+    }
+  }
+  __syncthreads();
+  uint32_t* out = tcnt + (size_t)c * NT;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) out[t] = hist[t];
 }
 
-// column scan over chunks for each (frame, tile): tcnt becomes the exclusive
-// prefix over chunks, ttot the tile's total
+// per (frame, tile): exclusive prefix over the frame's chunks; tile totals
 __global__ void tile_colscan_kernel(uint32_t* __restrict__ tcnt,
-                                    uint32_t* __restrict__ ttot, int NT,
-                                    int n_chunk) {
+                                    uint32_t* __restrict__ ttot,
+                                    const Header* __restrict__ hdr, int NT) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (t >= NT) return;
   uint32_t run = 0;
-  uint32_t* col = tcnt + (size_t)b * n_chunk * NT + t;
-  for (int c = 0; c < n_chunk; ++c) {
-    const uint32_t v = col[(size_t)c * NT];
-    col[(size_t)c * NT] = run;
+  const uint32_t c0 = hdr->coff[b], c1 = hdr->coff[b + 1];
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint32_t v = tcnt[(size_t)c * NT + t];
+    tcnt[(size_t)c * NT + t] = run;
     run += v;
   }
   ttot[(size_t)b * NT + t] = run;
@@ -230,56 +382,69 @@ __global__ void __launch_bounds__(1024)
     tile_scan_kernel(uint32_t* __restrict__ ttot, uint2* __restrict__ ranges,
                      Header* __restrict__ hdr, int64_t S, int64_t cap) {
   __shared__ uint64_t s_total;
-  // keep the totals: the scan runs in place on a copy held in `ranges.x`
   for (int64_t i = threadIdx.x; i < S; i += blockDim.x) ranges[i].y = ttot[i];
   __syncthreads();
-  cta_exclusive_scan(ttot, S, &s_total);
+  cta_exclusive_scan<uint32_t>(ttot, S, &s_total);
   __syncthreads();
   const uint64_t total = s_total;
   for (int64_t i = threadIdx.x; i < S; i += blockDim.x) {
     const uint64_t s = ttot[i], e = s + ranges[i].y;
     ranges[i] = make_uint2((uint32_t)min(s, (uint64_t)cap), (uint32_t)min(e, (uint64_t)cap));
   }
-  if (threadIdx.x == 0) {
-    hdr->count = (int64_t)total;
-    if (total > (uint64_t)cap) set_status(hdr, GFTORF_ERR_CAPACITY);
-  }
+  if (threadIdx.x == 0 && total > (uint64_t)cap) set_status(hdr, GFTORF_ERR_CAPACITY);
 }
 
-// stable scatter of the instances: warp w of chunk c walks its Gaussians in
-// depth order, one Gaussian at a time, lanes spread over its tiles
+// Stable scatter of one chunk: warp w owns the instance sub-range
+// [s + w kChunk/nw, ...) and walks its Gaussians in depth order, one at a
+// time, lanes spread over the Gaussian's tiles of the sub-range; each tile's
+// cursor starts at tile base + chunk prefix + earlier warps' counts.
 __global__ void __launch_bounds__(256)
     tile_scatter_kernel(const uint32_t* __restrict__ sorted_ids,
                         const uint2* __restrict__ rect,
                         const Header* __restrict__ hdr,
+                        const uint32_t* __restrict__ eoff,
                         const uint32_t* __restrict__ tcnt,
                         const uint32_t* __restrict__ toff,
                         uint32_t* __restrict__ values, int N, int NT,
-                        int tiles_x, int n_chunk, int64_t cap) {
+                        int tiles_x, int B, int64_t cap) {
   extern __shared__ uint32_t cur[];  // [warps][NT]
-  const int c = blockIdx.x, b = blockIdx.y;
+  const int c = blockIdx.x;
+  if ((uint32_t)c >= hdr->coff[B]) return;
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int vis = (int)hdr->vis[b];
-  const int lo = c * kChunk;
-  if (lo >= vis) return;
+  const ChunkPos cp = chunk_pos(hdr, c);
+  const int vis = (int)hdr->vis[cp.b];
+  const uint32_t* eb = eoff + (size_t)cp.b * N;
+  const uint32_t* ids = sorted_ids + (size_t)cp.b * N;
+  const uint2* rc = rect + (size_t)cp.b * N;
   for (int i = threadIdx.x; i < nw * NT; i += blockDim.x) cur[i] = 0;
-  __syncthreads();
-  const int per = kChunk / nw;
-  const int wlo = lo + w * per, whi = min(wlo + per, vis);
-  const uint32_t* ids = sorted_ids + (size_t)b * N;
-  const uint2* rc = rect + (size_t)b * N;
+  const uint32_t per = kChunk / nw;
+  const uint32_t sw = cp.s + (uint32_t)w * per;
+  const uint32_t ew = min(sw + per, cp.e);
+  const bool active = sw < ew;
+  const int rw = active ? warp_upper_rank(eb, vis, sw, lane) : 0;
   uint32_t* my = cur + (size_t)w * NT;
-  // phase 1: per-warp tile counts
-  for (int pos = wlo + lane; pos < whi; pos += 32) {
-    int x0, y0, x1, y1;
-    unpack_rect(rc[ids[pos]], x0, y0, x1, y1);
-    for (int ty = y0; ty < y1; ++ty)
-      for (int tx = x0; tx < x1; ++tx) atomicAdd(&my[ty * tiles_x + tx], 1u);
+  __syncthreads();
+  // phase 1: this warp's tile counts
+  if (active) {
+    for (int r = rw + lane; r < vis; r += 32) {
+      const uint32_t eo = eb[r];
+      if (eo >= ew) break;
+      int x0, y0, x1, y1;
+      unpack_rect(rc[ids[r]], x0, y0, x1, y1);
+      const int wd = x1 - x0;
+      const uint32_t n = (uint32_t)(wd * (y1 - y0));
+      const uint32_t lo = max(sw, eo) - eo, hi = min(ew, eo + n) - eo;
+      int ky = (int)(lo / (uint32_t)wd), kx = (int)(lo - (uint32_t)ky * wd);
+      for (uint32_t k = lo; k < hi; ++k) {
+        atomicAdd(&my[(y0 + ky) * tiles_x + x0 + kx], 1u);
+        if (++kx == wd) kx = 0, ++ky;
+      }
+    }
   }
   __syncthreads();
-  // phase 2: cursors = tile base + chunk prefix + earlier warps of the chunk
-  const uint32_t* cc = tcnt + ((size_t)b * n_chunk + c) * NT;
-  const uint32_t* to = toff + (size_t)b * NT;
+  // phase 2: cursors
+  const uint32_t* cc = tcnt + (size_t)c * NT;
+  const uint32_t* to = toff + (size_t)cp.b * NT;
   for (int t = threadIdx.x; t < NT; t += blockDim.x) {
     uint32_t run = to[t] + cc[t];
     for (int ww = 0; ww < nw; ++ww) {
@@ -289,33 +454,42 @@ __global__ void __launch_bounds__(256)
     }
   }
   __syncthreads();
+  if (!active) return;
   // phase 3: ordered writes
-  for (int base = wlo; base < whi; base += 32) {
-    const int pos = base + lane;
-    uint32_t g = 0;
+  for (int base = rw;; base += 32) {
+    const int r = base + lane;
+    uint32_t eo = 0xFFFFFFFFu, g = 0;
     uint2 pr = make_uint2(0, 0);
-    if (pos < whi) {
-      g = ids[pos];
-      pr = rc[g];
+    if (r < vis) {
+      eo = eb[r];
+      if (eo < ew) {
+        g = ids[r];
+        pr = rc[g];
+      }
     }
-    const int cnt = min(32, whi - base);
+    const unsigned take = __ballot_sync(0xffffffffu, r < vis && eo < ew);
+    const int cnt = __popc(take);  // a prefix of the lanes (offsets increase)
     for (int j = 0; j < cnt; ++j) {
       const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
+      const uint32_t eoj = __shfl_sync(0xffffffffu, eo, j);
       uint2 rj;
       rj.x = __shfl_sync(0xffffffffu, pr.x, j);
       rj.y = __shfl_sync(0xffffffffu, pr.y, j);
       int x0, y0, x1, y1;
       unpack_rect(rj, x0, y0, x1, y1);
-      const int wd = x1 - x0, area = wd * (y1 - y0);
-      for (int k = lane; k < area; k += 32) {
-        const int ty = y0 + k / wd, tx = x0 + k % wd;
-        const int t = ty * tiles_x + tx;
+      const int wd = x1 - x0;
+      const uint32_t n = (uint32_t)(wd * (y1 - y0));
+      const uint32_t lo = max(sw, eoj) - eoj, hi = min(ew, eoj + n) - eoj;
+      for (uint32_t k = lo + lane; k < hi; k += 32) {
+        const int ky = (int)(k / (uint32_t)wd), kx = (int)(k - (uint32_t)ky * wd);
+        const int t = (y0 + ky) * tiles_x + x0 + kx;
         const uint32_t p = my[t];
         my[t] = p + 1;
         if ((int64_t)p < cap) values[p] = gj;
       }
       __syncwarp();
     }
+    if (cnt < 32) break;
   }
 }
 
@@ -360,47 +534,49 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   auto* i1 = at<uint32_t>(ws, L.off_ids2);
   auto* dh = at<uint32_t>(ws, L.off_dhist);
   auto* rect = at<const uint2>(ws, L.off_rect);
+  auto* ecnt = at<uint32_t>(ws, L.off_ecnt);
+  auto* bsum = at<uint64_t>(ws, L.off_bsum);
   auto* tcnt = at<uint32_t>(ws, L.off_tcnt);
   auto* ttot = at<uint32_t>(ws, L.off_toff);
   auto* ranges = at<uint2>(ws, L.off_ranges);
   auto* values = at<uint32_t>(ws, L.off_values);
   const uint32_t* sorted = i1;
-  if (L.N > 0) {
-    // depth sort: zkey -> (k0,i0) -> (k1,i1) -> (k0,i0) -> (k1,i1)
-    const uint32_t* kin = zkey;
-    const uint32_t* iin = nullptr;
-    uint32_t* kout[2] = {k0, k1};
-    uint32_t* iout[2] = {i0, i1};
-    dim3 g(L.n_dblk, L.B);
-    for (int pass = 0; pass < 4; ++pass) {
-      const int shift = 8 * pass;
-      dsort_hist_kernel<<<g, kSortThreads, 0, st>>>(kin, L.N, shift, dh, L.n_dblk);
-      dsort_scan_kernel<<<L.B, 1024, 0, st>>>(dh, L.n_dblk);
-      dsort_scatter_kernel<<<g, kSortThreads, 0, st>>>(kin, iin, kout[pass & 1],
-                                                       iout[pass & 1], L.N, shift,
-                                                       dh, L.n_dblk);
-      kin = kout[pass & 1];
-      iin = iout[pass & 1];
-    }
-    dim3 gc(L.n_chunk, L.B);
-    tile_count_kernel<<<gc, 256, (size_t)L.NT * 4, st>>>(sorted, rect, hdr, tcnt, L.N,
-                                                         L.NT, L.tiles_x, L.n_chunk);
-    count_launches(13);
-  } else {
-    cudaMemsetAsync(tcnt, 0, (size_t)L.B * L.n_chunk * L.NT * 4, st);
+  if (L.N == 0) {
+    cudaMemsetAsync(ranges, 0, (size_t)L.B * L.NT * sizeof(uint2), st);
+    return;
   }
-  dim3 gs((L.NT + 255) / 256, L.B);
-  tile_colscan_kernel<<<gs, 256, 0, st>>>(tcnt, ttot, L.NT, L.n_chunk);
+  // 1. depth sort: zkey -> (k0,i0) -> (k1,i1) -> (k0,i0) -> (k1,i1)
+  const uint32_t* kin = zkey;
+  const uint32_t* iin = nullptr;
+  uint32_t* kout[2] = {k0, k1};
+  uint32_t* iout[2] = {i0, i1};
+  dim3 g(L.n_dblk, L.B);
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 8 * pass;
+    dsort_hist_kernel<<<g, kSortThreads, 0, st>>>(kin, L.N, shift, dh, L.n_dblk);
+    dsort_scan_kernel<<<L.B, 1024, 0, st>>>(dh, L.n_dblk);
+    dsort_scatter_kernel<<<g, kSortThreads, 0, st>>>(kin, iin, kout[pass & 1], iout[pass & 1],
+                                                     L.N, shift, dh, L.n_dblk);
+    kin = kout[pass & 1];
+    iin = iout[pass & 1];
+  }
+  // 2. emission offsets of the depth-ordered Gaussians, chunk table
+  const int64_t S = (int64_t)L.B * L.N;
+  inst_count_kernel<<<dim3((L.N + 255) / 256, L.B), 256, 0, st>>>(sorted, rect, hdr, ecnt, L.N);
+  scan_reduce_kernel<<<L.n_scan, 256, 0, st>>>(ecnt, S, bsum);
+  scan_top_kernel<<<1, 1024, 0, st>>>(bsum, L.n_scan);
+  scan_down_kernel<<<L.n_scan, 256, 0, st>>>(ecnt, S, bsum);
+  chunk_table_kernel<<<1, 32, 0, st>>>(ecnt, bsum, L.n_scan, hdr, L.B, L.N, L.cap, L.n_chunk);
+  // 3. per-chunk tile counts, per-frame column scan, tile ranges
+  tile_count_kernel<<<L.n_chunk, 256, (size_t)L.NT * 4, st>>>(sorted, rect, hdr, ecnt, tcnt,
+                                                              L.N, L.NT, L.tiles_x, L.B);
+  tile_colscan_kernel<<<dim3((L.NT + 255) / 256, L.B), 256, 0, st>>>(tcnt, ttot, hdr, L.NT);
   tile_scan_kernel<<<1, 1024, 0, st>>>(ttot, ranges, hdr, (int64_t)L.B * L.NT, L.cap);
-  count_launches(2);
-  if (L.N > 0) {
-    dim3 gc(L.n_chunk, L.B);
-    const int nw = L.scatter_warps;
-    tile_scatter_kernel<<<gc, nw * 32, (size_t)nw * L.NT * 4, st>>>(
-        sorted, rect, hdr, tcnt, ttot, values, L.N, L.NT, L.tiles_x, L.n_chunk,
-        L.cap);
-    count_launches(1);
-  }
+  // 4. stable scatter
+  const int nw = L.scatter_warps;
+  tile_scatter_kernel<<<L.n_chunk, nw * 32, (size_t)nw * L.NT * 4, st>>>(
+      sorted, rect, hdr, ecnt, tcnt, ttot, values, L.N, L.NT, L.tiles_x, L.B, L.cap);
+  count_launches(12 + 9);
 }
 
 void launch_export_keys(const Layout& L, uint64_t* keys, unsigned char* ws,

@@ -20,8 +20,11 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
-// Tile binning: a chunk of depth-ordered Gaussians per CTA.
-constexpr int kChunk = 4096;
+// Tile binning: a chunk of kChunk consecutive instances (in emission order:
+// frame, depth rank, tile of the rectangle) per CTA.
+constexpr int kChunk = 16384;
+// Device-wide scans: elements per CTA.
+constexpr int kScanTile = 4096;
 
 // Per-frame camera in device memory (double; kernels round to their type).
 struct FrameDev {
@@ -49,6 +52,8 @@ struct Header {
   int64_t count;           // tile instances of the batch
   uint32_t queue[4];       // persistent work-queue heads (fwd, bwd)
   uint32_t vis[kMaxFrames];  // visible Gaussians per frame
+  uint32_t fstart[kMaxFrames + 1];  // first instance of each frame
+  uint32_t coff[kMaxFrames + 1];    // first binning chunk of each frame
 };
 
 // Host-computed byte layout of the workspace for one gftorf_dims.
@@ -58,11 +63,13 @@ struct Layout {
   int rec_stride;  // Reals per projected record (16-byte multiple)
   int g2d_stride;  // Reals per 2D-gradient row
   int n_dblk;      // depth-sort tiles per frame
-  int n_chunk;     // binning chunks per frame
+  int n_chunk;     // binning chunks of the batch (upper bound)
+  int n_scan;      // CTAs of the emission-offset scan
   int scatter_warps;
   int64_t cap;
   size_t off_header, off_table, off_rec, off_rect, off_zkey, off_zkey2,
-      off_ids, off_ids2, off_dhist, off_tcnt, off_toff, off_ranges,
+      off_ids, off_ids2, off_dhist, off_ecnt, off_bsum, off_tcnt, off_toff,
+      off_ranges,
       off_values, off_tfinal, off_nlast, off_g2d, total;
 };
 
