@@ -219,6 +219,33 @@ gftorf_status gftorf_sort_footprints(const gftorf_dims* dims, const float* u,
                                      int64_t* count, void* workspace,
                                      size_t workspace_bytes, void* stream);
 
+/* gftorf_sort_footprints without a workspace argument, for callers that
+ * cannot allocate device memory themselves: code running where cudaMalloc is
+ * not available or not allowed (inside a region being captured into a CUDA
+ * graph, a host callback, a plugin that may only touch buffers it was
+ * handed).  The paper has no counterpart; it is a packaging convenience.
+ * Same arguments, results and bit-exact ordering as gftorf_sort_footprints.
+ * Its scratch is a fixed 32 MiB device array inside the library, so:
+ *   - every GPU that loads the library holds those 32 MiB until process exit;
+ *   - problems whose binning scratch (about 32 B per (frame, Gaussian) plus
+ *     4 B per instance of dims->max_instances plus per-tile counters) does
+ *     not fit return GFTORF_ERR_WORKSPACE before any work is enqueued;
+ *   - the first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture;
+ *   - all calls share the one array: calls whose GPU work overlaps (other
+ *     streams, other host threads) race and corrupt each other's results;
+ *   - a capacity overflow is seen as *count > dims->max_instances (the lists
+ *     are then left empty); the device status word of a workspace is not
+ *     involved.
+ * It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * call. */
+gftorf_status gftorf_sort_footprints_noalloc(const gftorf_dims* dims,
+                                             const float* u, const float* v,
+                                             const int32_t* radius,
+                                             const float* z, uint64_t* keys,
+                                             uint32_t* values, uint32_t* ranges,
+                                             int64_t* count, void* stream);
+
 /* Copy the current batch's sorted tile instances out of the workspace:
  * keys[M] (as in gftorf_sort_footprints), values[M], ranges[B*tiles][2],
  * *count (all device; keys may be NULL).  For inspection and tests. */

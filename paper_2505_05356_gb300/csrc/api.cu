@@ -113,6 +113,42 @@ __global__ void store_table_kernel(Table t, Table* dst) {
 bool finite(float x) { return isfinite(x) != 0; }
 
 }  // namespace
+
+// Workspace layout holding only the regions the binning stages touch (the
+// projected records, per-pixel state and 2D-gradient regions are empty).
+bool binning_dims_ok(const gftorf_dims* d) { return dims_ok(d); }
+
+Layout binning_layout(const gftorf_dims* d) {
+  Layout L = make_layout(d);
+  const size_t BN = (size_t)L.B * L.N;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at_ = o;
+    o = align_up(o + bytes);
+    return at_;
+  };
+  L.off_header = take(sizeof(Header));
+  L.off_table = take(0);
+  L.off_rec = take(0);
+  L.off_rect = take(BN * sizeof(uint2));
+  L.off_zkey = take(BN * 4);
+  L.off_zkey2 = take(2 * BN * 4);
+  L.off_ids = take(BN * 4);
+  L.off_ids2 = take(BN * 4);
+  L.off_dhist = take((size_t)L.B * 256 * (L.n_dblk > 0 ? L.n_dblk : 1) * 4);
+  L.off_ecnt = take(BN * 4 + 4);
+  L.off_bsum = take((size_t)(L.n_scan + 1) * 8);
+  L.off_tcnt = take((size_t)L.n_chunk * L.NT * 4);
+  L.off_toff = take((size_t)L.B * L.NT * 4);
+  L.off_ranges = take((size_t)L.B * L.NT * sizeof(uint2));
+  L.off_values = take((size_t)(L.cap > 0 ? L.cap : 1) * 4);
+  L.off_tfinal = take(0);
+  L.off_nlast = take(0);
+  L.off_g2d = take(0);
+  L.total = o;
+  return L;
+}
+
 }  // namespace gftorf
 
 using namespace gftorf;

@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
     L.gftorf_zero_grad_buffers.argtypes = [_P(Dims), _P(Gradients), vp, sz, vp]
     L.gftorf_composite_bwd.argtypes = [_P(Dims), vp, vp, _P(Gradients), vp, sz, vp]
     L.gftorf_preprocess_bwd.argtypes = [_P(Dims), _P(Gaussians), _P(Gradients), vp, sz, vp]
+    L.gftorf_sort_footprints_noalloc.argtypes = [_P(Dims), vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.gftorf_sort_footprints_noalloc.restype = ctypes.c_int
     L.gftorf_kernel_launches.restype = ctypes.c_int64
     L.gftorf_kernel_launches.argtypes = []
     for name in ("gftorf_preprocess", "gftorf_render_fwd", "gftorf_render_bwd",
@@ -413,6 +415,27 @@ def sort_footprints(u, v, radius, z, width, height, tile=(16, 16), max_instances
     _check(code, "device status")
     m = int(cnt.value)
     return keys[:m], vals[:m], ranges
+
+
+def sort_footprints_noalloc(u, v, radius, z, width, height, tile=(16, 16), max_instances=1):
+    """gftorf_sort_footprints_noalloc: the same binning with the library's
+    fixed device scratch (no workspace).  Output buffers are allocated here by
+    torch for convenience; the entry point itself allocates nothing.
+    Returns (status, keys, values, ranges, count_tensor)."""
+    _require_cuda()
+    L = load()
+    B, n = u.shape
+    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, int(max_instances))
+    cap = max(1, int(max_instances))
+    keys = torch.empty(cap, dtype=torch.int64, device=u.device)
+    vals = torch.empty(cap, dtype=torch.int32, device=u.device)
+    tiles = (-(-width // tile[0])) * (-(-height // tile[1]))
+    ranges = torch.empty((B * tiles, 2), dtype=torch.int32, device=u.device)
+    count = torch.zeros(1, dtype=torch.int64, device=u.device)
+    code = L.gftorf_sort_footprints_noalloc(ctypes.byref(dims), _ptr(u), _ptr(v), _ptr(radius),
+                                            _ptr(z), _ptr(keys), _ptr(vals), _ptr(ranges),
+                                            _ptr(count), _stream())
+    return code, keys, vals, ranges, count
 
 
 # --- autograd ------------------------------------------------------------------
