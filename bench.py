@@ -145,7 +145,7 @@ def run_ours(args):
     tile = tuple(int(v) for v in args.tile.split("x"))
     sc.consts.tile_w, sc.consts.tile_h = tile
     r = gftorf.Renderer(N, B, W, H, len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad),
-                        tile=tile, render_mode=args.mode)
+                        tile=tile, render_mode=args.mode, pixels_per_thread=args.ppt)
     p = gftorf.params_from_scene(sc)
     fr = gftorf.frames_from_scene(sc)
     se = gftorf.sensor_from_scene(sc)
@@ -365,6 +365,7 @@ def run_ours(args):
                                    "%d timesteps per batch, 30 MHz x 4 offsets + ambient, "
                                    "30-100%% visible per frame" % (args.workload, N, W, H, B),
                        "frames_per_step": B, "tile": args.tile,
+                       "pixels_per_thread": args.ppt,
                        "render_mode": "persistent" if args.mode == 1 else "grid",
                        "cuda_graph": use_graph, "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (%.0f MB workspace per step)" % (r.ws_bytes / 1e6),
@@ -496,6 +497,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--mode", type=int, default=0, help="0 grid, 1 persistent")
+    ap.add_argument("--ppt", type=int, default=2, help="pixels per compositing thread")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")

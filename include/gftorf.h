@@ -79,6 +79,10 @@ typedef struct {
   int32_t dtype;         /* gftorf_dtype                                    */
   int32_t render_mode;   /* 0: one CTA per (frame, tile);
                             1: persistent CTAs over a (frame, tile) queue   */
+  int32_t pixels_per_thread; /* compositing pixels per thread: 1, 2 or 4
+                            (0: 2); tile_w * tile_h / it must be >= 32.
+                            Results do not depend on it.                    */
+  int32_t reserved;      /* must be 0                                       */
   int64_t max_instances; /* capacity of the (Gaussian, tile) instance list,
                             summed over the batch                           */
 } gftorf_dims;

@@ -59,6 +59,7 @@ struct Header {
 // Host-computed byte layout of the workspace for one gftorf_dims.
 struct Layout {
   int B, N, W, H, TW, TH, F, P, C, NF, dtype, real_size, mode;
+  int ppt;  // pixels per compositing thread (1, 2 or 4)
   int tiles_x, tiles_y, NT;
   int rec_stride;  // Reals per projected record (16-byte multiple)
   int g2d_stride;  // Reals per 2D-gradient row

@@ -1,6 +1,8 @@
-// render.cu -- per-tile compositing of raw C-ToF samples (Eq. 4) and its
-// backward re-walk (Eq. S3), one thread per pixel, one CTA per (frame, tile)
-// or persistent CTAs pulling (frame, tile) items from a queue.
+// render_impl.cuh -- per-tile compositing of raw C-ToF samples (Eq. 4) and its
+// backward re-walk (Eq. S3).  A thread owns PPT (1, 2 or 4) vertically
+// adjacent pixels of a tile, so each staged Gaussian record, its column
+// offset and (backward) its warp reduction serve PPT pixels; one CTA per
+// (frame, tile) or persistent CTAs pulling (frame, tile) items from a queue.
 //
 // Forward, per pixel, front to back over the tile's depth-ordered list:
 //   alpha = min(alpha_max, o 2^(power2)), power2 = log2(e) * power
@@ -19,6 +21,8 @@
 // them) and g_T = sum_c bg_c dL/dQ_c.  Per-Gaussian sums over the CTA's
 // pixels: warp shuffle reduction, shared-memory accumulation, then one
 // global atomic per value per CTA.
+#pragma once
+
 #include "gftorf_internal.cuh"
 
 namespace gftorf {
@@ -49,23 +53,6 @@ __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fm
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
-
-// exponent (log2 domain) and alpha of one Gaussian at one pixel
-template <typename Real>
-__device__ __forceinline__ void eval_alpha(const Real* r, Real fpx, Real fpy,
-                                           Real amax, Real& dx, Real& dy,
-                                           Real& pw, Real& G, Real& oG,
-                                           Real& alpha) {
-  dx = sub_rn(r[0], fpx);
-  dy = sub_rn(r[1], fpy);
-  const Real t1 = mul_rn(r[3], dy);
-  const Real t2 = fma_rn(r[2], dx, t1);
-  const Real t3 = mul_rn(mul_rn(r[4], dy), dy);
-  pw = fma_rn(dx, t2, t3);
-  G = ex2_approx(pw);
-  oG = mul_rn(r[5], G);
-  alpha = oG < amax ? oG : amax;
-}
 
 __device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
@@ -141,9 +128,18 @@ struct RenderGeom {
 };
 
 // ---------------------------------------------------------------------------
-// forward
+// forward: thread (lx, row group) owns PPT vertically adjacent pixels
 // ---------------------------------------------------------------------------
-template <typename Real, int F>
+
+// exponent (log2 domain) of one Gaussian at a pixel offset (dx, dy), with
+// ca_dx = ca * dx shared by the pixels of a column; one rounding per operation
+// so the backward replays the forward's decisions bit for bit
+template <typename Real>
+__device__ __forceinline__ Real power2(const Real* r, Real dx, Real ca_dx, Real dy) {
+  return fma_rn(dx, fma_rn(r[3], dy, ca_dx), mul_rn(mul_rn(r[4], dy), dy));
+}
+
+template <typename Real, int F, int PPT>
 __device__ __forceinline__ void render_tile_fwd(
     const TileCtx& tc, const RenderGeom& rg, const Table* __restrict__ tab,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
@@ -152,25 +148,36 @@ __device__ __forceinline__ void render_tile_fwd(
     uint32_t* __restrict__ nlast, Real* s_rec) {
   constexpr int NF = 2 * F + 1;
   constexpr int RS = rec_stride<Real, F>();
+  constexpr unsigned ALL = (1u << PPT) - 1u;
   const int nthr = blockDim.x, tid = threadIdx.x;
-  const int lx = tid % rg.TW, ly = tid / rg.TW;
-  const int px = tc.tx * rg.TW + lx, py = tc.ty * rg.TH + ly;
-  const bool inside = px < rg.W && py < rg.H;
-  const Real fpx = (Real)px + Real(0.5), fpy = (Real)py + Real(0.5);
+  const int lx = tid % rg.TW, ly0 = (tid / rg.TW) * PPT;
+  const int px = tc.tx * rg.TW + lx, py0 = tc.ty * rg.TH + ly0;
+  const Real fpx = (Real)px + Real(0.5);
+  Real fpy[PPT];
+  unsigned done = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    fpy[k] = (Real)(py0 + k) + Real(0.5);
+    if (!(px < rg.W && py0 + k < rg.H)) done |= 1u << k;
+  }
+  const unsigned outside = done;
   const Real amax = (Real)tab->alpha_max, amin = (Real)tab->alpha_min;
   const Real tmin = (Real)tab->t_min;
   const uint2 range = ranges[(size_t)tc.b * rg.NT + tc.tile];
   const Real* frec = rec + (size_t)tc.b * rg.N * RS;
 
-  Real T = 1;
-  Real acc[NF];
+  Real T[PPT], acc[PPT][NF];
+  uint32_t last[PPT];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) acc[f] = 0;
-  uint32_t last = range.x;
-  bool done = !inside;
+  for (int k = 0; k < PPT; ++k) {
+    T[k] = 1;
+    last[k] = range.x;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc[k][f] = 0;
+  }
 
   for (uint32_t base = range.x; base < range.y; base += nthr) {
-    if (__syncthreads_count(done) == nthr) break;
+    if (__syncthreads_count(done == ALL) == nthr) break;
     const uint32_t i = base + tid;
     if (i < range.y) {
       const uint32_t g = values[i];
@@ -181,43 +188,50 @@ __device__ __forceinline__ void render_tile_fwd(
     }
     __syncthreads();
     const int cnt = min((uint32_t)nthr, range.y - base);
-    if (!done) {
-      for (int j = 0; j < cnt; ++j) {
-        const Real* r = s_rec + j * RS;
-        Real dx, dy, pw, G, oG, alpha;
-        eval_alpha<Real>(r, fpx, fpy, amax, dx, dy, pw, G, oG, alpha);
-        if (pw > Real(0) || alpha < amin) continue;
-        const Real tn = T * (Real(1) - alpha);
-        if (tn < tmin) {
-          done = true;
-          break;
-        }
-        const Real w = alpha * T * T;
+    for (int j = 0; j < cnt && done != ALL; ++j) {
+      const Real* r = s_rec + j * RS;
+      const Real dx = sub_rn(r[0], fpx);
+      const Real ca_dx = mul_rn(r[2], dx);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) acc[f] += w * r[6 + f];
-        T = tn;
-        last = base + j + 1;
+      for (int k = 0; k < PPT; ++k) {
+        if (done & (1u << k)) continue;
+        const Real pw = power2(r, dx, ca_dx, sub_rn(r[1], fpy[k]));
+        const Real oG = mul_rn(r[5], ex2_approx(pw));
+        const Real alpha = oG < amax ? oG : amax;
+        if (pw > Real(0) || alpha < amin) continue;
+        const Real tn = T[k] * (Real(1) - alpha);
+        if (tn < tmin) {
+          done |= 1u << k;
+          continue;
+        }
+        const Real w = alpha * T[k] * T[k];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[k][f] += w * r[6 + f];
+        T[k] = tn;
+        last[k] = base + j + 1;
       }
     }
   }
-  if (inside) {
-    const size_t HW = (size_t)rg.W * rg.H;
-    const size_t pix = (size_t)py * rg.W + px;
+  const size_t HW = (size_t)rg.W * rg.H;
+  const Real* bgb = bg + (size_t)tc.b * rg.C;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    if (outside & (1u << k)) continue;
+    const size_t pix = (size_t)(py0 + k) * rg.W + px;
     Real* o = out + (size_t)tc.b * rg.C * HW + pix;
-    const Real* bgb = bg + (size_t)tc.b * rg.C;
     for (int f = 0; f < F; ++f)
       for (int j = 0; j < rg.P; ++j)
-        o[(size_t)(f * rg.P + j) * HW] = (Real)tab->cos_off[j] * acc[2 * f] +
-                                         (Real)tab->sin_off[j] * acc[2 * f + 1] +
-                                         bgb[f * rg.P + j] * T;
-    o[(size_t)(F * rg.P) * HW] = acc[2 * F] + bgb[F * rg.P] * T;
-    tfinal[(size_t)tc.b * HW + pix] = T;
-    nlast[(size_t)tc.b * HW + pix] = last - range.x;
+        o[(size_t)(f * rg.P + j) * HW] = (Real)tab->cos_off[j] * acc[k][2 * f] +
+                                         (Real)tab->sin_off[j] * acc[k][2 * f + 1] +
+                                         bgb[f * rg.P + j] * T[k];
+    o[(size_t)(F * rg.P) * HW] = acc[k][2 * F] + bgb[F * rg.P] * T[k];
+    tfinal[(size_t)tc.b * HW + pix] = T[k];
+    nlast[(size_t)tc.b * HW + pix] = last[k] - range.x;
   }
 }
 
-template <typename Real, int F>
-__global__ void __launch_bounds__(512)
+template <typename Real, int F, int PPT>
+__global__ void __launch_bounds__(512 / PPT)
     render_fwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
@@ -230,8 +244,8 @@ __global__ void __launch_bounds__(512)
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
-    render_tile_fwd<Real, F>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
-                             values, rec, bg, out, tfinal, nlast, s_rec);
+    render_tile_fwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                                  values, rec, bg, out, tfinal, nlast, s_rec);
     return;
   }
   __shared__ uint32_t s_item;
@@ -241,15 +255,15 @@ __global__ void __launch_bounds__(512)
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= items) break;
-    render_tile_fwd<Real, F>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
-                             values, rec, bg, out, tfinal, nlast, s_rec);
+    render_tile_fwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                                  values, rec, bg, out, tfinal, nlast, s_rec);
   }
 }
 
 // ---------------------------------------------------------------------------
 // backward
 // ---------------------------------------------------------------------------
-template <typename Real, int F>
+template <typename Real, int F, int PPT>
 __device__ __forceinline__ void render_tile_bwd(
     const TileCtx& tc, const RenderGeom& rg, const Table* __restrict__ tab,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
@@ -263,41 +277,55 @@ __device__ __forceinline__ void render_tile_bwd(
   constexpr int RS = rec_stride<Real, F>();
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
-  const int lx = tid % rg.TW, ly = tid / rg.TW;
-  const int px = tc.tx * rg.TW + lx, py = tc.ty * rg.TH + ly;
-  const bool inside = px < rg.W && py < rg.H;
-  const Real fpx = (Real)px + Real(0.5), fpy = (Real)py + Real(0.5);
+  const int lx = tid % rg.TW, ly0 = (tid / rg.TW) * PPT;
+  const int px = tc.tx * rg.TW + lx, py0 = tc.ty * rg.TH + ly0;
+  const Real fpx = (Real)px + Real(0.5);
   const Real amax = (Real)tab->alpha_max, amin = (Real)tab->alpha_min;
   const uint2 range = ranges[(size_t)tc.b * rg.NT + tc.tile];
   const Real* frec = rec + (size_t)tc.b * rg.N * RS;
   const size_t HW = (size_t)rg.W * rg.H;
-  const size_t pix = (size_t)py * rg.W + px;
-
-  // fold dL/dQ into accumulator gradients
-  Real gacc[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) gacc[f] = 0;
-  Real gT = 0, Tf = 1;
-  int nl = 0;
   const Real* bgb = bg + (size_t)tc.b * rg.C;
-  if (inside) {
-    const Real* go = dout + (size_t)tc.b * rg.C * HW + pix;
-    Tf = tfinal[(size_t)tc.b * HW + pix];
-    nl = (int)nlast[(size_t)tc.b * HW + pix];
-    for (int f = 0; f < F; ++f)
-      for (int j = 0; j < rg.P; ++j) {
-        const Real gq = go[(size_t)(f * rg.P + j) * HW];
-        gacc[2 * f] += (Real)tab->cos_off[j] * gq;
-        gacc[2 * f + 1] += (Real)tab->sin_off[j] * gq;
-        gT += bgb[f * rg.P + j] * gq;
-      }
-    gacc[2 * F] = go[(size_t)(F * rg.P) * HW];
-    gT += bgb[F * rg.P] * gacc[2 * F];
+
+  // fold dL/dQ into accumulator gradients, per pixel
+  Real fpy[PPT], Tf[PPT], gTf[PPT], gacc[PPT][NF];
+  int nl[PPT];
+  bool inside[PPT];
+  int thread_n = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    fpy[k] = (Real)(py0 + k) + Real(0.5);
+    inside[k] = px < rg.W && py0 + k < rg.H;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) gacc[k][f] = 0;
+    Real gT = 0;
+    Tf[k] = 1;
+    nl[k] = 0;
+    if (inside[k]) {
+      const size_t pix = (size_t)(py0 + k) * rg.W + px;
+      const Real* go = dout + (size_t)tc.b * rg.C * HW + pix;
+      Tf[k] = tfinal[(size_t)tc.b * HW + pix];
+      nl[k] = (int)nlast[(size_t)tc.b * HW + pix];
+      for (int f = 0; f < F; ++f)
+        for (int j = 0; j < rg.P; ++j) {
+          const Real gq = go[(size_t)(f * rg.P + j) * HW];
+          gacc[k][2 * f] += (Real)tab->cos_off[j] * gq;
+          gacc[k][2 * f + 1] += (Real)tab->sin_off[j] * gq;
+          gT += bgb[f * rg.P + j] * gq;
+        }
+      gacc[k][2 * F] = go[(size_t)(F * rg.P) * HW];
+      gT += bgb[F * rg.P] * gacc[k][2 * F];
+    }
+    gTf[k] = gT * Tf[k];
+    thread_n = max(thread_n, nl[k]);
   }
   // dL/dbg_c = sum over pixels of T_N dL/dQ_c (block reduce, one atomic each)
   if (dbg) {
     for (int c = 0; c < rg.C; ++c) {
-      Real v = inside ? Tf * dout[((size_t)tc.b * rg.C + c) * HW + pix] : Real(0);
+      Real v = 0;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k)
+        if (inside[k])
+          v += Tf[k] * dout[((size_t)tc.b * rg.C + c) * HW + (size_t)(py0 + k) * rg.W + px];
       v = warp_sum(v);
       if (lane == 0) s_red[wid] = v;
       __syncthreads();
@@ -310,7 +338,7 @@ __device__ __forceinline__ void render_tile_bwd(
     }
   }
   // longest list any pixel of the tile needs
-  int maxn = nl;
+  int maxn = thread_n;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
   if (lane == 0) reinterpret_cast<int*>(s_red)[wid] = maxn;
@@ -319,12 +347,14 @@ __device__ __forceinline__ void render_tile_bwd(
   for (int w = 0; w < nwarps; ++w) maxn = max(maxn, reinterpret_cast<int*>(s_red)[w]);
   __syncthreads();
 
-  Real T = Tf;
-  const Real gTf = gT * Tf;
-  const int slot = butterfly_slot<GS>(lane);
-  Real acc[NF];
+  Real T[PPT], acc[PPT][NF];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) acc[f] = 0;
+  for (int k = 0; k < PPT; ++k) {
+    T[k] = Tf[k];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc[k][f] = 0;
+  }
+  const int slot = butterfly_slot<GS>(lane);
   const Real ln2 = Real(kLn2);
   Real* gbase = g2d + (size_t)tc.b * rg.N * g2d_stride;
 
@@ -341,46 +371,61 @@ __device__ __forceinline__ void render_tile_bwd(
     }
     for (int k = tid; k < cnt * GS; k += nthr) s_grad[k] = Real(0);
     __syncthreads();
-    // warps whose pixels all stop before this batch skip it entirely
-    const int my_hi = min(nl, hi) - lo;  // entries [0, my_hi) are mine
-    int warp_hi = my_hi;
+    // entries [0, my_hi[k]) of this batch are pixel k's; warps whose pixels
+    // all stop before the batch skip it
+    int my_hi[PPT];
+    int thread_hi = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      my_hi[k] = min(nl[k], hi) - lo;
+      thread_hi = max(thread_hi, my_hi[k]);
+    }
+    int warp_hi = thread_hi;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) warp_hi = max(warp_hi, __shfl_xor_sync(0xffffffffu, warp_hi, o));
     for (int j = warp_hi - 1; j >= 0; --j) {
       const Real* r = s_rec + j * RS;
       Real c[GS];
 #pragma unroll
-      for (int k = 0; k < GS; ++k) c[k] = 0;
+      for (int q = 0; q < GS; ++q) c[q] = 0;
       bool has = false;
-      if (j < my_hi) {
-        Real dx, dy, pw, G, oG, alpha;
-        eval_alpha<Real>(r, fpx, fpy, amax, dx, dy, pw, G, oG, alpha);
-        if (!(pw > Real(0) || alpha < amin)) {
+      if (j < thread_hi) {
+        const Real dx = sub_rn(r[0], fpx);
+        const Real ca_dx = mul_rn(r[2], dx);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (j >= my_hi[k]) continue;
+          const Real dy = sub_rn(r[1], fpy[k]);
+          const Real pw = power2(r, dx, ca_dx, dy);
+          const Real G = ex2_approx(pw);
+          const Real oG = mul_rn(r[5], G);
+          const Real alpha = oG < amax ? oG : amax;
+          if (pw > Real(0) || alpha < amin) continue;
           has = true;
           const Real oma = Real(1) - alpha;
           const Real rcp = div_fast(Real(1), oma);
-          const Real Tk = T * rcp;
+          const Real Tk = T[k] * rcp;
           const Real T2 = Tk * Tk;
           const Real two_oma = oma + oma, oma2 = oma * oma, aT2 = alpha * T2;
-          Real dLda = -gTf * rcp;
+          Real dLda = -gTf[k] * rcp;
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             const Real q = r[6 + f];
-            dLda += gacc[f] * T2 * (q - two_oma * acc[f]);
-            c[6 + f] = gacc[f] * aT2;
-            acc[f] = alpha * q + oma2 * acc[f];
+            dLda += gacc[k][f] * T2 * (q - two_oma * acc[k][f]);
+            c[6 + f] += gacc[k][f] * aT2;
+            acc[k][f] = alpha * q + oma2 * acc[k][f];
           }
-          T = Tk;
+          T[k] = Tk;
           if (oG < amax) {
-            c[5] = dLda * G;
+            c[5] += dLda * G;
             const Real dLdp = dLda * alpha;  // d alpha / d power = alpha
             const Real e = dLdp * ln2;
-            c[0] = e * (Real(2) * r[2] * dx + r[3] * dy);
-            c[1] = e * (Real(2) * r[4] * dy + r[3] * dx);
+            c[0] += e * (Real(2) * r[2] * dx + r[3] * dy);
+            c[1] += e * (Real(2) * r[4] * dy + r[3] * dx);
             const Real h = Real(-0.5) * dLdp;
-            c[2] = h * dx * dx;
-            c[3] = -dLdp * dx * dy;
-            c[4] = h * dy * dy;
+            c[2] += h * dx * dx;
+            c[3] -= dLdp * dx * dy;
+            c[4] += h * dy * dy;
           }
         }
       }
@@ -401,8 +446,8 @@ __device__ __forceinline__ void render_tile_bwd(
   }
 }
 
-template <typename Real, int F>
-__global__ void __launch_bounds__(512)
+template <typename Real, int F, int PPT>
+__global__ void __launch_bounds__(512 / PPT)
     render_bwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
@@ -424,9 +469,9 @@ __global__ void __launch_bounds__(512)
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
-    render_tile_bwd<Real, F>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
-                             values, rec, bg, dout, tfinal, nlast, g2d,
-                             g2d_stride, dbg, s_rec, s_grad, s_id, s_red);
+    render_tile_bwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                                  values, rec, bg, dout, tfinal, nlast, g2d,
+                                  g2d_stride, dbg, s_rec, s_grad, s_id, s_red);
     return;
   }
   __shared__ uint32_t s_item;
@@ -436,9 +481,9 @@ __global__ void __launch_bounds__(512)
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= items) break;
-    render_tile_bwd<Real, F>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
-                             values, rec, bg, dout, tfinal, nlast, g2d,
-                             g2d_stride, dbg, s_rec, s_grad, s_id, s_red);
+    render_tile_bwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                                  values, rec, bg, dout, tfinal, nlast, g2d,
+                                  g2d_stride, dbg, s_rec, s_grad, s_id, s_red);
   }
 }
 
@@ -463,13 +508,13 @@ int persistent_grid(KernelT kernel, int threads, size_t smem) {
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-template <typename Real, int F>
+template <typename Real, int F, int PPT>
 void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                 cudaStream_t st) {
   constexpr int RS = rec_stride<Real, F>();
-  const int threads = L.TW * L.TH;
+  const int threads = L.TW * L.TH / PPT;
   const size_t smem = (size_t)threads * RS * sizeof(Real);
-  auto kernel = render_fwd_kernel<Real, F>;
+  auto kernel = render_fwd_kernel<Real, F, PPT>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -490,15 +535,15 @@ void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
   count_launches(1);
 }
 
-template <typename Real, int F>
+template <typename Real, int F, int PPT>
 void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
                 unsigned char* ws, cudaStream_t st) {
   constexpr int NF = 2 * F + 1;
   constexpr int RS = rec_stride<Real, F>();
-  const int threads = L.TW * L.TH;
+  const int threads = L.TW * L.TH / PPT;
   const size_t smem = (size_t)threads * (RS + 6 + NF) * sizeof(Real) +
                       32 * sizeof(Real) + (size_t)threads * sizeof(uint32_t);
-  auto kernel = render_bwd_kernel<Real, F>;
+  auto kernel = render_bwd_kernel<Real, F, PPT>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -520,16 +565,36 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
   count_launches(1);
 }
 
+template <typename Real, int F>
+void fwd_dispatch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
+                  cudaStream_t st) {
+  switch (L.ppt) {
+    case 1: fwd_launch<Real, F, 1>(L, bg, out, ws, st); break;
+    case 4: fwd_launch<Real, F, 4>(L, bg, out, ws, st); break;
+    default: fwd_launch<Real, F, 2>(L, bg, out, ws, st); break;
+  }
+}
+
+template <typename Real, int F>
+void bwd_dispatch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
+                  unsigned char* ws, cudaStream_t st) {
+  switch (L.ppt) {
+    case 1: bwd_launch<Real, F, 1>(L, bg, dout, dbg, ws, st); break;
+    case 4: bwd_launch<Real, F, 4>(L, bg, dout, dbg, ws, st); break;
+    default: bwd_launch<Real, F, 2>(L, bg, dout, dbg, ws, st); break;
+  }
+}
+
 }  // namespace
 
 template <typename Real>
 void launch_render_fwd(const Layout& L, const Real* bg, Real* out,
                        unsigned char* ws, cudaStream_t st) {
   switch (L.F) {
-    case 1: fwd_launch<Real, 1>(L, bg, out, ws, st); break;
-    case 2: fwd_launch<Real, 2>(L, bg, out, ws, st); break;
-    case 3: fwd_launch<Real, 3>(L, bg, out, ws, st); break;
-    default: fwd_launch<Real, 4>(L, bg, out, ws, st); break;
+    case 1: fwd_dispatch<Real, 1>(L, bg, out, ws, st); break;
+    case 2: fwd_dispatch<Real, 2>(L, bg, out, ws, st); break;
+    case 3: fwd_dispatch<Real, 3>(L, bg, out, ws, st); break;
+    default: fwd_dispatch<Real, 4>(L, bg, out, ws, st); break;
   }
 }
 
@@ -537,21 +602,11 @@ template <typename Real>
 void launch_render_bwd(const Layout& L, const Real* bg, const Real* dout,
                        Real* dbg, unsigned char* ws, cudaStream_t st) {
   switch (L.F) {
-    case 1: bwd_launch<Real, 1>(L, bg, dout, dbg, ws, st); break;
-    case 2: bwd_launch<Real, 2>(L, bg, dout, dbg, ws, st); break;
-    case 3: bwd_launch<Real, 3>(L, bg, dout, dbg, ws, st); break;
-    default: bwd_launch<Real, 4>(L, bg, dout, dbg, ws, st); break;
+    case 1: bwd_dispatch<Real, 1>(L, bg, dout, dbg, ws, st); break;
+    case 2: bwd_dispatch<Real, 2>(L, bg, dout, dbg, ws, st); break;
+    case 3: bwd_dispatch<Real, 3>(L, bg, dout, dbg, ws, st); break;
+    default: bwd_dispatch<Real, 4>(L, bg, dout, dbg, ws, st); break;
   }
 }
-
-template void launch_render_fwd<float>(const Layout&, const float*, float*,
-                                       unsigned char*, cudaStream_t);
-template void launch_render_fwd<double>(const Layout&, const double*, double*,
-                                        unsigned char*, cudaStream_t);
-template void launch_render_bwd<float>(const Layout&, const float*, const float*,
-                                       float*, unsigned char*, cudaStream_t);
-template void launch_render_bwd<double>(const Layout&, const double*,
-                                        const double*, double*, unsigned char*,
-                                        cudaStream_t);
 
 }  // namespace gftorf

@@ -30,6 +30,7 @@ class Dims(ctypes.Structure):
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("n_freq", ctypes.c_int32), ("n_offsets", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("render_mode", ctypes.c_int32),
+                ("pixels_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("max_instances", ctypes.c_int64)]
 
 
@@ -219,14 +220,14 @@ class Renderer:
 
     def __init__(self, n, frames, width, height, n_freq=1, n_offsets=4,
                  tile=(16, 16), dtype=torch.float32, render_mode=0,
-                 max_instances=None, device="cuda"):
+                 max_instances=None, device="cuda", pixels_per_thread=0):
         _require_cuda()
         self.lib = load()
         self.torch_dtype = dtype
         self.device = torch.device(device)
         self.dims = Dims(n, frames, width, height, tile[0], tile[1], n_freq,
                          n_offsets, F64 if dtype == torch.float64 else F32,
-                         render_mode, 0)
+                         render_mode, pixels_per_thread, 0, 0)
         self.C = n_freq * n_offsets + 1
         self.tiles_x = -(-width // tile[0])
         self.tiles_y = -(-height // tile[1])
@@ -393,7 +394,7 @@ def sort_footprints(u, v, radius, z, width, height, tile=(16, 16), max_instances
     if max_instances is None:
         r = radius.to(torch.int64).clamp(min=0)
         max_instances = int((((2 * r) // tile[0] + 2) * ((2 * r) // tile[1] + 2)).sum().item())
-    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, max(1, max_instances))
+    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, 0, 0, max(1, max_instances))
     nbytes = L.gftorf_workspace_size(ctypes.byref(dims))
     if nbytes == 0:
         raise GftorfError(ERR_ARG, "gftorf_workspace_size")
@@ -425,7 +426,7 @@ def sort_footprints_noalloc(u, v, radius, z, width, height, tile=(16, 16), max_i
     _require_cuda()
     L = load()
     B, n = u.shape
-    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, int(max_instances))
+    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, 0, 0, int(max_instances))
     cap = max(1, int(max_instances))
     keys = torch.empty(cap, dtype=torch.int64, device=u.device)
     vals = torch.empty(cap, dtype=torch.int32, device=u.device)

@@ -38,7 +38,8 @@ def test_version_and_status_strings(lib):
 
 def _dims(**kw):
     d = dict(n_gaussians=1000, n_frames=2, width=64, height=48, tile_w=16, tile_h=16,
-             n_freq=1, n_offsets=4, dtype=0, render_mode=0, max_instances=10000)
+             n_freq=1, n_offsets=4, dtype=0, render_mode=0, pixels_per_thread=0,
+             reserved=0, max_instances=10000)
     d.update(kw)
     return gftorf.Dims(*[d[k] for k, _ in gftorf.Dims._fields_])
 
@@ -53,6 +54,8 @@ def test_workspace_size_validates_dims(lib):
     for bad in (dict(n_frames=0), dict(n_frames=65), dict(width=0), dict(tile_w=12),
                 dict(tile_w=32, tile_h=16), dict(n_freq=0), dict(n_freq=5),
                 dict(n_offsets=9), dict(dtype=2), dict(render_mode=2),
+                dict(pixels_per_thread=3), dict(pixels_per_thread=8),
+                dict(tile_w=8, tile_h=8, pixels_per_thread=4),
                 dict(n_gaussians=-1), dict(max_instances=-1),
                 dict(max_instances=1 << 33)):
         assert lib.gftorf_workspace_size(ctypes.byref(_dims(**bad))) == 0, bad
@@ -102,7 +105,7 @@ def test_host_side_argument_errors(lib):
 
 def test_struct_layouts_match_header():
     # sizes fixed by the header's field lists (C layout, no hidden padding)
-    assert ctypes.sizeof(gftorf.Dims) == 10 * 4 + 8
+    assert ctypes.sizeof(gftorf.Dims) == 12 * 4 + 8
     assert ctypes.sizeof(gftorf.Frame) == 18 * 4
     assert ctypes.sizeof(gftorf.Sensor) == (4 + 8 + 1) * 4
     assert ctypes.sizeof(gftorf.Consts) == 6 * 4

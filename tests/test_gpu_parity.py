@@ -115,12 +115,31 @@ def test_capacity_overflow_is_reported_not_faulted():
     assert np.all(np.isfinite(res["out"]))
 
 
-def test_persistent_mode_bit_identical():
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_persistent_mode_bit_identical(ppt):
     sc = scenes.make_scene("batch_300k", 3, n=5000, width=96, height=64, frames=3)
-    a = run_gpu(sc, render_mode=0)
-    b = run_gpu(sc, render_mode=1)
+    a = run_gpu(sc, render_mode=0, pixels_per_thread=ppt)
+    b = run_gpu(sc, render_mode=1, pixels_per_thread=ppt)
     np.testing.assert_array_equal(a["out"], b["out"])
     np.testing.assert_array_equal(a["nlast"], b["nlast"])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 32)])
+def test_pixels_per_thread_bit_identical(tile):
+    """1, 2 or 4 pixels per compositing thread: same forward bit for bit,
+    same gradients up to atomic summation order."""
+    sc = scenes.make_scene("batch_300k", 8, n=4000, width=72, height=56, frames=2,
+                           tile=tile)
+    dout = scenes.random_dout(sc, 5)
+    ref = run_gpu(sc, dout, pixels_per_thread=1)
+    for ppt in (2, 4):
+        if tile[0] * tile[1] // ppt < 32:
+            continue
+        res = run_gpu(sc, dout, pixels_per_thread=ppt)
+        np.testing.assert_array_equal(res["out"], ref["out"])
+        np.testing.assert_array_equal(res["nlast"], ref["nlast"])
+        for k, (nrm, elem) in grads_close(res["grads"], ref["grads"]).items():
+            assert nrm <= 1e-5, (ppt, k, nrm)
 
 
 def test_batched_equals_per_frame():
