@@ -497,7 +497,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--mode", type=int, default=0, help="0 grid, 1 persistent")
-    ap.add_argument("--ppt", type=int, default=2, help="pixels per compositing thread")
+    ap.add_argument("--ppt", type=int, default=4, help="pixels per compositing thread")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")

@@ -56,7 +56,7 @@ Layout make_layout(const gftorf_dims* d) {
   L.tiles_y = (L.H + L.TH - 1) / L.TH;
   L.NT = L.tiles_x * L.tiles_y;
   const int per16 = 16 / L.real_size;
-  L.rec_stride = (6 + L.NF + per16 - 1) / per16 * per16;
+  L.rec_stride = (7 + L.NF + per16 - 1) / per16 * per16;
   L.g2d_stride = 6 + L.NF;
   L.n_dblk = (L.N + kSortTile - 1) / kSortTile;
   L.n_chunk = (int)((d->max_instances + kChunk - 1) / kChunk) + L.B;

@@ -360,21 +360,37 @@ __global__ void __launch_bounds__(256)
   for (int t = threadIdx.x; t < NT; t += blockDim.x) out[t] = hist[t];
 }
 
-// per (frame, tile): exclusive prefix over the frame's chunks; tile totals
-__global__ void tile_colscan_kernel(uint32_t* __restrict__ tcnt,
-                                    uint32_t* __restrict__ ttot,
-                                    const Header* __restrict__ hdr, int NT) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// per (frame, tile): exclusive prefix over the frame's chunks; tile totals.
+// A CTA covers 32 tiles (lanes, coalesced rows) and splits the frame's chunks
+// into 8 consecutive segments (warps): segment sums, then per-segment rescan.
+__global__ void __launch_bounds__(256)
+    tile_colscan_kernel(uint32_t* __restrict__ tcnt, uint32_t* __restrict__ ttot,
+                        const Header* __restrict__ hdr, int NT) {
+  __shared__ uint32_t s_seg[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
   const int b = blockIdx.y;
-  if (t >= NT) return;
-  uint32_t run = 0;
-  const uint32_t c0 = hdr->coff[b], c1 = hdr->coff[b + 1];
-  for (uint32_t c = c0; c < c1; ++c) {
-    const uint32_t v = tcnt[(size_t)c * NT + t];
-    tcnt[(size_t)c * NT + t] = run;
-    run += v;
+  const uint32_t c0 = hdr->coff[b], n = hdr->coff[b + 1] - c0;
+  const uint32_t seg = (n + 7) / 8;
+  const uint32_t s0 = c0 + min(n, (uint32_t)w * seg), s1 = c0 + min(n, (uint32_t)(w + 1) * seg);
+  uint32_t sum = 0;
+  if (t < NT) {
+#pragma unroll 4
+    for (uint32_t c = s0; c < s1; ++c) sum += tcnt[(size_t)c * NT + t];
   }
-  ttot[(size_t)b * NT + t] = run;
+  s_seg[w][lane] = sum;
+  __syncthreads();
+  uint32_t run = 0;
+  for (int ww = 0; ww < w; ++ww) run += s_seg[ww][lane];
+  if (t < NT) {
+#pragma unroll 4
+    for (uint32_t c = s0; c < s1; ++c) {
+      const uint32_t v = tcnt[(size_t)c * NT + t];
+      tcnt[(size_t)c * NT + t] = run;
+      run += v;
+    }
+    if (w == 7) ttot[(size_t)b * NT + t] = run;
+  }
 }
 
 // exclusive scan of the tile totals over (frame, tile); ranges; capacity
@@ -570,7 +586,7 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   // 3. per-chunk tile counts, per-frame column scan, tile ranges
   tile_count_kernel<<<L.n_chunk, 256, (size_t)L.NT * 4, st>>>(sorted, rect, hdr, ecnt, tcnt,
                                                               L.N, L.NT, L.tiles_x, L.B);
-  tile_colscan_kernel<<<dim3((L.NT + 255) / 256, L.B), 256, 0, st>>>(tcnt, ttot, hdr, L.NT);
+  tile_colscan_kernel<<<dim3((L.NT + 31) / 32, L.B), 256, 0, st>>>(tcnt, ttot, hdr, L.NT);
   tile_scan_kernel<<<1, 1024, 0, st>>>(ttot, ranges, hdr, (int64_t)L.B * L.NT, L.cap);
   // 4. stable scatter
   const int nw = L.scatter_warps;

@@ -15,7 +15,8 @@
 //   A = s r / d^2; features A sin psi_f, A cos psi_f (psi_f = 4 pi d f / c),
 //   and A for the ambient channel.
 // The record keeps the conic scaled by -log2(e)/2 (and -log2(e) for the
-// cross term) so that compositing evaluates exp() as one ex2.
+// cross term) and log2 of the opacity, so that compositing evaluates
+// o exp(power) as one ex2; 1/o follows the features.
 #include "gftorf_internal.cuh"
 
 namespace gftorf {
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256)
         o[2] = Real(-0.5 * kLog2e) * ca;
         o[3] = Real(-kLog2e) * cb;
         o[4] = Real(-0.5 * kLog2e) * cc;
-        o[5] = P.o;
+        o[5] = log2(P.o);  // alpha = 2^(power2 + log2 o)
         const Real A = (Real)tab->source * P.amp / (Q.d * Q.d);
 #pragma unroll
         for (int f = 0; f < F; ++f) {
@@ -212,8 +213,9 @@ __global__ void __launch_bounds__(256)
           o[7 + 2 * f] = A * c;
         }
         o[6 + 2 * F] = A;
+        o[6 + NF] = Real(1) / P.o;  // recovers G = alpha / o in the backward
 #pragma unroll
-        for (int k = 6 + NF; k < 6 + NF + 3; ++k)
+        for (int k = 7 + NF; k < 7 + NF + 3; ++k)
           if (k < rec_stride) o[k] = Real(0);
       }
     }

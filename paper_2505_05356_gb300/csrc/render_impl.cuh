@@ -5,7 +5,7 @@
 // (frame, tile) or persistent CTAs pulling (frame, tile) items from a queue.
 //
 // Forward, per pixel, front to back over the tile's depth-ordered list:
-//   alpha = min(alpha_max, o 2^(power2)), power2 = log2(e) * power
+//   alpha = min(alpha_max, 2^(power2 + log2 o)), power2 = log2(e) * power
 //   skip if power2 > 0 or alpha < alpha_min
 //   stop (without compositing) if T (1 - alpha) < t_min
 //   w = alpha T^2;  acc_f += w feature_f  (A sin psi_f, A cos psi_f, A)
@@ -30,15 +30,15 @@ namespace {
 
 constexpr double kLn2 = 0.69314718055994530942;
 
-template <typename Real>
-struct RecStride;  // Reals per record: 6 + 2F + 1, padded to 16 bytes
+// Reals per record: u, v, scaled conic (3), log2 o, 2F+1 features, 1/o,
+// padded to 16 bytes
 template <int F>
 struct RecStrideF {
-  static constexpr int value = ((6 + 2 * F + 1) + 3) / 4 * 4;
+  static constexpr int value = ((7 + 2 * F + 1) + 3) / 4 * 4;
 };
 template <int F>
 struct RecStrideD {
-  static constexpr int value = ((6 + 2 * F + 1) + 1) / 2 * 2;
+  static constexpr int value = ((7 + 2 * F + 1) + 1) / 2 * 2;
 };
 template <typename Real, int F>
 constexpr int rec_stride() {
@@ -131,12 +131,27 @@ struct RenderGeom {
 // forward: thread (lx, row group) owns PPT vertically adjacent pixels
 // ---------------------------------------------------------------------------
 
-// exponent (log2 domain) of one Gaussian at a pixel offset (dx, dy), with
-// ca_dx = ca * dx shared by the pixels of a column; one rounding per operation
-// so the backward replays the forward's decisions bit for bit
+// log2 of o G for one Gaussian at pixel offset (dx, dy), evaluated as a
+// quadratic in dy whose coefficients depend only on the column:
+//   cc' dy^2 + (cb' dx) dy + (ca' dx^2 + log2 o),
+// cb_dx and a_lo computed once per column and shared by its PPT pixels.  One
+// rounding per operation, so the backward replays the forward's decisions
+// bit for bit.  power2 > log2 o is the "power > 0" skip of the method.
 template <typename Real>
-__device__ __forceinline__ Real power2(const Real* r, Real dx, Real ca_dx, Real dy) {
-  return fma_rn(dx, fma_rn(r[3], dy, ca_dx), mul_rn(mul_rn(r[4], dy), dy));
+struct Column {
+  Real dx, cb_dx, a_lo;
+};
+template <typename Real>
+__device__ __forceinline__ Column<Real> column_of(const Real* r, Real fpx) {
+  Column<Real> c;
+  c.dx = sub_rn(r[0], fpx);
+  c.cb_dx = mul_rn(r[3], c.dx);
+  c.a_lo = fma_rn(mul_rn(r[2], c.dx), c.dx, r[5]);
+  return c;
+}
+template <typename Real>
+__device__ __forceinline__ Real log2_oG(const Real* r, const Column<Real>& c, Real dy) {
+  return fma_rn(fma_rn(r[4], dy, c.cb_dx), dy, c.a_lo);
 }
 
 template <typename Real, int F, int PPT>
@@ -190,15 +205,14 @@ __device__ __forceinline__ void render_tile_fwd(
     const int cnt = min((uint32_t)nthr, range.y - base);
     for (int j = 0; j < cnt && done != ALL; ++j) {
       const Real* r = s_rec + j * RS;
-      const Real dx = sub_rn(r[0], fpx);
-      const Real ca_dx = mul_rn(r[2], dx);
+      const Column<Real> col = column_of(r, fpx);
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (done & (1u << k)) continue;
-        const Real pw = power2(r, dx, ca_dx, sub_rn(r[1], fpy[k]));
-        const Real oG = mul_rn(r[5], ex2_approx(pw));
+        const Real lg = log2_oG(r, col, sub_rn(r[1], fpy[k]));
+        const Real oG = ex2_approx(lg);
         const Real alpha = oG < amax ? oG : amax;
-        if (pw > Real(0) || alpha < amin) continue;
+        if (lg > r[5] || alpha < amin) continue;
         const Real tn = T[k] * (Real(1) - alpha);
         if (tn < tmin) {
           done |= 1u << k;
@@ -390,17 +404,18 @@ __device__ __forceinline__ void render_tile_bwd(
       for (int q = 0; q < GS; ++q) c[q] = 0;
       bool has = false;
       if (j < thread_hi) {
-        const Real dx = sub_rn(r[0], fpx);
-        const Real ca_dx = mul_rn(r[2], dx);
+        const Column<Real> col = column_of(r, fpx);
+        const Real dx = col.dx;
+        const Real two_ca_dx = Real(2) * r[2] * dx;
+        const Real two_cc = Real(2) * r[4];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (j >= my_hi[k]) continue;
           const Real dy = sub_rn(r[1], fpy[k]);
-          const Real pw = power2(r, dx, ca_dx, dy);
-          const Real G = ex2_approx(pw);
-          const Real oG = mul_rn(r[5], G);
+          const Real lg = log2_oG(r, col, dy);
+          const Real oG = ex2_approx(lg);
           const Real alpha = oG < amax ? oG : amax;
-          if (pw > Real(0) || alpha < amin) continue;
+          if (lg > r[5] || alpha < amin) continue;
           has = true;
           const Real oma = Real(1) - alpha;
           const Real rcp = div_fast(Real(1), oma);
@@ -417,11 +432,11 @@ __device__ __forceinline__ void render_tile_bwd(
           }
           T[k] = Tk;
           if (oG < amax) {
-            c[5] += dLda * G;
+            c[5] += dLda * oG * r[6 + NF];  // d alpha / d o = G = alpha / o
             const Real dLdp = dLda * alpha;  // d alpha / d power = alpha
             const Real e = dLdp * ln2;
-            c[0] += e * (Real(2) * r[2] * dx + r[3] * dy);
-            c[1] += e * (Real(2) * r[4] * dy + r[3] * dx);
+            c[0] += e * (two_ca_dx + r[3] * dy);
+            c[1] += e * (two_cc * dy + col.cb_dx);
             const Real h = Real(-0.5) * dLdp;
             c[2] += h * dx * dx;
             c[3] -= dLdp * dx * dy;
