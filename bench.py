@@ -119,6 +119,18 @@ def _overrides(args):
     return o
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); identity on one process."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -142,16 +154,22 @@ def run_ours(args):
 
     sc = scenes.make_scene(args.workload, seed=rank, **_overrides(args))
     B, N, W, H = sc.frames, sc.n, sc.width, sc.height
-    tile = tuple(int(v) for v in args.tile.split("x"))
-    sc.consts.tile_w, sc.consts.tile_h = tile
-    r = gftorf.Renderer(N, B, W, H, len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad),
-                        tile=tile, render_mode=args.mode, pixels_per_thread=args.ppt)
+    nF, nP = len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad)
     p = gftorf.params_from_scene(sc)
     fr = gftorf.frames_from_scene(sc)
     se = gftorf.sensor_from_scene(sc)
     co = gftorf.consts_from_scene(sc)
     bg = torch.as_tensor(sc.bg, device="cuda")
     dout = torch.as_tensor(scenes.random_dout(sc, 100 + rank), device="cuda")
+    tile = tuple(int(v) for v in args.tile.split("x"))
+    ppt, mode = args.ppt, args.mode
+    tuned = None
+    if args.autotune:
+        from paper_2505_05356_gb300 import autotune
+        tuned = autotune.autotune(N, B, W, H, nF, nP, p, fr, se, co, bg, dout, steps=2)
+        tile, ppt, mode = tuned["tile"], tuned["ppt"], tuned["mode"]
+    r = gftorf.Renderer(N, B, W, H, nF, nP, tile=tile, render_mode=mode,
+                        pixels_per_thread=ppt)
     r.fit_capacity(p, fr, se, co, bg)
     out = torch.empty((B, sc.sensor.n_channels, H, W), device="cuda")
     grads = r.alloc_grads(p, bg)
@@ -209,10 +227,7 @@ def run_ours(args):
     code, count = r.read_status()
     if code != gftorf.OK:
         raise RuntimeError("device status %s" % gftorf.STATUS.get(code))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, "cuda")
     ms_per_step = ms / args.steps
     value = world * B * args.steps / (ms / 1e3)
 
@@ -302,19 +317,15 @@ def run_ours(args):
             e2e_step()
         a1.record()
         torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(a0.elapsed_time(a1), world, "cuda")
         e2e = {"value": round(world * B * args.steps / (ems / 1e3), 2), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # --- per-frame plain launches (no batching, no graph), same work ---
     plain = None
     if not args.skip_plain and rank == 0:
-        r1 = gftorf.Renderer(N, 1, W, H, len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad),
-                             tile=tile, render_mode=0,
+        r1 = gftorf.Renderer(N, 1, W, H, nF, nP, tile=tile, render_mode=0,
+                             pixels_per_thread=ppt,
                              max_instances=max(1024, int(r.capacity / B * 1.6)))
         gacc = {k: torch.zeros_like(v) for k, v in grads.items() if k not in ("bg", "delta")}
         p1s = []
@@ -364,9 +375,10 @@ def run_ours(args):
             "config": {"workload": "%s: %d dynamic Gaussians (cubic trajectories), %dx%d, "
                                    "%d timesteps per batch, 30 MHz x 4 offsets + ambient, "
                                    "30-100%% visible per frame" % (args.workload, N, W, H, B),
-                       "frames_per_step": B, "tile": args.tile,
-                       "pixels_per_thread": args.ppt,
-                       "render_mode": "persistent" if args.mode == 1 else "grid",
+                       "frames_per_step": B, "tile": "%dx%d" % tuple(tile),
+                       "pixels_per_thread": ppt,
+                       "render_mode": "persistent" if mode == 1 else "grid",
+                       "autotuned": tuned is not None,
                        "cuda_graph": use_graph, "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (%.0f MB workspace per step)" % (r.ws_bytes / 1e6),
                        "instances_per_step": instances, "pairs_per_step": pairs},
@@ -378,6 +390,7 @@ def run_ours(args):
             "per_frame_plain": plain,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "autotune": None if tuned is None else tuned["table"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -499,6 +512,8 @@ def main():
     ap.add_argument("--mode", type=int, default=0, help="0 grid, 1 persistent")
     ap.add_argument("--ppt", type=int, default=4, help="pixels per compositing thread")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use --tile/--ppt/--mode instead of timing every configuration")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

@@ -1,0 +1,68 @@
+"""Parity at the benchmark's full size (300k dynamic Gaussians, 640x480, 16
+timesteps) in the launch configurations bench.py times, on sampled pixels the
+oracle computes one by one, and gradients of a loss that only sees those
+pixels (exactly computable by the oracle)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as ora
+from paper_2505_05356_gb300 import gftorf, scenes
+from tests.gpu_helpers import grads_close
+
+pytestmark = pytest.mark.gpu
+
+K_PIX = 24  # sampled pixels per frame
+
+
+def _gpu(sc, tile, ppt, mode, dout=None):
+    r = gftorf.Renderer(sc.n, sc.frames, sc.width, sc.height, 1, 4, tile=tile,
+                        render_mode=mode, pixels_per_thread=ppt)
+    p = gftorf.params_from_scene(sc)
+    fr, se, co = (gftorf.frames_from_scene(sc), gftorf.sensor_from_scene(sc),
+                  gftorf.consts_from_scene(sc))
+    bg = torch.as_tensor(sc.bg, device="cuda")
+    r.fit_capacity(p, fr, se, co, bg)
+    r.preprocess(p, fr, se, co)
+    out = r.render_fwd(bg)
+    g = None
+    if dout is not None:
+        g = r.render_bwd(p, bg, torch.as_tensor(dout, device="cuda"))
+        g = {k: v.double().cpu().numpy() for k, v in g.items()}
+    code, cnt = r.read_status()
+    assert code == gftorf.OK
+    return out.double().cpu().numpy(), g, cnt
+
+
+@pytest.mark.parametrize("tile,ppt,mode", [((16, 16), 4, 0), ((8, 8), 2, 1), ((16, 32), 4, 0)])
+def test_full_size_sampled_pixels(tile, ppt, mode):
+    sc = scenes.make_scene("batch_300k", 0, tile=tile)
+    assert (sc.n, sc.frames, sc.width, sc.height) == (300_000, 16, 640, 480)
+    pix = scenes.sample_pixels(sc, K_PIX, seed=9)
+    full_grad = tile == (16, 16)
+    dout = np.zeros((sc.frames, 5, sc.height, sc.width), np.float32)
+    rng = np.random.default_rng(10)
+    refs = []
+    for b in range(sc.frames):
+        q, tf, amb, nc = ora.render_pixels(sc, b, pix[b], eps=ora.EPS_F32,
+                                           splats=ora.project(sc, b, ora.EPS_F32))
+        refs.append((q, amb))
+        keep = amb == 0
+        dout[b, :, pix[b, keep, 1], pix[b, keep, 0]] = rng.standard_normal((keep.sum(), 5))
+    out, g, cnt = _gpu(sc, tile, ppt, mode, dout if full_grad else None)
+    assert cnt > 50_000_000  # ~88M instances at 16x16
+    nflag, worst = 0, 0.0
+    for b in range(sc.frames):
+        q, amb = refs[b]
+        got = out[b][:, pix[b, :, 1], pix[b, :, 0]].T  # (K, C)
+        keep = (amb & ora.AMB_VALUE) == 0
+        nflag += int((~keep).sum())
+        scale = np.maximum(np.abs(q), np.sqrt((q ** 2).mean(axis=0, keepdims=True)) + 1e-30)
+        err = np.abs(got - q) / scale
+        worst = max(worst, float(err[keep].max()))
+    assert worst <= 1e-5, worst
+    assert nflag <= 0.1 * sc.frames * K_PIX, nflag
+    if full_grad:
+        g_ora = ora.backward(sc, dout.astype(np.float64))
+        for k, (nrm, elem) in grads_close(g, g_ora).items():
+            assert nrm <= 1e-3 and elem <= 1e-3, (k, nrm, elem)
