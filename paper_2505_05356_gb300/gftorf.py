@@ -258,9 +258,12 @@ class Renderer:
                 setattr(g, k, _ptr(t))
         return g
 
+    generation = 0  # bumped by every preprocess: identifies the workspace's batch
+
     def preprocess(self, params, frames: Sequence[Frame], sensor: Sensor, consts: Consts):
         arr = (Frame * len(frames))(*frames)
         self._keep = (params, arr)
+        self.generation += 1
         _check(self.lib.gftorf_preprocess(ctypes.byref(self.dims),
                                           ctypes.byref(self._gaussians(params)), arr,
                                           ctypes.byref(sensor), ctypes.byref(consts),
@@ -459,6 +462,8 @@ class RenderCToF(torch.autograd.Function):
         out = renderer.render_fwd(bg.contiguous())
         ctx.renderer = renderer
         ctx.params = params
+        ctx.setup = (frames, sensor, consts)
+        ctx.generation = renderer.generation
         ctx.save_for_backward(bg)
         return out
 
@@ -466,6 +471,10 @@ class RenderCToF(torch.autograd.Function):
     def backward(ctx, dout):
         (bg,) = ctx.saved_tensors
         r, p = ctx.renderer, ctx.params
+        if r.generation != ctx.generation:
+            # the workspace now holds another batch: recompute this one
+            r.preprocess(p, *ctx.setup)
+            r.render_fwd(bg.contiguous())
         want = ["means", "scales", "quats", "opacity", "amplitude", "bg"]
         if p["coeffs"] is not None:
             want.append("coeffs")
