@@ -361,12 +361,14 @@ __device__ __forceinline__ void render_tile_bwd(
   for (int w = 0; w < nwarps; ++w) maxn = max(maxn, reinterpret_cast<int*>(s_red)[w]);
   __syncthreads();
 
-  Real T[PPT], acc[PPT][NF];
+  // Per pixel only the projection of the Eq. S3 accumulators on the pixel's
+  // (fixed) accumulator gradient is needed: A = sum_f g_f acc_f obeys the same
+  // recursion, A <- alpha (g . q) + (1 - alpha)^2 A.
+  Real T[PPT], A[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     T[k] = Tf[k];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) acc[k][f] = 0;
+    A[k] = 0;
   }
   const int slot = butterfly_slot<GS>(lane);
   const Real ln2 = Real(kLn2);
@@ -405,9 +407,9 @@ __device__ __forceinline__ void render_tile_bwd(
       bool has = false;
       if (j < thread_hi) {
         const Column<Real> col = column_of(r, fpx);
-        const Real dx = col.dx;
-        const Real two_ca_dx = Real(2) * r[2] * dx;
-        const Real two_cc = Real(2) * r[4];
+        // moments over this thread's pixels (same column) of dL/dpower:
+        // S0 = sum d, S1 = sum d dy, S2 = sum d dy^2; S5 = sum dL/dalpha o G
+        Real S0 = 0, S1 = 0, S2 = 0, S5 = 0;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (j >= my_hi[k]) continue;
@@ -421,27 +423,32 @@ __device__ __forceinline__ void render_tile_bwd(
           const Real rcp = div_fast(Real(1), oma);
           const Real Tk = T[k] * rcp;
           const Real T2 = Tk * Tk;
-          const Real two_oma = oma + oma, oma2 = oma * oma, aT2 = alpha * T2;
-          Real dLda = -gTf[k] * rcp;
+          Real gq = 0;
 #pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            const Real q = r[6 + f];
-            dLda += gacc[k][f] * T2 * (q - two_oma * acc[k][f]);
-            c[6 + f] += gacc[k][f] * aT2;
-            acc[k][f] = alpha * q + oma2 * acc[k][f];
-          }
+          for (int f = 0; f < NF; ++f) gq += gacc[k][f] * r[6 + f];
+          const Real dLda = T2 * (gq - (oma + oma) * A[k]) - gTf[k] * rcp;
+          A[k] = alpha * gq + oma * oma * A[k];
+          const Real aT2 = alpha * T2;
+#pragma unroll
+          for (int f = 0; f < NF; ++f) c[6 + f] += gacc[k][f] * aT2;
           T[k] = Tk;
-          if (oG < amax) {
-            c[5] += dLda * oG * r[6 + NF];  // d alpha / d o = G = alpha / o
-            const Real dLdp = dLda * alpha;  // d alpha / d power = alpha
-            const Real e = dLdp * ln2;
-            c[0] += e * (two_ca_dx + r[3] * dy);
-            c[1] += e * (two_cc * dy + col.cb_dx);
-            const Real h = Real(-0.5) * dLdp;
-            c[2] += h * dx * dx;
-            c[3] -= dLdp * dx * dy;
-            c[4] += h * dy * dy;
+          if (oG < amax) {  // alpha = o G is not clamped: it depends on o, u, v, conic
+            S5 += dLda * oG;
+            const Real d = dLda * alpha;  // d alpha / d power = alpha
+            const Real t = d * dy;
+            S0 += d;
+            S1 += t;
+            S2 += t * dy;
           }
+        }
+        if (has) {
+          const Real dx = col.dx;
+          c[5] = S5 * r[6 + NF];  // d alpha / d o = G = alpha / o
+          c[0] = ln2 * (Real(2) * r[2] * dx * S0 + r[3] * S1);
+          c[1] = ln2 * (Real(2) * r[4] * S1 + col.cb_dx * S0);
+          c[2] = Real(-0.5) * dx * dx * S0;
+          c[3] = -dx * S1;
+          c[4] = Real(-0.5) * S2;
         }
       }
       if (__any_sync(0xffffffffu, has)) {
