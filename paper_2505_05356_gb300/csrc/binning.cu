@@ -123,15 +123,19 @@ __global__ void __launch_bounds__(kSortThreads)
   __shared__ uint32_t h[256];
   const int blk = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
   h[tid] = 0;
-  __syncthreads();
   const uint32_t* k = kin + (size_t)b * N;
-#pragma unroll 4
-  for (int it = 0; it < kSortItems; ++it) {
+  uint32_t d[kSortItems];
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {  // all loads in flight first
     const int pos = blk * kSortTile + it * kSortThreads + tid;
-    const bool valid = pos < N;
-    const uint32_t d = valid ? (k[pos] >> shift) & 255u : 256u + (tid & 31);
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (valid && __popc(peers & lanemask_lt()) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    d[it] = pos < N ? (k[pos] >> shift) & 255u : 256u + (tid & 31);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, d[it]);
+    if (d[it] < 256u && __popc(peers & lanemask_lt()) == 0)
+      atomicAdd(&h[d[it]], (uint32_t)__popc(peers));
   }
   __syncthreads();
   dh[((size_t)b * 256 + tid) * n_dblk + blk] = h[tid];
@@ -158,11 +162,17 @@ __global__ void __launch_bounds__(kSortThreads)
   const int start = blk * kSortTile + w * (kSortTile / kSortWarps);
   uint32_t key[kSortItems], id[kSortItems], loc[kSortItems];
 #pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {  // all loads in flight first
+    const int pos = start + it * 32 + lane;
+    const bool valid = pos < N;
+    key[it] = valid ? kin[fb + pos] : 0u;
+    id[it] = valid ? (iin ? iin[fb + pos] : (uint32_t)pos) : 0u;
+  }
+#pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
     const int pos = start + it * 32 + lane;
     const bool valid = pos < N;
-    const uint32_t k = valid ? kin[fb + pos] : 0u;
-    const uint32_t ident = valid ? (iin ? iin[fb + pos] : (uint32_t)pos) : 0u;
+    const uint32_t k = key[it];
     const uint32_t d = valid ? (k >> shift) & 255u : 256u + lane;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t rank = __popc(peers & lanemask_lt());
@@ -170,8 +180,6 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncwarp();
     if (valid && rank == 0) wc[w][d] = before + __popc(peers);
     __syncwarp();
-    key[it] = k;
-    id[it] = ident;
     loc[it] = before + rank;
   }
   __syncthreads();

@@ -15,10 +15,10 @@ constexpr int kMaxP = GFTORF_MAX_OFFSETS;
 constexpr int kMaxFrames = GFTORF_MAX_FRAMES;
 constexpr uint32_t kCulledKey = 0xFFFFFFFFu;
 
-// Depth sort geometry: 256 threads, 16 keys each, one tile of 4096 keys.
+// Depth sort geometry: 256 threads, 8 keys each, one tile of 2048 keys.
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 // Tile binning: a chunk of kChunk consecutive instances (in emission order:
 // frame, depth rank, tile of the rectangle) per CTA.

@@ -25,6 +25,10 @@
 
 #include "gftorf_internal.cuh"
 
+#ifndef GFTORF_PPT4_MIN_BLOCKS
+#define GFTORF_PPT4_MIN_BLOCKS 8
+#endif
+
 namespace gftorf {
 namespace {
 
@@ -154,6 +158,13 @@ __device__ __forceinline__ Real log2_oG(const Real* r, const Column<Real>& c, Re
   return fma_rn(fma_rn(r[4], dy, c.cb_dx), dy, c.a_lo);
 }
 
+// resident CTAs per SM the compiler is asked to fit (register budget); only
+// the 4-pixel variant (128 threads per 16x32 tile) is limited by registers
+template <int PPT>
+struct kMinBlocks {
+  static constexpr int value = PPT == 4 ? GFTORF_PPT4_MIN_BLOCKS : 0;
+};
+
 template <typename Real, int F, int PPT>
 __device__ __forceinline__ void render_tile_fwd(
     const TileCtx& tc, const RenderGeom& rg, const Table* __restrict__ tab,
@@ -245,7 +256,7 @@ __device__ __forceinline__ void render_tile_fwd(
 }
 
 template <typename Real, int F, int PPT>
-__global__ void __launch_bounds__(512 / PPT)
+__global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
     render_fwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
@@ -469,7 +480,7 @@ __device__ __forceinline__ void render_tile_bwd(
 }
 
 template <typename Real, int F, int PPT>
-__global__ void __launch_bounds__(512 / PPT)
+__global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
     render_bwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
