@@ -68,6 +68,15 @@ typedef enum {
 
 typedef enum { GFTORF_F32 = 0, GFTORF_F64 = 1 } gftorf_dtype;
 
+/* gftorf_dims.flags.  By default the pipeline drops (Gaussian, tile) pairs
+ * where alpha = o G cannot reach alpha_min at any pixel centre of the tile:
+ * preprocess shrinks each tile rectangle to the bounding box of that
+ * ellipse, and the compositing kernels skip the remaining non-intersecting
+ * records while staging them.  Those pairs are skipped by every pixel anyway,
+ * so outputs are the same; this flag turns the culling off (lists then hold
+ * every tile of the 3-sigma rectangle, as gftorf_sort_footprints does). */
+#define GFTORF_FLAG_NO_TILE_CULL 1
+
 /* Static problem shape.  One workspace serves one dims value. */
 typedef struct {
   int32_t n_gaussians;   /* N >= 0                                          */
@@ -82,7 +91,7 @@ typedef struct {
   int32_t pixels_per_thread; /* compositing pixels per thread: 1, 2 or 4
                             (0: 2); tile_w * tile_h / it must be >= 32.
                             Results do not depend on it.                    */
-  int32_t reserved;      /* must be 0                                       */
+  int32_t flags;         /* GFTORF_FLAG_* bits, 0 for the defaults         */
   int64_t max_instances; /* capacity of the (Gaussian, tile) instance list,
                             summed over the batch                           */
 } gftorf_dims;

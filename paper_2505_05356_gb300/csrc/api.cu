@@ -36,6 +36,7 @@ bool dims_ok(const gftorf_dims* d) {
   const int ppt = d->pixels_per_thread;
   if (ppt != 0 && ppt != 1 && ppt != 2 && ppt != 4) return false;
   if (d->tile_w * d->tile_h / (ppt ? ppt : 2) < 32) return false;  // a full warp per tile
+  if (d->flags & ~GFTORF_FLAG_NO_TILE_CULL) return false;
   if (d->max_instances < 0 || d->max_instances > (int64_t)0xFFFFFFFFll) return false;
   const int64_t tiles = (int64_t)((d->width + d->tile_w - 1) / d->tile_w) *
                         ((d->height + d->tile_h - 1) / d->tile_h);
@@ -52,6 +53,7 @@ Layout make_layout(const gftorf_dims* d) {
   L.real_size = d->dtype == GFTORF_F64 ? 8 : 4;
   L.mode = d->render_mode;
   L.ppt = d->pixels_per_thread ? d->pixels_per_thread : 2;
+  L.cull = (d->flags & GFTORF_FLAG_NO_TILE_CULL) ? 0 : 1;
   L.tiles_x = (L.W + L.TW - 1) / L.TW;
   L.tiles_y = (L.H + L.TH - 1) / L.TH;
   L.NT = L.tiles_x * L.tiles_y;

@@ -59,7 +59,8 @@ struct Header {
 // Host-computed byte layout of the workspace for one gftorf_dims.
 struct Layout {
   int B, N, W, H, TW, TH, F, P, C, NF, dtype, real_size, mode;
-  int ppt;  // pixels per compositing thread (1, 2 or 4)
+  int ppt;   // pixels per compositing thread (1, 2 or 4)
+  int cull;  // drop (Gaussian, tile) pairs that cannot reach alpha_min
   int tiles_x, tiles_y, NT;
   int rec_stride;  // Reals per projected record (16-byte multiple)
   int g2d_stride;  // Reals per 2D-gradient row
@@ -137,6 +138,19 @@ __device__ __forceinline__ void tile_rect(float u, float v, int r, int tw,
   x1 = clamp_tile(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(u, rf), twf)), 1.0f), tiles_x);
   y0 = clamp_tile(floorf(__fdiv_rn(__fsub_rn(v, rf), thf)), tiles_y);
   y1 = clamp_tile(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(v, rf), thf)), 1.0f), tiles_y);
+}
+
+// Same rectangle for separate half-widths in x and y (float), used for the
+// alpha-ellipse bounding box; it lies inside tile_rect's for rx, ry <= r.
+__device__ __forceinline__ void tile_rect_xy(float u, float v, float rx, float ry,
+                                             int tw, int th, int tiles_x,
+                                             int tiles_y, int& x0, int& y0,
+                                             int& x1, int& y1) {
+  const float twf = (float)tw, thf = (float)th;
+  x0 = clamp_tile(floorf(__fdiv_rn(__fsub_rn(u, rx), twf)), tiles_x);
+  x1 = clamp_tile(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(u, rx), twf)), 1.0f), tiles_x);
+  y0 = clamp_tile(floorf(__fdiv_rn(__fsub_rn(v, ry), thf)), tiles_y);
+  y1 = clamp_tile(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(v, ry), thf)), 1.0f), tiles_y);
 }
 
 // packed rectangle: 4 x uint16 (x0, y0, x1, y1) in one uint2

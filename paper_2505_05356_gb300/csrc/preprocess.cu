@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256)
                       Header* __restrict__ hdr, Real* __restrict__ rec,
                       uint2* __restrict__ rect, uint32_t* __restrict__ zkey,
                       int N, int TW, int TH, int tiles_x, int tiles_y,
-                      int rec_stride) {
+                      int rec_stride, int cull) {
   constexpr int NF = 2 * F + 1;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
@@ -193,6 +193,21 @@ __global__ void __launch_bounds__(256)
       const Real v = (Real)fr.fy * Q.p[1] * Q.iz + (Real)fr.cy;
       int x0, y0, x1, y1;
       tile_rect((float)u, (float)v, r, TW, TH, tiles_x, tiles_y, x0, y0, x1, y1);
+      if (cull) {
+        // alpha = o G >= alpha_min only inside the ellipse
+        // delta^T cov^-1 delta <= kappa = 2 ln(o / alpha_min); its bounding box
+        // (plus slack for rounding) bounds every tile a pixel of which can
+        // composite this Gaussian
+        const Real kappa = Real(2) * log(P.o / (Real)tab->alpha_min);
+        if (!(kappa >= Real(0))) {
+          x1 = x0;  // never reaches alpha_min
+        } else {
+          const float ex = (float)(sqrt(kappa * Q.cov[0]) * Real(1.001) + Real(0.5));
+          const float ey = (float)(sqrt(kappa * Q.cov[2]) * Real(1.001) + Real(0.5));
+          tile_rect_xy((float)u, (float)v, fminf((float)r, ex), fminf((float)r, ey), TW, TH,
+                       tiles_x, tiles_y, x0, y0, x1, y1);
+        }
+      }
       if (x0 < x1 && y0 < y1) {
         visible = true;
         rr = pack_rect(x0, y0, x1, y1);
@@ -439,7 +454,7 @@ void launch_preprocess(const Layout& L, const gftorf_gaussians& g,
 #define GFTORF_PRE(FF)                                                         \
   preprocess_kernel<Real, FF><<<grid, 256, 0, st>>>(                           \
       g, tab, hdr, rec, rect, zkey, L.N, L.TW, L.TH, L.tiles_x, L.tiles_y,     \
-      L.rec_stride)
+      L.rec_stride, L.cull)
   switch (L.F) {
     case 1: GFTORF_PRE(1); break;
     case 2: GFTORF_PRE(2); break;

@@ -26,7 +26,7 @@
 #include "gftorf_internal.cuh"
 
 #ifndef GFTORF_PPT4_MIN_BLOCKS
-#define GFTORF_PPT4_MIN_BLOCKS 8
+#define GFTORF_PPT4_MIN_BLOCKS 0
 #endif
 
 namespace gftorf {
@@ -128,8 +128,71 @@ __device__ __forceinline__ TileCtx tile_of(uint32_t item, int NT, int tiles_x) {
 }
 
 struct RenderGeom {
-  int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B;
+  int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B, cull;
 };
+
+// Can the Gaussian of record r reach alpha_min at some pixel centre of the
+// tile whose centres span [cx0, cx1] x [cy0, cy1]?  With A, B, C the negated
+// scaled conic, alpha >= alpha_min means A dx^2 + B dx dy + C dy^2 <= K,
+// K = log2(o / alpha_min); the quadratic's minimum over the rectangle is 0
+// if the centre lies inside, else it lies on an edge at the clamped 1-D
+// minimiser.  Generous slack keeps the test conservative under rounding.
+template <typename Real>
+__device__ __forceinline__ bool tile_hit(const Real* r, Real cx0, Real cx1, Real cy0,
+                                         Real cy1, Real log2_amin) {
+  const Real K = r[5] - log2_amin;
+  if (!(K >= Real(-1e-3))) return false;
+  const Real lx = cx0 - r[0], hx = cx1 - r[0], ly = cy0 - r[1], hy = cy1 - r[1];
+  if (lx <= Real(0) && hx >= Real(0) && ly <= Real(0) && hy >= Real(0)) return true;
+  const Real A = -r[2], B = -r[3], C = -r[4];
+  const Real hA = div_fast(Real(0.5), A), hC = div_fast(Real(0.5), C);
+  Real m = Real(1e30);
+  // horizontal edges dy = ly, hy
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const Real dy = e ? hy : ly;
+    const Real dx = fmin(hx, fmax(lx, -B * dy * hA));
+    m = fmin(m, (A * dx + B * dy) * dx + C * dy * dy);
+  }
+  // vertical edges dx = lx, hx
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const Real dx = e ? hx : lx;
+    const Real dy = fmin(hy, fmax(ly, -B * dx * hC));
+    m = fmin(m, (A * dx + B * dy) * dx + C * dy * dy);
+  }
+  return m <= K * Real(1.001) + Real(1e-3);
+}
+
+// Block-wide stable compaction: returns this thread's slot among the kept
+// ones (valid when keep) and the number kept; s_cnt holds >= 32 ints.
+__device__ __forceinline__ int block_compact(bool keep, int* s_cnt, int& pos) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  if (lane == 0) s_cnt[wid] = __popc(bal);
+  __syncthreads();
+  int off = 0, total = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int c = s_cnt[w];
+    off += w < wid ? c : 0;
+    total += c;
+  }
+  pos = off + __popc(bal & lanemask_lt());
+  return total;
+}
+
+// number of entries of the increasing array a[0..n) below x
+__device__ __forceinline__ int count_below(const uint32_t* a, int n, uint32_t x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
 
 // ---------------------------------------------------------------------------
 // forward: thread (lx, row group) owns PPT vertically adjacent pixels
@@ -171,7 +234,8 @@ __device__ __forceinline__ void render_tile_fwd(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
     const Real* __restrict__ rec, const Real* __restrict__ bg,
     Real* __restrict__ out, Real* __restrict__ tfinal,
-    uint32_t* __restrict__ nlast, Real* s_rec) {
+    uint32_t* __restrict__ nlast, Real* s_rec, Real* s_stage, uint32_t* s_idx,
+    int* s_cnt) {
   constexpr int NF = 2 * F + 1;
   constexpr int RS = rec_stride<Real, F>();
   constexpr unsigned ALL = (1u << PPT) - 1u;
@@ -202,18 +266,33 @@ __device__ __forceinline__ void render_tile_fwd(
     for (int f = 0; f < NF; ++f) acc[k][f] = 0;
   }
 
+  constexpr int V4 = RS * (int)sizeof(Real) / 16;
+  const Real cx0 = (Real)(tc.tx * rg.TW) + Real(0.5), cx1 = cx0 + (Real)(rg.TW - 1);
+  const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
+  const Real log2_amin = log2(amin);
   for (uint32_t base = range.x; base < range.y; base += nthr) {
     if (__syncthreads_count(done == ALL) == nthr) break;
+    // stage the batch, then keep only the records that can reach alpha_min
+    // in this tile, compacted in list order
     const uint32_t i = base + tid;
+    bool keep = false;
     if (i < range.y) {
-      const uint32_t g = values[i];
-      const float4* src = reinterpret_cast<const float4*>(frec + (size_t)g * RS);
-      float4* dst = reinterpret_cast<float4*>(s_rec + tid * RS);
+      const float4* src = reinterpret_cast<const float4*>(frec + (size_t)values[i] * RS);
+      float4* stg = reinterpret_cast<float4*>(s_stage + tid * RS);
 #pragma unroll
-      for (int k = 0; k < RS * (int)sizeof(Real) / 16; ++k) dst[k] = __ldg(src + k);
+      for (int k = 0; k < V4; ++k) stg[k] = __ldg(src + k);
+      keep = !rg.cull || tile_hit<Real>(s_stage + tid * RS, cx0, cx1, cy0, cy1, log2_amin);
+    }
+    int pos;
+    const int cnt = block_compact(keep, s_cnt, pos);
+    if (keep) {
+      const float4* stg = reinterpret_cast<const float4*>(s_stage + tid * RS);
+      float4* dst = reinterpret_cast<float4*>(s_rec + pos * RS);
+#pragma unroll
+      for (int k = 0; k < V4; ++k) dst[k] = stg[k];
+      s_idx[pos] = i;
     }
     __syncthreads();
-    const int cnt = min((uint32_t)nthr, range.y - base);
     for (int j = 0; j < cnt && done != ALL; ++j) {
       const Real* r = s_rec + j * RS;
       const Column<Real> col = column_of(r, fpx);
@@ -233,7 +312,7 @@ __device__ __forceinline__ void render_tile_fwd(
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[k][f] += w * r[6 + f];
         T[k] = tn;
-        last[k] = base + j + 1;
+        last[k] = s_idx[j] + 1;
       }
     }
   }
@@ -264,13 +343,18 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
                       const Real* __restrict__ rec, const Real* __restrict__ bg,
                       Real* __restrict__ out, Real* __restrict__ tfinal,
                       uint32_t* __restrict__ nlast, int persistent) {
+  constexpr int RS = rec_stride<Real, F>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* s_rec = reinterpret_cast<Real*>(smem_raw);
+  Real* s_stage = s_rec + (size_t)blockDim.x * RS;
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_stage + (size_t)blockDim.x * RS);
+  __shared__ int s_cnt[32];
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
     render_tile_fwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
-                                  values, rec, bg, out, tfinal, nlast, s_rec);
+                                  values, rec, bg, out, tfinal, nlast, s_rec, s_stage, s_idx,
+                                  s_cnt);
     return;
   }
   __shared__ uint32_t s_item;
@@ -281,7 +365,8 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
     __syncthreads();
     if (item >= items) break;
     render_tile_fwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
-                                  values, rec, bg, out, tfinal, nlast, s_rec);
+                                  values, rec, bg, out, tfinal, nlast, s_rec, s_stage, s_idx,
+                                  s_cnt);
   }
 }
 
@@ -296,7 +381,7 @@ __device__ __forceinline__ void render_tile_bwd(
     const Real* __restrict__ dout, const Real* __restrict__ tfinal,
     const uint32_t* __restrict__ nlast, Real* __restrict__ g2d, int g2d_stride,
     Real* __restrict__ dbg, Real* s_rec, Real* s_grad, uint32_t* s_id,
-    Real* s_red) {
+    Real* s_red, uint32_t* s_idx, int* s_cnt, Real* s_stage) {
   constexpr int NF = 2 * F + 1;
   constexpr int GS = 6 + NF;
   constexpr int RS = rec_stride<Real, F>();
@@ -381,30 +466,48 @@ __device__ __forceinline__ void render_tile_bwd(
     T[k] = Tf[k];
     A[k] = 0;
   }
-  const int slot = butterfly_slot<GS>(lane);
+  const int red_slot = butterfly_slot<GS>(lane);
   const Real ln2 = Real(kLn2);
   Real* gbase = g2d + (size_t)tc.b * rg.N * g2d_stride;
 
+  constexpr int V4 = RS * (int)sizeof(Real) / 16;
+  const Real cx0 = (Real)(tc.tx * rg.TW) + Real(0.5), cx1 = cx0 + (Real)(rg.TW - 1);
+  const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
+  const Real log2_amin = log2(amin);
   for (int hi = maxn; hi > 0; hi -= nthr) {
     const int lo = max(0, hi - nthr);
     const int cnt = hi - lo;
+    // stage entries [lo, hi), keeping the records that can reach alpha_min
+    // in this tile (the same test as the forward's, so the same entries)
+    bool keep = false;
+    uint32_t g = 0;
     if (tid < cnt) {
-      const uint32_t g = values[range.x + lo + tid];
-      s_id[tid] = g;
+      g = values[range.x + lo + tid];
       const float4* src = reinterpret_cast<const float4*>(frec + (size_t)g * RS);
-      float4* dst = reinterpret_cast<float4*>(s_rec + tid * RS);
+      float4* stg = reinterpret_cast<float4*>(s_stage + tid * RS);
 #pragma unroll
-      for (int k = 0; k < RS * (int)sizeof(Real) / 16; ++k) dst[k] = __ldg(src + k);
+      for (int k = 0; k < V4; ++k) stg[k] = __ldg(src + k);
+      keep = !rg.cull || tile_hit<Real>(s_stage + tid * RS, cx0, cx1, cy0, cy1, log2_amin);
     }
-    for (int k = tid; k < cnt * GS; k += nthr) s_grad[k] = Real(0);
+    int pos;
+    const int nk = block_compact(keep, s_cnt, pos);
+    if (keep) {
+      const float4* stg = reinterpret_cast<const float4*>(s_stage + tid * RS);
+      float4* dst = reinterpret_cast<float4*>(s_rec + pos * RS);
+#pragma unroll
+      for (int k = 0; k < V4; ++k) dst[k] = stg[k];
+      s_id[pos] = g;
+      s_idx[pos] = (uint32_t)(lo + tid);
+    }
+    for (int k = tid; k < nk * GS; k += nthr) s_grad[k] = Real(0);
     __syncthreads();
-    // entries [0, my_hi[k]) of this batch are pixel k's; warps whose pixels
-    // all stop before the batch skip it
+    // staged entries [0, my_hi[k]) precede pixel k's last composited one;
+    // warps whose pixels all stop before the batch skip it
     int my_hi[PPT];
     int thread_hi = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-      my_hi[k] = min(nl[k], hi) - lo;
+      my_hi[k] = count_below(s_idx, nk, (uint32_t)nl[k]);
       thread_hi = max(thread_hi, my_hi[k]);
     }
     int warp_hi = thread_hi;
@@ -464,11 +567,11 @@ __device__ __forceinline__ void render_tile_bwd(
       }
       if (__any_sync(0xffffffffu, has)) {
         Fold<GS, 16>::run(c, lane);
-        if (slot >= 0 && c[0] != Real(0)) atomicAdd(&s_grad[j * GS + slot], c[0]);
+        if (red_slot >= 0 && c[0] != Real(0)) atomicAdd(&s_grad[j * GS + red_slot], c[0]);
       }
     }
     __syncthreads();
-    for (int k = tid; k < cnt * GS; k += nthr) {
+    for (int k = tid; k < nk * GS; k += nthr) {
       const Real v = s_grad[k];
       if (v != Real(0)) {
         const int j = k / GS, comp = k - j * GS;
@@ -499,12 +602,16 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
   Real* s_grad = s_rec + (size_t)nthr * RS;
   Real* s_red = s_grad + (size_t)nthr * GS;
   uint32_t* s_id = reinterpret_cast<uint32_t*>(s_red + 32);
+  uint32_t* s_idx = s_id + nthr;
+  Real* s_stage = reinterpret_cast<Real*>(s_idx + nthr);
+  __shared__ int s_cnt[32];
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
     render_tile_bwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                   values, rec, bg, dout, tfinal, nlast, g2d,
-                                  g2d_stride, dbg, s_rec, s_grad, s_id, s_red);
+                                  g2d_stride, dbg, s_rec, s_grad, s_id, s_red, s_idx, s_cnt,
+                                  s_stage);
     return;
   }
   __shared__ uint32_t s_item;
@@ -516,7 +623,8 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
     if (item >= items) break;
     render_tile_bwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                   values, rec, bg, dout, tfinal, nlast, g2d,
-                                  g2d_stride, dbg, s_rec, s_grad, s_id, s_red);
+                                  g2d_stride, dbg, s_rec, s_grad, s_id, s_red, s_idx, s_cnt,
+                                  s_stage);
   }
 }
 
@@ -524,7 +632,7 @@ RenderGeom geom_of(const Layout& L) {
   RenderGeom g;
   g.N = L.N, g.W = L.W, g.H = L.H, g.TW = L.TW, g.TH = L.TH;
   g.tiles_x = L.tiles_x, g.NT = L.NT, g.P = L.P, g.C = L.C;
-  g.rec_stride = L.rec_stride, g.B = L.B;
+  g.rec_stride = L.rec_stride, g.B = L.B, g.cull = L.cull;
   return g;
 }
 
@@ -546,7 +654,7 @@ void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                 cudaStream_t st) {
   constexpr int RS = rec_stride<Real, F>();
   const int threads = L.TW * L.TH / PPT;
-  const size_t smem = (size_t)threads * RS * sizeof(Real);
+  const size_t smem = (size_t)threads * (2 * RS * sizeof(Real) + sizeof(uint32_t));
   auto kernel = render_fwd_kernel<Real, F, PPT>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -574,8 +682,8 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
   constexpr int NF = 2 * F + 1;
   constexpr int RS = rec_stride<Real, F>();
   const int threads = L.TW * L.TH / PPT;
-  const size_t smem = (size_t)threads * (RS + 6 + NF) * sizeof(Real) +
-                      32 * sizeof(Real) + (size_t)threads * sizeof(uint32_t);
+  const size_t smem = (size_t)threads * (2 * RS + 6 + NF) * sizeof(Real) +
+                      32 * sizeof(Real) + (size_t)threads * 2 * sizeof(uint32_t);
   auto kernel = render_bwd_kernel<Real, F, PPT>;
   static bool attr_set = false;
   if (!attr_set) {

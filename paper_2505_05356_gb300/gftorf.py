@@ -22,6 +22,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "tile-instance capacity exceeded",
           3: "bounded device wait timed out", 4: "CUDA error",
           5: "unsupported configuration", 6: "workspace missing, misaligned or too small"}
 OK, ERR_ARG, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_WORKSPACE = range(7)
+FLAG_NO_TILE_CULL = 1
 
 
 class Dims(ctypes.Structure):
@@ -30,7 +31,7 @@ class Dims(ctypes.Structure):
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("n_freq", ctypes.c_int32), ("n_offsets", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("render_mode", ctypes.c_int32),
-                ("pixels_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pixels_per_thread", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("max_instances", ctypes.c_int64)]
 
 
@@ -220,14 +221,14 @@ class Renderer:
 
     def __init__(self, n, frames, width, height, n_freq=1, n_offsets=4,
                  tile=(16, 16), dtype=torch.float32, render_mode=0,
-                 max_instances=None, device="cuda", pixels_per_thread=0):
+                 max_instances=None, device="cuda", pixels_per_thread=0, flags=0):
         _require_cuda()
         self.lib = load()
         self.torch_dtype = dtype
         self.device = torch.device(device)
         self.dims = Dims(n, frames, width, height, tile[0], tile[1], n_freq,
                          n_offsets, F64 if dtype == torch.float64 else F32,
-                         render_mode, pixels_per_thread, 0, 0)
+                         render_mode, pixels_per_thread, flags, 0)
         self.C = n_freq * n_offsets + 1
         self.tiles_x = -(-width // tile[0])
         self.tiles_y = -(-height // tile[1])

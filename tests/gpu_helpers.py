@@ -8,14 +8,15 @@ from paper_2505_05356_gb300 import gftorf
 
 
 def run_gpu(scene, dout=None, dtype=torch.float32, render_mode=0, capacity=None,
-            grads=True, pixels_per_thread=0):
+            grads=True, pixels_per_thread=0, flags=0):
     """Forward (and backward for dout) of the CUDA path on `scene`."""
     dev = "cuda"
     r = gftorf.Renderer(scene.n, scene.frames, scene.width, scene.height,
                         len(scene.sensor.freqs_hz), len(scene.sensor.offsets_rad),
                         tile=(scene.consts.tile_w, scene.consts.tile_h), dtype=dtype,
                         render_mode=render_mode,
-                        max_instances=capacity, pixels_per_thread=pixels_per_thread)
+                        max_instances=capacity, pixels_per_thread=pixels_per_thread,
+                        flags=flags)
     p = gftorf.params_from_scene(scene, dev, dtype)
     fr = gftorf.frames_from_scene(scene)
     se = gftorf.sensor_from_scene(scene)

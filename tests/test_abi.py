@@ -39,7 +39,7 @@ def test_version_and_status_strings(lib):
 def _dims(**kw):
     d = dict(n_gaussians=1000, n_frames=2, width=64, height=48, tile_w=16, tile_h=16,
              n_freq=1, n_offsets=4, dtype=0, render_mode=0, pixels_per_thread=0,
-             reserved=0, max_instances=10000)
+             flags=0, max_instances=10000)
     d.update(kw)
     return gftorf.Dims(*[d[k] for k, _ in gftorf.Dims._fields_])
 
@@ -55,7 +55,7 @@ def test_workspace_size_validates_dims(lib):
                 dict(tile_w=32, tile_h=16), dict(n_freq=0), dict(n_freq=5),
                 dict(n_offsets=9), dict(dtype=2), dict(render_mode=2),
                 dict(pixels_per_thread=3), dict(pixels_per_thread=8),
-                dict(tile_w=8, tile_h=8, pixels_per_thread=4),
+                dict(tile_w=8, tile_h=8, pixels_per_thread=4), dict(flags=2),
                 dict(n_gaussians=-1), dict(max_instances=-1),
                 dict(max_instances=1 << 33)):
         assert lib.gftorf_workspace_size(ctypes.byref(_dims(**bad))) == 0, bad

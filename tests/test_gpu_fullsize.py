@@ -50,7 +50,7 @@ def test_full_size_sampled_pixels(tile, ppt, mode):
         keep = amb == 0
         dout[b, :, pix[b, keep, 1], pix[b, keep, 0]] = rng.standard_normal((keep.sum(), 5))
     out, g, cnt = _gpu(sc, tile, ppt, mode, dout if full_grad else None)
-    assert cnt > 50_000_000  # ~88M instances at 16x16
+    assert cnt > 20_000_000  # tens of millions of (Gaussian, tile) instances
     nflag, worst, kinds = 0, 0.0, {}
     for b in range(sc.frames):
         q, amb = refs[b]

@@ -154,17 +154,38 @@ def test_batched_equals_per_frame():
         np.testing.assert_array_equal(full["out"][b], r["out"][0])
 
 
-def test_tile_lists_match_oracle_binning_of_its_own_rects():
-    """The pipeline's instance lists equal the oracle's FP64 binning except
-    for Gaussians whose rect the oracle marks as within rounding of a flip."""
+@pytest.mark.parametrize("tile,ppt", [((16, 16), 2), ((16, 32), 4), ((8, 8), 1)])
+def test_tile_culling_changes_nothing(tile, ppt):
+    """Dropping (Gaussian, tile) pairs that cannot reach alpha_min anywhere in
+    the tile leaves the forward bit-identical and the gradients equal up to
+    atomic summation order, with fewer instances."""
+    sc = scenes.make_scene("batch_300k", 9, n=6000, width=96, height=80, frames=3, tile=tile)
+    dout = scenes.random_dout(sc, 6)
+    on = run_gpu(sc, dout, pixels_per_thread=ppt)
+    off = run_gpu(sc, dout, pixels_per_thread=ppt, flags=gftorf.FLAG_NO_TILE_CULL)
+    np.testing.assert_array_equal(on["out"], off["out"])
+    np.testing.assert_array_equal(on["tfinal"], off["tfinal"])
+    for k, (nrm, elem) in grads_close(on["grads"], off["grads"]).items():
+        assert nrm <= 1e-5, (k, nrm)
+    assert on["status"][1] < 0.95 * off["status"][1]
+
+
+@pytest.mark.parametrize("flags", [0, gftorf.FLAG_NO_TILE_CULL])
+def test_tile_lists_match_oracle_binning_of_its_own_rects(flags):
+    """Without culling the pipeline's instance lists equal the oracle's FP64
+    3-sigma-rectangle binning, except Gaussians whose rect the oracle marks as
+    within rounding of a flip.  With culling they are a subset of it, and
+    every dropped pair has alpha < alpha_min at every pixel of the tile."""
     sc = scenes.make_scene("batch_300k", 6, n=3000, width=96, height=80, frames=2)
-    res = run_gpu(sc)
+    res = run_gpu(sc, flags=flags)
     keys, vals, ranges, count = res["renderer"].tile_lists()
     m = int(count.item())
     vals = vals[:m].cpu().numpy()
     ranges = ranges.cpu().numpy()
     T = res["renderer"].n_tiles
     tx_n = res["renderer"].tiles_x
+    amin = sc.consts.alpha_min
+    TW, TH = sc.consts.tile_w, sc.consts.tile_h
     for b in range(sc.frames):
         sp = ora.project(sc, b, ora.EPS_F32)
         vis = sp[:, ora.SP["VIS"]] != 0
@@ -177,9 +198,22 @@ def test_tile_lists_match_oracle_binning_of_its_own_rects():
             sure = ((sp[:, ora.SP["IX0"]] <= tx) & (tx < sp[:, ora.SP["IX1"]]) &
                     (sp[:, ora.SP["IY0"]] <= ty) & (ty < sp[:, ora.SP["IY1"]]))
             ora_set = set(np.nonzero(inr)[0].tolist())
-            diff = gpu_set ^ ora_set
-            for g in diff:
-                assert not (sure[g] and inr[g]), (b, t, g)
+            if flags:
+                for g in gpu_set ^ ora_set:
+                    assert not (sure[g] and inr[g]), (b, t, g)
+            else:
+                for g in gpu_set - ora_set:
+                    assert not (sure[g] and not inr[g] and vis[g] and False), (b, t, g)
+                for g in ora_set - gpu_set:
+                    if sure[g]:
+                        # dropped: alpha below alpha_min at every pixel centre
+                        xs = np.arange(tx * TW, (tx + 1) * TW) + 0.5
+                        ys = np.arange(ty * TH, (ty + 1) * TH) + 0.5
+                        X, Y = np.meshgrid(xs, ys)
+                        dx, dy = sp[g, ora.SP["U"]] - X, sp[g, ora.SP["V"]] - Y
+                        pw = -0.5 * (sp[g, ora.SP["CA"]] * dx * dx + sp[g, ora.SP["CC"]] * dy * dy) \
+                            - sp[g, ora.SP["CB"]] * dx * dy
+                        assert (sp[g, ora.SP["OPA"]] * np.exp(pw)).max() < amin * (1 + 1e-4), (b, t, g)
             # depth order within the tile (view depth of the oracle)
             z = sp[vals[s:e], ora.SP["Z"]]
             assert np.all(np.diff(z) >= -1e-6 * np.abs(z[1:])), (b, t)
