@@ -249,14 +249,16 @@ def run_ours(args):
     stage_ms = {s_: sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
                 for i, s_ in enumerate(stages)}
 
-    # --- algorithmic work of this batch ---
-    keys, vals, ranges, cnt = r.tile_lists(with_keys=False)
-    tf, nl = r.pixel_state()
-    rg = ranges.to(torch.int64)
-    lens = (rg[:, 1] - rg[:, 0]).reshape(B, r.tiles_y, r.tiles_x)
-    lens_px = lens.repeat_interleave(tile[1], 1).repeat_interleave(tile[0], 2)[:, :H, :W]
-    pairs = int(torch.minimum(nl.to(torch.int64) + 1, lens_px).sum().item())
-    instances = int(cnt.item())
+    # --- algorithmic work of this batch: evaluated (pixel, Gaussian) pairs
+    # counted by the forward's counting instantiation on the same inputs ---
+    rc = gftorf.Renderer(N, B, W, H, nF, nP, tile=tile, render_mode=mode,
+                         pixels_per_thread=ppt, flags=gftorf.FLAG_COUNT_PAIRS,
+                         max_instances=r.capacity)
+    rc.preprocess(p, fr, se, co)
+    rc.render_fwd(bg)
+    instances, pairs = rc.counters()
+    del rc
+    torch.cuda.empty_cache()
     peaks, peak_kind = _peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count

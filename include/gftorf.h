@@ -76,6 +76,11 @@ typedef enum { GFTORF_F32 = 0, GFTORF_F64 = 1 } gftorf_dtype;
  * so outputs are the same; this flag turns the culling off (lists then hold
  * every tile of the 3-sigma rectangle, as gftorf_sort_footprints does). */
 #define GFTORF_FLAG_NO_TILE_CULL 1
+/* gftorf_dims.flags: the forward also counts the (pixel, Gaussian) pairs it
+ * evaluates (each pixel: the staged entries up to and including the one that
+ * stops it), readable with gftorf_read_counters.  Same outputs; a separate
+ * kernel instantiation, for measurement. */
+#define GFTORF_FLAG_COUNT_PAIRS 2
 
 /* Static problem shape.  One workspace serves one dims value. */
 typedef struct {
@@ -285,6 +290,13 @@ gftorf_status gftorf_read_device_status(const gftorf_dims* dims,
 /* Number of CUDA kernels this library has enqueued so far in this process
  * (host-side counter; a captured graph's replays are not counted again). */
 int64_t gftorf_kernel_launches(void);
+
+/* Synchronises `stream`; counters[0] = tile instances of the last binning,
+ * counters[1] = (pixel, Gaussian) pairs the last forward evaluated (0 unless
+ * dims->flags has GFTORF_FLAG_COUNT_PAIRS).  counters: HOST int64[2]. */
+gftorf_status gftorf_read_counters(const gftorf_dims* dims, void* workspace,
+                                   size_t workspace_bytes, int64_t* counters,
+                                   void* stream);
 
 /* Static description of a status code. */
 const char* gftorf_status_string(gftorf_status status);

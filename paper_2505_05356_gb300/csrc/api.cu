@@ -36,7 +36,7 @@ bool dims_ok(const gftorf_dims* d) {
   const int ppt = d->pixels_per_thread;
   if (ppt != 0 && ppt != 1 && ppt != 2 && ppt != 4) return false;
   if (d->tile_w * d->tile_h / (ppt ? ppt : 2) < 32) return false;  // a full warp per tile
-  if (d->flags & ~GFTORF_FLAG_NO_TILE_CULL) return false;
+  if (d->flags & ~(GFTORF_FLAG_NO_TILE_CULL | GFTORF_FLAG_COUNT_PAIRS)) return false;
   if (d->max_instances < 0 || d->max_instances > (int64_t)0xFFFFFFFFll) return false;
   const int64_t tiles = (int64_t)((d->width + d->tile_w - 1) / d->tile_w) *
                         ((d->height + d->tile_h - 1) / d->tile_h);
@@ -54,6 +54,7 @@ Layout make_layout(const gftorf_dims* d) {
   L.mode = d->render_mode;
   L.ppt = d->pixels_per_thread ? d->pixels_per_thread : 2;
   L.cull = (d->flags & GFTORF_FLAG_NO_TILE_CULL) ? 0 : 1;
+  L.count_pairs = (d->flags & GFTORF_FLAG_COUNT_PAIRS) ? 1 : 0;
   L.tiles_x = (L.W + L.TW - 1) / L.TW;
   L.tiles_y = (L.H + L.TH - 1) / L.TH;
   L.NT = L.tiles_x * L.tiles_y;
@@ -164,6 +165,24 @@ extern "C" {
 int32_t gftorf_version(void) { return 100; }
 
 int64_t gftorf_kernel_launches(void) { return gftorf::launches_so_far(); }
+
+gftorf_status gftorf_read_counters(const gftorf_dims* dims, void* workspace,
+                                   size_t workspace_bytes, int64_t* counters,
+                                   void* stream) {
+  if (!dims_ok(dims) || !counters) return GFTORF_ERR_ARG;
+  const Layout L = make_layout(dims);
+  gftorf_status s = check_ws(L, workspace, workspace_bytes);
+  if (s != GFTORF_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Header h;
+  if (cudaMemcpyAsync(&h, static_cast<unsigned char*>(workspace) + L.off_header, sizeof(h),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GFTORF_ERR_CUDA;
+  counters[0] = h.count;
+  counters[1] = (int64_t)h.pairs;
+  return GFTORF_OK;
+}
 
 const char* gftorf_status_string(gftorf_status s) {
   switch (s) {

@@ -50,6 +50,7 @@ struct Header {
   int32_t status;
   int32_t pad0;
   int64_t count;           // tile instances of the batch
+  unsigned long long pairs;  // evaluated (pixel, Gaussian) pairs (when counted)
   uint32_t queue[4];       // persistent work-queue heads (fwd, bwd)
   uint32_t vis[kMaxFrames];  // visible Gaussians per frame
   uint32_t fstart[kMaxFrames + 1];  // first instance of each frame
@@ -61,6 +62,7 @@ struct Layout {
   int B, N, W, H, TW, TH, F, P, C, NF, dtype, real_size, mode;
   int ppt;   // pixels per compositing thread (1, 2 or 4)
   int cull;  // drop (Gaussian, tile) pairs that cannot reach alpha_min
+  int count_pairs;  // count evaluated (pixel, Gaussian) pairs in the forward
   int tiles_x, tiles_y, NT;
   int rec_stride;  // Reals per projected record (16-byte multiple)
   int g2d_stride;  // Reals per 2D-gradient row

@@ -228,14 +228,14 @@ struct kMinBlocks {
   static constexpr int value = PPT == 4 ? GFTORF_PPT4_MIN_BLOCKS : 0;
 };
 
-template <typename Real, int F, int PPT>
+template <typename Real, int F, int PPT, bool COUNT>
 __device__ __forceinline__ void render_tile_fwd(
     const TileCtx& tc, const RenderGeom& rg, const Table* __restrict__ tab,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
     const Real* __restrict__ rec, const Real* __restrict__ bg,
     Real* __restrict__ out, Real* __restrict__ tfinal,
     uint32_t* __restrict__ nlast, Real* s_rec, Real* s_stage, uint32_t* s_idx,
-    int* s_cnt) {
+    int* s_cnt, Header* __restrict__ hdr) {
   constexpr int NF = 2 * F + 1;
   constexpr int RS = rec_stride<Real, F>();
   constexpr unsigned ALL = (1u << PPT) - 1u;
@@ -258,6 +258,7 @@ __device__ __forceinline__ void render_tile_fwd(
 
   Real T[PPT], acc[PPT][NF];
   uint32_t last[PPT];
+  uint32_t evals = 0;  // evaluated pairs (COUNT only)
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     T[k] = 1;
@@ -299,6 +300,7 @@ __device__ __forceinline__ void render_tile_fwd(
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (done & (1u << k)) continue;
+        if (COUNT) ++evals;
         const Real lg = log2_oG(r, col, sub_rn(r[1], fpy[k]));
         const Real oG = ex2_approx(lg);
         const Real alpha = oG < amax ? oG : amax;
@@ -315,6 +317,12 @@ __device__ __forceinline__ void render_tile_fwd(
         last[k] = s_idx[j] + 1;
       }
     }
+  }
+  if (COUNT) {
+    unsigned long long e = evals;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((tid & 31) == 0 && e) atomicAdd(&hdr->pairs, e);
   }
   const size_t HW = (size_t)rg.W * rg.H;
   const Real* bgb = bg + (size_t)tc.b * rg.C;
@@ -334,7 +342,7 @@ __device__ __forceinline__ void render_tile_fwd(
   }
 }
 
-template <typename Real, int F, int PPT>
+template <typename Real, int F, int PPT, bool COUNT>
 __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
     render_fwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
                       Header* __restrict__ hdr,
@@ -352,9 +360,9 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
-    render_tile_fwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
-                                  values, rec, bg, out, tfinal, nlast, s_rec, s_stage, s_idx,
-                                  s_cnt);
+    render_tile_fwd<Real, F, PPT, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                                         values, rec, bg, out, tfinal, nlast, s_rec, s_stage,
+                                         s_idx, s_cnt, hdr);
     return;
   }
   __shared__ uint32_t s_item;
@@ -364,9 +372,9 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= items) break;
-    render_tile_fwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
-                                  values, rec, bg, out, tfinal, nlast, s_rec, s_stage, s_idx,
-                                  s_cnt);
+    render_tile_fwd<Real, F, PPT, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+                                         values, rec, bg, out, tfinal, nlast, s_rec, s_stage,
+                                         s_idx, s_cnt, hdr);
   }
 }
 
@@ -649,13 +657,13 @@ int persistent_grid(KernelT kernel, int threads, size_t smem) {
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-template <typename Real, int F, int PPT>
+template <typename Real, int F, int PPT, bool COUNT>
 void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                 cudaStream_t st) {
   constexpr int RS = rec_stride<Real, F>();
   const int threads = L.TW * L.TH / PPT;
   const size_t smem = (size_t)threads * (2 * RS * sizeof(Real) + sizeof(uint32_t));
-  auto kernel = render_fwd_kernel<Real, F, PPT>;
+  auto kernel = render_fwd_kernel<Real, F, PPT, COUNT>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -709,10 +717,18 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
 template <typename Real, int F>
 void fwd_dispatch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                   cudaStream_t st) {
+  if (L.count_pairs) {
+    switch (L.ppt) {
+      case 1: fwd_launch<Real, F, 1, true>(L, bg, out, ws, st); break;
+      case 4: fwd_launch<Real, F, 4, true>(L, bg, out, ws, st); break;
+      default: fwd_launch<Real, F, 2, true>(L, bg, out, ws, st); break;
+    }
+    return;
+  }
   switch (L.ppt) {
-    case 1: fwd_launch<Real, F, 1>(L, bg, out, ws, st); break;
-    case 4: fwd_launch<Real, F, 4>(L, bg, out, ws, st); break;
-    default: fwd_launch<Real, F, 2>(L, bg, out, ws, st); break;
+    case 1: fwd_launch<Real, F, 1, false>(L, bg, out, ws, st); break;
+    case 4: fwd_launch<Real, F, 4, false>(L, bg, out, ws, st); break;
+    default: fwd_launch<Real, F, 2, false>(L, bg, out, ws, st); break;
   }
 }
 

@@ -23,6 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "tile-instance capacity exceeded",
           5: "unsupported configuration", 6: "workspace missing, misaligned or too small"}
 OK, ERR_ARG, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_WORKSPACE = range(7)
 FLAG_NO_TILE_CULL = 1
+FLAG_COUNT_PAIRS = 2
 
 
 class Dims(ctypes.Structure):
@@ -109,6 +110,8 @@ def load(build_if_missing: bool = True):
     L.gftorf_preprocess_bwd.argtypes = [_P(Dims), _P(Gaussians), _P(Gradients), vp, sz, vp]
     L.gftorf_sort_footprints_noalloc.argtypes = [_P(Dims), vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.gftorf_sort_footprints_noalloc.restype = ctypes.c_int
+    L.gftorf_read_counters.argtypes = [_P(Dims), vp, sz, _P(ctypes.c_int64), vp]
+    L.gftorf_read_counters.restype = ctypes.c_int
     L.gftorf_kernel_launches.restype = ctypes.c_int64
     L.gftorf_kernel_launches.argtypes = []
     for name in ("gftorf_preprocess", "gftorf_render_fwd", "gftorf_render_bwd",
@@ -346,6 +349,14 @@ class Renderer:
         code = self.lib.gftorf_read_device_status(ctypes.byref(self.dims), self.ws_ptr,
                                                   self.ws_bytes, ctypes.byref(cnt), _stream())
         return code, int(cnt.value)
+
+    def counters(self):
+        """(instances, evaluated pairs) of the last binning / forward; pairs
+        are counted only with FLAG_COUNT_PAIRS.  Synchronises."""
+        buf = (ctypes.c_int64 * 2)()
+        _check(self.lib.gftorf_read_counters(ctypes.byref(self.dims), self.ws_ptr, self.ws_bytes,
+                                             buf, _stream()), "gftorf_read_counters")
+        return int(buf[0]), int(buf[1])
 
     def check(self):
         code, cnt = self.read_status()
