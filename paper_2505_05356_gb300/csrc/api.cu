@@ -76,7 +76,7 @@ Layout make_layout(const gftorf_dims* d) {
     return at_;
   };
   L.off_header = take(sizeof(Header));
-  L.off_table = take(sizeof(Table));
+  L.off_table = take(sizeof(Table) + sizeof(TableT<float>));
   L.off_rec = take(BN * L.rec_stride * L.real_size);
   L.off_rect = take(BN * sizeof(uint2));
   L.off_zkey = take(BN * 4);
@@ -84,6 +84,7 @@ Layout make_layout(const gftorf_dims* d) {
   L.off_ids = take(BN * 4);
   L.off_ids2 = take(BN * 4);
   L.off_dhist = take((size_t)L.B * 256 * (L.n_dblk > 0 ? L.n_dblk : 1) * 4);
+  L.off_dtot = take((size_t)L.B * 256 * 4);
   L.off_ecnt = take((size_t)L.B * L.N * 4 + 4);
   L.off_bsum = take((size_t)(L.n_scan + 1) * 8);
   L.off_tcnt = take((size_t)L.n_chunk * L.NT * 4);
@@ -114,7 +115,11 @@ __global__ void store_table_kernel(Table t, Table* dst) {
   const int n = sizeof(Table) / sizeof(double);
   const double* s = reinterpret_cast<const double*>(&t);
   double* d = reinterpret_cast<double*>(dst);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+  float* f = reinterpret_cast<float*>(dst + 1);  // TableT<float>: same fields
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    d[i] = s[i];
+    f[i] = (float)s[i];
+  }
 }
 
 bool finite(float x) { return isfinite(x) != 0; }
@@ -143,6 +148,7 @@ Layout binning_layout(const gftorf_dims* d) {
   L.off_ids = take(BN * 4);
   L.off_ids2 = take(BN * 4);
   L.off_dhist = take((size_t)L.B * 256 * (L.n_dblk > 0 ? L.n_dblk : 1) * 4);
+  L.off_dtot = take((size_t)L.B * 256 * 4);
   L.off_ecnt = take(BN * 4 + 4);
   L.off_bsum = take((size_t)(L.n_scan + 1) * 8);
   L.off_tcnt = take((size_t)L.n_chunk * L.NT * 4);
@@ -223,7 +229,7 @@ gftorf_status gftorf_preprocess(const gftorf_dims* dims,
       return GFTORF_ERR_ARG;
     for (int k = 0; k < 12; ++k)
       if (!finite(f.world_to_cam[k])) return GFTORF_ERR_ARG;
-    FrameDev& d = t.fr[b];
+    FrameT<double>& d = t.fr[b];
     d.fx = f.fx, d.fy = f.fy, d.cx = f.cx, d.cy = f.cy;
     for (int r = 0; r < 3; ++r) {
       for (int c = 0; c < 3; ++c) d.R[3 * r + c] = f.world_to_cam[4 * r + c];

@@ -141,10 +141,33 @@ __global__ void __launch_bounds__(kSortThreads)
   dh[((size_t)b * 256 + tid) * n_dblk + blk] = h[tid];
 }
 
-__global__ void __launch_bounds__(1024)
-    dsort_scan_kernel(uint32_t* __restrict__ dh, int n_dblk) {
-  cta_exclusive_scan<uint32_t>(dh + (size_t)blockIdx.x * 256 * n_dblk,
-                               (int64_t)256 * n_dblk, nullptr);
+// Offsets for the scatter, in two short steps: each (frame, digit) row of
+// per-tile counts is scanned by one warp (in place, row total kept), then each
+// frame's 256 row totals by one CTA; offset = digit base + row prefix.
+__global__ void __launch_bounds__(256)
+    dsort_scan_rows_kernel(uint32_t* __restrict__ dh, uint32_t* __restrict__ dtot,
+                           int rows, int n_dblk) {
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  uint32_t* a = dh + (size_t)row * n_dblk;
+  uint32_t carry = 0;
+  for (int base = 0; base < n_dblk; base += 32) {
+    const int i = base + lane;
+    const uint32_t v = i < n_dblk ? a[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (i < n_dblk) a[i] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) dtot[row] = carry;
+}
+
+__global__ void __launch_bounds__(256) dsort_scan_digits_kernel(uint32_t* __restrict__ dtot) {
+  cta_exclusive_scan<uint32_t>(dtot + (size_t)blockIdx.x * 256, 256, nullptr);
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -152,7 +175,7 @@ __global__ void __launch_bounds__(kSortThreads)
                          const uint32_t* __restrict__ iin,
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ iout,
                          int N, int shift, const uint32_t* __restrict__ dh,
-                         int n_dblk) {
+                         const uint32_t* __restrict__ dtot, int n_dblk) {
   __shared__ uint32_t wc[kSortWarps][256];
   const int blk = blockIdx.x, b = blockIdx.y;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -185,7 +208,7 @@ __global__ void __launch_bounds__(kSortThreads)
   __syncthreads();
   {
     const int d = tid;  // 256 threads, one digit each
-    uint32_t run = dh[((size_t)b * 256 + d) * n_dblk + blk];
+    uint32_t run = dtot[(size_t)b * 256 + d] + dh[((size_t)b * 256 + d) * n_dblk + blk];
 #pragma unroll
     for (int ww = 0; ww < kSortWarps; ++ww) {
       const uint32_t t = wc[ww][d];
@@ -557,6 +580,7 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   auto* i0 = at<uint32_t>(ws, L.off_ids);
   auto* i1 = at<uint32_t>(ws, L.off_ids2);
   auto* dh = at<uint32_t>(ws, L.off_dhist);
+  auto* dtot = at<uint32_t>(ws, L.off_dtot);
   auto* rect = at<const uint2>(ws, L.off_rect);
   auto* ecnt = at<uint32_t>(ws, L.off_ecnt);
   auto* bsum = at<uint64_t>(ws, L.off_bsum);
@@ -578,9 +602,10 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 8 * pass;
     dsort_hist_kernel<<<g, kSortThreads, 0, st>>>(kin, L.N, shift, dh, L.n_dblk);
-    dsort_scan_kernel<<<L.B, 1024, 0, st>>>(dh, L.n_dblk);
+    dsort_scan_rows_kernel<<<(L.B * 256 + 7) / 8, 256, 0, st>>>(dh, dtot, L.B * 256, L.n_dblk);
+    dsort_scan_digits_kernel<<<L.B, 256, 0, st>>>(dtot);
     dsort_scatter_kernel<<<g, kSortThreads, 0, st>>>(kin, iin, kout[pass & 1], iout[pass & 1],
-                                                     L.N, shift, dh, L.n_dblk);
+                                                     L.N, shift, dh, dtot, L.n_dblk);
     kin = kout[pass & 1];
     iin = iout[pass & 1];
   }
@@ -600,7 +625,7 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   const int nw = L.scatter_warps;
   tile_scatter_kernel<<<L.n_chunk, nw * 32, (size_t)nw * L.NT * 4, st>>>(
       sorted, rect, hdr, ecnt, tcnt, ttot, values, L.N, L.NT, L.tiles_x, L.B, L.cap);
-  count_launches(12 + 9);
+  count_launches(16 + 9);
 }
 
 void launch_export_keys(const Layout& L, uint64_t* keys, unsigned char* ws,

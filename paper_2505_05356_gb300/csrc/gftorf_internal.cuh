@@ -26,24 +26,29 @@ constexpr int kChunk = 16384;
 // Device-wide scans: elements per CTA.
 constexpr int kScanTile = 4096;
 
-// Per-frame camera in device memory (double; kernels round to their type).
-struct FrameDev {
-  double fx, fy, cx, cy;
-  double R[9];
-  double t[3];
-  double near_plane, time;
-  double limx, limy;  // guard * half field of view (tan), x and y
+// Per-frame camera in device memory.
+template <typename T>
+struct FrameT {
+  T fx, fy, cx, cy;
+  T R[9];
+  T t[3];
+  T near_plane, time;
+  T limx, limy;  // guard * half field of view (tan), x and y
 };
 
 // Everything a batch needs besides the arrays: written into the workspace by
-// gftorf_preprocess, read by the later kernels.
-struct Table {
-  FrameDev fr[kMaxFrames];
-  double kf[kMaxF];  // 4 f / c: psi / pi per metre of distance
-  double cos_off[kMaxP], sin_off[kMaxP];
-  double source;
-  double dilation, alpha_max, alpha_min, t_min, sigma_cut;
+// gftorf_preprocess, read by the later kernels.  Kept in double and, for the
+// single-precision kernels, in float (conversions from double are slow on
+// this part, so FP32 kernels never touch the double copy).
+template <typename T>
+struct TableT {
+  FrameT<T> fr[kMaxFrames];
+  T kf[kMaxF];  // 4 f / c: psi / pi per metre of distance
+  T cos_off[kMaxP], sin_off[kMaxP];
+  T source;
+  T dilation, alpha_max, alpha_min, t_min, sigma_cut;
 };
+using Table = TableT<double>;
 
 // Device-side status block at the start of the workspace.
 struct Header {
@@ -72,7 +77,7 @@ struct Layout {
   int scatter_warps;
   int64_t cap;
   size_t off_header, off_table, off_rec, off_rect, off_zkey, off_zkey2,
-      off_ids, off_ids2, off_dhist, off_ecnt, off_bsum, off_tcnt, off_toff,
+      off_ids, off_ids2, off_dhist, off_dtot, off_ecnt, off_bsum, off_tcnt, off_toff,
       off_ranges,
       off_values, off_tfinal, off_nlast, off_g2d, total;
 };
@@ -109,6 +114,14 @@ void launch_render_bwd(const Layout& L, const Real* bg, const Real* dout,
 template <typename T>
 __host__ __device__ inline T* at(unsigned char* ws, size_t off) {
   return reinterpret_cast<T*>(ws + off);
+}
+
+// the batch table in the kernels' own precision (the float copy follows the
+// double one in the workspace)
+template <typename Real>
+__host__ __device__ inline const TableT<Real>* table_of(unsigned char* ws, size_t off) {
+  return sizeof(Real) == 8 ? reinterpret_cast<const TableT<Real>*>(ws + off)
+                           : reinterpret_cast<const TableT<Real>*>(ws + off + sizeof(Table));
 }
 
 __device__ __forceinline__ void set_status(Header* h, int32_t code) {

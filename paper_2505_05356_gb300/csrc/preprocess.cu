@@ -83,7 +83,7 @@ struct Geo {
 
 template <typename Real>
 __device__ __forceinline__ void geometry(const Params<Real>& P,
-                                         const FrameDev& fr, const Real* delta,
+                                         const FrameT<Real>& fr, const Real* delta,
                                          Real dil, Geo<Real>& Q) {
   const Real t = (Real)fr.time;
 #pragma unroll
@@ -161,7 +161,7 @@ __device__ __forceinline__ void geometry(const Params<Real>& P,
 
 template <typename Real, int F>
 __global__ void __launch_bounds__(256)
-    preprocess_kernel(gftorf_gaussians G, const Table* __restrict__ tab,
+    preprocess_kernel(gftorf_gaussians G, const TableT<Real>* __restrict__ tab,
                       Header* __restrict__ hdr, Real* __restrict__ rec,
                       uint2* __restrict__ rect, uint32_t* __restrict__ zkey,
                       int N, int TW, int TH, int tiles_x, int tiles_y,
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256)
   const int b = blockIdx.y;
   bool visible = false;
   if (g < N) {
-    const FrameDev& fr = tab->fr[b];
+    const FrameT<Real>& fr = tab->fr[b];
     Params<Real> P;
     load_params<Real>(G, g, P);
     const Real* delta =
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256)
 template <typename Real, int F>
 __global__ void __launch_bounds__(128)
     preprocess_bwd_kernel(gftorf_gaussians G, gftorf_gradients D,
-                          const Table* __restrict__ tab,
+                          const TableT<Real>* __restrict__ tab,
                           const uint2* __restrict__ rect,
                           const Real* __restrict__ g2d, int g2d_stride, int N,
                           int B) {
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(128)
       if (gdelta) gdelta[0] = gdelta[1] = gdelta[2] = Real(0);
       continue;
     }
-    const FrameDev& fr = tab->fr[b];
+    const FrameT<Real>& fr = tab->fr[b];
     const Real t = (Real)fr.time;
     const Real* delta =
         G.delta ? static_cast<const Real*>(G.delta) + bg * 3 : nullptr;
@@ -446,7 +446,7 @@ void launch_preprocess(const Layout& L, const gftorf_gaussians& g,
                        unsigned char* ws, cudaStream_t st) {
   if (L.N == 0) return;
   dim3 grid((L.N + 255) / 256, L.B);
-  auto* tab = at<const Table>(ws, L.off_table);
+  auto* tab = table_of<Real>(ws, L.off_table);
   auto* hdr = at<Header>(ws, L.off_header);
   auto* rec = at<Real>(ws, L.off_rec);
   auto* rect = at<uint2>(ws, L.off_rect);
@@ -471,7 +471,7 @@ void launch_preprocess_bwd(const Layout& L, const gftorf_gaussians& g,
                            cudaStream_t st) {
   if (L.N == 0) return;
   dim3 grid((L.N + 127) / 128);
-  auto* tab = at<const Table>(ws, L.off_table);
+  auto* tab = table_of<Real>(ws, L.off_table);
   auto* rect = at<const uint2>(ws, L.off_rect);
   auto* g2d = at<const Real>(ws, L.off_g2d);
 #define GFTORF_PREB(FF)                                                        \

@@ -230,7 +230,7 @@ struct kMinBlocks {
 
 template <typename Real, int F, int PPT, bool COUNT>
 __device__ __forceinline__ void render_tile_fwd(
-    const TileCtx& tc, const RenderGeom& rg, const Table* __restrict__ tab,
+    const TileCtx& tc, const RenderGeom& rg, const TableT<Real>* __restrict__ tab,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
     const Real* __restrict__ rec, const Real* __restrict__ bg,
     Real* __restrict__ out, Real* __restrict__ tfinal,
@@ -344,7 +344,7 @@ __device__ __forceinline__ void render_tile_fwd(
 
 template <typename Real, int F, int PPT, bool COUNT>
 __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
-    render_fwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
+    render_fwd_kernel(RenderGeom rg, const TableT<Real>* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
                       const uint32_t* __restrict__ values,
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
 // ---------------------------------------------------------------------------
 template <typename Real, int F, int PPT>
 __device__ __forceinline__ void render_tile_bwd(
-    const TileCtx& tc, const RenderGeom& rg, const Table* __restrict__ tab,
+    const TileCtx& tc, const RenderGeom& rg, const TableT<Real>* __restrict__ tab,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
     const Real* __restrict__ rec, const Real* __restrict__ bg,
     const Real* __restrict__ dout, const Real* __restrict__ tfinal,
@@ -592,7 +592,7 @@ __device__ __forceinline__ void render_tile_bwd(
 
 template <typename Real, int F, int PPT>
 __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
-    render_bwd_kernel(RenderGeom rg, const Table* __restrict__ tab,
+    render_bwd_kernel(RenderGeom rg, const TableT<Real>* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
                       const uint32_t* __restrict__ values,
@@ -677,7 +677,7 @@ void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
     cudaMemsetAsync(&hdr->queue[0], 0, sizeof(uint32_t), st);
   }
   kernel<<<grid, threads, smem, st>>>(
-      geom_of(L), at<const Table>(ws, L.off_table), hdr,
+      geom_of(L), table_of<Real>(ws, L.off_table), hdr,
       at<const uint2>(ws, L.off_ranges), at<const uint32_t>(ws, L.off_values),
       at<const Real>(ws, L.off_rec), bg, out, at<Real>(ws, L.off_tfinal),
       at<uint32_t>(ws, L.off_nlast), L.mode == 1);
@@ -706,7 +706,7 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
     cudaMemsetAsync(&hdr->queue[1], 0, sizeof(uint32_t), st);
   }
   kernel<<<grid, threads, smem, st>>>(
-      geom_of(L), at<const Table>(ws, L.off_table), hdr,
+      geom_of(L), table_of<Real>(ws, L.off_table), hdr,
       at<const uint2>(ws, L.off_ranges), at<const uint32_t>(ws, L.off_values),
       at<const Real>(ws, L.off_rec), bg, dout, at<const Real>(ws, L.off_tfinal),
       at<const uint32_t>(ws, L.off_nlast), at<Real>(ws, L.off_g2d),
