@@ -212,26 +212,32 @@ __global__ void __launch_bounds__(256)
         visible = true;
         rr = pack_rect(x0, y0, x1, y1);
         key = __float_as_uint((float)Q.p[2]);
-        Real* o = rec + bg * rec_stride;
+        // assemble the record in registers, store it as 16-byte vectors
+        constexpr int RSC = (7 + NF + 16 / sizeof(Real) - 1) / (16 / sizeof(Real)) *
+                            (16 / sizeof(Real));
+        Real o[RSC];
         o[0] = u;
         o[1] = v;
         o[2] = Real(-0.5 * kLog2e) * ca;
         o[3] = Real(-kLog2e) * cb;
         o[4] = Real(-0.5 * kLog2e) * cc;
         o[5] = log2(P.o);  // alpha = 2^(power2 + log2 o)
-        const Real A = (Real)tab->source * P.amp / (Q.d * Q.d);
+        const Real A = tab->source * P.amp / (Q.d * Q.d);
 #pragma unroll
         for (int f = 0; f < F; ++f) {
-          Real s, c;
-          sincospi_t((Real)tab->kf[f] * Q.d, &s, &c);
-          o[6 + 2 * f] = A * s;
-          o[7 + 2 * f] = A * c;
+          Real sn, cs;
+          sincospi_t(tab->kf[f] * Q.d, &sn, &cs);
+          o[6 + 2 * f] = A * sn;
+          o[7 + 2 * f] = A * cs;
         }
         o[6 + 2 * F] = A;
         o[6 + NF] = Real(1) / P.o;  // recovers G = alpha / o in the backward
 #pragma unroll
-        for (int k = 7 + NF; k < 7 + NF + 3; ++k)
-          if (k < rec_stride) o[k] = Real(0);
+        for (int k = 7 + NF; k < RSC; ++k) o[k] = Real(0);
+        float4* dst = reinterpret_cast<float4*>(rec + bg * RSC);
+        const float4* srcv = reinterpret_cast<const float4*>(o);
+#pragma unroll
+        for (int k = 0; k < RSC * (int)sizeof(Real) / 16; ++k) dst[k] = srcv[k];
       }
     }
     rect[bg] = rr;
