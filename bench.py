@@ -119,6 +119,28 @@ def _overrides(args):
     return o
 
 
+KERNEL_OF_STAGE = {"composite_bwd": "render_bwd_kernel", "composite_fwd": "render_fwd_kernel"}
+
+
+def _traffic(stage, frames):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu
+    capture (profiles/traffic.json), scaled to `frames`; None when the
+    kernel's source changed since the capture or none exists."""
+    import hashlib
+    kern = KERNEL_OF_STAGE.get(stage)
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if kern is None or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(kern)
+    src = os.path.join(ROOT, "paper_2505_05356_gb300", "csrc", "render_impl.cuh")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if not rec or rec.get("source_sha256_16") != h:
+        return None
+    return int(rec["dram_bytes_per_launch_2frames"] * frames / rec["frames_in_capture"])
+
+
 def max_over_ranks(x: float, world: int, device) -> float:
     """The largest value of x over all ranks (the job's time is its slowest
     rank's); identity on one process."""
@@ -280,7 +302,7 @@ def run_ours(args):
     achieved = amount / (stage_ms[dom] / 1e3)
     roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 2),
                 "peak": round(peak, 2), "unit": unit, "frac": round(achieved / peak, 4),
-                "traffic": None, "peak_source": peak_kind}
+                "traffic": _traffic(dom, B), "peak_source": peak_kind}
     stage_rows = {}
     for s_ in stages:
         b_, a_, u_, pk_ = work[s_]
