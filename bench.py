@@ -193,7 +193,7 @@ def run_ours(args):
     r = gftorf.Renderer(N, B, W, H, nF, nP, tile=tile, render_mode=mode,
                         pixels_per_thread=ppt)
     r.fit_capacity(p, fr, se, co, bg)
-    out = torch.empty((B, sc.sensor.n_channels, H, W), device="cuda")
+    out = torch.empty((B, sc.n_channels, H, W), device="cuda")
     grads = r.alloc_grads(p, bg)
 
     def step():
@@ -444,10 +444,10 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
     t1 = time.perf_counter()
     ora.render_pixels(one, 0, pix, sp)
     t2 = time.perf_counter()
-    dout = np.zeros((sc.sensor.n_channels, sc.height, sc.width))
+    dout = np.zeros((sc.n_channels, sc.height, sc.width))
     dout[:, pix[:, 1], pix[:, 0]] = 1.0
     nf = 2 * len(sc.sensor.freqs_hz) + 1
-    g2d = np.zeros((sc.n, 6 + nf))
+    g2d = np.zeros((sc.n, 7 + nf))
     lib = ora.lib()
     fr, se, co = ora.pack_frame(one, 0), ora.pack_sensor(one), ora.pack_consts(one)
     lib.ora_backward_2d(sc.n, ora._p(sp), ora._p(fr), ora._p(se), ora._p(co),

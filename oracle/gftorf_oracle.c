@@ -34,8 +34,10 @@ int ora_num_threads(void) {
 }
 
 static int n_feat(const double* sensor) { return 2 * (int)sensor[ORA_SE_F] + 1; }
-static int n_chan(const double* sensor) {
-  return (int)sensor[ORA_SE_F] * (int)sensor[ORA_SE_P] + 1;
+static int n_chan(const double* sensor, const double* consts) {
+  const int F = (int)sensor[ORA_SE_F];
+  return F * (int)sensor[ORA_SE_P] + 1 + (consts[ORA_CO_PHASOR] != 0.0 ? 2 * F : 0) +
+         (consts[ORA_CO_DEPTH] != 0.0 ? 1 : 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -44,7 +46,7 @@ static int n_chan(const double* sensor) {
 /* exact Jacobian; the forward pass uses the real part.                      */
 /* ------------------------------------------------------------------------ */
 
-/* 2D record: u, v, conic a, b, c, opacity, features[2F+1] */
+/* 2D record: u, v, conic a, b, c, opacity, features[2F+1], distance d */
 #define REC_U 0
 #define REC_V 1
 #define REC_A 2
@@ -158,6 +160,7 @@ static void project_complex(const cplx* th, const double* frame,
     rec[REC_FEAT + 2 * f + 1] = A * ccos(psi);
   }
   rec[REC_FEAT + 2 * F] = A;
+  rec[REC_FEAT + 2 * F + 1] = dist;  /* the mean depth's d_k (Eq. 5) */
 
   if (aux) {
     aux->z = creal(z);
@@ -213,7 +216,7 @@ void ora_project(int n, const double* means, const double* coeffs,
   const double er = eps[ORA_EPS_RECT];
 #pragma omp parallel for schedule(static)
   for (int g = 0; g < n; ++g) {
-    cplx th[ORA_NPARAM], rec[REC_FEAT + ORA_MAX_FEAT];
+    cplx th[ORA_NPARAM], rec[REC_FEAT + ORA_MAX_FEAT + 1];
     proj_aux aux;
     double* sp = splats + (size_t)g * ORA_SP_LEN;
     memset(sp, 0, sizeof(double) * ORA_SP_LEN);
@@ -326,7 +329,8 @@ typedef struct {
 
 /* Front-to-back walk of one pixel.  Returns the number of composited
  * Gaussians (steps[] filled if non-NULL), the accumulators acc[2F+1]
- * (sum alpha T^2 feature) and the final one-way transmittance. */
+ * (sum alpha T^2 feature), acc[2F+1] = sum alpha T d (mean depth, one-way T)
+ * and the final one-way transmittance. */
 static int composite_pixel(const double* splats, const cand_t* cand, int m,
                            double px, double py, const double* sensor,
                            const double* consts, const double* eps,
@@ -338,7 +342,7 @@ static int composite_pixel(const double* splats, const cand_t* cand, int m,
   double T = 1.0;
   int k = 0, flags = 0;
   double prev_z = -INFINITY;
-  for (int f = 0; f < nf; ++f) acc[f] = 0.0;
+  for (int f = 0; f <= nf; ++f) acc[f] = 0.0;
   for (int i = 0; i < m; ++i) {
     const double* sp = splats + (size_t)cand[i].g * ORA_SP_LEN;
     double dx = sp[ORA_SP_U] - px, dy = sp[ORA_SP_V] - py;
@@ -367,6 +371,7 @@ static int composite_pixel(const double* splats, const cand_t* cand, int m,
     if (t_next < tmin) break; /* early stop; this Gaussian is not composited */
     double w = alpha * T * T;  /* squared transmittance: round trip */
     for (int f = 0; f < nf; ++f) acc[f] += w * sp[ORA_SP_FEAT + f];
+    acc[nf] += alpha * T * sp[ORA_SP_D]; /* Eq. 5: one-way transmittance */
     if (steps) {
       steps[k].g = cand[i].g;
       steps[k].alpha = alpha;
@@ -385,9 +390,11 @@ static int composite_pixel(const double* splats, const cand_t* cand, int m,
 }
 
 /* raw samples from the accumulators: Q_fj = cos(phi_j) S_f + sin(phi_j) C_f
- * + bg_fj T, i.e. sum w A sin(psi + phi_j) + bg T; ambient = I + bg_amb T */
+ * + bg_fj T, i.e. sum w A sin(psi + phi_j) + bg T; ambient = I + bg_amb T;
+ * phasor (Eq. 3) = 2 (C_f + i S_f) + bg T; mean depth (Eq. 5) as summed */
 static void samples_from_acc(const double* acc, double T, const double* bg,
-                             const double* sensor, double* q, size_t stride) {
+                             const double* sensor, const double* consts,
+                             double* q, size_t stride) {
   const int F = (int)sensor[ORA_SE_F], P = (int)sensor[ORA_SE_P];
   for (int f = 0; f < F; ++f)
     for (int j = 0; j < P; ++j) {
@@ -395,7 +402,15 @@ static void samples_from_acc(const double* acc, double T, const double* bg,
       q[(size_t)(f * P + j) * stride] =
           cos(phi) * acc[2 * f] + sin(phi) * acc[2 * f + 1] + bg[f * P + j] * T;
     }
-  q[(size_t)(F * P) * stride] = acc[2 * F] + bg[F * P] * T;
+  int c = F * P;
+  q[(size_t)c * stride] = acc[2 * F] + bg[c] * T;
+  ++c;
+  if (consts[ORA_CO_PHASOR] != 0.0)
+    for (int f = 0; f < F; ++f, c += 2) {
+      q[(size_t)c * stride] = 2.0 * acc[2 * f + 1] + bg[c] * T;
+      q[(size_t)(c + 1) * stride] = 2.0 * acc[2 * f] + bg[c + 1] * T;
+    }
+  if (consts[ORA_CO_DEPTH] != 0.0) q[(size_t)c * stride] = acc[2 * F + 1];
 }
 
 static int max_candidates(int n) { return n > 0 ? n : 1; }
@@ -405,7 +420,7 @@ void ora_render_pixels(int n, const double* splats, const double* frame,
                        const double* bg, const double* eps, int npix,
                        const int32_t* pix, double* out, double* tfinal,
                        int32_t* ambig, int32_t* ncontrib) {
-  const int C = n_chan(sensor);
+  const int C = n_chan(sensor, consts);
   const int tw = (int)consts[ORA_CO_TW], th = (int)consts[ORA_CO_TH];
 #pragma omp parallel
   {
@@ -414,11 +429,11 @@ void ora_render_pixels(int n, const double* splats, const double* frame,
     for (int i = 0; i < npix; ++i) {
       int x = pix[2 * i], y = pix[2 * i + 1];
       int m = collect_candidates(n, splats, x / tw, y / th, cand);
-      double acc[ORA_MAX_FEAT], T;
+      double acc[ORA_MAX_FEAT + 1], T;
       int flags = 0;
       int k = composite_pixel(splats, cand, m, x + 0.5, y + 0.5, sensor, consts,
                               eps, acc, &T, &flags, NULL);
-      samples_from_acc(acc, T, bg, sensor, out + (size_t)i * C, 1);
+      samples_from_acc(acc, T, bg, sensor, consts, out + (size_t)i * C, 1);
       if (tfinal) tfinal[i] = T;
       if (ambig) ambig[i] = flags;
       if (ncontrib) ncontrib[i] = k;
@@ -447,12 +462,12 @@ void ora_render_frame(int n, const double* splats, const double* frame,
       int m = collect_candidates(n, splats, tx, ty, cand);
       for (int y = ty * th; y < (ty + 1) * th && y < H; ++y)
         for (int x = tx * tw; x < (tx + 1) * tw && x < W; ++x) {
-          double acc[ORA_MAX_FEAT], T;
+          double acc[ORA_MAX_FEAT + 1], T;
           int flags = 0;
           int k = composite_pixel(splats, cand, m, x + 0.5, y + 0.5, sensor,
                                   consts, eps, acc, &T, &flags, NULL);
           size_t p = (size_t)y * W + x;
-          samples_from_acc(acc, T, bg, sensor, out + p, HW);
+          samples_from_acc(acc, T, bg, sensor, consts, out + p, HW);
           if (tfinal) tfinal[p] = T;
           if (ambig) ambig[p] = flags;
           if (ncontrib) ncontrib[p] = k;
@@ -475,7 +490,8 @@ void ora_backward_2d(int n, const double* splats, const double* frame,
   const int tw = (int)consts[ORA_CO_TW], th = (int)consts[ORA_CO_TH];
   const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
   const int F = (int)sensor[ORA_SE_F], P = (int)sensor[ORA_SE_P];
-  const int C = F * P + 1, nf = 2 * F + 1, stride = 6 + nf;
+  const int C = n_chan(sensor, consts), nf = 2 * F + 1, stride = 7 + nf;
+  const int phasor = consts[ORA_CO_PHASOR] != 0.0, depth = consts[ORA_CO_DEPTH] != 0.0;
   const size_t HW = (size_t)W * H;
   const double zero_eps[ORA_EPS_LEN] = {0, 0, 0, 0};
 #pragma omp parallel
@@ -493,7 +509,7 @@ void ora_backward_2d(int n, const double* splats, const double* frame,
           for (int c = 0; c < C; ++c) any |= dout[c * HW + p] != 0.0;
           if (!any) continue;
           if (m < 0) m = collect_candidates(n, splats, tx, ty, cand);
-          double acc_fwd[ORA_MAX_FEAT], Tf;
+          double acc_fwd[ORA_MAX_FEAT + 1], Tf;
           int K = composite_pixel(splats, cand, m, x + 0.5, y + 0.5, sensor,
                                   consts, zero_eps, acc_fwd, &Tf, NULL, steps);
           /* dL/d(accumulator): fold the raw-sample gradients (Q is linear
@@ -510,14 +526,27 @@ void ora_backward_2d(int n, const double* splats, const double* frame,
             }
           gacc[2 * F] = dout[(size_t)(F * P) * HW + p];
           gT += bg[F * P] * gacc[2 * F];
+          int c = F * P + 1;
+          if (phasor)
+            for (int f = 0; f < F; ++f, c += 2) {  /* Re = 2 C_f, Im = 2 S_f */
+              double gre = dout[(size_t)c * HW + p], gim = dout[(size_t)(c + 1) * HW + p];
+              gacc[2 * f + 1] += 2.0 * gre;
+              gacc[2 * f] += 2.0 * gim;
+              gT += bg[c] * gre + bg[c + 1] * gim;
+            }
+          const double gD = depth ? dout[(size_t)c * HW + p] : 0.0;
           if (dbg)
-            for (int c = 0; c < C; ++c) atomic_add(&dbg[c], Tf * dout[c * HW + p]);
+            for (int cc = 0; cc < C; ++cc) {
+              if (depth && cc == C - 1) continue; /* Eq. 5 has no background */
+              atomic_add(&dbg[cc], Tf * dout[cc * HW + p]);
+            }
 
           /* back to front: Eq. S3 with squared transmittance,
            * dq/dalpha_k = T_k^2 (q_k + 2 (alpha_k - 1) acc_k),
            * acc_{k-1} = alpha_k q_k + (1 - alpha_k)^2 acc_k, acc_last = 0;
            * plus the background term d(bg T_N)/dalpha_k = -bg T_N/(1-alpha_k) */
           double acc[ORA_MAX_FEAT] = {0};
+          double accD = 0.0; /* one-way recursion of the mean depth */
           for (int k = K - 1; k >= 0; --k) {
             const step_t* s = &steps[k];
             const double* sp = splats + (size_t)s->g * ORA_SP_LEN;
@@ -529,6 +558,14 @@ void ora_backward_2d(int n, const double* splats, const double* frame,
               dL_dalpha += gacc[f] * T2 * (q + 2.0 * (a - 1.0) * acc[f]);
               atomic_add(&gg[6 + f], gacc[f] * a * T2);
               acc[f] = a * q + (1.0 - a) * (1.0 - a) * acc[f];
+            }
+            if (depth) {
+              /* d D / d alpha_k = T_k (d_k - accD_k), accD_{k-1} = alpha_k d_k
+               * + (1 - alpha_k) accD_k (3DGS recursion, one-way T) */
+              const double d = sp[ORA_SP_D];
+              dL_dalpha += gD * s->T * (d - accD);
+              atomic_add(&gg[6 + nf], gD * a * s->T);
+              accD = a * d + (1.0 - a) * accD;
             }
             if (s->clamped) continue; /* alpha = alpha_max does not vary */
             /* alpha = o G, G = exp(power) */
@@ -555,7 +592,7 @@ void ora_backward_params(int n, const double* means, const double* coeffs,
                          const double* sensor, const double* consts,
                          const double* splats, const double* g2d,
                          double* grads) {
-  const int nf = n_feat(sensor), stride = 6 + nf;
+  const int nf = n_feat(sensor), stride = 7 + nf;
   const double h = 1e-30; /* complex step */
 #pragma omp parallel for schedule(dynamic, 64)
   for (int g = 0; g < n; ++g) {
@@ -563,7 +600,7 @@ void ora_backward_params(int n, const double* means, const double* coeffs,
     int any = 0;
     for (int r = 0; r < stride; ++r) any |= gg[r] != 0.0;
     if (!any || splats[(size_t)g * ORA_SP_LEN + ORA_SP_VIS] == 0.0) continue;
-    cplx th[ORA_NPARAM], rec[REC_FEAT + ORA_MAX_FEAT];
+    cplx th[ORA_NPARAM], rec[REC_FEAT + ORA_MAX_FEAT + 1];
     gather_theta(g, means, coeffs, scales, quats, opacity, amplitude, delta, th);
     for (int i = 0; i < ORA_NPARAM; ++i) {
       cplx saved = th[i];

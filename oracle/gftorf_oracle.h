@@ -55,10 +55,13 @@ enum {
   ORA_SE_S = ORA_SE_OFF + ORA_MAX_P,      /* source intensity s */
   ORA_SE_LEN
 };
-/* screen-space constants */
+/* screen-space constants and optional output channels */
 enum {
   ORA_CO_DIL = 0, ORA_CO_AMAX, ORA_CO_AMIN, ORA_CO_TMIN, ORA_CO_GUARD,
-  ORA_CO_SIGMA, ORA_CO_TW, ORA_CO_TH, ORA_CO_LEN
+  ORA_CO_SIGMA, ORA_CO_TW, ORA_CO_TH,
+  ORA_CO_PHASOR, /* != 0: add the Eq. 3 phasor (Re, Im per frequency) */
+  ORA_CO_DEPTH,  /* != 0: add the Eq. 5 mean depth (one-way T)         */
+  ORA_CO_LEN
 };
 /* ambiguity margins (relative): a lower-precision implementation may take
  * a decision the other way when the oracle's value is this close to it */
@@ -108,7 +111,11 @@ void ora_project(int n, const double* means, const double* coeffs,
 /* Raw C-ToF samples for a list of pixels of one frame (Eq. 4).
  * pix[npix*2] = (x, y) pixel indices; bg[C]; out[npix*C]; tfinal[npix];
  * ambig[npix] (ORA_AMB_* flags); ncontrib[npix] (# composited Gaussians).
- * C = F*P + 1 (raw samples frequency-major, then ambient). */
+ * Channels: the F*P raw samples (frequency-major), the ambient channel, then
+ * with ORA_CO_PHASOR the phasor Re, Im of each frequency (Eq. 3:
+ * p = p_bg T_N + sum 2 A_k exp(i psi_k) alpha_k T_k^2), then with
+ * ORA_CO_DEPTH the mean depth sum d_k alpha_k T_k (Eq. 5, one-way T, no
+ * background term). */
 void ora_render_pixels(int n, const double* splats, const double* frame,
                        const double* sensor, const double* consts,
                        const double* bg, const double* eps, int npix,
@@ -123,9 +130,11 @@ void ora_render_frame(int n, const double* splats, const double* frame,
                       double* tfinal, int32_t* ambig, int32_t* ncontrib);
 
 /* Gradient of L = sum dout * out for one frame w.r.t. the per-Gaussian 2D
- * record (u, v, conic a, b, c, opacity, features[2F+1]) -- Eq. S3 recursion.
- * dout[C*H*W]; pixels whose dout is all zero are skipped.
- * g2d[n * (6 + 2F+1)] is ACCUMULATED into; dbg[C] accumulated (may be NULL). */
+ * record (u, v, conic a, b, c, opacity, features[2F+1], distance d) -- the
+ * Eq. S3 recursion for the squared-transmittance channels and the 3DGS
+ * one-way recursion for the mean depth.  dout[C*H*W]; pixels whose dout is
+ * all zero are skipped.  g2d[n * (7 + 2F+1)] is ACCUMULATED into; dbg[C]
+ * accumulated (may be NULL). */
 void ora_backward_2d(int n, const double* splats, const double* frame,
                      const double* sensor, const double* consts,
                      const double* bg, const double* dout, double* g2d,

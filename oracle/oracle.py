@@ -19,7 +19,7 @@ _LIB = None
 MAX_F, MAX_P = 4, 8
 FR_LEN = 20
 SE_LEN = 1 + MAX_F + 1 + MAX_P + 1
-CO_LEN = 8
+CO_LEN = 10
 NPARAM = 24
 SP = dict(VIS=0, U=1, V=2, CA=3, CB=4, CC=5, OPA=6, Z=7, D=8, RAD=9,
           X0=10, Y0=11, X1=12, Y1=13, MX0=14, MY0=15, MX1=16, MY1=17,
@@ -106,7 +106,16 @@ def pack_sensor(scene) -> np.ndarray:
 def pack_consts(scene) -> np.ndarray:
     k = scene.consts
     return np.array([k.dilation, k.alpha_max, k.alpha_min, k.t_min, k.guard,
-                     k.sigma_cut, k.tile_w, k.tile_h], np.float64)
+                     k.sigma_cut, k.tile_w, k.tile_h, float(getattr(k, "phasor", False)),
+                     float(getattr(k, "depth", False))], np.float64)
+
+
+def n_channels(scene) -> int:
+    """Output channels: F*P raw + ambient (+ 2F phasor) (+ depth)."""
+    F = len(scene.sensor.freqs_hz)
+    k = scene.consts
+    return (F * len(scene.sensor.offsets_rad) + 1 + (2 * F if getattr(k, "phasor", False) else 0)
+            + (1 if getattr(k, "depth", False) else 0))
 
 
 def _copy64(a):
@@ -148,7 +157,7 @@ def render_frame(scene, b: int, splats=None, eps=EPS_NONE, bg=None):
     """(out (C,H,W), tfinal (H,W), ambig (H,W), ncontrib (H,W)) for frame b."""
     if splats is None:
         splats = project(scene, b, eps)
-    C, H, W = scene.sensor.n_channels, scene.height, scene.width
+    C, H, W = n_channels(scene), scene.height, scene.width
     out = np.zeros((C, H, W))
     tf = np.zeros((H, W))
     amb = np.zeros((H, W), np.int32)
@@ -166,7 +175,7 @@ def render_pixels(scene, b: int, pix: np.ndarray, splats=None, eps=EPS_NONE):
     if splats is None:
         splats = project(scene, b, eps)
     pix = np.ascontiguousarray(pix, np.int32)
-    k, C = pix.shape[0], scene.sensor.n_channels
+    k, C = pix.shape[0], n_channels(scene)
     out = np.zeros((k, C))
     tf = np.zeros(k)
     amb = np.zeros(k, np.int32)
@@ -194,12 +203,12 @@ def backward(scene, dout: np.ndarray, params: Params = None, want_2d=False):
 
     Returns a dict with means (N,3), coeffs (N,3,3), scales (N,3), quats (N,4),
     opacity (N,), amplitude (N,), delta (B,N,3), bg (B,C) and, when want_2d,
-    g2d (B, N, 6+2F+1) -- gradients w.r.t. (u, v, conic a, b, c, opacity,
-    features)."""
+    g2d (B, N, 7+2F+1) -- gradients w.r.t. (u, v, conic a, b, c, opacity,
+    features, distance)."""
     P = params or Params(scene)
     n, B = scene.n, scene.frames
     nf = 2 * len(scene.sensor.freqs_hz) + 1
-    C = scene.sensor.n_channels
+    C = n_channels(scene)
     grads = np.zeros((n, NPARAM))
     gdelta = np.zeros((B, n, 3))
     gbg = np.zeros((B, C))
@@ -208,7 +217,7 @@ def backward(scene, dout: np.ndarray, params: Params = None, want_2d=False):
     for b in range(B):
         sp = project(scene, b, EPS_NONE, P)
         fr = pack_frame(scene, b)
-        g2d = np.zeros((n, 6 + nf))
+        g2d = np.zeros((n, 7 + nf))
         db = np.ascontiguousarray(dout[b], np.float64)
         lib().ora_backward_2d(n, _p(sp), _p(fr), _p(se), _p(co),
                               _p(_f64(scene.bg[b])), _p(db), _p(g2d), _p(gbg[b]))

@@ -63,6 +63,8 @@ class Consts:
     sigma_cut: float = 3.0
     tile_w: int = 16
     tile_h: int = 16
+    phasor: bool = False  # extra Eq. 3 phasor channels (Re, Im per frequency)
+    depth: bool = False   # extra Eq. 5 mean-depth channel
 
     def rounded(self) -> "Consts":
         """The same constants rounded to float32 (what a single-precision
@@ -70,7 +72,7 @@ class Consts:
         r = lambda v: float(np.float32(v))
         return Consts(r(self.dilation), r(self.alpha_max), r(self.alpha_min),
                       r(self.t_min), r(self.guard), r(self.sigma_cut),
-                      self.tile_w, self.tile_h)
+                      self.tile_w, self.tile_h, self.phasor, self.depth)
 
 
 @dataclasses.dataclass
@@ -91,6 +93,13 @@ class Scene:
     @property
     def n(self) -> int:
         return int(self.means.shape[0])
+
+    @property
+    def n_channels(self) -> int:
+        """Raw samples + ambient (+ phasor Re, Im per frequency) (+ depth)."""
+        F = len(self.sensor.freqs_hz)
+        return (self.sensor.n_channels + (2 * F if self.consts.phasor else 0) +
+                (1 if self.consts.depth else 0))
 
     @property
     def frames(self) -> int:
@@ -153,7 +162,8 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
     """Build one of the named synthetic workloads (see module docstring).
 
     Overrides: n, width, height, frames, freqs_hz, offsets_rad, tile, bg
-    ('zero' | 'random'), z_range, coeff_std, visible_min, consts.
+    ('zero' | 'random'), z_range, coeff_std, visible_min, consts, phasor,
+    depth.
     """
     rng = np.random.default_rng(seed)
     if name == "static_1k":
@@ -191,9 +201,12 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
             delta[b, hide, 0] = 10.0
     sensor = Sensor([float(F32(f)) for f in d["freqs_hz"]],
                     [float(F32(o)) for o in d["offsets_rad"]], 1.0)
-    consts = d.get("consts") or Consts(tile_w=d["tile"][0], tile_h=d["tile"][1])
+    consts = d.get("consts") or Consts(tile_w=d["tile"][0], tile_h=d["tile"][1],
+                                       phasor=d.get("phasor", False),
+                                       depth=d.get("depth", False))
     consts = consts.rounded()
-    C = sensor.n_channels
+    C = sensor.n_channels + (2 * len(sensor.freqs_hz) if consts.phasor else 0) + \
+        (1 if consts.depth else 0)
     if d["bg"] == "random":
         bg = rng.uniform(-1.0, 1.0, (frames, C)).astype(F32)
     else:
@@ -206,7 +219,7 @@ def random_dout(scene: Scene, seed: int = 1, density: float = 1.0) -> np.ndarray
     """A seeded loss gradient dL/d(out), shape (B, C, H, W), float32.
     density < 1 keeps only that fraction of pixels (the rest exactly 0)."""
     rng = np.random.default_rng(seed)
-    B, C, H, W = scene.frames, scene.sensor.n_channels, scene.height, scene.width
+    B, C, H, W = scene.frames, scene.n_channels, scene.height, scene.width
     g = rng.standard_normal((B, C, H, W)).astype(F32)
     if density < 1.0:
         keep = rng.random((B, 1, H, W)) < density

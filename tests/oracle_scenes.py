@@ -28,13 +28,14 @@ def tiny_scene(positions, scales, quats=None, opacity=None, amplitude=None,
     if world_to_cam is not None:
         cam.world_to_cam = np.asarray(world_to_cam, np.float64)
     frames = len(times)
-    C = sensor.n_channels
+    consts = consts or scenes.Consts()
+    C = sensor.n_channels + (2 * len(freqs) if consts.phasor else 0) + (1 if consts.depth else 0)
     if bg is None:
         bg = np.zeros((frames, C))
     bg = np.broadcast_to(np.asarray(bg, np.float64), (frames, C)).copy()
     return scenes.Scene(positions, coeffs, scales, quats, opacity, amplitude,
                         np.asarray(times, np.float64), [cam] * frames, delta,
-                        sensor, consts or scenes.Consts(), bg)
+                        sensor, consts, bg)
 
 
 def at_pixel(cam, px, py, z):

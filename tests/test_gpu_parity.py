@@ -93,7 +93,7 @@ def test_empty_scene_and_all_culled():
     sc.means[:, 2] = -1.0
     res = run_gpu(sc, scenes.random_dout(sc, 2))
     assert res["status"] == (gftorf.OK, 0)
-    for c in range(sc.sensor.n_channels):
+    for c in range(sc.n_channels):
         assert np.all(res["out"][0, c] == sc.bg[0, c].astype(np.float64))
     assert np.all(res["tfinal"] == 1.0) and np.all(res["nlast"] == 0)
     for k in ("means", "scales", "quats", "opacity", "amplitude"):

@@ -375,7 +375,7 @@ def _loss(sc, dout, params):
 def test_gradient_matches_central_differences(seed, freqs):
     sc = _fd_scene(seed, freqs=freqs)
     rng = np.random.default_rng(100 + seed)
-    dout = rng.standard_normal((sc.frames, sc.sensor.n_channels, sc.height, sc.width))
+    dout = rng.standard_normal((sc.frames, sc.n_channels, sc.height, sc.width))
     g = ora.backward(sc, dout)
     base = ora.Params(sc)
     L0, _ = _loss(sc, dout, base)
@@ -448,3 +448,82 @@ def test_s3_recursion_against_direct_derivative():
     g = ora.backward(sc, dout, want_2d=True)
     # d L / d o_k = d L / d alpha_k * G_k with G_k = 1 at the centre
     np.testing.assert_allclose(g["g2d"][0][:, 5], grads, rtol=1e-10, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# extra channels: phasor (Eq. 3) and mean depth (Eq. 5)
+# --------------------------------------------------------------------------
+
+def _consts(**kw):
+    from paper_2505_05356_gb300 import scenes
+    return scenes.Consts(**kw)
+
+
+def test_phasor_and_depth_single_and_two_gaussians():
+    """One opaque Gaussian: phasor = 2 (0.99 A) exp(i psi) + p_bg T_N (Eq. 3)
+    and mean depth = 0.99 d (Eq. 5, one-way T).  Two Gaussians: the depth
+    weights are alpha_1 and alpha_2 (1 - alpha_1) -- one-way, unlike the
+    squared transmittance of the C-ToF channels."""
+    cam = tiny_scene([[0, 0, 1]], 0.1).cameras[0]
+    p = np.array(at_pixel(cam, 25.5, 18.5, 1.0))
+    d = 2.3
+    pos = p / np.linalg.norm(p) * d
+    bg = np.array([0.1, 0.2, 0.3, 0.4, -0.3, 0.7, -0.2, 5.0])  # last: depth (unused)
+    sc = tiny_scene([pos], 0.03, opacity=[0.9999], amplitude=[0.8], bg=bg,
+                    consts=_consts(phasor=True, depth=True))
+    q, T, k = _render_px(sc, 25, 18)
+    assert q.shape == (8,) and k == 1
+    A = 0.8 / d ** 2
+    psi = 4 * math.pi * d * 30e6 / C_LIGHT
+    re, im = q[5] - 0.01 * bg[5], q[6] - 0.01 * bg[6]
+    assert math.hypot(re, im) == pytest.approx(2 * 0.99 * A, rel=1e-12)
+    assert math.atan2(im, re) % (2 * math.pi) == pytest.approx(psi % (2 * math.pi), abs=1e-12)
+    assert q[7] == pytest.approx(0.99 * d, rel=1e-12)
+    # two Gaussians on the pixel
+    pa, pb = at_pixel(cam, 20.5, 30.5, 1.2), at_pixel(cam, 20.5, 30.5, 2.5)
+    sc2 = tiny_scene([pb, pa], 0.03, opacity=[0.7, 0.4], consts=_consts(depth=True))
+    q2, T2, k2 = _render_px(sc2, 20, 30)
+    d1, d2 = np.linalg.norm(pa), np.linalg.norm(pb)
+    assert q2[5] == pytest.approx(0.4 * d1 + 0.7 * (1 - 0.4) * d2, rel=1e-12)
+
+
+def test_phasor_equals_quad_differences():
+    """With a common bias on each quad pair the phasor is the quad
+    differences of Sec. 3: Re = Q_pi/2 - Q_3pi/2, Im = Q_0 - Q_pi."""
+    from paper_2505_05356_gb300 import scenes
+    sc = scenes.make_scene("static_1k", 13, n=300, width=40, height=32, phasor=True)
+    sc.sensor.offsets_rad = list(GOLDEN["phase_offsets_rad"]["value"])
+    sc.bg[:] = 0.0
+    out, tf, _, _ = ora.render(sc)
+    np.testing.assert_allclose(out[0, 5], out[0, 1] - out[0, 3], atol=1e-12)
+    np.testing.assert_allclose(out[0, 6], out[0, 0] - out[0, 2], atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_gradient_with_phasor_and_depth_matches_central_differences(seed):
+    sc = _fd_scene(seed, n=5, freqs=(30e6, 80e6))
+    sc.consts = _consts(phasor=True, depth=True)
+    C = ora.n_channels(sc)
+    assert C == 8 + 1 + 4 + 1
+    sc.bg = np.random.default_rng(seed).uniform(-1, 1, (sc.frames, C))
+    rng = np.random.default_rng(200 + seed)
+    dout = rng.standard_normal((sc.frames, C, sc.height, sc.width))
+    g = ora.backward(sc, dout)
+    base = ora.Params(sc)
+    L0, _ = _loss(sc, dout, base)
+    checked = 0
+    for name in ["means", "opacity", "amplitude", "scales", "quats", "coeffs"]:
+        flat = getattr(base, name).reshape(-1)
+        for i in range(flat.size):
+            h = 1e-6 * max(1.0, abs(flat[i]))
+            vals = []
+            for sgn in (1, -1):
+                P = ora.Params(sc)
+                getattr(P, name).reshape(-1)[i] = flat[i] + sgn * h
+                vals.append(_loss(sc, dout, P)[0])
+            fd = (vals[0] - vals[1]) / (2 * h)
+            if abs((vals[0] - L0) / h - (L0 - vals[1]) / h) > 1e-3 * (abs(fd) + 1e-3):
+                continue
+            assert g[name].reshape(-1)[i] == pytest.approx(fd, rel=2e-5, abs=2e-6 * (1 + abs(fd)))
+            checked += 1
+    assert checked > 80
