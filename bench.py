@@ -112,6 +112,9 @@ class ClockSampler:
 def _overrides(args):
     """Smaller variants of the workload (profiling captures only)."""
     o = {}
+    for ch in (args.extra_channels or "").split(","):
+        if ch in ("phasor", "depth"):
+            o[ch] = True
     if args.frames:
         o["frames"] = args.frames
     if args.n:
@@ -177,6 +180,7 @@ def run_ours(args):
     sc = scenes.make_scene(args.workload, seed=rank, **_overrides(args))
     B, N, W, H = sc.frames, sc.n, sc.width, sc.height
     nF, nP = len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad)
+    xflags = gftorf.flags_from_scene(sc)
     p = gftorf.params_from_scene(sc)
     fr = gftorf.frames_from_scene(sc)
     se = gftorf.sensor_from_scene(sc)
@@ -188,12 +192,13 @@ def run_ours(args):
     tuned = None
     if args.autotune:
         from paper_2505_05356_gb300 import autotune
-        tuned = autotune.autotune(N, B, W, H, nF, nP, p, fr, se, co, bg, dout, steps=2)
+        tuned = autotune.autotune(N, B, W, H, nF, nP, p, fr, se, co, bg, dout, steps=2,
+                                  flags=xflags)
         tile, ppt, mode = tuned["tile"], tuned["ppt"], tuned["mode"]
     r = gftorf.Renderer(N, B, W, H, nF, nP, tile=tile, render_mode=mode,
-                        pixels_per_thread=ppt)
+                        pixels_per_thread=ppt, flags=xflags)
     r.fit_capacity(p, fr, se, co, bg)
-    out = torch.empty((B, sc.n_channels, H, W), device="cuda")
+    out = torch.empty((B, r.C, H, W), device="cuda")
     grads = r.alloc_grads(p, bg)
 
     def step():
@@ -274,7 +279,7 @@ def run_ours(args):
     # --- algorithmic work of this batch: evaluated (pixel, Gaussian) pairs
     # counted by the forward's counting instantiation on the same inputs ---
     rc = gftorf.Renderer(N, B, W, H, nF, nP, tile=tile, render_mode=mode,
-                         pixels_per_thread=ppt, flags=gftorf.FLAG_COUNT_PAIRS,
+                         pixels_per_thread=ppt, flags=gftorf.FLAG_COUNT_PAIRS | xflags,
                          max_instances=r.capacity)
     rc.preprocess(p, fr, se, co)
     rc.render_fwd(bg)
@@ -349,7 +354,7 @@ def run_ours(args):
     plain = None
     if not args.skip_plain and rank == 0:
         r1 = gftorf.Renderer(N, 1, W, H, nF, nP, tile=tile, render_mode=0,
-                             pixels_per_thread=ppt,
+                             pixels_per_thread=ppt, flags=xflags,
                              max_instances=max(1024, int(r.capacity / B * 1.6)))
         gacc = {k: torch.zeros_like(v) for k, v in grads.items() if k not in ("bg", "delta")}
         p1s = []
@@ -400,6 +405,7 @@ def run_ours(args):
                                    "%d timesteps per batch, 30 MHz x 4 offsets + ambient, "
                                    "30-100%% visible per frame" % (args.workload, N, W, H, B),
                        "frames_per_step": B, "tile": "%dx%d" % tuple(tile),
+                       "channels": r.C,
                        "pixels_per_thread": ppt,
                        "render_mode": "persistent" if mode == 1 else "grid",
                        "autotuned": tuned is not None,
@@ -544,6 +550,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--frames", type=int, default=0, help="override frames per batch")
     ap.add_argument("--n", type=int, default=0, help="override the Gaussian count")
+    ap.add_argument("--extra-channels", default="",
+                    help="comma list of extra outputs: phasor (Eq. 3), depth (Eq. 5)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

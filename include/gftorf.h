@@ -40,7 +40,9 @@
  *     p (camera frame) projects to (fx p_x / p_z + cx, fy p_y / p_z + cy).
  *   - Outputs are channel-major: out[frame][channel][y][x]; channels are the
  *     F*P raw samples, frequency-major (f0 phi0, f0 phi1, ..., f1 phi0, ...),
- *     then the ambient channel; C = F*P + 1.
+ *     then the ambient channel, then (GFTORF_FLAG_PHASOR) Re, Im of the
+ *     phasor of each frequency, then (GFTORF_FLAG_DEPTH) the mean depth;
+ *     C = F*P + 1 (+ 2F) (+ 1).
  */
 #ifndef GFTORF_H
 #define GFTORF_H
@@ -81,6 +83,14 @@ typedef enum { GFTORF_F32 = 0, GFTORF_F64 = 1 } gftorf_dtype;
  * stops it), readable with gftorf_read_counters.  Same outputs; a separate
  * kernel instantiation, for measurement. */
 #define GFTORF_FLAG_COUNT_PAIRS 2
+/* gftorf_dims.flags: extra output channels after the raw samples and the
+ * ambient channel.  PHASOR adds, per frequency, the real and imaginary part
+ * of the C-ToF phasor of Eq. 3, p = p_bg T_N + sum 2 A_k exp(i psi_k)
+ * alpha_k T_k^2 (two channels, background from bg).  DEPTH adds the mean
+ * depth of Eq. 5, sum d_k alpha_k T_k with the ONE-WAY transmittance and no
+ * background term (its bg entry is ignored, its dL/dbg is 0). */
+#define GFTORF_FLAG_PHASOR 4
+#define GFTORF_FLAG_DEPTH 8
 
 /* Static problem shape.  One workspace serves one dims value. */
 typedef struct {

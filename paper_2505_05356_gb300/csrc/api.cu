@@ -36,7 +36,9 @@ bool dims_ok(const gftorf_dims* d) {
   const int ppt = d->pixels_per_thread;
   if (ppt != 0 && ppt != 1 && ppt != 2 && ppt != 4) return false;
   if (d->tile_w * d->tile_h / (ppt ? ppt : 2) < 32) return false;  // a full warp per tile
-  if (d->flags & ~(GFTORF_FLAG_NO_TILE_CULL | GFTORF_FLAG_COUNT_PAIRS)) return false;
+  if (d->flags & ~(GFTORF_FLAG_NO_TILE_CULL | GFTORF_FLAG_COUNT_PAIRS | GFTORF_FLAG_PHASOR |
+                   GFTORF_FLAG_DEPTH))
+    return false;
   if (d->max_instances < 0 || d->max_instances > (int64_t)0xFFFFFFFFll) return false;
   const int64_t tiles = (int64_t)((d->width + d->tile_w - 1) / d->tile_w) *
                         ((d->height + d->tile_h - 1) / d->tile_h);
@@ -55,12 +57,15 @@ Layout make_layout(const gftorf_dims* d) {
   L.ppt = d->pixels_per_thread ? d->pixels_per_thread : 2;
   L.cull = (d->flags & GFTORF_FLAG_NO_TILE_CULL) ? 0 : 1;
   L.count_pairs = (d->flags & GFTORF_FLAG_COUNT_PAIRS) ? 1 : 0;
+  L.phasor = (d->flags & GFTORF_FLAG_PHASOR) ? 1 : 0;
+  L.depth = (d->flags & GFTORF_FLAG_DEPTH) ? 1 : 0;
+  L.C = L.F * L.P + 1 + (L.phasor ? 2 * L.F : 0) + (L.depth ? 1 : 0);
   L.tiles_x = (L.W + L.TW - 1) / L.TW;
   L.tiles_y = (L.H + L.TH - 1) / L.TH;
   L.NT = L.tiles_x * L.tiles_y;
   const int per16 = 16 / L.real_size;
-  L.rec_stride = (7 + L.NF + per16 - 1) / per16 * per16;
-  L.g2d_stride = 6 + L.NF;
+  L.rec_stride = (8 + L.NF + per16 - 1) / per16 * per16;
+  L.g2d_stride = 7 + L.NF;
   L.n_dblk = (L.N + kSortTile - 1) / kSortTile;
   L.n_chunk = (int)((d->max_instances + kChunk - 1) / kChunk) + L.B;
   L.n_scan = (int)(((size_t)L.B * L.N + kScanTile - 1) / kScanTile);

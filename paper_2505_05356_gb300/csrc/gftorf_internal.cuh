@@ -68,6 +68,7 @@ struct Layout {
   int ppt;   // pixels per compositing thread (1, 2 or 4)
   int cull;  // drop (Gaussian, tile) pairs that cannot reach alpha_min
   int count_pairs;  // count evaluated (pixel, Gaussian) pairs in the forward
+  int phasor, depth;  // extra output channels (Eq. 3 phasor, Eq. 5 depth)
   int tiles_x, tiles_y, NT;
   int rec_stride;  // Reals per projected record (16-byte multiple)
   int g2d_stride;  // Reals per 2D-gradient row
@@ -100,12 +101,28 @@ void launch_footprints(const Layout& L, const float* u, const float* v,
 void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st);
 void launch_export_keys(const Layout& L, uint64_t* keys, unsigned char* ws,
                         cudaStream_t st);
+template <typename Real, bool DEPTH>
+void launch_render_fwd_t(const Layout& L, const Real* bg, Real* out,
+                         unsigned char* ws, cudaStream_t st);
+template <typename Real, bool DEPTH>
+void launch_render_bwd_t(const Layout& L, const Real* bg, const Real* dout,
+                         Real* dbg, unsigned char* ws, cudaStream_t st);
 template <typename Real>
-void launch_render_fwd(const Layout& L, const Real* bg, Real* out,
-                       unsigned char* ws, cudaStream_t st);
+inline void launch_render_fwd(const Layout& L, const Real* bg, Real* out,
+                              unsigned char* ws, cudaStream_t st) {
+  if (L.depth)
+    launch_render_fwd_t<Real, true>(L, bg, out, ws, st);
+  else
+    launch_render_fwd_t<Real, false>(L, bg, out, ws, st);
+}
 template <typename Real>
-void launch_render_bwd(const Layout& L, const Real* bg, const Real* dout,
-                       Real* dbg, unsigned char* ws, cudaStream_t st);
+inline void launch_render_bwd(const Layout& L, const Real* bg, const Real* dout,
+                              Real* dbg, unsigned char* ws, cudaStream_t st) {
+  if (L.depth)
+    launch_render_bwd_t<Real, true>(L, bg, dout, dbg, ws, st);
+  else
+    launch_render_bwd_t<Real, false>(L, bg, dout, dbg, ws, st);
+}
 
 // ---------------------------------------------------------------------------
 // device helpers

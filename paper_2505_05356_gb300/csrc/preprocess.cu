@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256)
         rr = pack_rect(x0, y0, x1, y1);
         key = __float_as_uint((float)Q.p[2]);
         // assemble the record in registers, store it as 16-byte vectors
-        constexpr int RSC = (7 + NF + 16 / sizeof(Real) - 1) / (16 / sizeof(Real)) *
+        constexpr int RSC = (8 + NF + 16 / sizeof(Real) - 1) / (16 / sizeof(Real)) *
                             (16 / sizeof(Real));
         Real o[RSC];
         o[0] = u;
@@ -232,8 +232,9 @@ __global__ void __launch_bounds__(256)
         }
         o[6 + 2 * F] = A;
         o[6 + NF] = Real(1) / P.o;  // recovers G = alpha / o in the backward
+        o[7 + NF] = Q.d;            // d_k of the mean depth (Eq. 5)
 #pragma unroll
-        for (int k = 7 + NF; k < RSC; ++k) o[k] = Real(0);
+        for (int k = 8 + NF; k < RSC; ++k) o[k] = Real(0);
         float4* dst = reinterpret_cast<float4*>(rec + bg * RSC);
         const float4* srcv = reinterpret_cast<const float4*>(o);
 #pragma unroll
@@ -271,13 +272,14 @@ __global__ void __launch_bounds__(128)
     Real* gdelta = D.delta ? static_cast<Real*>(D.delta) + bg * 3 : nullptr;
     const uint2 rr = rect[bg];
     const Real* gr = g2d + bg * g2d_stride;
-    Real gu = 0, gv = 0, ga = 0, gb = 0, gcn = 0, gop = 0, gf[NF];
+    Real gu = 0, gv = 0, ga = 0, gb = 0, gcn = 0, gop = 0, gdist = 0, gf[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) gf[f] = 0;
     bool any = false;
     if (rr.x != rr.y || rr.x != 0) {  // visible in this frame
       gu = gr[0], gv = gr[1], ga = gr[2], gb = gr[3], gcn = gr[4], gop = gr[5];
-      any = gu != 0 || gv != 0 || ga != 0 || gb != 0 || gcn != 0 || gop != 0;
+      gdist = gr[6 + NF];  // through the mean depth's d_k
+      any = gu != 0 || gv != 0 || ga != 0 || gb != 0 || gcn != 0 || gop != 0 || gdist != 0;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         gf[f] = gr[6 + f];
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(128)
       gd += gpsi * Real(kPiD) * kf;
     }
     gamp += gA * (Real)tab->source * id * id;
-    gd += gA * Real(-2) * A * id;
+    gd += gA * Real(-2) * A * id + gdist;
     Real gp[3] = {gd * Q.p[0] * id, gd * Q.p[1] * id, gd * Q.p[2] * id};
 
     // --- mean 2D ---

@@ -25,9 +25,7 @@
 
 #include "gftorf_internal.cuh"
 
-#ifndef GFTORF_PPT4_MIN_BLOCKS
-#define GFTORF_PPT4_MIN_BLOCKS 0
-#endif
+
 
 namespace gftorf {
 namespace {
@@ -35,14 +33,14 @@ namespace {
 constexpr double kLn2 = 0.69314718055994530942;
 
 // Reals per record: u, v, scaled conic (3), log2 o, 2F+1 features, 1/o,
-// padded to 16 bytes
+// distance d, padded to 16 bytes
 template <int F>
 struct RecStrideF {
-  static constexpr int value = ((7 + 2 * F + 1) + 3) / 4 * 4;
+  static constexpr int value = ((8 + 2 * F + 1) + 3) / 4 * 4;
 };
 template <int F>
 struct RecStrideD {
-  static constexpr int value = ((7 + 2 * F + 1) + 1) / 2 * 2;
+  static constexpr int value = ((8 + 2 * F + 1) + 1) / 2 * 2;
 };
 template <typename Real, int F>
 constexpr int rec_stride() {
@@ -128,7 +126,7 @@ __device__ __forceinline__ TileCtx tile_of(uint32_t item, int NT, int tiles_x) {
 }
 
 struct RenderGeom {
-  int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B, cull;
+  int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B, cull, phasor;
 };
 
 // Can the Gaussian of record r reach alpha_min at some pixel centre of the
@@ -221,14 +219,15 @@ __device__ __forceinline__ Real log2_oG(const Real* r, const Column<Real>& c, Re
   return fma_rn(fma_rn(r[4], dy, c.cb_dx), dy, c.a_lo);
 }
 
-// resident CTAs per SM the compiler is asked to fit (register budget); only
-// the 4-pixel variant (128 threads per 16x32 tile) is limited by registers
-template <int PPT>
+// Resident CTAs per SM the compiler is asked to fit (register budget).  Only
+// the 4-pixel variants (128 threads per 16x32 tile) are register limited: the
+// forward keeps 7 CTAs (<= 72 registers), the backward 6 (<= 80).
+template <int PPT, bool BWD>
 struct kMinBlocks {
-  static constexpr int value = PPT == 4 ? GFTORF_PPT4_MIN_BLOCKS : 0;
+  static constexpr int value = PPT == 4 ? (BWD ? 6 : 7) : 0;
 };
 
-template <typename Real, int F, int PPT, bool COUNT>
+template <typename Real, int F, int PPT, bool DEPTH, bool COUNT>
 __device__ __forceinline__ void render_tile_fwd(
     const TileCtx& tc, const RenderGeom& rg, const TableT<Real>* __restrict__ tab,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
@@ -256,12 +255,13 @@ __device__ __forceinline__ void render_tile_fwd(
   const uint2 range = ranges[(size_t)tc.b * rg.NT + tc.tile];
   const Real* frec = rec + (size_t)tc.b * rg.N * RS;
 
-  Real T[PPT], acc[PPT][NF];
+  Real T[PPT], acc[PPT][NF], accD[PPT];  // accD: mean depth (DEPTH only)
   uint32_t last[PPT];
   uint32_t evals = 0;  // evaluated pairs (COUNT only)
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     T[k] = 1;
+    accD[k] = 0;
     last[k] = range.x;
 #pragma unroll
     for (int f = 0; f < NF; ++f) acc[k][f] = 0;
@@ -313,6 +313,7 @@ __device__ __forceinline__ void render_tile_fwd(
         const Real w = alpha * T[k] * T[k];
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[k][f] += w * r[6 + f];
+        if (DEPTH) accD[k] += alpha * T[k] * r[7 + NF];  // Eq. 5: one-way T
         T[k] = tn;
         last[k] = s_idx[j] + 1;
       }
@@ -337,13 +338,21 @@ __device__ __forceinline__ void render_tile_fwd(
                                          (Real)tab->sin_off[j] * acc[k][2 * f + 1] +
                                          bgb[f * rg.P + j] * T[k];
     o[(size_t)(F * rg.P) * HW] = acc[k][2 * F] + bgb[F * rg.P] * T[k];
+    int c = F * rg.P + 1;
+    if (rg.phasor) {  // Eq. 3: p = 2 (C_f + i S_f) + p_bg T_N
+      for (int f = 0; f < F; ++f, c += 2) {
+        o[(size_t)c * HW] = Real(2) * acc[k][2 * f + 1] + bgb[c] * T[k];
+        o[(size_t)(c + 1) * HW] = Real(2) * acc[k][2 * f] + bgb[c + 1] * T[k];
+      }
+    }
+    if (DEPTH) o[(size_t)c * HW] = accD[k];
     tfinal[(size_t)tc.b * HW + pix] = T[k];
     nlast[(size_t)tc.b * HW + pix] = last[k] - range.x;
   }
 }
 
-template <typename Real, int F, int PPT, bool COUNT>
-__global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
+template <typename Real, int F, int PPT, bool DEPTH, bool COUNT>
+__global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT, false>::value)
     render_fwd_kernel(RenderGeom rg, const TableT<Real>* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
-    render_tile_fwd<Real, F, PPT, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+    render_tile_fwd<Real, F, PPT, DEPTH, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                          values, rec, bg, out, tfinal, nlast, s_rec, s_stage,
                                          s_idx, s_cnt, hdr);
     return;
@@ -372,7 +381,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= items) break;
-    render_tile_fwd<Real, F, PPT, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+    render_tile_fwd<Real, F, PPT, DEPTH, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                          values, rec, bg, out, tfinal, nlast, s_rec, s_stage,
                                          s_idx, s_cnt, hdr);
   }
@@ -381,7 +390,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
 // ---------------------------------------------------------------------------
 // backward
 // ---------------------------------------------------------------------------
-template <typename Real, int F, int PPT>
+template <typename Real, int F, int PPT, bool DEPTH>
 __device__ __forceinline__ void render_tile_bwd(
     const TileCtx& tc, const RenderGeom& rg, const TableT<Real>* __restrict__ tab,
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ values,
@@ -391,7 +400,7 @@ __device__ __forceinline__ void render_tile_bwd(
     Real* __restrict__ dbg, Real* s_rec, Real* s_grad, uint32_t* s_id,
     Real* s_red, uint32_t* s_idx, int* s_cnt, Real* s_stage) {
   constexpr int NF = 2 * F + 1;
-  constexpr int GS = 6 + NF;
+  constexpr int GS = 6 + NF + (DEPTH ? 1 : 0);
   constexpr int RS = rec_stride<Real, F>();
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
@@ -405,7 +414,7 @@ __device__ __forceinline__ void render_tile_bwd(
   const Real* bgb = bg + (size_t)tc.b * rg.C;
 
   // fold dL/dQ into accumulator gradients, per pixel
-  Real fpy[PPT], Tf[PPT], gTf[PPT], gacc[PPT][NF];
+  Real fpy[PPT], Tf[PPT], gTf[PPT], gacc[PPT][NF], gD[PPT];
   int nl[PPT];
   bool inside[PPT];
   int thread_n = 0;
@@ -415,6 +424,7 @@ __device__ __forceinline__ void render_tile_bwd(
     inside[k] = px < rg.W && py0 + k < rg.H;
 #pragma unroll
     for (int f = 0; f < NF; ++f) gacc[k][f] = 0;
+    gD[k] = 0;
     Real gT = 0;
     Tf[k] = 1;
     nl[k] = 0;
@@ -432,13 +442,23 @@ __device__ __forceinline__ void render_tile_bwd(
         }
       gacc[k][2 * F] = go[(size_t)(F * rg.P) * HW];
       gT += bgb[F * rg.P] * gacc[k][2 * F];
+      int c = F * rg.P + 1;
+      if (rg.phasor) {  // Re = 2 C_f, Im = 2 S_f
+        for (int f = 0; f < F; ++f, c += 2) {
+          const Real gre = go[(size_t)c * HW], gim = go[(size_t)(c + 1) * HW];
+          gacc[k][2 * f + 1] += Real(2) * gre;
+          gacc[k][2 * f] += Real(2) * gim;
+          gT += bgb[c] * gre + bgb[c + 1] * gim;
+        }
+      }
+      if (DEPTH) gD[k] = go[(size_t)c * HW];
     }
     gTf[k] = gT * Tf[k];
     thread_n = max(thread_n, nl[k]);
   }
   // dL/dbg_c = sum over pixels of T_N dL/dQ_c (block reduce, one atomic each)
   if (dbg) {
-    for (int c = 0; c < rg.C; ++c) {
+    for (int c = 0; c < rg.C - (DEPTH ? 1 : 0); ++c) {  // Eq. 5 has no background
       Real v = 0;
 #pragma unroll
       for (int k = 0; k < PPT; ++k)
@@ -468,11 +488,14 @@ __device__ __forceinline__ void render_tile_bwd(
   // Per pixel only the projection of the Eq. S3 accumulators on the pixel's
   // (fixed) accumulator gradient is needed: A = sum_f g_f acc_f obeys the same
   // recursion, A <- alpha (g . q) + (1 - alpha)^2 A.
-  Real T[PPT], A[PPT];
+  // BD likewise projects the one-way mean-depth recursion (DEPTH only):
+  // BD <- alpha gD d + (1 - alpha) BD, d depth / d alpha_k = T_k (d_k - accD_k)
+  Real T[PPT], A[PPT], BD[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     T[k] = Tf[k];
     A[k] = 0;
+    BD[k] = 0;
   }
   const int red_slot = butterfly_slot<GS>(lane);
   const Real ln2 = Real(kLn2);
@@ -548,8 +571,14 @@ __device__ __forceinline__ void render_tile_bwd(
           Real gq = 0;
 #pragma unroll
           for (int f = 0; f < NF; ++f) gq += gacc[k][f] * r[6 + f];
-          const Real dLda = T2 * (gq - (oma + oma) * A[k]) - gTf[k] * rcp;
+          Real dLda = T2 * (gq - (oma + oma) * A[k]) - gTf[k] * rcp;
           A[k] = alpha * gq + oma * oma * A[k];
+          if (DEPTH) {
+            const Real gDd = gD[k] * r[7 + NF];
+            dLda += Tk * (gDd - BD[k]);
+            c[6 + NF] += gD[k] * alpha * Tk;
+            BD[k] = alpha * gDd + oma * BD[k];
+          }
           const Real aT2 = alpha * T2;
 #pragma unroll
           for (int f = 0; f < NF; ++f) c[6 + f] += gacc[k][f] * aT2;
@@ -590,8 +619,8 @@ __device__ __forceinline__ void render_tile_bwd(
   }
 }
 
-template <typename Real, int F, int PPT>
-__global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
+template <typename Real, int F, int PPT, bool DEPTH>
+__global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT, true>::value)
     render_bwd_kernel(RenderGeom rg, const TableT<Real>* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
@@ -602,7 +631,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
                       const uint32_t* __restrict__ nlast, Real* __restrict__ g2d,
                       int g2d_stride, Real* __restrict__ dbg, int persistent) {
   constexpr int NF = 2 * F + 1;
-  constexpr int GS = 6 + NF;
+  constexpr int GS = 6 + NF + (DEPTH ? 1 : 0);
   constexpr int RS = rec_stride<Real, F>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nthr = blockDim.x;
@@ -616,7 +645,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
-    render_tile_bwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+    render_tile_bwd<Real, F, PPT, DEPTH>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                   values, rec, bg, dout, tfinal, nlast, g2d,
                                   g2d_stride, dbg, s_rec, s_grad, s_id, s_red, s_idx, s_cnt,
                                   s_stage);
@@ -629,7 +658,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT>::value)
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= items) break;
-    render_tile_bwd<Real, F, PPT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+    render_tile_bwd<Real, F, PPT, DEPTH>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                   values, rec, bg, dout, tfinal, nlast, g2d,
                                   g2d_stride, dbg, s_rec, s_grad, s_id, s_red, s_idx, s_cnt,
                                   s_stage);
@@ -640,7 +669,7 @@ RenderGeom geom_of(const Layout& L) {
   RenderGeom g;
   g.N = L.N, g.W = L.W, g.H = L.H, g.TW = L.TW, g.TH = L.TH;
   g.tiles_x = L.tiles_x, g.NT = L.NT, g.P = L.P, g.C = L.C;
-  g.rec_stride = L.rec_stride, g.B = L.B, g.cull = L.cull;
+  g.rec_stride = L.rec_stride, g.B = L.B, g.cull = L.cull, g.phasor = L.phasor;
   return g;
 }
 
@@ -657,13 +686,13 @@ int persistent_grid(KernelT kernel, int threads, size_t smem) {
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-template <typename Real, int F, int PPT, bool COUNT>
+template <typename Real, int F, int PPT, bool DEPTH, bool COUNT>
 void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                 cudaStream_t st) {
   constexpr int RS = rec_stride<Real, F>();
   const int threads = L.TW * L.TH / PPT;
   const size_t smem = (size_t)threads * (2 * RS * sizeof(Real) + sizeof(uint32_t));
-  auto kernel = render_fwd_kernel<Real, F, PPT, COUNT>;
+  auto kernel = render_fwd_kernel<Real, F, PPT, DEPTH, COUNT>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -684,15 +713,16 @@ void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
   count_launches(1);
 }
 
-template <typename Real, int F, int PPT>
+template <typename Real, int F, int PPT, bool DEPTH>
 void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
                 unsigned char* ws, cudaStream_t st) {
   constexpr int NF = 2 * F + 1;
+  constexpr int GS = 6 + NF + (DEPTH ? 1 : 0);
   constexpr int RS = rec_stride<Real, F>();
   const int threads = L.TW * L.TH / PPT;
-  const size_t smem = (size_t)threads * (2 * RS + 6 + NF) * sizeof(Real) +
+  const size_t smem = (size_t)threads * (2 * RS + GS) * sizeof(Real) +
                       32 * sizeof(Real) + (size_t)threads * 2 * sizeof(uint32_t);
-  auto kernel = render_bwd_kernel<Real, F, PPT>;
+  auto kernel = render_bwd_kernel<Real, F, PPT, DEPTH>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -714,55 +744,55 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
   count_launches(1);
 }
 
-template <typename Real, int F>
+template <typename Real, int F, bool DEPTH>
 void fwd_dispatch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                   cudaStream_t st) {
   if (L.count_pairs) {
     switch (L.ppt) {
-      case 1: fwd_launch<Real, F, 1, true>(L, bg, out, ws, st); break;
-      case 4: fwd_launch<Real, F, 4, true>(L, bg, out, ws, st); break;
-      default: fwd_launch<Real, F, 2, true>(L, bg, out, ws, st); break;
+      case 1: fwd_launch<Real, F, 1, DEPTH, true>(L, bg, out, ws, st); break;
+      case 4: fwd_launch<Real, F, 4, DEPTH, true>(L, bg, out, ws, st); break;
+      default: fwd_launch<Real, F, 2, DEPTH, true>(L, bg, out, ws, st); break;
     }
     return;
   }
   switch (L.ppt) {
-    case 1: fwd_launch<Real, F, 1, false>(L, bg, out, ws, st); break;
-    case 4: fwd_launch<Real, F, 4, false>(L, bg, out, ws, st); break;
-    default: fwd_launch<Real, F, 2, false>(L, bg, out, ws, st); break;
+    case 1: fwd_launch<Real, F, 1, DEPTH, false>(L, bg, out, ws, st); break;
+    case 4: fwd_launch<Real, F, 4, DEPTH, false>(L, bg, out, ws, st); break;
+    default: fwd_launch<Real, F, 2, DEPTH, false>(L, bg, out, ws, st); break;
   }
 }
 
-template <typename Real, int F>
+template <typename Real, int F, bool DEPTH>
 void bwd_dispatch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
                   unsigned char* ws, cudaStream_t st) {
   switch (L.ppt) {
-    case 1: bwd_launch<Real, F, 1>(L, bg, dout, dbg, ws, st); break;
-    case 4: bwd_launch<Real, F, 4>(L, bg, dout, dbg, ws, st); break;
-    default: bwd_launch<Real, F, 2>(L, bg, dout, dbg, ws, st); break;
+    case 1: bwd_launch<Real, F, 1, DEPTH>(L, bg, dout, dbg, ws, st); break;
+    case 4: bwd_launch<Real, F, 4, DEPTH>(L, bg, dout, dbg, ws, st); break;
+    default: bwd_launch<Real, F, 2, DEPTH>(L, bg, dout, dbg, ws, st); break;
   }
 }
 
 }  // namespace
 
-template <typename Real>
-void launch_render_fwd(const Layout& L, const Real* bg, Real* out,
+template <typename Real, bool DEPTH>
+void launch_render_fwd_t(const Layout& L, const Real* bg, Real* out,
                        unsigned char* ws, cudaStream_t st) {
   switch (L.F) {
-    case 1: fwd_dispatch<Real, 1>(L, bg, out, ws, st); break;
-    case 2: fwd_dispatch<Real, 2>(L, bg, out, ws, st); break;
-    case 3: fwd_dispatch<Real, 3>(L, bg, out, ws, st); break;
-    default: fwd_dispatch<Real, 4>(L, bg, out, ws, st); break;
+    case 1: fwd_dispatch<Real, 1, DEPTH>(L, bg, out, ws, st); break;
+    case 2: fwd_dispatch<Real, 2, DEPTH>(L, bg, out, ws, st); break;
+    case 3: fwd_dispatch<Real, 3, DEPTH>(L, bg, out, ws, st); break;
+    default: fwd_dispatch<Real, 4, DEPTH>(L, bg, out, ws, st); break;
   }
 }
 
-template <typename Real>
-void launch_render_bwd(const Layout& L, const Real* bg, const Real* dout,
+template <typename Real, bool DEPTH>
+void launch_render_bwd_t(const Layout& L, const Real* bg, const Real* dout,
                        Real* dbg, unsigned char* ws, cudaStream_t st) {
   switch (L.F) {
-    case 1: bwd_dispatch<Real, 1>(L, bg, dout, dbg, ws, st); break;
-    case 2: bwd_dispatch<Real, 2>(L, bg, dout, dbg, ws, st); break;
-    case 3: bwd_dispatch<Real, 3>(L, bg, dout, dbg, ws, st); break;
-    default: bwd_dispatch<Real, 4>(L, bg, dout, dbg, ws, st); break;
+    case 1: bwd_dispatch<Real, 1, DEPTH>(L, bg, dout, dbg, ws, st); break;
+    case 2: bwd_dispatch<Real, 2, DEPTH>(L, bg, dout, dbg, ws, st); break;
+    case 3: bwd_dispatch<Real, 3, DEPTH>(L, bg, dout, dbg, ws, st); break;
+    default: bwd_dispatch<Real, 4, DEPTH>(L, bg, dout, dbg, ws, st); break;
   }
 }
 

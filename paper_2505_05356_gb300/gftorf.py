@@ -24,6 +24,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "tile-instance capacity exceeded",
 OK, ERR_ARG, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_WORKSPACE = range(7)
 FLAG_NO_TILE_CULL = 1
 FLAG_COUNT_PAIRS = 2
+FLAG_PHASOR = 4
+FLAG_DEPTH = 8
 
 
 class Dims(ctypes.Structure):
@@ -197,6 +199,13 @@ def sensor_from_scene(scene) -> Sensor:
     return make_sensor(s.freqs_hz, s.offsets_rad, s.source_intensity)
 
 
+def flags_from_scene(scene) -> int:
+    """Output-channel flags a scene's constants ask for."""
+    k = scene.consts
+    return ((FLAG_PHASOR if getattr(k, "phasor", False) else 0) |
+            (FLAG_DEPTH if getattr(k, "depth", False) else 0))
+
+
 def consts_from_scene(scene) -> Consts:
     k = scene.consts
     return make_consts(k.dilation, k.alpha_max, k.alpha_min, k.t_min, k.guard, k.sigma_cut)
@@ -232,7 +241,8 @@ class Renderer:
         self.dims = Dims(n, frames, width, height, tile[0], tile[1], n_freq,
                          n_offsets, F64 if dtype == torch.float64 else F32,
                          render_mode, pixels_per_thread, flags, 0)
-        self.C = n_freq * n_offsets + 1
+        self.C = (n_freq * n_offsets + 1 + (2 * n_freq if flags & FLAG_PHASOR else 0) +
+                  (1 if flags & FLAG_DEPTH else 0))
         self.tiles_x = -(-width // tile[0])
         self.tiles_y = -(-height // tile[1])
         self.n_tiles = self.tiles_x * self.tiles_y

@@ -55,7 +55,7 @@ def test_workspace_size_validates_dims(lib):
                 dict(tile_w=32, tile_h=16), dict(n_freq=0), dict(n_freq=5),
                 dict(n_offsets=9), dict(dtype=2), dict(render_mode=2),
                 dict(pixels_per_thread=3), dict(pixels_per_thread=8),
-                dict(tile_w=8, tile_h=8, pixels_per_thread=4), dict(flags=4),
+                dict(tile_w=8, tile_h=8, pixels_per_thread=4), dict(flags=16),
                 dict(n_gaussians=-1), dict(max_instances=-1),
                 dict(max_instances=1 << 33)):
         assert lib.gftorf_workspace_size(ctypes.byref(_dims(**bad))) == 0, bad

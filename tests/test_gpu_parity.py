@@ -26,6 +26,9 @@ SMALL = [
     ("static_1k", dict(offsets_rad=[0.1, 0.9, 2.0, 2.5, 3.3, 4.0, 5.1, 6.0])),
     ("dynamic_100k", dict(n=3000, width=96, height=80, frames=3)),
     ("batch_300k", dict(n=4000, width=80, height=64, frames=4)),
+    ("batch_300k", dict(n=3000, width=72, height=56, frames=2, phasor=True, depth=True)),
+    ("static_1k", dict(freqs_hz=[30e6, 80e6], z_range=(0.5, 6.0), phasor=True, depth=True,
+                       tile=(16, 32))),
 ]
 
 
@@ -73,7 +76,7 @@ def test_fp64_path_matches_oracle_tightly():
     """The double-precision instantiation of every kernel agrees with the
     oracle to ~1e-9 (the formulas, not just the tolerance, agree)."""
     sc = scenes.make_scene("batch_300k", 5, n=1500, width=64, height=48, frames=2,
-                           freqs_hz=[30e6, 80e6])
+                           freqs_hz=[30e6, 80e6], phasor=True, depth=True)
     eps64 = (1e-9, 1e-10, 1.2e-7, 1e-9)  # depth keys are single precision
     q_ora, tf_ora, amb, nc = ora.render(sc, eps64)
     dout = scenes.random_dout(sc, 4)
