@@ -62,8 +62,39 @@ typedef struct {
   double det;
 } proj_aux;
 
+/* Real spherical harmonics of degree 0..3 (orthonormal on the unit sphere),
+ * Cartesian form at a unit vector, without the Condon-Shortley phase; the
+ * normalisations are written out from their closed forms. */
+static cplx sh_basis_c(int l, cplx x, cplx y, cplx z) {
+  const double pi = kPi;
+  switch (l) {
+    case 0: return 0.5 * sqrt(1.0 / pi);
+    case 1: return sqrt(3.0 / (4.0 * pi)) * y;
+    case 2: return sqrt(3.0 / (4.0 * pi)) * z;
+    case 3: return sqrt(3.0 / (4.0 * pi)) * x;
+    case 4: return 0.5 * sqrt(15.0 / pi) * x * y;
+    case 5: return 0.5 * sqrt(15.0 / pi) * y * z;
+    case 6: return 0.25 * sqrt(5.0 / pi) * (2.0 * z * z - x * x - y * y);
+    case 7: return 0.5 * sqrt(15.0 / pi) * x * z;
+    case 8: return 0.25 * sqrt(15.0 / pi) * (x * x - y * y);
+    case 9: return 0.25 * sqrt(35.0 / (2.0 * pi)) * y * (3.0 * x * x - y * y);
+    case 10: return 0.5 * sqrt(105.0 / pi) * x * y * z;
+    case 11: return 0.25 * sqrt(21.0 / (2.0 * pi)) * y * (4.0 * z * z - x * x - y * y);
+    case 12: return 0.25 * sqrt(7.0 / pi) * z * (2.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+    case 13: return 0.25 * sqrt(21.0 / (2.0 * pi)) * x * (4.0 * z * z - x * x - y * y);
+    case 14: return 0.25 * sqrt(105.0 / pi) * z * (x * x - y * y);
+    case 15: return 0.25 * sqrt(35.0 / (2.0 * pi)) * x * (x * x - 3.0 * y * y);
+  }
+  return 0.0;
+}
+
+double ora_sh_basis(int l, double x, double y, double z) {
+  return creal(sh_basis_c(l, x, y, z));
+}
+
 /* theta: mu[0..2], c1[3..5], c2[6..8], c3[9..11], scale[12..14],
- * quat[15..18] (w x y z), opacity[19], amplitude[20], delta[21..23]. */
+ * quat[15..18] (w x y z), opacity[19], amplitude[20], delta[21..23],
+ * sh[24..39]. */
 static void project_complex(const cplx* th, const double* frame,
                             const double* sensor, const double* consts,
                             cplx* rec, proj_aux* aux) {
@@ -151,8 +182,25 @@ static void project_complex(const cplx* th, const double* frame,
   rec[REC_C] = s00 / det;
   rec[REC_O] = th[19];
 
+  /* reflectivity r_k (Sec. 4, C-ToF image formation): a scalar, or view
+   * dependent through up to 16 real SH coefficients evaluated at the unit
+   * direction from the optical centre to the (deformed) centre, with the
+   * 3DGS colour convention r = max(0, 0.5 + sum_l sh_l Y_l) */
+  cplx refl = th[20];
+  const int nsh = (int)consts[ORA_CO_NSH];
+  if (nsh > 0) {
+    cplx dir[3];
+    for (int a = 0; a < 3; ++a) {
+      double o_a = -(Rt[0 * 4 + a] * Rt[3] + Rt[1 * 4 + a] * Rt[7] + Rt[2 * 4 + a] * Rt[11]);
+      dir[a] = (x[a] - o_a) / dist;
+    }
+    cplx val = 0.5;
+    for (int l = 0; l < nsh; ++l) val += th[24 + l] * sh_basis_c(l, dir[0], dir[1], dir[2]);
+    refl = creal(val) > 0.0 ? val : 0.0;
+  }
+
   /* C-ToF terms (Sec. 3, Eq. 3/4): A = s r / d^2, psi_f = 4 pi d f / c */
-  cplx A = sensor[ORA_SE_S] * th[20] / (dist * dist);
+  cplx A = sensor[ORA_SE_S] * refl / (dist * dist);
   int F = (int)sensor[ORA_SE_F];
   for (int f = 0; f < F; ++f) {
     cplx psi = 4.0 * kPi * dist * sensor[ORA_SE_FREQ + f] / kLightSpeed;
@@ -175,7 +223,7 @@ static void project_complex(const cplx* th, const double* frame,
 static void gather_theta(int g, const double* means, const double* coeffs,
                          const double* scales, const double* quats,
                          const double* opacity, const double* amplitude,
-                         const double* delta, cplx* th) {
+                         const double* delta, const double* sh, cplx* th) {
   for (int a = 0; a < 3; ++a) th[a] = means[3 * g + a];
   for (int a = 0; a < 9; ++a) th[3 + a] = coeffs ? coeffs[9 * g + a] : 0.0;
   for (int a = 0; a < 3; ++a) th[12 + a] = scales[3 * g + a];
@@ -183,6 +231,7 @@ static void gather_theta(int g, const double* means, const double* coeffs,
   th[19] = opacity[g];
   th[20] = amplitude[g];
   for (int a = 0; a < 3; ++a) th[21 + a] = delta ? delta[3 * g + a] : 0.0;
+  for (int l = 0; l < ORA_MAX_SH; ++l) th[24 + l] = sh ? sh[(size_t)ORA_MAX_SH * g + l] : 0.0;
 }
 
 static int clampi(double v, int lo, int hi) {
@@ -205,7 +254,7 @@ static int rect_empty(const double* r) { return r[0] >= r[2] || r[1] >= r[3]; }
 void ora_project(int n, const double* means, const double* coeffs,
                  const double* scales, const double* quats,
                  const double* opacity, const double* amplitude,
-                 const double* delta, const double* frame,
+                 const double* delta, const double* sh, const double* frame,
                  const double* sensor, const double* consts,
                  const double* eps, double* splats) {
   const int W = (int)frame[ORA_FR_W], H = (int)frame[ORA_FR_H];
@@ -220,7 +269,7 @@ void ora_project(int n, const double* means, const double* coeffs,
     proj_aux aux;
     double* sp = splats + (size_t)g * ORA_SP_LEN;
     memset(sp, 0, sizeof(double) * ORA_SP_LEN);
-    gather_theta(g, means, coeffs, scales, quats, opacity, amplitude, delta, th);
+    gather_theta(g, means, coeffs, scales, quats, opacity, amplitude, delta, sh, th);
     project_complex(th, frame, sensor, consts, rec, &aux);
 
     double u = creal(rec[REC_U]), v = creal(rec[REC_V]);
@@ -588,7 +637,7 @@ void ora_backward_2d(int n, const double* splats, const double* frame,
 void ora_backward_params(int n, const double* means, const double* coeffs,
                          const double* scales, const double* quats,
                          const double* opacity, const double* amplitude,
-                         const double* delta, const double* frame,
+                         const double* delta, const double* sh, const double* frame,
                          const double* sensor, const double* consts,
                          const double* splats, const double* g2d,
                          double* grads) {
@@ -601,7 +650,7 @@ void ora_backward_params(int n, const double* means, const double* coeffs,
     for (int r = 0; r < stride; ++r) any |= gg[r] != 0.0;
     if (!any || splats[(size_t)g * ORA_SP_LEN + ORA_SP_VIS] == 0.0) continue;
     cplx th[ORA_NPARAM], rec[REC_FEAT + ORA_MAX_FEAT + 1];
-    gather_theta(g, means, coeffs, scales, quats, opacity, amplitude, delta, th);
+    gather_theta(g, means, coeffs, scales, quats, opacity, amplitude, delta, sh, th);
     for (int i = 0; i < ORA_NPARAM; ++i) {
       cplx saved = th[i];
       th[i] = creal(saved) + I * h;

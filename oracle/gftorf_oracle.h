@@ -37,7 +37,9 @@
 #define ORA_MAX_F 4
 #define ORA_MAX_P 8
 #define ORA_MAX_FEAT (2 * ORA_MAX_F + 1)
-#define ORA_NPARAM 24 /* mu[3] c[9] scale[3] quat[4] opacity amplitude delta[3] */
+#define ORA_MAX_SH 16
+/* mu[3] c[9] scale[3] quat[4] opacity amplitude delta[3] sh[16] */
+#define ORA_NPARAM (24 + ORA_MAX_SH)
 
 /* one frame: camera + time */
 enum {
@@ -61,6 +63,9 @@ enum {
   ORA_CO_SIGMA, ORA_CO_TW, ORA_CO_TH,
   ORA_CO_PHASOR, /* != 0: add the Eq. 3 phasor (Re, Im per frequency) */
   ORA_CO_DEPTH,  /* != 0: add the Eq. 5 mean depth (one-way T)         */
+  ORA_CO_NSH,    /* 0: scalar reflectivity; 1, 4, 9, 16: SH of degree
+                    0..3, r = max(0, 0.5 + sum_l sh_l Y_l(dir)), dir the
+                    unit vector from the optical centre to the Gaussian */
   ORA_CO_LEN
 };
 /* ambiguity margins (relative): a lower-precision implementation may take
@@ -99,14 +104,19 @@ int ora_num_threads(void);
 /* Project all n Gaussians for one frame (Sec. 4; 3DGS EWA convention).
  * params: means[n*3], coeffs[n*9] (c1 xyz, c2 xyz, c3 xyz), scales[n*3],
  * quats[n*4] (w,x,y,z, any norm), opacity[n], amplitude[n], delta[n*3] or
- * NULL.  eps[ORA_EPS_LEN] sets the margins behind ORA_SP_UNCERT and the
- * outer/inner rects.  out: splats[n * ORA_SP_LEN]. */
+ * NULL, sh[n*ORA_MAX_SH] (read when consts[ORA_CO_NSH] > 0) or NULL.
+ * eps[ORA_EPS_LEN] sets the margins behind ORA_SP_UNCERT and the outer/inner
+ * rects.  out: splats[n * ORA_SP_LEN]. */
 void ora_project(int n, const double* means, const double* coeffs,
                  const double* scales, const double* quats,
                  const double* opacity, const double* amplitude,
-                 const double* delta, const double* frame,
+                 const double* delta, const double* sh, const double* frame,
                  const double* sensor, const double* consts,
                  const double* eps, double* splats);
+
+/* Real spherical harmonic basis function l (0..15, degree-major) at the unit
+ * vector (x, y, z). */
+double ora_sh_basis(int l, double x, double y, double z);
 
 /* Raw C-ToF samples for a list of pixels of one frame (Eq. 4).
  * pix[npix*2] = (x, y) pixel indices; bg[C]; out[npix*C]; tfinal[npix];
@@ -142,11 +152,11 @@ void ora_backward_2d(int n, const double* splats, const double* frame,
 
 /* Chain the 2D-record gradient of one frame to the Gaussian parameters
  * through the projection with its exact complex-step Jacobian.
- * grads[n * ORA_NPARAM] ACCUMULATED (mu3 c9 s3 q4 o r delta3). */
+ * grads[n * ORA_NPARAM] ACCUMULATED (mu3 c9 s3 q4 o r delta3 sh16). */
 void ora_backward_params(int n, const double* means, const double* coeffs,
                          const double* scales, const double* quats,
                          const double* opacity, const double* amplitude,
-                         const double* delta, const double* frame,
+                         const double* delta, const double* sh, const double* frame,
                          const double* sensor, const double* consts,
                          const double* splats, const double* g2d,
                          double* grads);

@@ -19,8 +19,9 @@ _LIB = None
 MAX_F, MAX_P = 4, 8
 FR_LEN = 20
 SE_LEN = 1 + MAX_F + 1 + MAX_P + 1
-CO_LEN = 10
-NPARAM = 24
+CO_LEN = 11
+MAX_SH = 16
+NPARAM = 24 + MAX_SH
 SP = dict(VIS=0, U=1, V=2, CA=3, CB=4, CC=5, OPA=6, Z=7, D=8, RAD=9,
           X0=10, Y0=11, X1=12, Y1=13, MX0=14, MY0=15, MX1=16, MY1=17,
           IX0=18, IY0=19, IX1=20, IY1=21, UNCERT=22, AMP=23, FEAT=24)
@@ -52,13 +53,15 @@ def lib():
         L = ctypes.CDLL(path)
         L.ora_splat_len.restype = ctypes.c_int
         L.ora_num_threads.restype = ctypes.c_int
-        L.ora_project.argtypes = [ctypes.c_int] + [_d] * 12
+        L.ora_project.argtypes = [ctypes.c_int] + [_d] * 13
+        L.ora_sh_basis.argtypes = [ctypes.c_int] + [ctypes.c_double] * 3
+        L.ora_sh_basis.restype = ctypes.c_double
         L.ora_render_pixels.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _d,
                                         ctypes.c_int, _i32, _d, _d, _i32, _i32]
         L.ora_render_frame.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _d,
                                        _d, _d, _i32, _i32]
         L.ora_backward_2d.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _d, _d, _d]
-        L.ora_backward_params.argtypes = [ctypes.c_int] + [_d] * 13
+        L.ora_backward_params.argtypes = [ctypes.c_int] + [_d] * 14
         L.ora_bin_f32.argtypes = [ctypes.c_int, ctypes.c_int, _f32, _f32, _i32,
                                   _f32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int64, _u64, _u32, _u32]
@@ -107,7 +110,18 @@ def pack_consts(scene) -> np.ndarray:
     k = scene.consts
     return np.array([k.dilation, k.alpha_max, k.alpha_min, k.t_min, k.guard,
                      k.sigma_cut, k.tile_w, k.tile_h, float(getattr(k, "phasor", False)),
-                     float(getattr(k, "depth", False))], np.float64)
+                     float(getattr(k, "depth", False)), float(n_sh(scene))], np.float64)
+
+
+def n_sh(scene) -> int:
+    """SH coefficients per Gaussian (0: scalar reflectivity)."""
+    sh = getattr(scene, "sh", None)
+    return 0 if sh is None else int(np.asarray(sh).shape[1])
+
+
+def sh_basis(l: int, x: float, y: float, z: float) -> float:
+    """Real SH basis function l (degree-major, 0..15) at a unit vector."""
+    return lib().ora_sh_basis(l, x, y, z)
 
 
 def n_channels(scene) -> int:
@@ -135,6 +149,12 @@ class Params:
         self.amplitude = _copy64(over.get("amplitude", scene.amplitude))
         de = over.get("delta", scene.delta)
         self.delta = _copy64(de) if de is not None else None
+        sh = over.get("sh", getattr(scene, "sh", None))
+        self.sh = None
+        if sh is not None:
+            sh = np.asarray(sh, np.float64)
+            self.sh = np.zeros((scene.n, MAX_SH))
+            self.sh[:, :sh.shape[1]] = sh
 
     def delta_of(self, b):
         return None if self.delta is None else np.ascontiguousarray(self.delta[b])
@@ -147,7 +167,7 @@ def project(scene, b: int, eps=EPS_NONE, params: Params = None) -> np.ndarray:
     out = np.zeros((n, lib().ora_splat_len()))
     e = np.asarray(eps, np.float64)
     lib().ora_project(n, _p(P.means), _p(P.coeffs), _p(P.scales), _p(P.quats),
-                      _p(P.opacity), _p(P.amplitude), _p(P.delta_of(b)),
+                      _p(P.opacity), _p(P.amplitude), _p(P.delta_of(b)), _p(P.sh),
                       _p(pack_frame(scene, b)), _p(pack_sensor(scene)),
                       _p(pack_consts(scene)), _p(e), _p(out))
     return out
@@ -202,7 +222,8 @@ def backward(scene, dout: np.ndarray, params: Params = None, want_2d=False):
     """Analytic FP64 gradient of L = sum(dout * render(scene)).
 
     Returns a dict with means (N,3), coeffs (N,3,3), scales (N,3), quats (N,4),
-    opacity (N,), amplitude (N,), delta (B,N,3), bg (B,C) and, when want_2d,
+    opacity (N,), amplitude (N,), delta (B,N,3), bg (B,C), sh (N, n_sh) when
+    the scene has SH reflectivity and, when want_2d,
     g2d (B, N, 7+2F+1) -- gradients w.r.t. (u, v, conic a, b, c, opacity,
     features, distance)."""
     P = params or Params(scene)
@@ -224,7 +245,7 @@ def backward(scene, dout: np.ndarray, params: Params = None, want_2d=False):
         gb = np.zeros((n, NPARAM))
         lib().ora_backward_params(n, _p(P.means), _p(P.coeffs), _p(P.scales),
                                   _p(P.quats), _p(P.opacity), _p(P.amplitude),
-                                  _p(P.delta_of(b)), _p(fr), _p(se), _p(co),
+                                  _p(P.delta_of(b)), _p(P.sh), _p(fr), _p(se), _p(co),
                                   _p(sp), _p(g2d), _p(gb))
         grads += gb
         gdelta[b] = gb[:, 21:24]
@@ -234,6 +255,8 @@ def backward(scene, dout: np.ndarray, params: Params = None, want_2d=False):
                scales=grads[:, 12:15], quats=grads[:, 15:19],
                opacity=grads[:, 19], amplitude=grads[:, 20], delta=gdelta,
                bg=gbg)
+    if n_sh(scene):
+        out["sh"] = grads[:, 24:24 + n_sh(scene)].copy()
     if want_2d:
         out["g2d"] = np.stack(g2ds)
     return out

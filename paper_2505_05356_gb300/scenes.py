@@ -89,6 +89,11 @@ class Scene:
     sensor: Sensor
     consts: Consts
     bg: np.ndarray          # (B, C) background per channel
+    sh: Optional[np.ndarray] = None  # (N, n_sh) SH reflectivity, n_sh in 1,4,9,16
+
+    @property
+    def n_sh(self) -> int:
+        return 0 if self.sh is None else int(self.sh.shape[1])
 
     @property
     def n(self) -> int:
@@ -163,7 +168,9 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
 
     Overrides: n, width, height, frames, freqs_hz, offsets_rad, tile, bg
     ('zero' | 'random'), z_range, coeff_std, visible_min, consts, phasor,
-    depth.
+    depth, sh_degree (0..3: view-dependent reflectivity from (degree+1)^2 SH
+    coefficients; the DC term reproduces the scalar amplitude draw, the others
+    are N(0, sh_std) with sh_std 0.03 by default).
     """
     rng = np.random.default_rng(seed)
     if name == "static_1k":
@@ -211,8 +218,16 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
         bg = rng.uniform(-1.0, 1.0, (frames, C)).astype(F32)
     else:
         bg = np.zeros((frames, C), F32)
+    sh = None
+    deg = d.get("sh_degree")
+    if deg is not None:
+        k = (int(deg) + 1) ** 2
+        sh = rng.normal(0.0, d.get("sh_std", 0.03), (d["n"], k))
+        # DC basis value 1 / (2 sqrt(pi)): r = 0.5 + sh_0 Y_0 + ... = amplitude + ...
+        sh[:, 0] = (amplitude - 0.5) * (2.0 * math.sqrt(math.pi))
+        sh = sh.astype(F32)
     return Scene(means, coeffs, scales, quats, opacity, amplitude, times,
-                 [cam] * frames, delta, sensor, consts, bg)
+                 [cam] * frames, delta, sensor, consts, bg, sh)
 
 
 def random_dout(scene: Scene, seed: int = 1, density: float = 1.0) -> np.ndarray:

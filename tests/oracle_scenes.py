@@ -11,7 +11,7 @@ C_LIGHT = 299792458.0
 def tiny_scene(positions, scales, quats=None, opacity=None, amplitude=None,
                width=64, height=64, freqs=(30e6,), offsets=None, bg=None,
                coeffs=None, times=(0.0,), world_to_cam=None, consts=None,
-               source_intensity=1.0, delta=None):
+               source_intensity=1.0, delta=None, sh=None):
     """Scene with the given Gaussians (float64 values kept exactly)."""
     positions = np.asarray(positions, np.float64).reshape(-1, 3)
     n = positions.shape[0]
@@ -35,7 +35,8 @@ def tiny_scene(positions, scales, quats=None, opacity=None, amplitude=None,
     bg = np.broadcast_to(np.asarray(bg, np.float64), (frames, C)).copy()
     return scenes.Scene(positions, coeffs, scales, quats, opacity, amplitude,
                         np.asarray(times, np.float64), [cam] * frames, delta,
-                        sensor, consts, bg)
+                        sensor, consts, bg,
+                        None if sh is None else np.asarray(sh, np.float64).reshape(n, -1))
 
 
 def at_pixel(cam, px, py, z):

@@ -527,3 +527,129 @@ def test_gradient_with_phasor_and_depth_matches_central_differences(seed):
             assert g[name].reshape(-1)[i] == pytest.approx(fd, rel=2e-5, abs=2e-6 * (1 + abs(fd)))
             checked += 1
     assert checked > 80
+
+
+# --------------------------------------------------------------------------
+# view-dependent reflectivity from spherical harmonics (Sec. 4)
+# --------------------------------------------------------------------------
+
+def _sh_scipy(l_index, x, y, z):
+    """Real SH without the Condon-Shortley phase, from scipy's complex
+    Y_l^m: m > 0 -> sqrt2 (-1)^m Re Y_l^m, m < 0 -> sqrt2 (-1)^m Im Y_l^|m|."""
+    from scipy.special import sph_harm_y
+    l = int(math.isqrt(l_index))
+    m = l_index - l * l - l
+    theta = math.acos(max(-1.0, min(1.0, z)))
+    phi = math.atan2(y, x)
+    if m == 0:
+        return float(np.real(sph_harm_y(l, 0, theta, phi)))
+    c = sph_harm_y(l, abs(m), theta, phi)
+    sgn = -1.0 if abs(m) % 2 else 1.0
+    return math.sqrt(2.0) * sgn * float(np.real(c) if m > 0 else np.imag(c))
+
+
+def test_sh_basis_orthonormal_by_quadrature():
+    """Gauss-Legendre in cos(theta) x uniform phi integrates products of
+    degree <= 6 exactly: the 16 basis functions are orthonormal."""
+    xs, ws = np.polynomial.legendre.leggauss(8)
+    nphi = 16
+    Y = []
+    wts = []
+    for ct, w in zip(xs, ws):
+        st = math.sqrt(1.0 - ct * ct)
+        for j in range(nphi):
+            ph = 2.0 * math.pi * j / nphi
+            x, y, z = st * math.cos(ph), st * math.sin(ph), ct
+            Y.append([ora.sh_basis(l, x, y, z) for l in range(16)])
+            wts.append(w * 2.0 * math.pi / nphi)
+    Y = np.asarray(Y)
+    G = Y.T @ (Y * np.asarray(wts)[:, None])
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-13)
+
+
+def test_sh_basis_matches_scipy_real_form():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        v = rng.standard_normal(3)
+        v /= np.linalg.norm(v)
+        for l in range(16):
+            assert ora.sh_basis(l, *v) == pytest.approx(_sh_scipy(l, *v), abs=1e-13), l
+
+
+@pytest.mark.parametrize("n_sh", [1, 4, 9, 16])
+def test_sh_reflectivity_uses_world_direction_from_optical_centre(n_sh):
+    """A = s r / d^2 with r = max(0, 0.5 + sum c_l Y_l(dir)), dir the unit
+    vector from the optical centre to the centre in world coordinates (a
+    rotated, shifted camera separates world and camera frames)."""
+    R = Rotation.from_euler("xyz", [0.2, -0.3, 0.25]).as_matrix()
+    centre = np.array([0.3, -0.2, -0.4])
+    rt = np.concatenate([R, (-R @ centre)[:, None]], 1)
+    rng = np.random.default_rng(n_sh)
+    xs = [centre + R.T @ np.array([0.1, -0.05, 2.0]),
+          centre + R.T @ np.array([-0.2, 0.1, 1.5])]
+    sh = rng.normal(0.0, 0.4, (2, n_sh))
+    sh[1, 0] = -3.0  # negative before the clamp: r = 0
+    sc = tiny_scene(xs, 0.05, world_to_cam=rt, sh=sh, source_intensity=1.7)
+    sp = ora.project(sc, 0)
+    for k in range(2):
+        d = np.linalg.norm(xs[k] - centre)
+        u = (xs[k] - centre) / d
+        r = 0.5 + sum(sh[k, l] * _sh_scipy(l, *u) for l in range(n_sh))
+        r = max(r, 0.0)
+        assert sp[k, SP["FEAT"] + 2] == pytest.approx(1.7 * r / d ** 2, rel=1e-12, abs=1e-15)
+    assert sp[1, SP["FEAT"] + 2] == 0.0
+
+
+def test_sh_degree_zero_equals_scalar_amplitude():
+    """n_sh = 1 with c_0 = (r - 0.5) / Y_0 reproduces the scalar model."""
+    rng = np.random.default_rng(5)
+    sc = _fd_scene(5, n=6, frames=1)
+    out0, _, _, _ = ora.render(sc)
+    sc.sh = ((sc.amplitude - 0.5) * 2.0 * math.sqrt(math.pi))[:, None]
+    sc.amplitude = rng.uniform(0.0, 1.0, sc.n)  # ignored under SH
+    out1, _, _, _ = ora.render(sc)
+    np.testing.assert_allclose(out1, out0, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed,n_sh", [(11, 16), (12, 4)])
+def test_gradient_with_sh_matches_central_differences(seed, n_sh):
+    sc = _fd_scene(seed, n=5)
+    R = Rotation.from_euler("xyz", [0.05, -0.1, 0.08]).as_matrix()
+    centre = np.array([0.1, -0.05, -0.2])
+    rt = np.concatenate([R, (-R @ centre)[:, None]], 1)
+    for cam in sc.cameras:
+        cam.world_to_cam = rt
+    rng = np.random.default_rng(300 + seed)
+    sc.sh = rng.normal(0.0, 0.2, (sc.n, n_sh))
+    sc.sh[:, 0] = 0.8
+    dout = rng.standard_normal((sc.frames, sc.n_channels, sc.height, sc.width))
+    g = ora.backward(sc, dout)
+    assert g["sh"].shape == (sc.n, n_sh)
+    assert np.all(g["amplitude"] == 0.0)
+    base = ora.Params(sc)
+    L0, _ = _loss(sc, dout, base)
+    checked = 0
+    for name in ["sh", "means", "coeffs", "delta"]:
+        arr = getattr(base, name)
+        idx = [(k, l) for k in range(sc.n) for l in range(n_sh)] if name == "sh" else \
+            list(range(arr.size))
+        for i in idx:
+            get = (lambda P: P.sh[i]) if name == "sh" else \
+                (lambda P, name=name: getattr(P, name).reshape(-1)[i])
+            x0 = get(base)
+            h = 1e-6 * max(1.0, abs(x0))
+            vals = []
+            for sgn in (1, -1):
+                P = ora.Params(sc)
+                if name == "sh":
+                    P.sh[i] = x0 + sgn * h
+                else:
+                    getattr(P, name).reshape(-1)[i] = x0 + sgn * h
+                vals.append(_loss(sc, dout, P)[0])
+            fd = (vals[0] - vals[1]) / (2 * h)
+            if abs((vals[0] - L0) / h - (L0 - vals[1]) / h) > 1e-3 * (abs(fd) + 1e-3):
+                continue
+            ga = g[name][i] if name == "sh" else g[name].reshape(-1)[i]
+            assert ga == pytest.approx(fd, rel=2e-5, abs=2e-6 * (1 + abs(fd))), (name, i)
+            checked += 1
+    assert checked > 60
