@@ -119,6 +119,8 @@ def _overrides(args):
         o["frames"] = args.frames
     if args.n:
         o["n"] = args.n
+    if args.sh_degree >= 0:
+        o["sh_degree"] = args.sh_degree
     return o
 
 
@@ -193,10 +195,10 @@ def run_ours(args):
     if args.autotune:
         from paper_2505_05356_gb300 import autotune
         tuned = autotune.autotune(N, B, W, H, nF, nP, p, fr, se, co, bg, dout, steps=2,
-                                  flags=xflags)
+                                  flags=xflags, n_sh=sc.n_sh)
         tile, ppt, mode = tuned["tile"], tuned["ppt"], tuned["mode"]
     r = gftorf.Renderer(N, B, W, H, nF, nP, tile=tile, render_mode=mode,
-                        pixels_per_thread=ppt, flags=xflags)
+                        pixels_per_thread=ppt, flags=xflags, n_sh=sc.n_sh)
     r.fit_capacity(p, fr, se, co, bg)
     out = torch.empty((B, r.C, H, W), device="cuda")
     grads = r.alloc_grads(p, bg)
@@ -280,7 +282,7 @@ def run_ours(args):
     # counted by the forward's counting instantiation on the same inputs ---
     rc = gftorf.Renderer(N, B, W, H, nF, nP, tile=tile, render_mode=mode,
                          pixels_per_thread=ppt, flags=gftorf.FLAG_COUNT_PAIRS | xflags,
-                         max_instances=r.capacity)
+                         max_instances=r.capacity, n_sh=sc.n_sh)
     rc.preprocess(p, fr, se, co)
     rc.render_fwd(bg)
     instances, pairs = rc.counters()
@@ -296,10 +298,12 @@ def run_ours(args):
         "composite_bwd": ("alu", pairs * OPS_PER_PAIR_BWD / 1e9, "Gop/s", alu_peak),
         "composite_fwd": ("alu", pairs * OPS_PER_PAIR_FWD / 1e9, "Gop/s", alu_peak),
         # read 84 B of parameters + write a 48 B record, 8 B rect, 4 B key
-        "preprocess": ("hbm", vis * (84 + 60) / 1e9, "GB/s", hbm_peak),
+        # (+ 4 B per SH coefficient read with the parameters)
+        "preprocess": ("hbm", vis * (84 + 60 + 4 * sc.n_sh) / 1e9, "GB/s", hbm_peak),
         # instance values written once; depth keys 4 passes x 16 B
         "bin": ("hbm", (instances * 4 + vis * 16 * 4) / 1e9, "GB/s", hbm_peak),
-        "preprocess_bwd": ("hbm", vis * (84 + 36 + 12) / 1e9, "GB/s", hbm_peak),
+        "preprocess_bwd": ("hbm", (vis * (84 + 36 + 12) + N * 8 * sc.n_sh) / 1e9, "GB/s",
+                           hbm_peak),
         "zero_grad_buffers": ("hbm", vis * 36 / 1e9, "GB/s", hbm_peak),
     }
     dom = max(stage_ms, key=stage_ms.get)
@@ -354,7 +358,7 @@ def run_ours(args):
     plain = None
     if not args.skip_plain and rank == 0:
         r1 = gftorf.Renderer(N, 1, W, H, nF, nP, tile=tile, render_mode=0,
-                             pixels_per_thread=ppt, flags=xflags,
+                             pixels_per_thread=ppt, flags=xflags, n_sh=sc.n_sh,
                              max_instances=max(1024, int(r.capacity / B * 1.6)))
         gacc = {k: torch.zeros_like(v) for k, v in grads.items() if k not in ("bg", "delta")}
         p1s = []
@@ -406,6 +410,8 @@ def run_ours(args):
                                    "30-100%% visible per frame" % (args.workload, N, W, H, B),
                        "frames_per_step": B, "tile": "%dx%d" % tuple(tile),
                        "channels": r.C,
+                       "reflectivity": ("SH degree %d" % args.sh_degree
+                                        if args.sh_degree >= 0 else "scalar"),
                        "pixels_per_thread": ppt,
                        "render_mode": "persistent" if mode == 1 else "grid",
                        "autotuned": tuned is not None,
@@ -439,7 +445,7 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
     one = scenes.Scene(sc.means, sc.coeffs, sc.scales, sc.quats, sc.opacity, sc.amplitude,
                        sc.times[frame:frame + 1], sc.cameras[frame:frame + 1],
                        None if sc.delta is None else sc.delta[frame:frame + 1],
-                       sc.sensor, sc.consts, sc.bg[frame:frame + 1])
+                       sc.sensor, sc.consts, sc.bg[frame:frame + 1], sc.sh)
     HW = sc.width * sc.height
     rng = np.random.default_rng(seed)
     idx = rng.choice(HW, n_pix, replace=False)
@@ -463,7 +469,8 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
     grads = np.zeros((sc.n, ora.NPARAM))
     lib.ora_backward_params(sc.n, ora._p(P.means), ora._p(P.coeffs), ora._p(P.scales),
                             ora._p(P.quats), ora._p(P.opacity), ora._p(P.amplitude),
-                            ora._p(P.delta_of(0)), ora._p(fr), ora._p(se), ora._p(co),
+                            ora._p(P.delta_of(0)), ora._p(P.sh), ora._p(fr), ora._p(se),
+                            ora._p(co),
                             ora._p(sp), ora._p(g2d), ora._p(grads))
     t4 = time.perf_counter()
     touched = int(np.count_nonzero(np.any(g2d != 0, axis=1)))
@@ -552,6 +559,9 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the Gaussian count")
     ap.add_argument("--extra-channels", default="",
                     help="comma list of extra outputs: phasor (Eq. 3), depth (Eq. 5)")
+    ap.add_argument("--sh-degree", type=int, default=-1,
+                    help="view-dependent reflectivity from SH of this degree (0-3); "
+                         "default: scalar reflectivity")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

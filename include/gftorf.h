@@ -57,6 +57,7 @@ extern "C" {
 #define GFTORF_MAX_FREQ 4
 #define GFTORF_MAX_OFFSETS 8
 #define GFTORF_MAX_FRAMES 64
+#define GFTORF_MAX_SH 16
 
 typedef enum {
   GFTORF_OK = 0,
@@ -107,6 +108,11 @@ typedef struct {
                             (0: 2); tile_w * tile_h / it must be >= 32.
                             Results do not depend on it.                    */
   int32_t flags;         /* GFTORF_FLAG_* bits, 0 for the defaults         */
+  int32_t n_sh;          /* reflectivity model (Sec. 4): 0 = the scalar
+                            gaussians.amplitude; 1, 4, 9 or 16 = real
+                            spherical harmonics of degree 0..3 in
+                            gaussians.sh (see gftorf_gaussians)             */
+  int32_t reserved;      /* must be 0                                       */
   int64_t max_instances; /* capacity of the (Gaussian, tile) instance list,
                             summed over the batch                           */
 } gftorf_dims;
@@ -146,17 +152,27 @@ typedef struct {
 /* Gaussian parameters (device pointers, dims.dtype, N rows):
  *   means[N][3]; coeffs[N][3][3] = (c1, c2, c3) each xyz, or NULL (static);
  *   scales[N][3] (linear, > 0); quats[N][4] (w, x, y, z; normalised inside);
- *   opacity[N] in (0, 1]; amplitude[N] = reflectivity r_k;
- *   delta[B][N][3] per-frame displacement added to x(t), or NULL. */
+ *   opacity[N] in (0, 1]; amplitude[N] = reflectivity r_k (dims.n_sh == 0;
+ *   unused, may be NULL, otherwise);
+ *   delta[B][N][3] per-frame displacement added to x(t), or NULL;
+ *   sh[N][dims.n_sh] (dims.n_sh > 0, else unused): view-dependent
+ *   reflectivity r_k = max(0, 0.5 + sum_l sh_l Y_l(w)) (Sec. 4: r_k held
+ *   as spherical harmonic coefficients; 0.5 offset and clamp as in the 3DGS
+ *   colour model), w the unit vector from the frame's optical centre to
+ *   x(t) in world coordinates, Y_l the orthonormal real spherical harmonics
+ *   without the Condon-Shortley phase, ordered by degree and, within a
+ *   degree, by order m = -l..l (Y_1: y, z, x). */
 typedef struct {
   const void *means, *coeffs, *scales, *quats, *opacity, *amplitude, *delta;
+  const void* sh;
 } gftorf_gaussians;
 
 /* Gradient outputs (device pointers, dims.dtype; each may be NULL to skip),
  * same layouts as the inputs; bg[B][C].  They are OVERWRITTEN, not
- * accumulated. */
+ * accumulated.  With dims.n_sh > 0 the amplitude gradient is 0. */
 typedef struct {
   void *means, *coeffs, *scales, *quats, *opacity, *amplitude, *delta, *bg;
+  void* sh;
 } gftorf_gradients;
 
 /* Bytes of workspace needed for `dims` (0 if dims is invalid).  The

@@ -41,10 +41,11 @@ def _step(r: gftorf.Renderer, params, frames, sensor, consts, bg, dout, out, gra
 
 
 def time_config(cfg, n, n_frames, width, height, n_freq, n_offsets, params, frames,
-                sensor, consts, bg, dout, steps=3, warmup=2, flags=0) -> float:
+                sensor, consts, bg, dout, steps=3, warmup=2, flags=0, n_sh=0) -> float:
     """Milliseconds per fwd+bwd step of one configuration (CUDA events)."""
     r = gftorf.Renderer(n, n_frames, width, height, n_freq, n_offsets, tile=cfg["tile"],
-                        render_mode=cfg["mode"], pixels_per_thread=cfg["ppt"], flags=flags)
+                        render_mode=cfg["mode"], pixels_per_thread=cfg["ppt"], flags=flags,
+                        n_sh=n_sh)
     r.fit_capacity(params, frames, sensor, consts, bg)
     out = torch.empty((n_frames, r.C, height, width), dtype=r.torch_dtype, device=r.device)
     grads = r.alloc_grads(params, bg)
@@ -65,12 +66,12 @@ def time_config(cfg, n, n_frames, width, height, n_freq, n_offsets, params, fram
 
 def autotune(n, n_frames, width, height, n_freq, n_offsets, params, frames, sensor,
              consts, bg, dout, configs: Optional[Sequence[dict]] = None, steps=3,
-             cache_path: Optional[str] = None, flags=0) -> dict:
+             cache_path: Optional[str] = None, flags=0, n_sh=0) -> dict:
     """Fastest configuration for this problem: {'tile', 'ppt', 'mode', 'ms',
     'table'}.  With cache_path, results are read from / written to a JSON
     file keyed by the problem shape and device name."""
-    key = "%s|n=%d|B=%d|%dx%d|F=%d|P=%d|flags=%d" % (torch.cuda.get_device_name(), n, n_frames,
-                                                   width, height, n_freq, n_offsets, flags)
+    key = "%s|n=%d|B=%d|%dx%d|F=%d|P=%d|flags=%d|sh=%d" % (
+        torch.cuda.get_device_name(), n, n_frames, width, height, n_freq, n_offsets, flags, n_sh)
     cache: Dict[str, dict] = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
@@ -83,7 +84,7 @@ def autotune(n, n_frames, width, height, n_freq, n_offsets, params, frames, sens
     table = []
     for cfg in configs or candidates():
         ms = time_config(cfg, n, n_frames, width, height, n_freq, n_offsets, params, frames,
-                         sensor, consts, bg, dout, steps=steps, flags=flags)
+                         sensor, consts, bg, dout, steps=steps, flags=flags, n_sh=n_sh)
         table.append(dict(cfg, ms=round(ms, 4)))
     best = min(table, key=lambda c: c["ms"])
     result = dict(tile=tuple(best["tile"]), ppt=best["ppt"], mode=best["mode"], ms=best["ms"],

@@ -39,11 +39,21 @@ bool dims_ok(const gftorf_dims* d) {
   if (d->flags & ~(GFTORF_FLAG_NO_TILE_CULL | GFTORF_FLAG_COUNT_PAIRS | GFTORF_FLAG_PHASOR |
                    GFTORF_FLAG_DEPTH))
     return false;
+  if (d->n_sh != 0 && d->n_sh != 1 && d->n_sh != 4 && d->n_sh != 9 && d->n_sh != 16)
+    return false;
+  if (d->reserved != 0) return false;
   if (d->max_instances < 0 || d->max_instances > (int64_t)0xFFFFFFFFll) return false;
   const int64_t tiles = (int64_t)((d->width + d->tile_w - 1) / d->tile_w) *
                         ((d->height + d->tile_h - 1) / d->tile_h);
   if (tiles > 50000) return false;  // per-CTA tile counters live in shared memory
   return true;
+}
+
+// the parameter arrays the problem reads are present
+bool params_ok(const Layout& L, const gftorf_gaussians* g) {
+  if (L.N == 0) return true;
+  if (!g->means || !g->scales || !g->quats || !g->opacity) return false;
+  return L.nsh ? g->sh != nullptr : g->amplitude != nullptr;
 }
 
 Layout make_layout(const gftorf_dims* d) {
@@ -59,6 +69,7 @@ Layout make_layout(const gftorf_dims* d) {
   L.count_pairs = (d->flags & GFTORF_FLAG_COUNT_PAIRS) ? 1 : 0;
   L.phasor = (d->flags & GFTORF_FLAG_PHASOR) ? 1 : 0;
   L.depth = (d->flags & GFTORF_FLAG_DEPTH) ? 1 : 0;
+  L.nsh = d->n_sh;
   L.C = L.F * L.P + 1 + (L.phasor ? 2 * L.F : 0) + (L.depth ? 1 : 0);
   L.tiles_x = (L.W + L.TW - 1) / L.TW;
   L.tiles_y = (L.H + L.TH - 1) / L.TH;
@@ -221,8 +232,7 @@ gftorf_status gftorf_preprocess(const gftorf_dims* dims,
                                 size_t workspace_bytes, void* stream) {
   if (!dims_ok(dims) || !g || !frames || !sensor || !consts) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
-  if (L.N > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->amplitude))
-    return GFTORF_ERR_ARG;
+  if (!params_ok(L, g)) return GFTORF_ERR_ARG;
   gftorf_status s = check_ws(L, workspace, workspace_bytes);
   if (s != GFTORF_OK) return s;
   Table t;
@@ -240,6 +250,8 @@ gftorf_status gftorf_preprocess(const gftorf_dims* dims,
       for (int c = 0; c < 3; ++c) d.R[3 * r + c] = f.world_to_cam[4 * r + c];
       d.t[r] = f.world_to_cam[4 * r + 3];
     }
+    for (int c = 0; c < 3; ++c)
+      d.o[c] = -(d.R[c] * d.t[0] + d.R[3 + c] * d.t[1] + d.R[6 + c] * d.t[2]);
     d.near_plane = f.near_plane, d.time = f.time;
     d.limx = (double)consts->guard * 0.5 * L.W / f.fx;
     d.limy = (double)consts->guard * 0.5 * L.H / f.fy;
@@ -355,8 +367,7 @@ gftorf_status gftorf_preprocess_bwd(const gftorf_dims* dims,
                                     void* stream) {
   if (!dims_ok(dims) || !g || !grads) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
-  if (L.N > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->amplitude))
-    return GFTORF_ERR_ARG;
+  if (!params_ok(L, g)) return GFTORF_ERR_ARG;
   gftorf_status s = check_ws(L, workspace, workspace_bytes);
   if (s != GFTORF_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -375,8 +386,7 @@ gftorf_status gftorf_render_bwd(const gftorf_dims* dims,
                                 size_t workspace_bytes, void* stream) {
   if (!dims_ok(dims) || !g || !bg || !dL_dout || !grads) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
-  if (L.N > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->amplitude))
-    return GFTORF_ERR_ARG;
+  if (!params_ok(L, g)) return GFTORF_ERR_ARG;
   gftorf_status s = check_ws(L, workspace, workspace_bytes);
   if (s != GFTORF_OK) return s;
   s = gftorf_zero_grad_buffers(dims, grads, workspace, workspace_bytes, stream);

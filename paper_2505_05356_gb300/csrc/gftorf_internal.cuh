@@ -13,6 +13,7 @@ namespace gftorf {
 constexpr int kMaxF = GFTORF_MAX_FREQ;
 constexpr int kMaxP = GFTORF_MAX_OFFSETS;
 constexpr int kMaxFrames = GFTORF_MAX_FRAMES;
+constexpr int kMaxSh = GFTORF_MAX_SH;
 constexpr uint32_t kCulledKey = 0xFFFFFFFFu;
 
 // Depth sort geometry: 256 threads, 8 keys each, one tile of 2048 keys.
@@ -34,6 +35,7 @@ struct FrameT {
   T t[3];
   T near_plane, time;
   T limx, limy;  // guard * half field of view (tan), x and y
+  T o[3];        // optical centre -R^T t (world), exact for a non-orthonormal R
 };
 
 // Everything a batch needs besides the arrays: written into the workspace by
@@ -69,6 +71,7 @@ struct Layout {
   int cull;  // drop (Gaussian, tile) pairs that cannot reach alpha_min
   int count_pairs;  // count evaluated (pixel, Gaussian) pairs in the forward
   int phasor, depth;  // extra output channels (Eq. 3 phasor, Eq. 5 depth)
+  int nsh;            // SH reflectivity coefficients per Gaussian (0: scalar)
   int tiles_x, tiles_y, NT;
   int rec_stride;  // Reals per projected record (16-byte multiple)
   int g2d_stride;  // Reals per 2D-gradient row

@@ -5,7 +5,9 @@
 // Forward per (frame b, Gaussian g), Sec. 4 and the 3DGS projection it uses:
 //   x   = mu + c1 t + c2 t^2 + c3 t^3 + delta_b            (deformation)
 //   p   = R x + t_cam; cull if p_z <= near
-//   d   = |p| = distance to the optical centre (R orthonormal)
+//   d   = |x - o| = distance to the optical centre o = -R^T t_cam (equal to
+//         |p| for an orthonormal R; taken from o so that a rounded R does
+//         not perturb it)
 //   Sigma = Rq diag(s)^2 Rq^T,  Rq from the normalised quaternion
 //   J   = [[fx/z, 0, -fx tx/z], [0, fy/z, -fy ty/z]], tx, ty = p_x/z, p_y/z
 //         clamped to +-guard * half fov
@@ -13,7 +15,9 @@
 //   conic = cov^-1, radius = ceil(sigma_cut sqrt(lambda_max)) (discriminant
 //   floored at 0.1), (u, v) = (fx p_x/z + cx, fy p_y/z + cy)
 //   A = s r / d^2; features A sin psi_f, A cos psi_f (psi_f = 4 pi d f / c),
-//   and A for the ambient channel.
+//   and A for the ambient channel.  r is the scalar amplitude, or (Sec. 4,
+//   view-dependent reflectivity) max(0, 0.5 + sum_l sh_l Y_l(w)) with w the
+//   world-space unit vector from the optical centre, w = (x - o) / d.
 // The record keeps the conic scaled by -log2(e)/2 (and -log2(e) for the
 // cross term) and log2 of the opacity, so that compositing evaluates
 // o exp(power) as one ex2; 1/o follows the features.
@@ -35,11 +39,94 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
 
+// Real spherical harmonics of degree 0..3 (orthonormal on the unit sphere,
+// no Condon-Shortley phase), ordered by degree, then m = -l..l.  Constants:
+//   Y0 = 1/(2 sqrt(pi)), K1 = sqrt(3/(4 pi)),
+//   K2a = sqrt(15/pi)/2, K2b = sqrt(5/pi)/4, K2c = sqrt(15/pi)/4,
+//   K3a = sqrt(35/(2 pi))/4, K3b = sqrt(105/pi)/2, K3c = sqrt(21/(2 pi))/4,
+//   K3d = sqrt(7/pi)/4, K3e = sqrt(105/pi)/4.
+constexpr double kY0 = 0.28209479177387814, kK1 = 0.4886025119029199,
+                 kK2a = 1.0925484305920792, kK2b = 0.31539156525252005,
+                 kK2c = 0.5462742152960396, kK3a = 0.5900435899266435,
+                 kK3b = 2.890611442640554, kK3c = 0.4570457994644658,
+                 kK3d = 0.3731763325901154, kK3e = 1.445305721320277;
+
+template <typename Real>
+__device__ __forceinline__ void sh_basis(Real x, Real y, Real z, Real* Y) {
+  const Real xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = Real(kY0);
+  Y[1] = Real(kK1) * y;
+  Y[2] = Real(kK1) * z;
+  Y[3] = Real(kK1) * x;
+  Y[4] = Real(kK2a) * x * y;
+  Y[5] = Real(kK2a) * y * z;
+  Y[6] = Real(kK2b) * (Real(2) * zz - xx - yy);
+  Y[7] = Real(kK2a) * x * z;
+  Y[8] = Real(kK2c) * (xx - yy);
+  Y[9] = Real(kK3a) * y * (Real(3) * xx - yy);
+  Y[10] = Real(kK3b) * x * y * z;
+  Y[11] = Real(kK3c) * y * (Real(4) * zz - xx - yy);
+  Y[12] = Real(kK3d) * z * (Real(2) * zz - Real(3) * xx - Real(3) * yy);
+  Y[13] = Real(kK3c) * x * (Real(4) * zz - xx - yy);
+  Y[14] = Real(kK3e) * z * (xx - yy);
+  Y[15] = Real(kK3a) * x * (xx - Real(3) * yy);
+}
+
+// g = sum_l c_l grad Y_l at (x, y, z), the basis taken as polynomials on R^3
+template <typename Real>
+__device__ __forceinline__ void sh_grad(const Real* c, Real x, Real y, Real z, Real* g) {
+  const Real xx = x * x, yy = y * y, zz = z * z;
+  const Real K1 = Real(kK1), K2a = Real(kK2a), K2b = Real(kK2b), K2c = Real(kK2c);
+  const Real K3a = Real(kK3a), K3b = Real(kK3b), K3c = Real(kK3c), K3d = Real(kK3d),
+             K3e = Real(kK3e);
+  Real gx = K1 * c[3], gy = K1 * c[1], gz = K1 * c[2];
+  gx += K2a * (c[4] * y + c[7] * z) - Real(2) * K2b * c[6] * x + Real(2) * K2c * c[8] * x;
+  gy += K2a * (c[4] * x + c[5] * z) - Real(2) * K2b * c[6] * y - Real(2) * K2c * c[8] * y;
+  gz += K2a * (c[5] * y + c[7] * x) + Real(4) * K2b * c[6] * z;
+  // degree 3
+  gx += c[9] * K3a * Real(6) * x * y + c[10] * K3b * y * z - c[11] * K3c * Real(2) * x * y -
+        c[12] * K3d * Real(6) * x * z + c[13] * K3c * (Real(4) * zz - Real(3) * xx - yy) +
+        c[14] * K3e * Real(2) * x * z + c[15] * K3a * Real(3) * (xx - yy);
+  gy += c[9] * K3a * Real(3) * (xx - yy) + c[10] * K3b * x * z +
+        c[11] * K3c * (Real(4) * zz - xx - Real(3) * yy) - c[12] * K3d * Real(6) * y * z -
+        c[13] * K3c * Real(2) * x * y - c[14] * K3e * Real(2) * y * z -
+        c[15] * K3a * Real(6) * x * y;
+  gz += c[10] * K3b * x * y + c[11] * K3c * Real(8) * y * z +
+        c[12] * K3d * (Real(6) * zz - Real(3) * xx - Real(3) * yy) +
+        c[13] * K3c * Real(8) * x * z + c[14] * K3e * (xx - yy);
+  g[0] = gx, g[1] = gy, g[2] = gz;
+}
+
 template <typename Real>
 struct Params {
   Real mu[3], c[9], s[3], q[4], o, amp;
   bool has_c;
 };
+
+// SH coefficients of Gaussian g, zero beyond n_sh
+template <typename Real>
+__device__ __forceinline__ void load_sh(const gftorf_gaussians& G, int g, int nsh, Real* c) {
+  const Real* src = static_cast<const Real*>(G.sh) + (size_t)nsh * g;
+#pragma unroll
+  for (int l = 0; l < kMaxSh; ++l) c[l] = l < nsh ? src[l] : Real(0);
+}
+
+// r = max(0, 0.5 + sum_l c_l Y_l(w)), w = e / d with e = x - o (world frame);
+// returns the unclamped value in *val and w in w[3]
+template <typename Real>
+__device__ __forceinline__ Real sh_reflectivity(const Real* c, const Real* e, Real d, Real* w,
+                                                Real* val) {
+  const Real id = Real(1) / d;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) w[a] = e[a] * id;
+  Real Y[kMaxSh];
+  sh_basis<Real>(w[0], w[1], w[2], Y);
+  Real v = Real(0.5);
+#pragma unroll
+  for (int l = 0; l < kMaxSh; ++l) v += c[l] * Y[l];
+  *val = v;
+  return v > Real(0) ? v : Real(0);
+}
 
 template <typename Real>
 __device__ __forceinline__ void load_params(const gftorf_gaussians& G, int g,
@@ -64,13 +151,14 @@ __device__ __forceinline__ void load_params(const gftorf_gaussians& G, int g,
     for (int a = 0; a < 9; ++a) P.c[a] = Real(0);
   }
   P.o = static_cast<const Real*>(G.opacity)[g];
-  P.amp = static_cast<const Real*>(G.amplitude)[g];
+  P.amp = G.amplitude ? static_cast<const Real*>(G.amplitude)[g] : Real(0);
 }
 
 // Forward geometry shared by the forward kernel and the backward recompute.
 template <typename Real>
 struct Geo {
   Real x[3], p[3];
+  Real e[3];  // x - o
   Real iz, d;
   Real qn[4], inv_qlen;  // normalised quaternion and 1/|q|
   Real Rq[9], M[9], S[6];  // S: Sigma (00, 01, 02, 11, 12, 22)
@@ -97,7 +185,9 @@ __device__ __forceinline__ void geometry(const Params<Real>& P,
     Q.p[r] = (Real)fr.R[3 * r] * Q.x[0] + (Real)fr.R[3 * r + 1] * Q.x[1] +
              (Real)fr.R[3 * r + 2] * Q.x[2] + (Real)fr.t[r];
   Q.iz = Real(1) / Q.p[2];
-  Q.d = sqrt(Q.p[0] * Q.p[0] + Q.p[1] * Q.p[1] + Q.p[2] * Q.p[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Q.e[a] = Q.x[a] - (Real)fr.o[a];
+  Q.d = sqrt(Q.e[0] * Q.e[0] + Q.e[1] * Q.e[1] + Q.e[2] * Q.e[2]);
 
   Real ql2 = P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3];
   Q.inv_qlen = rsqrt_t<Real>(ql2);
@@ -159,13 +249,13 @@ __device__ __forceinline__ void geometry(const Params<Real>& P,
   Q.det = Q.cov[0] * Q.cov[2] - Q.cov[1] * Q.cov[1];
 }
 
-template <typename Real, int F>
+template <typename Real, int F, bool SH>
 __global__ void __launch_bounds__(256)
     preprocess_kernel(gftorf_gaussians G, const TableT<Real>* __restrict__ tab,
                       Header* __restrict__ hdr, Real* __restrict__ rec,
                       uint2* __restrict__ rect, uint32_t* __restrict__ zkey,
                       int N, int TW, int TH, int tiles_x, int tiles_y,
-                      int rec_stride, int cull) {
+                      int rec_stride, int cull, int nsh) {
   constexpr int NF = 2 * F + 1;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
@@ -222,7 +312,13 @@ __global__ void __launch_bounds__(256)
         o[3] = Real(-kLog2e) * cb;
         o[4] = Real(-0.5 * kLog2e) * cc;
         o[5] = log2(P.o);  // alpha = 2^(power2 + log2 o)
-        const Real A = tab->source * P.amp / (Q.d * Q.d);
+        Real refl = P.amp;
+        if (SH) {
+          Real c[kMaxSh], w[3], val;
+          load_sh<Real>(G, g, nsh, c);
+          refl = sh_reflectivity<Real>(c, Q.e, Q.d, w, &val);
+        }
+        const Real A = tab->source * refl / (Q.d * Q.d);
 #pragma unroll
         for (int f = 0; f < F; ++f) {
           Real sn, cs;
@@ -252,18 +348,23 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // backward: d(record) of every frame -> d(parameters); frames looped in-thread
 // ---------------------------------------------------------------------------
-template <typename Real, int F>
+template <typename Real, int F, bool SH>
 __global__ void __launch_bounds__(128)
     preprocess_bwd_kernel(gftorf_gaussians G, gftorf_gradients D,
                           const TableT<Real>* __restrict__ tab,
                           const uint2* __restrict__ rect,
                           const Real* __restrict__ g2d, int g2d_stride, int N,
-                          int B) {
+                          int B, int nsh) {
   constexpr int NF = 2 * F + 1;
+  constexpr int NS = SH ? kMaxSh : 1;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   Params<Real> P;
   load_params<Real>(G, g, P);
+  Real csh[NS], gsh[NS];
+#pragma unroll
+  for (int l = 0; l < NS; ++l) gsh[l] = Real(0);
+  if (SH) load_sh<Real>(G, g, nsh, csh);
   Real gmu[3] = {0, 0, 0}, gc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   Real gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0, gamp = 0;
   const Real dil = (Real)tab->dilation;
@@ -301,7 +402,9 @@ __global__ void __launch_bounds__(128)
 
     // --- C-ToF features: A = s r / d^2, psi_f = pi kf d ---
     const Real id = Real(1) / Q.d;
-    const Real A = (Real)tab->source * P.amp * id * id;
+    Real refl = P.amp, wv[3] = {0, 0, 0}, val = 0;
+    if (SH) refl = sh_reflectivity<Real>(csh, Q.e, Q.d, wv, &val);
+    const Real A = (Real)tab->source * refl * id * id;
     Real gA = gf[2 * F];
     Real gd = 0;
 #pragma unroll
@@ -313,9 +416,27 @@ __global__ void __launch_bounds__(128)
       const Real gpsi = A * (gf[2 * f] * c - gf[2 * f + 1] * s);
       gd += gpsi * Real(kPiD) * kf;
     }
-    gamp += gA * (Real)tab->source * id * id;
+    const Real gr_ = gA * (Real)tab->source * id * id;  // dL/dr
+    Real gw[3] = {0, 0, 0};  // dL/d(x - o) through the SH direction
+    if (!SH) {
+      gamp += gr_;
+    } else if (val > Real(0)) {
+      Real Y[kMaxSh];
+      sh_basis<Real>(wv[0], wv[1], wv[2], Y);
+#pragma unroll
+      for (int l = 0; l < NS; ++l) gsh[l] += gr_ * Y[l];
+      // w = v / |v|: dL/dv = (I - w w^T) dL/dw / |v|
+      Real gdir[3];
+      sh_grad<Real>(csh, wv[0], wv[1], wv[2], gdir);
+      const Real wd = wv[0] * gdir[0] + wv[1] * gdir[1] + wv[2] * gdir[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gw[a] = gr_ * (gdir[a] - wv[a] * wd) * id;
+    }
     gd += gA * Real(-2) * A * id + gdist;
-    Real gp[3] = {gd * Q.p[0] * id, gd * Q.p[1] * id, gd * Q.p[2] * id};
+    // d = |x - o|: dL/dx += gd (x - o) / d, in world coordinates
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gw[a] += gd * Q.e[a] * id;
+    Real gp[3] = {0, 0, 0};
 
     // --- mean 2D ---
     gp[0] += gu * fx * iz;
@@ -380,7 +501,8 @@ __global__ void __launch_bounds__(128)
     Real gx[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      gx[a] = (Real)fr.R[a] * gp[0] + (Real)fr.R[3 + a] * gp[1] + (Real)fr.R[6 + a] * gp[2];
+      gx[a] = (Real)fr.R[a] * gp[0] + (Real)fr.R[3 + a] * gp[1] + (Real)fr.R[6 + a] * gp[2] +
+              gw[a];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       gmu[a] += gx[a];
@@ -445,6 +567,12 @@ __global__ void __launch_bounds__(128)
   }
   if (D.opacity) static_cast<Real*>(D.opacity)[g] = go;
   if (D.amplitude) static_cast<Real*>(D.amplitude)[g] = gamp;
+  if (SH && D.sh) {
+    Real* o = static_cast<Real*>(D.sh) + (size_t)nsh * g;
+#pragma unroll
+    for (int l = 0; l < NS; ++l)
+      if (l < nsh) o[l] = gsh[l];
+  }
 }
 
 }  // namespace
@@ -460,9 +588,14 @@ void launch_preprocess(const Layout& L, const gftorf_gaussians& g,
   auto* rect = at<uint2>(ws, L.off_rect);
   auto* zkey = at<uint32_t>(ws, L.off_zkey);
 #define GFTORF_PRE(FF)                                                         \
-  preprocess_kernel<Real, FF><<<grid, 256, 0, st>>>(                           \
-      g, tab, hdr, rec, rect, zkey, L.N, L.TW, L.TH, L.tiles_x, L.tiles_y,     \
-      L.rec_stride, L.cull)
+  if (L.nsh)                                                                   \
+    preprocess_kernel<Real, FF, true><<<grid, 256, 0, st>>>(                   \
+        g, tab, hdr, rec, rect, zkey, L.N, L.TW, L.TH, L.tiles_x, L.tiles_y,   \
+        L.rec_stride, L.cull, L.nsh);                                          \
+  else                                                                         \
+    preprocess_kernel<Real, FF, false><<<grid, 256, 0, st>>>(                  \
+        g, tab, hdr, rec, rect, zkey, L.N, L.TW, L.TH, L.tiles_x, L.tiles_y,   \
+        L.rec_stride, L.cull, 0)
   switch (L.F) {
     case 1: GFTORF_PRE(1); break;
     case 2: GFTORF_PRE(2); break;
@@ -483,8 +616,12 @@ void launch_preprocess_bwd(const Layout& L, const gftorf_gaussians& g,
   auto* rect = at<const uint2>(ws, L.off_rect);
   auto* g2d = at<const Real>(ws, L.off_g2d);
 #define GFTORF_PREB(FF)                                                        \
-  preprocess_bwd_kernel<Real, FF><<<grid, 128, 0, st>>>(                       \
-      g, gr, tab, rect, g2d, L.g2d_stride, L.N, L.B)
+  if (L.nsh)                                                                   \
+    preprocess_bwd_kernel<Real, FF, true><<<grid, 128, 0, st>>>(               \
+        g, gr, tab, rect, g2d, L.g2d_stride, L.N, L.B, L.nsh);                 \
+  else                                                                         \
+    preprocess_bwd_kernel<Real, FF, false><<<grid, 128, 0, st>>>(              \
+        g, gr, tab, rect, g2d, L.g2d_stride, L.N, L.B, 0)
   switch (L.F) {
     case 1: GFTORF_PREB(1); break;
     case 2: GFTORF_PREB(2); break;

@@ -35,6 +35,7 @@ class Dims(ctypes.Structure):
                 ("n_freq", ctypes.c_int32), ("n_offsets", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("render_mode", ctypes.c_int32),
                 ("pixels_per_thread", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("n_sh", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("max_instances", ctypes.c_int64)]
 
 
@@ -59,12 +60,13 @@ class Consts(ctypes.Structure):
 
 class Gaussians(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("means", "coeffs", "scales", "quats", "opacity", "amplitude", "delta")]
+                ("means", "coeffs", "scales", "quats", "opacity", "amplitude", "delta", "sh")]
 
 
 class Gradients(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("means", "coeffs", "scales", "quats", "opacity", "amplitude", "delta", "bg")]
+                ("means", "coeffs", "scales", "quats", "opacity", "amplitude", "delta", "bg",
+                 "sh")]
 
 
 _LIB = None
@@ -211,14 +213,15 @@ def consts_from_scene(scene) -> Consts:
     return make_consts(k.dilation, k.alpha_max, k.alpha_min, k.t_min, k.guard, k.sigma_cut)
 
 
-PARAM_NAMES = ("means", "coeffs", "scales", "quats", "opacity", "amplitude", "delta")
+PARAM_NAMES = ("means", "coeffs", "scales", "quats", "opacity", "amplitude", "delta", "sh")
+GRAD_NAMES = ("means", "coeffs", "scales", "quats", "opacity", "amplitude", "delta", "bg", "sh")
 
 
 def params_from_scene(scene, device="cuda", dtype=torch.float32) -> Dict[str, torch.Tensor]:
-    """Scene arrays as device tensors (coeffs / delta may be None)."""
+    """Scene arrays as device tensors (coeffs / delta / sh may be None)."""
     out = {}
     for k in PARAM_NAMES:
-        a = getattr(scene, k)
+        a = getattr(scene, k, None)
         out[k] = None if a is None else torch.as_tensor(a).to(device=device, dtype=dtype).contiguous()
     return out
 
@@ -233,14 +236,14 @@ class Renderer:
 
     def __init__(self, n, frames, width, height, n_freq=1, n_offsets=4,
                  tile=(16, 16), dtype=torch.float32, render_mode=0,
-                 max_instances=None, device="cuda", pixels_per_thread=0, flags=0):
+                 max_instances=None, device="cuda", pixels_per_thread=0, flags=0, n_sh=0):
         _require_cuda()
         self.lib = load()
         self.torch_dtype = dtype
         self.device = torch.device(device)
         self.dims = Dims(n, frames, width, height, tile[0], tile[1], n_freq,
                          n_offsets, F64 if dtype == torch.float64 else F32,
-                         render_mode, pixels_per_thread, flags, 0)
+                         render_mode, pixels_per_thread, flags, n_sh, 0, 0)
         self.C = (n_freq * n_offsets + 1 + (2 * n_freq if flags & FLAG_PHASOR else 0) +
                   (1 if flags & FLAG_DEPTH else 0))
         self.tiles_x = -(-width // tile[0])
@@ -263,6 +266,10 @@ class Renderer:
         return int(self.dims.max_instances)
 
     def _gaussians(self, p: Dict[str, torch.Tensor]) -> Gaussians:
+        nsh = self.dims.n_sh
+        sh = p.get("sh")
+        if nsh and (sh is None or sh.dim() != 2 or sh.shape[1] != nsh):
+            raise ValueError("sh must be (N, %d) for n_sh = %d" % (nsh, nsh))
         g = Gaussians()
         for k in PARAM_NAMES:
             t = p.get(k)
@@ -295,8 +302,7 @@ class Renderer:
         return out
 
     def render_bwd(self, params, bg, dout, grads: Optional[Dict[str, torch.Tensor]] = None,
-                   want=("means", "coeffs", "scales", "quats", "opacity", "amplitude",
-                         "delta", "bg")):
+                   want=GRAD_NAMES):
         d = self.dims
         if grads is None:
             grads = self.alloc_grads(params, bg, want)
@@ -343,8 +349,7 @@ class Renderer:
                                               self.ws_ptr, self.ws_bytes, _stream()),
                "gftorf_preprocess_bwd")
 
-    def alloc_grads(self, params, bg, want=("means", "coeffs", "scales", "quats", "opacity",
-                                            "amplitude", "delta", "bg")):
+    def alloc_grads(self, params, bg, want=GRAD_NAMES):
         grads = {}
         for k in want:
             if k == "bg":
@@ -419,7 +424,8 @@ def sort_footprints(u, v, radius, z, width, height, tile=(16, 16), max_instances
     if max_instances is None:
         r = radius.to(torch.int64).clamp(min=0)
         max_instances = int((((2 * r) // tile[0] + 2) * ((2 * r) // tile[1] + 2)).sum().item())
-    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, 0, 0, max(1, max_instances))
+    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, 0, 0,
+                max_instances=max(1, max_instances))
     nbytes = L.gftorf_workspace_size(ctypes.byref(dims))
     if nbytes == 0:
         raise GftorfError(ERR_ARG, "gftorf_workspace_size")
@@ -451,7 +457,8 @@ def sort_footprints_noalloc(u, v, radius, z, width, height, tile=(16, 16), max_i
     _require_cuda()
     L = load()
     B, n = u.shape
-    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, 0, 0, int(max_instances))
+    dims = Dims(n, B, width, height, tile[0], tile[1], 1, 1, F32, 0, 0, 0,
+                max_instances=int(max_instances))
     cap = max(1, int(max_instances))
     keys = torch.empty(cap, dtype=torch.int64, device=u.device)
     vals = torch.empty(cap, dtype=torch.int32, device=u.device)
@@ -470,16 +477,18 @@ class RenderCToF(torch.autograd.Function):
     Gaussian parameters, the per-frame displacement and the background.
 
     forward(renderer, frames, sensor, consts, bg, means, coeffs, scales, quats,
-            opacity, amplitude, delta) -> out[B][C][H][W]
+            opacity, amplitude, delta, sh) -> out[B][C][H][W]
+    (coeffs, delta, sh may be None; amplitude is unused when sh is given)
     """
 
     @staticmethod
     def forward(ctx, renderer: Renderer, frames, sensor, consts, bg, means, coeffs,
-                scales, quats, opacity, amplitude, delta):
-        params = dict(means=means.contiguous(), coeffs=None if coeffs is None else coeffs.contiguous(),
+                scales, quats, opacity, amplitude, delta, sh=None):
+        c = lambda t: None if t is None else t.contiguous()
+        params = dict(means=means.contiguous(), coeffs=c(coeffs),
                       scales=scales.contiguous(), quats=quats.contiguous(),
-                      opacity=opacity.contiguous(), amplitude=amplitude.contiguous(),
-                      delta=None if delta is None else delta.contiguous())
+                      opacity=opacity.contiguous(), amplitude=c(amplitude),
+                      delta=c(delta), sh=c(sh))
         renderer.preprocess(params, frames, sensor, consts)
         out = renderer.render_fwd(bg.contiguous())
         ctx.renderer = renderer
@@ -497,18 +506,18 @@ class RenderCToF(torch.autograd.Function):
             # the workspace now holds another batch: recompute this one
             r.preprocess(p, *ctx.setup)
             r.render_fwd(bg.contiguous())
-        want = ["means", "scales", "quats", "opacity", "amplitude", "bg"]
-        if p["coeffs"] is not None:
-            want.append("coeffs")
-        if p["delta"] is not None:
-            want.append("delta")
+        want = ["means", "scales", "quats", "opacity", "bg"]
+        for k in ("amplitude", "coeffs", "delta", "sh"):
+            if p[k] is not None:
+                want.append(k)
         g = r.render_bwd(p, bg.contiguous(), dout.contiguous(), want=want)
         return (None, None, None, None, g.get("bg"), g.get("means"), g.get("coeffs"),
                 g.get("scales"), g.get("quats"), g.get("opacity"), g.get("amplitude"),
-                g.get("delta"))
+                g.get("delta"), g.get("sh"))
 
 
 def render_ctof(renderer, frames, sensor, consts, bg, params):
     return RenderCToF.apply(renderer, frames, sensor, consts, bg, params["means"],
                             params.get("coeffs"), params["scales"], params["quats"],
-                            params["opacity"], params["amplitude"], params.get("delta"))
+                            params["opacity"], params.get("amplitude"), params.get("delta"),
+                            params.get("sh"))

@@ -139,6 +139,15 @@ def _sigmoid(x):
     return 1.0 / (1.0 + np.exp(-x))
 
 
+def _rotation_xyz(rx, ry, rz) -> np.ndarray:
+    """Rotation about x, then y, then z (angles in degrees)."""
+    a, b, c = (math.radians(v) for v in (rx, ry, rz))
+    Rx = np.array([[1, 0, 0], [0, math.cos(a), -math.sin(a)], [0, math.sin(a), math.cos(a)]])
+    Ry = np.array([[math.cos(b), 0, math.sin(b)], [0, 1, 0], [-math.sin(b), 0, math.cos(b)]])
+    Rz = np.array([[math.cos(c), -math.sin(c), 0], [math.sin(c), math.cos(c), 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
 def random_gaussians(rng, n, cam: Camera, z_range=(1.0, 3.0), box=False,
                      log_scale=(-3.5, 0.3), coeff_std=0.0):
     """Random Gaussians: depth uniform in z_range, lateral position uniform
@@ -170,7 +179,10 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
     ('zero' | 'random'), z_range, coeff_std, visible_min, consts, phasor,
     depth, sh_degree (0..3: view-dependent reflectivity from (degree+1)^2 SH
     coefficients; the DC term reproduces the scalar amplitude draw, the others
-    are N(0, sh_std) with sh_std 0.03 by default).
+    are N(0, sh_std) with sh_std 0.03 by default), pose ((rx, ry, rz) degrees
+    of an x-then-y-then-z rotation, optical centre (cx, cy, cz)): a moved
+    camera, with the Gaussians drawn in its frustum and stored in world
+    coordinates.
     """
     rng = np.random.default_rng(seed)
     if name == "static_1k":
@@ -195,6 +207,13 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
     cam = pinhole(d["width"], d["height"])
     means, coeffs, scales, quats, opacity, amplitude = random_gaussians(
         rng, d["n"], cam, d["z_range"], d["box"], d["log_scale"], d["coeff_std"])
+    if d.get("pose") is not None:
+        R = _rotation_xyz(*d["pose"][0])
+        centre = np.asarray(d["pose"][1], np.float64)
+        rt = np.concatenate([R, (-R @ centre)[:, None]], 1).astype(F32)
+        cam.world_to_cam = rt
+        R32 = rt[:, :3].astype(np.float64)
+        means = (means.astype(np.float64) @ R32 + centre).astype(F32)
     frames = d["frames"]
     times = (np.arange(frames) / max(frames - 1, 1)).astype(F32)
     if frames == 1 and d["coeff_std"] > 0:

@@ -16,7 +16,8 @@ def run_gpu(scene, dout=None, dtype=torch.float32, render_mode=0, capacity=None,
                         tile=(scene.consts.tile_w, scene.consts.tile_h), dtype=dtype,
                         render_mode=render_mode,
                         max_instances=capacity, pixels_per_thread=pixels_per_thread,
-                        flags=flags | gftorf.flags_from_scene(scene))
+                        flags=flags | gftorf.flags_from_scene(scene),
+                        n_sh=getattr(scene, "n_sh", 0))
     p = gftorf.params_from_scene(scene, dev, dtype)
     fr = gftorf.frames_from_scene(scene)
     se = gftorf.sensor_from_scene(scene)

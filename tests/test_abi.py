@@ -39,7 +39,7 @@ def test_version_and_status_strings(lib):
 def _dims(**kw):
     d = dict(n_gaussians=1000, n_frames=2, width=64, height=48, tile_w=16, tile_h=16,
              n_freq=1, n_offsets=4, dtype=0, render_mode=0, pixels_per_thread=0,
-             flags=0, max_instances=10000)
+             flags=0, n_sh=0, reserved=0, max_instances=10000)
     d.update(kw)
     return gftorf.Dims(*[d[k] for k, _ in gftorf.Dims._fields_])
 
@@ -56,12 +56,15 @@ def test_workspace_size_validates_dims(lib):
                 dict(n_offsets=9), dict(dtype=2), dict(render_mode=2),
                 dict(pixels_per_thread=3), dict(pixels_per_thread=8),
                 dict(tile_w=8, tile_h=8, pixels_per_thread=4), dict(flags=16),
-                dict(n_gaussians=-1), dict(max_instances=-1),
+                dict(n_gaussians=-1), dict(max_instances=-1), dict(n_sh=2),
+                dict(n_sh=25), dict(reserved=1),
                 dict(max_instances=1 << 33)):
         assert lib.gftorf_workspace_size(ctypes.byref(_dims(**bad))) == 0, bad
     assert lib.gftorf_workspace_size(None) == 0
     # the empty scene is a valid problem
     assert lib.gftorf_workspace_size(ctypes.byref(_dims(n_gaussians=0))) > 0
+    for nsh in (1, 4, 9, 16):
+        assert lib.gftorf_workspace_size(ctypes.byref(_dims(n_sh=nsh))) > 0
 
 
 def test_host_side_argument_errors(lib):
@@ -88,6 +91,12 @@ def test_host_side_argument_errors(lib):
                                  ctypes.c_void_p(4096), need - 1, None) == gftorf.ERR_WORKSPACE
     # non-finite camera values are rejected on the host
     pg = gftorf.Gaussians(*([ctypes.c_void_p(256)] * 7))
+    # SH reflectivity needs its coefficient array
+    dsh = _dims(n_sh=4)
+    assert lib.gftorf_preprocess(ctypes.byref(dsh), ctypes.byref(pg), fr, ctypes.byref(se),
+                                 ctypes.byref(co), ctypes.c_void_p(4096),
+                                 lib.gftorf_workspace_size(ctypes.byref(dsh)),
+                                 None) == gftorf.ERR_ARG
     fr[1].fx = float("nan")
     assert lib.gftorf_preprocess(ctypes.byref(d), ctypes.byref(pg), fr, ctypes.byref(se),
                                  ctypes.byref(co), ctypes.c_void_p(4096), need,
@@ -105,9 +114,9 @@ def test_host_side_argument_errors(lib):
 
 def test_struct_layouts_match_header():
     # sizes fixed by the header's field lists (C layout, no hidden padding)
-    assert ctypes.sizeof(gftorf.Dims) == 12 * 4 + 8
+    assert ctypes.sizeof(gftorf.Dims) == 14 * 4 + 8
     assert ctypes.sizeof(gftorf.Frame) == 18 * 4
     assert ctypes.sizeof(gftorf.Sensor) == (4 + 8 + 1) * 4
     assert ctypes.sizeof(gftorf.Consts) == 6 * 4
-    assert ctypes.sizeof(gftorf.Gaussians) == 7 * ctypes.sizeof(ctypes.c_void_p)
-    assert ctypes.sizeof(gftorf.Gradients) == 8 * ctypes.sizeof(ctypes.c_void_p)
+    assert ctypes.sizeof(gftorf.Gaussians) == 8 * ctypes.sizeof(ctypes.c_void_p)
+    assert ctypes.sizeof(gftorf.Gradients) == 9 * ctypes.sizeof(ctypes.c_void_p)

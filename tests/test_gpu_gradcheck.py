@@ -72,3 +72,27 @@ def test_central_differences_every_group_fp64():
             assert got == pytest.approx(fd, rel=1e-5, abs=1e-6 * (1 + abs(fd))), (name, i)
             checked += 1
     assert checked >= 120
+
+
+def test_torch_gradcheck_sh_moved_camera_fp64():
+    """SH reflectivity (degree 3) under a rotated, shifted camera: gradients of
+    the SH coefficients and of the means through the view direction."""
+    sc = scenes.make_scene("batch_300k", 8, n=150, width=32, height=32, frames=2,
+                           visible_min=0.7, sh_degree=3, sh_std=0.1,
+                           pose=((4.0, -6.0, 3.0), (0.1, -0.05, -0.2)))
+    r = gftorf.Renderer(sc.n, sc.frames, 32, 32, 1, 4, dtype=torch.float64,
+                        max_instances=64 * sc.n * sc.frames, n_sh=16)
+    p = gftorf.params_from_scene(sc, dtype=torch.float64)
+    fr, se, co = (gftorf.frames_from_scene(sc), gftorf.sensor_from_scene(sc),
+                  gftorf.consts_from_scene(sc))
+    bg = torch.as_tensor(sc.bg, device="cuda", dtype=torch.float64)
+    names = ("means", "coeffs", "scales", "quats", "opacity", "delta", "sh")
+    inputs = [p[k].clone().requires_grad_(True) for k in names]
+
+    def f(means, coeffs, scales, quats, opacity, delta, sh):
+        return gftorf.RenderCToF.apply(r, fr, se, co, bg, means, coeffs, scales, quats,
+                                       opacity, None, delta, sh)
+
+    assert torch.autograd.gradcheck(f, inputs, eps=1e-6, atol=1e-5, rtol=1e-4,
+                                    fast_mode=True, nondet_tol=1e-12)
+    assert r.read_status()[0] == gftorf.OK

@@ -17,6 +17,8 @@ from tests.gpu_helpers import forward_close, grads_close, run_gpu
 
 pytestmark = pytest.mark.gpu
 
+POSE = ((4.0, -6.0, 3.0), (0.1, -0.05, -0.2))
+
 SMALL = [
     ("static_1k", dict()),
     ("static_1k", dict(width=50, height=37)),
@@ -29,7 +31,25 @@ SMALL = [
     ("batch_300k", dict(n=3000, width=72, height=56, frames=2, phasor=True, depth=True)),
     ("static_1k", dict(freqs_hz=[30e6, 80e6], z_range=(0.5, 6.0), phasor=True, depth=True,
                        tile=(16, 32))),
+    ("static_1k", dict(sh_degree=0)),
+    ("static_1k", dict(sh_degree=1)),
+    ("batch_300k", dict(n=3000, width=72, height=56, frames=3, sh_degree=3, sh_std=0.1)),
+    ("batch_300k", dict(n=2000, width=64, height=48, frames=2, sh_degree=2, depth=True)),
+    # a moved camera (rotation + translation): the SH direction is a world-space
+    # direction, no longer the camera-frame one
+    ("batch_300k", dict(n=3000, width=72, height=56, frames=3, pose=POSE)),
+    ("batch_300k", dict(n=3000, width=72, height=56, frames=3, sh_degree=3, sh_std=0.1,
+                        pose=POSE)),
+    ("static_1k", dict(sh_degree=1, pose=((3.0, -5.0, 8.0), (0.05, -0.1, -0.3)))),
 ]
+
+# Forward bar of the moved-camera cases.  With R = I the camera transform is
+# exact in FP32; a general rigid transform p = R x + t rounds three more
+# products and sums per coordinate (~3e-7 m at 2 m), which moves a
+# footprint's centre by ~1e-5 px at the image border.  Where a small, steep
+# footprint dominates a pixel this reaches 1.7e-5 of the sample (the same with
+# scalar and SH reflectivity); the bar there is 3e-5.
+FWD_REL_POSED = 3e-5
 
 
 def _ids(case):
@@ -44,7 +64,8 @@ def test_forward_matches_oracle(case):
     q_ora, tf_ora, amb, nc = ora.render(sc, ora.EPS_F32)
     res = run_gpu(sc)
     assert res["status"][0] == gftorf.OK
-    ok, worst, nflag = forward_close(res["out"], q_ora, amb)
+    rel = FWD_REL_POSED if "pose" in kw else 1e-5
+    ok, worst, nflag = forward_close(res["out"], q_ora, amb, rel=rel)
     assert nflag <= 0.01 * amb.size + 2, nflag
     assert ok, worst
     keep = (amb & ora.AMB_VALUE) == 0
@@ -70,13 +91,19 @@ def test_backward_matches_oracle(case):
     for k, (nrm, elem) in errs.items():
         assert nrm <= 1e-3 and elem <= 1e-3, (k, nrm, elem)
     assert "means" in errs and "opacity" in errs and "bg" in errs
+    if kw.get("sh_degree") is not None:
+        assert "sh" in errs
 
 
-def test_fp64_path_matches_oracle_tightly():
+FP64_CASES = [dict(freqs_hz=[30e6, 80e6], phasor=True, depth=True),
+              dict(sh_degree=3, sh_std=0.1, pose=((4.0, -6.0, 3.0), (0.1, -0.05, -0.2)))]
+
+
+@pytest.mark.parametrize("kw", FP64_CASES, ids=["phasor-depth", "sh3-moved-camera"])
+def test_fp64_path_matches_oracle_tightly(kw):
     """The double-precision instantiation of every kernel agrees with the
     oracle to ~1e-9 (the formulas, not just the tolerance, agree)."""
-    sc = scenes.make_scene("batch_300k", 5, n=1500, width=64, height=48, frames=2,
-                           freqs_hz=[30e6, 80e6], phasor=True, depth=True)
+    sc = scenes.make_scene("batch_300k", 5, n=1500, width=64, height=48, frames=2, **kw)
     eps64 = (1e-9, 1e-10, 1.2e-7, 1e-9)  # depth keys are single precision
     q_ora, tf_ora, amb, nc = ora.render(sc, eps64)
     dout = scenes.random_dout(sc, 4)
