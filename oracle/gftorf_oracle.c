@@ -104,11 +104,21 @@ static void project_complex(const cplx* th, const double* frame,
   const double cx = frame[ORA_FR_CX], cy = frame[ORA_FR_CY];
   const double W = frame[ORA_FR_W], H = frame[ORA_FR_H];
 
-  /* deformation: cubic trajectory plus per-frame displacement */
+  /* deformation: cubic trajectory plus per-frame displacement; between two
+   * timesteps t0 < t1, Eq. 7: x(t) = ((t1 - t) x(t0) + (t - t0) x(t1)) / (t1 - t0)
+   * (the paper's unit-spaced integer steps, rescaled to time) */
+  const double t0 = frame[ORA_FR_T0], t1 = frame[ORA_FR_T1];
   cplx x[3];
-  for (int a = 0; a < 3; ++a)
-    x[a] = th[a] + th[3 + a] * t + th[6 + a] * (t * t) + th[9 + a] * (t * t * t) +
-           th[21 + a];
+  for (int a = 0; a < 3; ++a) {
+    if (t1 > t0) {
+      cplx xa = th[a] + th[3 + a] * t0 + th[6 + a] * (t0 * t0) + th[9 + a] * (t0 * t0 * t0);
+      cplx xb = th[a] + th[3 + a] * t1 + th[6 + a] * (t1 * t1) + th[9 + a] * (t1 * t1 * t1);
+      x[a] = ((t1 - t) * xa + (t - t0) * xb) / (t1 - t0) + th[21 + a];
+    } else {
+      x[a] = th[a] + th[3 + a] * t + th[6 + a] * (t * t) + th[9 + a] * (t * t * t) +
+             th[21 + a];
+    }
+  }
 
   /* view transform p = R x + t */
   cplx p[3];
@@ -442,12 +452,12 @@ static int composite_pixel(const double* splats, const cand_t* cand, int m,
  * + bg_fj T, i.e. sum w A sin(psi + phi_j) + bg T; ambient = I + bg_amb T;
  * phasor (Eq. 3) = 2 (C_f + i S_f) + bg T; mean depth (Eq. 5) as summed */
 static void samples_from_acc(const double* acc, double T, const double* bg,
-                             const double* sensor, const double* consts,
-                             double* q, size_t stride) {
+                             const double* frame, const double* sensor,
+                             const double* consts, double* q, size_t stride) {
   const int F = (int)sensor[ORA_SE_F], P = (int)sensor[ORA_SE_P];
   for (int f = 0; f < F; ++f)
     for (int j = 0; j < P; ++j) {
-      double phi = sensor[ORA_SE_OFF + j];
+      double phi = sensor[ORA_SE_OFF + j] + frame[ORA_FR_PHASE];
       q[(size_t)(f * P + j) * stride] =
           cos(phi) * acc[2 * f] + sin(phi) * acc[2 * f + 1] + bg[f * P + j] * T;
     }
@@ -482,14 +492,13 @@ void ora_render_pixels(int n, const double* splats, const double* frame,
       int flags = 0;
       int k = composite_pixel(splats, cand, m, x + 0.5, y + 0.5, sensor, consts,
                               eps, acc, &T, &flags, NULL);
-      samples_from_acc(acc, T, bg, sensor, consts, out + (size_t)i * C, 1);
+      samples_from_acc(acc, T, bg, frame, sensor, consts, out + (size_t)i * C, 1);
       if (tfinal) tfinal[i] = T;
       if (ambig) ambig[i] = flags;
       if (ncontrib) ncontrib[i] = k;
     }
     free(cand);
   }
-  (void)frame;
 }
 
 void ora_render_frame(int n, const double* splats, const double* frame,
@@ -516,7 +525,7 @@ void ora_render_frame(int n, const double* splats, const double* frame,
           int k = composite_pixel(splats, cand, m, x + 0.5, y + 0.5, sensor,
                                   consts, eps, acc, &T, &flags, NULL);
           size_t p = (size_t)y * W + x;
-          samples_from_acc(acc, T, bg, sensor, consts, out + p, HW);
+          samples_from_acc(acc, T, bg, frame, sensor, consts, out + p, HW);
           if (tfinal) tfinal[p] = T;
           if (ambig) ambig[p] = flags;
           if (ncontrib) ncontrib[p] = k;
@@ -568,7 +577,7 @@ void ora_backward_2d(int n, const double* splats, const double* frame,
           for (int f = 0; f < F; ++f)
             for (int j = 0; j < P; ++j) {
               double gq = dout[(size_t)(f * P + j) * HW + p];
-              double phi = sensor[ORA_SE_OFF + j];
+              double phi = sensor[ORA_SE_OFF + j] + frame[ORA_FR_PHASE];
               gacc[2 * f] += cos(phi) * gq;
               gacc[2 * f + 1] += sin(phi) * gq;
               gT += bg[f * P + j] * gq;

@@ -10,7 +10,8 @@
  * What it computes (all in double precision):
  *   - time-varying Gaussian positions x_k(t) = mu + c1 t + c2 t^2 + c3 t^3
  *     (+ an optional per-frame displacement), i.e. the deformation step that
- *     stands in for the paper's MLP offsets (Sec. 5 "Pipeline");
+ *     stands in for the paper's MLP offsets (Sec. 5 "Pipeline"), optionally
+ *     interpolated linearly between two timesteps (Eq. 7);
  *   - EWA projection of each 3D Gaussian to a 2D conic (the 3DGS convention
  *     the paper builds on, Sec. 4 "GS image formation model");
  *   - the raw C-ToF quad formation of Eq. 4 (T_k squared for the round trip,
@@ -47,6 +48,12 @@ enum {
   ORA_FR_RT,               /* 12 values, row-major 3x4 world->camera [R | t] */
   ORA_FR_NEAR = ORA_FR_RT + 12,
   ORA_FR_TIME,
+  ORA_FR_PHASE,  /* added to every sensor phase offset in this frame: an
+                    asynchronously captured raw frame (Sec. 4) samples its
+                    own offset at its own time */
+  ORA_FR_T0,     /* Eq. 7: with T0 < T1 the positions at TIME are the linear */
+  ORA_FR_T1,     /* interpolation of those at the timesteps T0 and T1;
+                    T0 == T1: positions at TIME directly */
   ORA_FR_LEN
 };
 /* sensor */

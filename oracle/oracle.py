@@ -17,7 +17,7 @@ _LIB = None
 
 # packed layouts (gftorf_oracle.h)
 MAX_F, MAX_P = 4, 8
-FR_LEN = 20
+FR_LEN = 23
 SE_LEN = 1 + MAX_F + 1 + MAX_P + 1
 CO_LEN = 11
 MAX_SH = 16
@@ -92,6 +92,11 @@ def pack_frame(scene, b: int) -> np.ndarray:
     fr[6:18] = np.asarray(cam.world_to_cam, np.float64).reshape(12)
     fr[18] = cam.near
     fr[19] = float(scene.times[b])
+    ph = getattr(scene, "frame_phase", None)
+    fr[20] = 0.0 if ph is None else float(ph[b])
+    it = getattr(scene, "interp_times", None)
+    if it is not None:
+        fr[21], fr[22] = float(it[b][0]), float(it[b][1])
     return fr
 
 

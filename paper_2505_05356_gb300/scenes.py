@@ -90,6 +90,8 @@ class Scene:
     consts: Consts
     bg: np.ndarray          # (B, C) background per channel
     sh: Optional[np.ndarray] = None  # (N, n_sh) SH reflectivity, n_sh in 1,4,9,16
+    frame_phase: Optional[np.ndarray] = None   # (B,) rad added to the offsets
+    interp_times: Optional[np.ndarray] = None  # (B, 2) Eq. 7 bracketing timesteps
 
     @property
     def n_sh(self) -> int:
@@ -182,7 +184,11 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
     are N(0, sh_std) with sh_std 0.03 by default), pose ((rx, ry, rz) degrees
     of an x-then-y-then-z rotation, optical centre (cx, cy, cz)): a moved
     camera, with the Gaussians drawn in its frustum and stored in world
-    coordinates.
+    coordinates.  async_capture=True: asynchronous raw capture (Sec. 4), one
+    raw sample per frame (P = 1, sensor offset 0) with frame b at tick b
+    (t_b = b / (B - 1)) sampling phase offset (pi/2) (b mod 4); the first frame
+    of each quartet is an integer timestep and the others interpolate the
+    positions linearly between it and the next quartet's first frame (Eq. 7).
     """
     rng = np.random.default_rng(seed)
     if name == "static_1k":
@@ -203,6 +209,8 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
     d.update(dict(offsets_rad=[0.0, math.pi / 2, math.pi, 3 * math.pi / 2],
                   tile=(16, 16), bg="random", log_scale=(-3.5, 0.3)))
     d.update(over)
+    if d.get("async_capture"):
+        d["offsets_rad"] = [0.0]
 
     cam = pinhole(d["width"], d["height"])
     means, coeffs, scales, quats, opacity, amplitude = random_gaussians(
@@ -245,8 +253,14 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
         # DC basis value 1 / (2 sqrt(pi)): r = 0.5 + sh_0 Y_0 + ... = amplitude + ...
         sh[:, 0] = (amplitude - 0.5) * (2.0 * math.sqrt(math.pi))
         sh = sh.astype(F32)
+    phase = interp = None
+    if d.get("async_capture"):
+        tick = 1.0 / max(frames - 1, 1)
+        phase = np.array([(math.pi / 2) * (b % 4) for b in range(frames)], F32)
+        t0 = np.array([4 * (b // 4) * tick for b in range(frames)])
+        interp = np.stack([t0, t0 + 4 * tick], 1).astype(F32)
     return Scene(means, coeffs, scales, quats, opacity, amplitude, times,
-                 [cam] * frames, delta, sensor, consts, bg, sh)
+                 [cam] * frames, delta, sensor, consts, bg, sh, phase, interp)
 
 
 def random_dout(scene: Scene, seed: int = 1, density: float = 1.0) -> np.ndarray:

@@ -11,7 +11,8 @@ C_LIGHT = 299792458.0
 def tiny_scene(positions, scales, quats=None, opacity=None, amplitude=None,
                width=64, height=64, freqs=(30e6,), offsets=None, bg=None,
                coeffs=None, times=(0.0,), world_to_cam=None, consts=None,
-               source_intensity=1.0, delta=None, sh=None):
+               source_intensity=1.0, delta=None, sh=None, frame_phase=None,
+               interp_times=None):
     """Scene with the given Gaussians (float64 values kept exactly)."""
     positions = np.asarray(positions, np.float64).reshape(-1, 3)
     n = positions.shape[0]
@@ -36,7 +37,10 @@ def tiny_scene(positions, scales, quats=None, opacity=None, amplitude=None,
     return scenes.Scene(positions, coeffs, scales, quats, opacity, amplitude,
                         np.asarray(times, np.float64), [cam] * frames, delta,
                         sensor, consts, bg,
-                        None if sh is None else np.asarray(sh, np.float64).reshape(n, -1))
+                        None if sh is None else np.asarray(sh, np.float64).reshape(n, -1),
+                        None if frame_phase is None else np.asarray(frame_phase, np.float64),
+                        None if interp_times is None else
+                        np.asarray(interp_times, np.float64).reshape(frames, 2))
 
 
 def at_pixel(cam, px, py, z):

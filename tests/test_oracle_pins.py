@@ -653,3 +653,88 @@ def test_gradient_with_sh_matches_central_differences(seed, n_sh):
             assert ga == pytest.approx(fd, rel=2e-5, abs=2e-6 * (1 + abs(fd))), (name, i)
             checked += 1
     assert checked > 60
+
+
+# --------------------------------------------------------------------------
+# asynchronous raw capture and piecewise-linear motion (Sec. 4, Eq. 7)
+# --------------------------------------------------------------------------
+
+def test_eq7_interpolates_positions_between_timesteps():
+    """Positions at t in [t0, t1] are the linear interpolation of those at t0
+    and t1 (numpy polynomial evaluation of the trajectory at both ends); a
+    linear trajectory is reproduced exactly, t = t0 gives x(t0)."""
+    mu = np.array([0.1, -0.2, 2.0])
+    c = np.array([[0.3, -0.1, 0.2], [0.5, 0.4, -0.3], [-0.6, 0.2, 0.4]])
+    t0, t1 = 0.2, 0.6
+    times = (0.2, 0.35, 0.5, 0.6)
+    sc = tiny_scene([mu], 0.05, coeffs=c[None], times=times,
+                    interp_times=[[t0, t1]] * len(times))
+    cam = sc.cameras[0]
+
+    def traj(t):
+        return mu + c[0] * t + c[1] * t ** 2 + c[2] * t ** 3
+
+    for b, t in enumerate(times):
+        x = traj(t0) + (t - t0) / (t1 - t0) * (traj(t1) - traj(t0))
+        sp = ora.project(sc, b)[0]
+        assert sp[SP["U"]] == pytest.approx(cam.fx * x[0] / x[2] + cam.cx, rel=1e-13)
+        assert sp[SP["V"]] == pytest.approx(cam.fy * x[1] / x[2] + cam.cy, rel=1e-13)
+        assert sp[SP["D"]] == pytest.approx(np.linalg.norm(x), rel=1e-14)
+    # a mid-interval frame differs from the exact trajectory for a curved path
+    exact = tiny_scene([mu], 0.05, coeffs=c[None], times=(0.35,))
+    assert abs(ora.project(exact, 0)[0][SP["D"]] - ora.project(sc, 1)[0][SP["D"]]) > 1e-4
+    # a straight path is reproduced exactly
+    c_lin = c.copy()
+    c_lin[1:] = 0.0
+    lin = tiny_scene([mu], 0.05, coeffs=c_lin[None], times=(0.35,), interp_times=[[t0, t1]])
+    lin_exact = tiny_scene([mu], 0.05, coeffs=c_lin[None], times=(0.35,))
+    np.testing.assert_allclose(ora.project(lin, 0), ora.project(lin_exact, 0), rtol=1e-13,
+                               atol=1e-15)
+
+
+def test_async_frame_equals_matching_channel_of_synchronous_quartet():
+    """A frame that samples one offset phi (P = 1, frame phase phi) equals the
+    channel phi of a synchronous four-offset frame at the same time."""
+    sc4 = _fd_scene(21, n=6, frames=1)
+    offs = [0.0, math.pi / 2, math.pi, 3 * math.pi / 2]
+    sc4.sensor.offsets_rad = offs
+    q4, tf4, _, _ = ora.render(sc4)
+    for j, phi in enumerate(offs):
+        sc1 = _fd_scene(21, n=6, frames=1)
+        sc1.sensor.offsets_rad = [0.0]
+        sc1.bg = np.stack([sc4.bg[:, j], sc4.bg[:, 4]], 1)
+        sc1.frame_phase = np.array([phi])
+        q1, tf1, _, _ = ora.render(sc1)
+        np.testing.assert_allclose(q1[0, 0], q4[0, j], rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(q1[0, 1], q4[0, 4], rtol=1e-13, atol=1e-15)
+        np.testing.assert_array_equal(tf1, tf4)
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_gradient_async_interpolated_matches_central_differences(seed):
+    sc = _fd_scene(seed, n=5, frames=3)
+    sc.sensor.offsets_rad = [0.0]
+    sc.frame_phase = np.array([0.0, math.pi / 2, math.pi])
+    sc.interp_times = np.array([[0.1, 0.7], [0.1, 0.7], [0.1, 0.7]])
+    sc.bg = np.random.default_rng(seed).uniform(-1, 1, (sc.frames, 2))
+    rng = np.random.default_rng(400 + seed)
+    dout = rng.standard_normal((sc.frames, sc.n_channels, sc.height, sc.width))
+    g = ora.backward(sc, dout)
+    base = ora.Params(sc)
+    L0, _ = _loss(sc, dout, base)
+    checked = 0
+    for name in ["means", "coeffs", "delta", "opacity", "amplitude"]:
+        flat = getattr(base, name).reshape(-1)
+        for i in range(flat.size):
+            h = 1e-6 * max(1.0, abs(flat[i]))
+            vals = []
+            for sgn in (1, -1):
+                P = ora.Params(sc)
+                getattr(P, name).reshape(-1)[i] = flat[i] + sgn * h
+                vals.append(_loss(sc, dout, P)[0])
+            fd = (vals[0] - vals[1]) / (2 * h)
+            if abs((vals[0] - L0) / h - (L0 - vals[1]) / h) > 1e-3 * (abs(fd) + 1e-3):
+                continue
+            assert g[name].reshape(-1)[i] == pytest.approx(fd, rel=2e-5, abs=2e-6 * (1 + abs(fd)))
+            checked += 1
+    assert checked > 60
