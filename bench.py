@@ -121,6 +121,8 @@ def _overrides(args):
         o["n"] = args.n
     if args.sh_degree >= 0:
         o["sh_degree"] = args.sh_degree
+    if args.async_capture:
+        o["async_capture"] = True
     return o
 
 
@@ -406,12 +408,17 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; shaped like the paper's C-ToF scenes)",
             "config": {"workload": "%s: %d dynamic Gaussians (cubic trajectories), %dx%d, "
-                                   "%d timesteps per batch, 30 MHz x 4 offsets + ambient, "
-                                   "30-100%% visible per frame" % (args.workload, N, W, H, B),
+                                   "%d timesteps per batch, %s MHz x %d offsets + ambient, "
+                                   "30-100%% visible per frame" % (
+                                       args.workload, N, W, H, B,
+                                       "+".join("%g" % (f / 1e6) for f in sc.sensor.freqs_hz),
+                                       nP),
                        "frames_per_step": B, "tile": "%dx%d" % tuple(tile),
                        "channels": r.C,
                        "reflectivity": ("SH degree %d" % args.sh_degree
                                         if args.sh_degree >= 0 else "scalar"),
+                       "capture": ("asynchronous (1 offset per frame, Eq. 7 motion)"
+                                   if args.async_capture else "synchronous quartets"),
                        "pixels_per_thread": ppt,
                        "render_mode": "persistent" if mode == 1 else "grid",
                        "autotuned": tuned is not None,
@@ -559,6 +566,9 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the Gaussian count")
     ap.add_argument("--extra-channels", default="",
                     help="comma list of extra outputs: phasor (Eq. 3), depth (Eq. 5)")
+    ap.add_argument("--async-capture", action="store_true",
+                    help="asynchronous raw capture: one phase offset per frame, Eq. 7 "
+                         "piecewise-linear motion between quartets")
     ap.add_argument("--sh-degree", type=int, default=-1,
                     help="view-dependent reflectivity from SH of this degree (0-3); "
                          "default: scalar reflectivity")

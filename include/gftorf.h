@@ -121,12 +121,24 @@ typedef struct {
  * transform [R | t] (R orthonormal, row-major 3x4), near-plane cull distance (> 0)
  * on the view depth, and the frame's time t for the deformation.  Sec. 4:
  * emitter co-located with the camera, so d_k is the distance from the
- * Gaussian centre to the optical centre o = -R^T t. */
+ * Gaussian centre to the optical centre o = -R^T t.
+ *   phase_offset_rad: added to every sensor phase offset in this frame.  An
+ *     asynchronously captured raw sequence (Sec. 4: each raw frame at its own
+ *     time) is a batch with n_offsets = 1, sensor offset 0 and the frame's
+ *     own offset here.  0 for synchronous capture.
+ *   interp_t0, interp_t1: Eq. 7 piecewise-linear motion.  With
+ *     interp_t0 < interp_t1 the positions at `time` are the linear
+ *     interpolation of the deformed positions at the two timesteps,
+ *     x = ((t1 - t) x(t0) + (t - t0) x(t1)) / (t1 - t0), plus delta_b;
+ *     with interp_t0 == interp_t1 (e.g. both 0) x = x(time) + delta_b.
+ *     interp_t0 > interp_t1 is an error. */
 typedef struct {
   float fx, fy, cx, cy;
   float world_to_cam[12];
   float near_plane;
   float time;
+  float phase_offset_rad;
+  float interp_t0, interp_t1;
 } gftorf_frame;
 
 /* C-ToF sensor (Sec. 3): modulation frequencies f (Hz), phase offsets phi_j
@@ -183,7 +195,8 @@ typedef struct {
 size_t gftorf_workspace_size(const gftorf_dims* dims);
 
 /* Deformation + projection + C-ToF features for all frames (Sec. 4, Eq. 3/4
- * terms; deformation x(t) = mu + c1 t + c2 t^2 + c3 t^3 + delta_b).
+ * terms; deformation x(t) = mu + c1 t + c2 t^2 + c3 t^3 + delta_b, or its
+ * Eq. 7 interpolation, see gftorf_frame).
  * frames: HOST array of dims->n_frames entries; sensor, consts: HOST.
  * Resets the device status word. */
 gftorf_status gftorf_preprocess(const gftorf_dims* dims,

@@ -240,7 +240,9 @@ gftorf_status gftorf_preprocess(const gftorf_dims* dims,
   for (int b = 0; b < L.B; ++b) {
     const gftorf_frame& f = frames[b];
     if (!(f.fx > 0) || !(f.fy > 0) || !finite(f.cx) || !finite(f.cy) ||
-        !(f.near_plane > 0) || !finite(f.near_plane) || !finite(f.time))
+        !(f.near_plane > 0) || !finite(f.near_plane) || !finite(f.time) ||
+        !finite(f.phase_offset_rad) || !finite(f.interp_t0) || !finite(f.interp_t1) ||
+        f.interp_t0 > f.interp_t1)
       return GFTORF_ERR_ARG;
     for (int k = 0; k < 12; ++k)
       if (!finite(f.world_to_cam[k])) return GFTORF_ERR_ARG;
@@ -253,6 +255,18 @@ gftorf_status gftorf_preprocess(const gftorf_dims* dims,
     for (int c = 0; c < 3; ++c)
       d.o[c] = -(d.R[c] * d.t[0] + d.R[3 + c] * d.t[1] + d.R[6 + c] * d.t[2]);
     d.near_plane = f.near_plane, d.time = f.time;
+    // c_k multiplies t^k, or under Eq. 7 the interpolation of t0^k and t1^k
+    const double tt = f.time, t0 = f.interp_t0, t1 = f.interp_t1;
+    double p0 = 1, p1 = 1, pt = 1;
+    for (int k = 0; k < 3; ++k) {
+      p0 *= t0, p1 *= t1, pt *= tt;
+      d.tp[k] = t1 > t0 ? ((t1 - tt) * p0 + (tt - t0) * p1) / (t1 - t0) : pt;
+    }
+    for (int j = 0; j < L.P; ++j) {
+      const double phi = (double)sensor->offset_rad[j] + (double)f.phase_offset_rad;
+      d.cos_off[j] = cos(phi);
+      d.sin_off[j] = sin(phi);
+    }
     d.limx = (double)consts->guard * 0.5 * L.W / f.fx;
     d.limy = (double)consts->guard * 0.5 * L.H / f.fy;
   }
@@ -260,11 +274,8 @@ gftorf_status gftorf_preprocess(const gftorf_dims* dims,
     if (!finite(sensor->freq_hz[k]) || sensor->freq_hz[k] < 0) return GFTORF_ERR_ARG;
     t.kf[k] = 4.0 * (double)sensor->freq_hz[k] / kLightSpeed;
   }
-  for (int j = 0; j < L.P; ++j) {
+  for (int j = 0; j < L.P; ++j)
     if (!finite(sensor->offset_rad[j])) return GFTORF_ERR_ARG;
-    t.cos_off[j] = cos((double)sensor->offset_rad[j]);
-    t.sin_off[j] = sin((double)sensor->offset_rad[j]);
-  }
   if (!finite(sensor->source_intensity)) return GFTORF_ERR_ARG;
   t.source = sensor->source_intensity;
   if (!(consts->dilation >= 0) || !(consts->alpha_max > 0) || !(consts->alpha_max <= 1) ||

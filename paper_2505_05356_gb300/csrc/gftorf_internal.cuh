@@ -36,6 +36,9 @@ struct FrameT {
   T near_plane, time;
   T limx, limy;  // guard * half field of view (tan), x and y
   T o[3];        // optical centre -R^T t (world), exact for a non-orthonormal R
+  T tp[3];       // deformation weights of c1, c2, c3: (t, t^2, t^3), or their
+                 // Eq. 7 interpolation between the frame's two timesteps
+  T cos_off[kMaxP], sin_off[kMaxP];  // phase offsets + the frame's own offset
 };
 
 // Everything a batch needs besides the arrays: written into the workspace by
@@ -46,7 +49,6 @@ template <typename T>
 struct TableT {
   FrameT<T> fr[kMaxFrames];
   T kf[kMaxF];  // 4 f / c: psi / pi per metre of distance
-  T cos_off[kMaxP], sin_off[kMaxP];
   T source;
   T dilation, alpha_max, alpha_min, t_min, sigma_cut;
 };

@@ -4,6 +4,8 @@
 //
 // Forward per (frame b, Gaussian g), Sec. 4 and the 3DGS projection it uses:
 //   x   = mu + c1 t + c2 t^2 + c3 t^3 + delta_b            (deformation)
+//         (under Eq. 7 each t^k is replaced by its linear interpolation
+//         between the frame's two timesteps; the table holds the weights)
 //   p   = R x + t_cam; cull if p_z <= near
 //   d   = |x - o| = distance to the optical centre o = -R^T t_cam (equal to
 //         |p| for an orthonormal R; taken from o so that a rounded R does
@@ -173,10 +175,9 @@ template <typename Real>
 __device__ __forceinline__ void geometry(const Params<Real>& P,
                                          const FrameT<Real>& fr, const Real* delta,
                                          Real dil, Geo<Real>& Q) {
-  const Real t = (Real)fr.time;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    Real x = P.mu[a] + t * (P.c[a] + t * (P.c[3 + a] + t * P.c[6 + a]));
+    Real x = P.mu[a] + (P.c[a] * fr.tp[0] + P.c[3 + a] * fr.tp[1] + P.c[6 + a] * fr.tp[2]);
     if (delta) x += delta[a];
     Q.x[a] = x;
   }
@@ -348,8 +349,11 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // backward: d(record) of every frame -> d(parameters); frames looped in-thread
 // ---------------------------------------------------------------------------
+// 4 CTAs (16 warps) per SM for the scalar-reflectivity float kernels (<= 128
+// registers); the SH variants carry 32 more live values and run at 3; the
+// double-precision (checking) variants are left unconstrained
 template <typename Real, int F, bool SH>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 1 : (SH ? 3 : 4))
     preprocess_bwd_kernel(gftorf_gaussians G, gftorf_gradients D,
                           const TableT<Real>* __restrict__ tab,
                           const uint2* __restrict__ rect,
@@ -392,7 +396,6 @@ __global__ void __launch_bounds__(128)
       continue;
     }
     const FrameT<Real>& fr = tab->fr[b];
-    const Real t = (Real)fr.time;
     const Real* delta =
         G.delta ? static_cast<const Real*>(G.delta) + bg * 3 : nullptr;
     Geo<Real> Q;
@@ -506,9 +509,9 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       gmu[a] += gx[a];
-      gc[a] += gx[a] * t;
-      gc[3 + a] += gx[a] * t * t;
-      gc[6 + a] += gx[a] * t * t * t;
+      gc[a] += gx[a] * fr.tp[0];
+      gc[3 + a] += gx[a] * fr.tp[1];
+      gc[6 + a] += gx[a] * fr.tp[2];
     }
     if (gdelta) {
       gdelta[0] = gx[0];

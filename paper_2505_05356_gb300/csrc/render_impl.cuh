@@ -334,8 +334,8 @@ __device__ __forceinline__ void render_tile_fwd(
     Real* o = out + (size_t)tc.b * rg.C * HW + pix;
     for (int f = 0; f < F; ++f)
       for (int j = 0; j < rg.P; ++j)
-        o[(size_t)(f * rg.P + j) * HW] = (Real)tab->cos_off[j] * acc[k][2 * f] +
-                                         (Real)tab->sin_off[j] * acc[k][2 * f + 1] +
+        o[(size_t)(f * rg.P + j) * HW] = (Real)tab->fr[tc.b].cos_off[j] * acc[k][2 * f] +
+                                         (Real)tab->fr[tc.b].sin_off[j] * acc[k][2 * f + 1] +
                                          bgb[f * rg.P + j] * T[k];
     o[(size_t)(F * rg.P) * HW] = acc[k][2 * F] + bgb[F * rg.P] * T[k];
     int c = F * rg.P + 1;
@@ -436,8 +436,8 @@ __device__ __forceinline__ void render_tile_bwd(
       for (int f = 0; f < F; ++f)
         for (int j = 0; j < rg.P; ++j) {
           const Real gq = go[(size_t)(f * rg.P + j) * HW];
-          gacc[k][2 * f] += (Real)tab->cos_off[j] * gq;
-          gacc[k][2 * f + 1] += (Real)tab->sin_off[j] * gq;
+          gacc[k][2 * f] += (Real)tab->fr[tc.b].cos_off[j] * gq;
+          gacc[k][2 * f + 1] += (Real)tab->fr[tc.b].sin_off[j] * gq;
           gT += bgb[f * rg.P + j] * gq;
         }
       gacc[k][2 * F] = go[(size_t)(F * rg.P) * HW];

@@ -43,7 +43,9 @@ class Frame(ctypes.Structure):
     _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("world_to_cam", ctypes.c_float * 12),
-                ("near_plane", ctypes.c_float), ("time", ctypes.c_float)]
+                ("near_plane", ctypes.c_float), ("time", ctypes.c_float),
+                ("phase_offset_rad", ctypes.c_float), ("interp_t0", ctypes.c_float),
+                ("interp_t1", ctypes.c_float)]
 
 
 class Sensor(ctypes.Structure):
@@ -159,13 +161,20 @@ def _require_cuda():
 
 
 # --- argument builders -------------------------------------------------------
-def make_frame(fx, fy, cx, cy, world_to_cam, near_plane, time) -> Frame:
+def make_frame(fx, fy, cx, cy, world_to_cam, near_plane, time, phase_offset_rad=0.0,
+               interp=None) -> Frame:
+    """interp = (t0, t1): Eq. 7 interpolation of the positions between two
+    timesteps; phase_offset_rad: this frame's own phase offset (asynchronous
+    raw capture)."""
     f = Frame()
     f.fx, f.fy, f.cx, f.cy = fx, fy, cx, cy
     wc = [float(v) for v in torch.as_tensor(world_to_cam, dtype=torch.float64).reshape(12)]
     for i in range(12):
         f.world_to_cam[i] = wc[i]
     f.near_plane, f.time = near_plane, time
+    f.phase_offset_rad = phase_offset_rad
+    if interp is not None:
+        f.interp_t0, f.interp_t1 = float(interp[0]), float(interp[1])
     return f
 
 
@@ -190,9 +199,13 @@ def make_consts(dilation=0.3, alpha_max=0.99, alpha_min=1.0 / 255.0, t_min=1e-4,
 
 def frames_from_scene(scene) -> List[Frame]:
     out = []
+    ph = getattr(scene, "frame_phase", None)
+    it = getattr(scene, "interp_times", None)
     for b, cam in enumerate(scene.cameras):
         out.append(make_frame(cam.fx, cam.fy, cam.cx, cam.cy, cam.world_to_cam,
-                              cam.near, float(scene.times[b])))
+                              cam.near, float(scene.times[b]),
+                              0.0 if ph is None else float(ph[b]),
+                              None if it is None else it[b]))
     return out
 
 

@@ -102,6 +102,12 @@ def test_host_side_argument_errors(lib):
                                  ctypes.byref(co), ctypes.c_void_p(4096), need,
                                  None) == gftorf.ERR_ARG
     fr[1].fx = 50.0
+    # Eq. 7 bracket out of order
+    fr[0].interp_t0, fr[0].interp_t1 = 0.5, 0.25
+    assert lib.gftorf_preprocess(ctypes.byref(d), ctypes.byref(pg), fr, ctypes.byref(se),
+                                 ctypes.byref(co), ctypes.c_void_p(4096), need,
+                                 None) == gftorf.ERR_ARG
+    fr[0].interp_t0, fr[0].interp_t1 = 0.0, 0.0
     co.alpha_max = 1.5
     assert lib.gftorf_preprocess(ctypes.byref(d), ctypes.byref(pg), fr, ctypes.byref(se),
                                  ctypes.byref(co), ctypes.c_void_p(4096), need,
@@ -115,7 +121,7 @@ def test_host_side_argument_errors(lib):
 def test_struct_layouts_match_header():
     # sizes fixed by the header's field lists (C layout, no hidden padding)
     assert ctypes.sizeof(gftorf.Dims) == 14 * 4 + 8
-    assert ctypes.sizeof(gftorf.Frame) == 18 * 4
+    assert ctypes.sizeof(gftorf.Frame) == 21 * 4
     assert ctypes.sizeof(gftorf.Sensor) == (4 + 8 + 1) * 4
     assert ctypes.sizeof(gftorf.Consts) == 6 * 4
     assert ctypes.sizeof(gftorf.Gaussians) == 8 * ctypes.sizeof(ctypes.c_void_p)

@@ -41,6 +41,10 @@ SMALL = [
     ("batch_300k", dict(n=3000, width=72, height=56, frames=3, sh_degree=3, sh_std=0.1,
                         pose=POSE)),
     ("static_1k", dict(sh_degree=1, pose=((3.0, -5.0, 8.0), (0.05, -0.1, -0.3)))),
+    # asynchronous raw capture: one offset per frame, Eq. 7 motion between quartets
+    ("batch_300k", dict(n=3000, width=72, height=56, frames=8, async_capture=True)),
+    ("dynamic_100k", dict(n=3000, width=64, height=48, frames=5, async_capture=True,
+                          freqs_hz=[30e6, 80e6], z_range=(0.5, 6.0))),
 ]
 
 # Forward bar of the moved-camera cases.  With R = I the camera transform is
@@ -96,10 +100,11 @@ def test_backward_matches_oracle(case):
 
 
 FP64_CASES = [dict(freqs_hz=[30e6, 80e6], phasor=True, depth=True),
-              dict(sh_degree=3, sh_std=0.1, pose=((4.0, -6.0, 3.0), (0.1, -0.05, -0.2)))]
+              dict(sh_degree=3, sh_std=0.1, pose=((4.0, -6.0, 3.0), (0.1, -0.05, -0.2))),
+              dict(async_capture=True)]
 
 
-@pytest.mark.parametrize("kw", FP64_CASES, ids=["phasor-depth", "sh3-moved-camera"])
+@pytest.mark.parametrize("kw", FP64_CASES, ids=["phasor-depth", "sh3-moved-camera", "async-eq7"])
 def test_fp64_path_matches_oracle_tightly(kw):
     """The double-precision instantiation of every kernel agrees with the
     oracle to ~1e-9 (the formulas, not just the tolerance, agree)."""
@@ -247,3 +252,21 @@ def test_tile_lists_match_oracle_binning_of_its_own_rects(flags):
             # depth order within the tile (view depth of the oracle)
             z = sp[vals[s:e], ora.SP["Z"]]
             assert np.all(np.diff(z) >= -1e-6 * np.abs(z[1:])), (b, t)
+
+
+def test_async_frame_equals_channel_of_synchronous_quartet():
+    """One raw frame that samples offset phi_j (P = 1, the frame's own phase
+    offset) is bit-identical to channel j of the synchronous quartet."""
+    import math
+    sync = scenes.make_scene("batch_300k", 14, n=4000, width=80, height=64, frames=1)
+    rs = run_gpu(sync)
+    offs = sync.sensor.offsets_rad
+    for j in range(4):
+        one = scenes.make_scene("batch_300k", 14, n=4000, width=80, height=64, frames=1)
+        one.sensor.offsets_rad = [0.0]
+        one.frame_phase = np.array([offs[j]], np.float32)
+        one.bg = np.stack([sync.bg[:, j], sync.bg[:, 4]], 1)
+        r1 = run_gpu(one)
+        np.testing.assert_array_equal(r1["out"][0, 0], rs["out"][0, j])
+        np.testing.assert_array_equal(r1["out"][0, 1], rs["out"][0, 4])
+    assert abs(offs[1] - math.pi / 2) < 1e-6
