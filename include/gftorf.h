@@ -14,7 +14,7 @@
  *   gftorf_preprocess  -- deform each Gaussian to the frame's time
  *                         x(t) = mu + c1 t + c2 t^2 + c3 t^3 (+ delta_b),
  *                         project (EWA, 3DGS convention), depth, tile bounds,
- *                         C-ToF features (Sec. 4, Eq. 3/4 terms).
+ *                         C-ToF features (Sec. 3, Eq. 3/4 terms).
  *   gftorf_render_fwd  -- depth radix sort, tile-key duplication, stable tile
  *                         sort, per-tile ranges, then front-to-back
  *                         compositing of Eq. 4 per pixel.
@@ -108,7 +108,7 @@ typedef struct {
                             (0: 2); tile_w * tile_h / it must be >= 32.
                             Results do not depend on it.                    */
   int32_t flags;         /* GFTORF_FLAG_* bits, 0 for the defaults         */
-  int32_t n_sh;          /* reflectivity model (Sec. 4): 0 = the scalar
+  int32_t n_sh;          /* reflectivity model (Sec. 3): 0 = the scalar
                             gaussians.amplitude; 1, 4, 9 or 16 = real
                             spherical harmonics of degree 0..3 in
                             gaussians.sh (see gftorf_gaussians)             */
@@ -119,11 +119,11 @@ typedef struct {
 
 /* One frame (host struct): pinhole camera with a rigid world->camera
  * transform [R | t] (R orthonormal, row-major 3x4), near-plane cull distance (> 0)
- * on the view depth, and the frame's time t for the deformation.  Sec. 4:
+ * on the view depth, and the frame's time t for the deformation.  Sec. 3:
  * emitter co-located with the camera, so d_k is the distance from the
  * Gaussian centre to the optical centre o = -R^T t.
  *   phase_offset_rad: added to every sensor phase offset in this frame.  An
- *     asynchronously captured raw sequence (Sec. 4: each raw frame at its own
+ *     asynchronously captured raw sequence (Sec. 3: each raw frame at its own
  *     time) is a batch with n_offsets = 1, sensor offset 0 and the frame's
  *     own offset here.  0 for synchronous capture.
  *   interp_t0, interp_t1: Eq. 7 piecewise-linear motion.  With
@@ -141,7 +141,7 @@ typedef struct {
   float interp_t0, interp_t1;
 } gftorf_frame;
 
-/* C-ToF sensor (Sec. 3): modulation frequencies f (Hz), phase offsets phi_j
+/* C-ToF sensor (Sec. 2): modulation frequencies f (Hz), phase offsets phi_j
  * of the reference signal (rad, shared by all frequencies), source
  * intensity s.  Raw sample j of frequency f is A sin(psi_f + phi_j). */
 typedef struct {
@@ -151,7 +151,7 @@ typedef struct {
 } gftorf_sensor;
 
 /* Screen-space constants of the 3DGS rasterizer the paper builds on
- * (Sec. 5, implementation details).  Defaults: dilation 0.3 (added to the 2D
+ * (Sec. 4, implementation details).  Defaults: dilation 0.3 (added to the 2D
  * covariance diagonal), alpha_max 0.99 (alpha = min(alpha_max, o G)),
  * alpha_min 1/255 (smaller alphas are skipped), t_min 1e-4 (the walk stops
  * before a Gaussian that would take the one-way T below it), guard 1.3
@@ -168,7 +168,7 @@ typedef struct {
  *   unused, may be NULL, otherwise);
  *   delta[B][N][3] per-frame displacement added to x(t), or NULL;
  *   sh[N][dims.n_sh] (dims.n_sh > 0, else unused): view-dependent
- *   reflectivity r_k = max(0, 0.5 + sum_l sh_l Y_l(w)) (Sec. 4: r_k held
+ *   reflectivity r_k = max(0, 0.5 + sum_l sh_l Y_l(w)) (Sec. 3: r_k held
  *   as spherical harmonic coefficients; 0.5 offset and clamp as in the 3DGS
  *   colour model), w the unit vector from the frame's optical centre to
  *   x(t) in world coordinates, Y_l the orthonormal real spherical harmonics
@@ -194,7 +194,7 @@ typedef struct {
  * transmittance and last-contributor index, 2D gradients). */
 size_t gftorf_workspace_size(const gftorf_dims* dims);
 
-/* Deformation + projection + C-ToF features for all frames (Sec. 4, Eq. 3/4
+/* Deformation + projection + C-ToF features for all frames (Sec. 3, Eq. 3/4
  * terms; deformation x(t) = mu + c1 t + c2 t^2 + c3 t^3 + delta_b, or its
  * Eq. 7 interpolation, see gftorf_frame).
  * frames: HOST array of dims->n_frames entries; sensor, consts: HOST.

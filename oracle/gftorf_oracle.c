@@ -41,7 +41,7 @@ static int n_chan(const double* sensor, const double* consts) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Projection (Sec. 4 with the 3DGS EWA splatting it builds on).             */
+/* Projection (Sec. 3 with the 3DGS EWA splatting it builds on).             */
 /* Written over complex numbers so that the complex-step method gives its    */
 /* exact Jacobian; the forward pass uses the real part.                      */
 /* ------------------------------------------------------------------------ */
@@ -192,7 +192,7 @@ static void project_complex(const cplx* th, const double* frame,
   rec[REC_C] = s00 / det;
   rec[REC_O] = th[19];
 
-  /* reflectivity r_k (Sec. 4, C-ToF image formation): a scalar, or view
+  /* reflectivity r_k (Sec. 3, C-ToF image formation): a scalar, or view
    * dependent through up to 16 real SH coefficients evaluated at the unit
    * direction from the optical centre to the (deformed) centre, with the
    * 3DGS colour convention r = max(0, 0.5 + sum_l sh_l Y_l) */
@@ -209,7 +209,7 @@ static void project_complex(const cplx* th, const double* frame,
     refl = creal(val) > 0.0 ? val : 0.0;
   }
 
-  /* C-ToF terms (Sec. 3, Eq. 3/4): A = s r / d^2, psi_f = 4 pi d f / c */
+  /* C-ToF terms (Sec. 2, Eq. 3/4): A = s r / d^2, psi_f = 4 pi d f / c */
   cplx A = sensor[ORA_SE_S] * refl / (dist * dist);
   int F = (int)sensor[ORA_SE_F];
   for (int f = 0; f < F; ++f) {

@@ -10,13 +10,13 @@
  * What it computes (all in double precision):
  *   - time-varying Gaussian positions x_k(t) = mu + c1 t + c2 t^2 + c3 t^3
  *     (+ an optional per-frame displacement), i.e. the deformation step that
- *     stands in for the paper's MLP offsets (Sec. 5 "Pipeline"), optionally
+ *     stands in for the paper's MLP offsets (Sec. 4 "Pipeline"), optionally
  *     interpolated linearly between two timesteps (Eq. 7);
  *   - EWA projection of each 3D Gaussian to a 2D conic (the 3DGS convention
- *     the paper builds on, Sec. 4 "GS image formation model");
+ *     the paper builds on, Sec. 3 "GS image formation model");
  *   - the raw C-ToF quad formation of Eq. 4 (T_k squared for the round trip,
  *     amplitude s r_k / d_k^2, phase psi_k = 4 pi d_k f / c), generalised to
- *     arbitrary phase offsets as sin(psi_k + phi_j) (Sec. 3, the Q_phi model),
+ *     arbitrary phase offsets as sin(psi_k + phi_j) (Sec. 2, the Q_phi model),
  *     plus an ambient channel sum_k alpha_k T_k^2 A_k + bg T_N;
  *   - its gradient: the squared-transmittance opacity recursion of Eq. S3,
  *     and an exact (complex-step) Jacobian of the projection.
@@ -49,7 +49,7 @@ enum {
   ORA_FR_NEAR = ORA_FR_RT + 12,
   ORA_FR_TIME,
   ORA_FR_PHASE,  /* added to every sensor phase offset in this frame: an
-                    asynchronously captured raw frame (Sec. 4) samples its
+                    asynchronously captured raw frame (Sec. 3) samples its
                     own offset at its own time */
   ORA_FR_T0,     /* Eq. 7: with T0 < T1 the positions at TIME are the linear */
   ORA_FR_T1,     /* interpolation of those at the timesteps T0 and T1;
@@ -108,7 +108,7 @@ extern "C" {
 int ora_splat_len(void);
 int ora_num_threads(void);
 
-/* Project all n Gaussians for one frame (Sec. 4; 3DGS EWA convention).
+/* Project all n Gaussians for one frame (Sec. 3; 3DGS EWA convention).
  * params: means[n*3], coeffs[n*9] (c1 xyz, c2 xyz, c3 xyz), scales[n*3],
  * quats[n*4] (w,x,y,z, any norm), opacity[n], amplitude[n], delta[n*3] or
  * NULL, sh[n*ORA_MAX_SH] (read when consts[ORA_CO_NSH] > 0) or NULL.

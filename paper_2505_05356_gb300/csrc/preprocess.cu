@@ -2,7 +2,7 @@
 // (frame, Gaussian), and the backward chain rule back to the Gaussian
 // parameters (summed over frames in-thread, so the sum order is fixed).
 //
-// Forward per (frame b, Gaussian g), Sec. 4 and the 3DGS projection it uses:
+// Forward per (frame b, Gaussian g), Sec. 3 and the 3DGS projection it uses:
 //   x   = mu + c1 t + c2 t^2 + c3 t^3 + delta_b            (deformation)
 //         (under Eq. 7 each t^k is replaced by its linear interpolation
 //         between the frame's two timesteps; the table holds the weights)
@@ -17,7 +17,7 @@
 //   conic = cov^-1, radius = ceil(sigma_cut sqrt(lambda_max)) (discriminant
 //   floored at 0.1), (u, v) = (fx p_x/z + cx, fy p_y/z + cy)
 //   A = s r / d^2; features A sin psi_f, A cos psi_f (psi_f = 4 pi d f / c),
-//   and A for the ambient channel.  r is the scalar amplitude, or (Sec. 4,
+//   and A for the ambient channel.  r is the scalar amplitude, or (Sec. 3,
 //   view-dependent reflectivity) max(0, 0.5 + sum_l sh_l Y_l(w)) with w the
 //   world-space unit vector from the optical centre, w = (x - o) / d.
 // The record keeps the conic scaled by -log2(e)/2 (and -log2(e) for the

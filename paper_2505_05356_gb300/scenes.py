@@ -9,7 +9,7 @@ them losslessly).
 
 Scene shapes (the paper's datasets are not available; these stand in for
 their shape: a static monocular camera, fast lateral/axial motion, depths
-within about one unambiguous range, raw quartets; Sec. 6 "Datasets"):
+within about one unambiguous range, raw quartets; Sec. 5 "Datasets"):
 
 * ``static_1k``   -- 1,000 static Gaussians, 64x64, 30 MHz, 4 offsets.
 * ``dynamic_100k`` -- 100,000 Gaussians on cubic trajectories, 640x480.
@@ -184,7 +184,7 @@ def make_scene(name: str, seed: int = 0, **over) -> Scene:
     are N(0, sh_std) with sh_std 0.03 by default), pose ((rx, ry, rz) degrees
     of an x-then-y-then-z rotation, optical centre (cx, cy, cz)): a moved
     camera, with the Gaussians drawn in its frustum and stored in world
-    coordinates.  async_capture=True: asynchronous raw capture (Sec. 4), one
+    coordinates.  async_capture=True: asynchronous raw capture (Sec. 3), one
     raw sample per frame (P = 1, sensor offset 0) with frame b at tick b
     (t_b = b / (B - 1)) sampling phase offset (pi/2) (b mod 4); the first frame
     of each quartet is an integer timestep and the others interpolate the

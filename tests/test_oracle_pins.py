@@ -1,7 +1,7 @@
 """Pins of the FP64 oracle against what the paper and the mathematics fix.
 
 Each test checks the oracle against something other than itself: closed
-forms (Sec. 3 quad model, Eq. 1 depth, Eq. 4 with squared transmittance),
+forms (Sec. 2 quad model, Eq. 1 depth, Eq. 4 with squared transmittance),
 special cases that reduce to a library routine (scipy rotations, numpy
 linear algebra), brute force on tiny inputs, and central finite differences
 of its own forward for its analytic gradient (Eq. S3 + projection chain).
@@ -28,7 +28,7 @@ def _render_px(scene, px, py, b=0):
 
 
 # --------------------------------------------------------------------------
-# image formation (Sec. 3, Eq. 1, Eq. 4)
+# image formation (Sec. 2, Eq. 1, Eq. 4)
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("d,f", [(2.0, 30e6), (1.3, 30e6), (2.0, 80e6), (6.0, 30e6)])
@@ -59,13 +59,13 @@ def test_single_opaque_gaussian_quads_and_depth(d, f):
     d_u = C_LIGHT / (2 * f)
     d_rec = C_LIGHT * psi_rec / (4 * math.pi * f)
     assert d_rec == pytest.approx(d % d_u, abs=1e-9)
-    # amplitude relation of Sec. 3: A = 1/2 sqrt((Q0-Qpi)^2 + (Qpi/2-Q3pi/2)^2)
+    # amplitude relation of Sec. 2: A = 1/2 sqrt((Q0-Qpi)^2 + (Qpi/2-Q3pi/2)^2)
     amp = 0.5 * math.hypot(q[0] - q[2], q[1] - q[3])
     assert amp == pytest.approx(0.99 * A, rel=1e-12)
 
 
 def test_golden_phase_and_range():
-    """Golden closed forms of Sec. 3: psi at 2 m, wrapping at 80 MHz, d_u."""
+    """Golden closed forms of Sec. 2: psi at 2 m, wrapping at 80 MHz, d_u."""
     for case in GOLDEN["unambiguous_range"]["cases"]:
         assert C_LIGHT / (2 * case["f_hz"]) == pytest.approx(case["d_u_m"], rel=1e-15)
     c30, c80 = GOLDEN["phase_of_depth"]["cases"]
@@ -83,7 +83,7 @@ def test_golden_phase_and_range():
 
 def test_phase_wrap_equivalence():
     """A Gaussian at d and one at d + d_u (falloff compensated through the
-    amplitude) give identical raw samples (Sec. 3 phase wrapping)."""
+    amplitude) give identical raw samples (Sec. 2 phase wrapping)."""
     f = 80e6
     d_u = C_LIGHT / (2 * f)
     cam = tiny_scene([[0, 0, 1]], 0.1).cameras[0]
@@ -200,7 +200,7 @@ def test_alpha_floor_and_early_stop():
 
 
 # --------------------------------------------------------------------------
-# projection (3DGS EWA convention, Sec. 4) against library routines
+# projection (3DGS EWA convention, Sec. 3) against library routines
 # --------------------------------------------------------------------------
 
 def _conic_at(sc, g=0):
@@ -249,7 +249,7 @@ def test_projection_off_axis_isotropic(pos):
 
 def test_moved_camera_uses_distance_to_optical_centre():
     """Falloff and phase use the distance to the optical centre o = -R^T t
-    (Sec. 4), not the view depth; the view depth orders Gaussians."""
+    (Sec. 3), not the view depth; the view depth orders Gaussians."""
     R = Rotation.from_euler("xyz", [0.1, -0.2, 0.3]).as_matrix()
     centre = np.array([0.4, -0.3, -0.5])
     rt = np.concatenate([R, (-R @ centre)[:, None]], 1)
@@ -489,7 +489,7 @@ def test_phasor_and_depth_single_and_two_gaussians():
 
 def test_phasor_equals_quad_differences():
     """With a common bias on each quad pair the phasor is the quad
-    differences of Sec. 3: Re = Q_pi/2 - Q_3pi/2, Im = Q_0 - Q_pi."""
+    differences of Sec. 2: Re = Q_pi/2 - Q_3pi/2, Im = Q_0 - Q_pi."""
     from paper_2505_05356_gb300 import scenes
     sc = scenes.make_scene("static_1k", 13, n=300, width=40, height=32, phasor=True)
     sc.sensor.offsets_rad = list(GOLDEN["phase_offsets_rad"]["value"])
@@ -530,7 +530,7 @@ def test_gradient_with_phasor_and_depth_matches_central_differences(seed):
 
 
 # --------------------------------------------------------------------------
-# view-dependent reflectivity from spherical harmonics (Sec. 4)
+# view-dependent reflectivity from spherical harmonics (Sec. 3)
 # --------------------------------------------------------------------------
 
 def _sh_scipy(l_index, x, y, z):
@@ -656,7 +656,7 @@ def test_gradient_with_sh_matches_central_differences(seed, n_sh):
 
 
 # --------------------------------------------------------------------------
-# asynchronous raw capture and piecewise-linear motion (Sec. 4, Eq. 7)
+# asynchronous raw capture and piecewise-linear motion (Sec. 3, Eq. 7)
 # --------------------------------------------------------------------------
 
 def test_eq7_interpolates_positions_between_timesteps():
