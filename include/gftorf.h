@@ -337,6 +337,63 @@ gftorf_status gftorf_read_counters(const gftorf_dims* dims, void* workspace,
                                    size_t workspace_bytes, int64_t* counters,
                                    void* stream);
 
+/* ---- Optimisation loop (Sec. 4: raw-quad L2 loss, Adam with betas (0.9,
+ * 0.999) and epsilon 1e-15, a fresh random background every iteration) ----
+ * Three calls that, with the render calls above, make one fitting iteration
+ * that needs no host round trip (so it can be captured in a CUDA graph):
+ *   gftorf_train_begin -> gftorf_preprocess -> gftorf_render_fwd ->
+ *   gftorf_l2_loss -> gftorf_render_bwd -> gftorf_adam_step.
+ * All FP32. */
+
+/* Device-resident loop state: caller-owned device memory, 8-byte aligned,
+ * all zero before the first iteration. */
+typedef struct {
+  int64_t step;        /* iterations begun: Adam's t                         */
+  double loss;         /* the current iteration's loss (gftorf_l2_loss adds) */
+  int64_t reserved[2];
+} gftorf_train_state;
+
+/* Starts an iteration: state->step += 1, state->loss = 0 and, if bg is not
+ * NULL, a fresh background bg[n_bg] (device) uniform in [-1, 1): value i of
+ * iteration s is 2u - 1, u = (top 24 bits of the k-th output of SplitMix64
+ * seeded with `seed`) * 2^-24, k = (s - 1) n_bg + i + 1.  One CTA;
+ * n_bg <= 65536. */
+gftorf_status gftorf_train_begin(gftorf_train_state* state, float* bg, int64_t n_bg,
+                                 uint64_t seed, void* stream);
+
+/* Raw-sample L2 loss of a rendered batch (the L_q term of Eq. 9, without
+ * SSIM): L = mean over frames, raw channels c < n_freq * n_offsets and
+ * pixels of (out - target)^2.  out, target, dL_dout: device [B][C][H][W]
+ * (C as for gftorf_render_fwd); dL_dout gets 2 (out - target) / M on the raw
+ * channels and 0 on the others (ambient, phasor, depth); L is added to
+ * state->loss.  dims->dtype must be GFTORF_F32. */
+gftorf_status gftorf_l2_loss(const gftorf_dims* dims, const float* out, const float* target,
+                             float* dL_dout, gftorf_train_state* state, void* stream);
+
+#define GFTORF_MAX_ADAM_GROUPS 12
+
+/* One parameter group of gftorf_adam_step: n values at param (updated in
+ * place), their gradient, Adam's first and second moments m, v (updated in
+ * place, zero before the first step), the learning rate, and the box
+ * [lo, hi] the updated values are clamped to (use +-INFINITY for none).
+ * Device pointers, FP32; grad may alias nothing else in the call. */
+typedef struct {
+  float* param;
+  const float* grad;
+  float* m;
+  float* v;
+  int64_t n;
+  float lr, lo, hi;
+} gftorf_adam_group;
+
+/* Adam (Kingma and Ba 2015, Algorithm 1) at t = max(1, state->step) over up to
+ * GFTORF_MAX_ADAM_GROUPS groups (HOST array) in one launch:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   p = clamp(p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), lo, hi). */
+gftorf_status gftorf_adam_step(const gftorf_adam_group* groups, int n_groups, float beta1,
+                               float beta2, float eps, const gftorf_train_state* state,
+                               void* stream);
+
 /* Static description of a status code. */
 const char* gftorf_status_string(gftorf_status status);
 

@@ -146,6 +146,10 @@ bool finite(float x) { return isfinite(x) != 0; }
 // projected records, per-pixel state and 2D-gradient regions are empty).
 bool binning_dims_ok(const gftorf_dims* d) { return dims_ok(d); }
 
+// Shape checks and channel layout for the optimisation-loop entry points.
+bool train_dims_ok(const gftorf_dims* d) { return dims_ok(d); }
+Layout train_layout(const gftorf_dims* d) { return make_layout(d); }
+
 Layout binning_layout(const gftorf_dims* d) {
   Layout L = make_layout(d);
   const size_t BN = (size_t)L.B * L.N;

@@ -9,7 +9,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
-from typing import Dict, List, Optional, Sequence
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
@@ -63,6 +63,15 @@ class Consts(ctypes.Structure):
 class Gaussians(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
                 ("means", "coeffs", "scales", "quats", "opacity", "amplitude", "delta", "sh")]
+
+
+class AdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float),
+                ("lo", ctypes.c_float), ("hi", ctypes.c_float)]
+
+
+MAX_ADAM_GROUPS = 12
 
 
 class Gradients(ctypes.Structure):
@@ -120,11 +129,16 @@ def load(build_if_missing: bool = True):
     L.gftorf_read_counters.restype = ctypes.c_int
     L.gftorf_kernel_launches.restype = ctypes.c_int64
     L.gftorf_kernel_launches.argtypes = []
+    L.gftorf_train_begin.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_uint64, vp]
+    L.gftorf_l2_loss.argtypes = [_P(Dims), vp, vp, vp, vp, vp]
+    L.gftorf_adam_step.argtypes = [_P(AdamGroup), ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, vp, vp]
     for name in ("gftorf_preprocess", "gftorf_render_fwd", "gftorf_render_bwd",
                  "gftorf_sort_footprints", "gftorf_export_tile_lists",
                  "gftorf_export_pixel_state", "gftorf_read_device_status",
                  "gftorf_bin", "gftorf_composite_fwd", "gftorf_zero_grad_buffers",
-                 "gftorf_composite_bwd", "gftorf_preprocess_bwd"):
+                 "gftorf_composite_bwd", "gftorf_preprocess_bwd", "gftorf_train_begin",
+                 "gftorf_l2_loss", "gftorf_adam_step"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -534,3 +548,76 @@ def render_ctof(renderer, frames, sensor, consts, bg, params):
                             params.get("coeffs"), params["scales"], params["quats"],
                             params["opacity"], params.get("amplitude"), params.get("delta"),
                             params.get("sh"))
+
+
+# --- optimisation loop ---------------------------------------------------------
+def new_train_state(device="cuda") -> torch.Tensor:
+    """Zeroed gftorf_train_state (32 bytes) on the device."""
+    return torch.zeros(4, dtype=torch.int64, device=device)
+
+
+def train_step_count(state: torch.Tensor) -> int:
+    return int(state[0].item())
+
+
+def train_loss(state: torch.Tensor) -> float:
+    """The current iteration's loss (synchronises)."""
+    return float(state.view(torch.float64)[1].item())
+
+
+def train_begin(state: torch.Tensor, bg: Optional[torch.Tensor], seed: int):
+    """Device-side iteration start: step += 1, loss = 0, fresh random bg."""
+    L = load()
+    n = 0 if bg is None else bg.numel()
+    if bg is not None and (bg.dtype != torch.float32 or not bg.is_contiguous()):
+        raise ValueError("bg must be contiguous float32")
+    _check(L.gftorf_train_begin(_ptr(state), _ptr(bg), n, seed & ((1 << 64) - 1), _stream()),
+           "gftorf_train_begin")
+
+
+def l2_loss(renderer: "Renderer", out, target, dout, state):
+    """dL/dout of the raw-sample L2 loss (written into dout); adds L to the
+    state's loss."""
+    _check(renderer.lib.gftorf_l2_loss(ctypes.byref(renderer.dims), _ptr(out), _ptr(target),
+                                       _ptr(dout), _ptr(state), _stream()), "gftorf_l2_loss")
+
+
+class Adam:
+    """Fused projected Adam over named parameter tensors (one launch).
+
+    lrs: name -> learning rate; bounds: name -> (lo, hi).  Moments live here;
+    the step count comes from the device-side train state."""
+
+    def __init__(self, params: Dict[str, torch.Tensor], lrs: Dict[str, float],
+                 bounds: Optional[Dict[str, Tuple[float, float]]] = None,
+                 betas=(0.9, 0.999), eps=1e-15):
+        self.lib = load()
+        self.names = [k for k in lrs if params.get(k) is not None]
+        if len(self.names) > MAX_ADAM_GROUPS:
+            raise ValueError("at most %d parameter groups" % MAX_ADAM_GROUPS)
+        self.params = params
+        self.m = {k: torch.zeros_like(params[k]) for k in self.names}
+        self.v = {k: torch.zeros_like(params[k]) for k in self.names}
+        self.lrs = dict(lrs)
+        self.bounds = dict(bounds or {})
+        self.betas, self.eps = betas, eps
+
+    def _groups(self, grads):
+        arr = (AdamGroup * len(self.names))()
+        for i, k in enumerate(self.names):
+            p, g = self.params[k], grads[k]
+            if (p.dtype != torch.float32 or g.dtype != torch.float32 or g.shape != p.shape
+                    or not p.is_contiguous() or not g.is_contiguous()):
+                raise ValueError("group %s: contiguous float32 param and grad of the same "
+                                 "shape required" % k)
+            lo, hi = self.bounds.get(k, (-math.inf, math.inf))
+            arr[i] = AdamGroup(_ptr(p), _ptr(g), _ptr(self.m[k]), _ptr(self.v[k]), p.numel(),
+                               self.lrs[k], lo, hi)
+        return arr
+
+    def step(self, grads: Dict[str, torch.Tensor], state: torch.Tensor):
+        arr = self._groups(grads)
+        self._keep = arr
+        _check(self.lib.gftorf_adam_step(arr, len(self.names), self.betas[0], self.betas[1],
+                                         self.eps, _ptr(state), _stream()),
+               "gftorf_adam_step")

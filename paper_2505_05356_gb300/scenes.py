@@ -284,3 +284,75 @@ def sample_pixels(scene: Scene, k: int, seed: int = 2) -> np.ndarray:
         out[b, :, 0] = idx % scene.width
         out[b, :, 1] = idx // scene.width
     return out
+
+
+def make_fit_scenes(seed: int = 4, n_backdrop: int = 270_000, n_rod: int = 30_000,
+                    n_init: int = 300_000, frames: int = 60, width: int = 640,
+                    height: int = 480):
+    """Ground truth and initial guess of the optimisation-loop workload.
+
+    Ground truth: a static backdrop (a wall at z = 5 m and a 1 m box around
+    z = 3.5 m, n_backdrop surface Gaussians) and an elongated object (a 0.8 m
+    rod of n_rod Gaussians, scales elongated along it) swinging about a pivot
+    in the image plane, theta(t) = A sin(pi t) with a 2 m/s peak tip speed,
+    seen in `frames` raw frames at t = b / (frames - 1) (the swing enters
+    through the per-frame displacement).  Initial guess (Sec. 4,
+    "Initialization"): n_init Gaussians uniform in the frustum between 1 and
+    6 m, reflectivity 0.1, static (zero trajectory coefficients).
+    Returns (gt, init) Scenes sharing cameras, times and sensor.
+    """
+    rng = np.random.default_rng(seed)
+    cam = pinhole(width, height)
+    hx, hy = (width / 2.0) / cam.fx, (height / 2.0) / cam.fy
+    # backdrop: 70 % on the wall, 30 % on the box faces
+    n_wall = int(0.7 * n_backdrop)
+    n_box = n_backdrop - n_wall
+    wall = np.stack([rng.uniform(-1, 1, n_wall) * hx * 5.0, rng.uniform(-1, 1, n_wall) * hy * 5.0,
+                     np.full(n_wall, 5.0) + rng.normal(0, 0.005, n_wall)], 1)
+    face = rng.integers(0, 6, n_box)
+    uv = rng.uniform(-0.5, 0.5, (n_box, 2))
+    box = np.zeros((n_box, 3))
+    ax = face // 2
+    sgn = np.where(face % 2 == 0, -0.5, 0.5)
+    for a in range(3):
+        on = ax == a
+        others = [k for k in range(3) if k != a]
+        box[on, a] = sgn[on]
+        box[on, others[0]] = uv[on, 0]
+        box[on, others[1]] = uv[on, 1]
+    box += np.array([0.8, 0.4, 3.5])
+    # rod along +x from the pivot at rest, swinging in the x-y plane
+    pivot = np.array([-0.9, -0.3, 2.5])
+    s_along = rng.uniform(0.0, 0.8, n_rod)
+    rod = pivot + np.stack([s_along, rng.normal(0, 0.01, n_rod), rng.normal(0, 0.01, n_rod)], 1)
+    means = np.concatenate([wall, box, rod]).astype(F32)
+    n = means.shape[0]
+    scales = np.empty((n, 3))
+    scales[:n_backdrop] = np.exp(rng.normal(-4.2, 0.2, (n_backdrop, 3)))
+    scales[n_backdrop:] = np.stack([np.exp(rng.normal(-3.9, 0.1, n_rod)),
+                                    np.exp(rng.normal(-5.0, 0.1, n_rod)),
+                                    np.exp(rng.normal(-5.0, 0.1, n_rod))], 1)
+    quats = np.tile([1.0, 0.0, 0.0, 0.0], (n, 1))
+    quats[:n_backdrop] = _unit_quats(rng, n_backdrop)
+    opacity = np.concatenate([rng.uniform(0.6, 0.99, n_backdrop), np.full(n_rod, 0.95)])
+    amplitude = np.concatenate([rng.uniform(0.3, 0.9, n_backdrop), np.full(n_rod, 0.8)])
+    times = (np.arange(frames) / max(frames - 1, 1)).astype(F32)
+    A = 2.0 / (0.8 * math.pi)  # peak angular speed A pi, tip speed 0.8 A pi = 2 m/s
+    delta = np.zeros((frames, n, 3), F32)
+    rel = means[n_backdrop:].astype(np.float64) - pivot
+    for b, t in enumerate(times):
+        th = A * math.sin(math.pi * float(t))
+        c, s_ = math.cos(th), math.sin(th)
+        rot = np.stack([c * rel[:, 0] - s_ * rel[:, 1], s_ * rel[:, 0] + c * rel[:, 1],
+                        rel[:, 2]], 1)
+        delta[b, n_backdrop:] = (rot - rel).astype(F32)
+    sensor = Sensor([float(F32(30e6))], [float(F32(o)) for o in
+                                         (0.0, math.pi / 2, math.pi, 3 * math.pi / 2)], 1.0)
+    consts = Consts().rounded()
+    bg = np.zeros((frames, sensor.n_channels), F32)
+    gt = Scene(means, None, scales.astype(F32), quats.astype(F32), opacity.astype(F32),
+               amplitude.astype(F32), times, [cam] * frames, delta, sensor, consts, bg)
+    m0, _, s0, q0, o0, _ = random_gaussians(rng, n_init, cam, (1.0, 6.0))
+    init = Scene(m0, np.zeros((n_init, 3, 3), F32), s0, q0, o0, np.full(n_init, 0.1, F32),
+                 times, [cam] * frames, None, sensor, consts, bg.copy())
+    return gt, init

@@ -124,5 +124,25 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gftorf.Frame) == 21 * 4
     assert ctypes.sizeof(gftorf.Sensor) == (4 + 8 + 1) * 4
     assert ctypes.sizeof(gftorf.Consts) == 6 * 4
+    assert ctypes.sizeof(gftorf.AdamGroup) == 4 * 8 + 8 + 3 * 4 + 4  # tail padding to 8
     assert ctypes.sizeof(gftorf.Gaussians) == 8 * ctypes.sizeof(ctypes.c_void_p)
     assert ctypes.sizeof(gftorf.Gradients) == 9 * ctypes.sizeof(ctypes.c_void_p)
+
+
+def test_training_calls_reject_bad_arguments_on_host(lib):
+    st = ctypes.c_void_p(4096)
+    assert lib.gftorf_train_begin(None, None, 0, 0, None) == gftorf.ERR_ARG
+    assert lib.gftorf_train_begin(ctypes.c_void_p(4100), None, 0, 0, None) == gftorf.ERR_ARG
+    assert lib.gftorf_train_begin(st, ctypes.c_void_p(256), 1 << 20, 0, None) == gftorf.ERR_ARG
+    d64 = _dims(dtype=1)
+    assert lib.gftorf_l2_loss(ctypes.byref(d64), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                              ctypes.c_void_p(256), st, None) == gftorf.ERR_ARG
+    assert lib.gftorf_l2_loss(ctypes.byref(_dims()), None, ctypes.c_void_p(256),
+                              ctypes.c_void_p(256), st, None) == gftorf.ERR_ARG
+    groups = (gftorf.AdamGroup * 13)()
+    assert lib.gftorf_adam_step(groups, 13, 0.9, 0.999, 1e-15, st, None) == gftorf.ERR_ARG
+    groups[0] = gftorf.AdamGroup(256, 256, 256, 256, 10, 0.1, 1.0, 0.0)  # lo > hi
+    assert lib.gftorf_adam_step(groups, 1, 0.9, 0.999, 1e-15, st, None) == gftorf.ERR_ARG
+    assert lib.gftorf_adam_step(groups, 0, 1.5, 0.999, 1e-15, st, None) == gftorf.ERR_ARG
+    # nothing to update: returns before touching the device
+    assert lib.gftorf_adam_step(groups, 0, 0.9, 0.999, 1e-15, st, None) == gftorf.OK
