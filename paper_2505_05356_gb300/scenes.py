@@ -356,3 +356,22 @@ def make_fit_scenes(seed: int = 4, n_backdrop: int = 270_000, n_rod: int = 30_00
     init = Scene(m0, np.zeros((n_init, 3, 3), F32), s0, q0, o0, np.full(n_init, 0.1, F32),
                  times, [cam] * frames, None, sensor, consts, bg.copy())
     return gt, init
+
+
+def init_mlp_params(seed: int = 0, head_std: float = 1e-5, width: int = 256, depth: int = 8,
+                    in_pad: int = 128, in_used: int = 84) -> np.ndarray:
+    """Packed float32 parameters of the deformation MLP (layout in
+    paper_2505_05356_gb300/mlp.py) drawn as in Sec. 4 ("MLP"): zero biases,
+    Xavier-normal hidden weights (std sqrt(2 / (fan_in + fan_out)), fan_in the
+    84 used inputs for the first layer, whose padding columns are 0), and the
+    head drawn from N(0, head_std) (1e-5 in the paper)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for li in range(depth):
+        fan_in = in_used if li == 0 else width
+        k = in_pad if li == 0 else width
+        W = np.zeros((width, k))
+        W[:, :fan_in] = rng.normal(0.0, math.sqrt(2.0 / (fan_in + width)), (width, fan_in))
+        parts += [W.reshape(-1), np.zeros(width)]
+    parts += [rng.normal(0.0, head_std, 3 * width), np.zeros(3)]
+    return np.concatenate(parts).astype(F32)
