@@ -394,6 +394,65 @@ gftorf_status gftorf_adam_step(const gftorf_adam_group* groups, int n_groups, fl
                                float beta2, float eps, const gftorf_train_state* state,
                                void* stream);
 
+/* ---- Deformation MLP (Sec. 4, "MLP") on the tensor cores ----
+ * delta_x[b][g] = MLP(gamma(means[g] * inv_scale), gamma(times[b])): the
+ * positions rescaled by inv_scale (the paper uses 1 / d_u, the unambiguous
+ * range), positional encoding gamma(p) = (p, sin(2^l pi p), cos(2^l pi p),
+ * l = 0..9) laid out as [x_0..2, (sin x_0..2, cos x_0..2) for l = 0..9, t,
+ * (sin t, cos t) for l = 0..9] (84 values, zero-padded to
+ * GFTORF_MLP_INPUT), GFTORF_MLP_DEPTH hidden layers of GFTORF_MLP_WIDTH
+ * units with ReLU, a linear head to the 3 components.  The output feeds
+ * gftorf_gaussians.delta; its gradient grads.delta feeds the backward.
+ * Parameters: one packed FP32 device vector of gftorf_mlp_param_count()
+ * values, [W_0 (256 x 128), b_0, W_1 (256 x 256), b_1, ..., W_7, b_7,
+ * W_head (3 x 256), b_head (3)], each W row-major (out, in).  Matrix
+ * products run in BF16 on the tensor cores with FP32 accumulation (weights,
+ * encoded inputs, hidden activations and back-propagated pre-activation
+ * gradients rounded to BF16); biases, the output and the encoding's gradient
+ * stay FP32.  The workspace (caller-owned device memory, 256-byte aligned,
+ * gftorf_mlp_workspace_size bytes) keeps the activations from the forward
+ * for the backward.  n_frames in [1, GFTORF_MAX_FRAMES]; times: HOST
+ * array of n_frames values. */
+#define GFTORF_MLP_WIDTH 256
+#define GFTORF_MLP_DEPTH 8
+#define GFTORF_MLP_INPUT 128
+
+size_t gftorf_mlp_param_count(void);
+size_t gftorf_mlp_workspace_size(int32_t n_gaussians, int32_t n_frames);
+
+/* delta[B][N][3] (device, FP32) for the packed parameters theta (device)
+ * and means[N][3] (device).  GFTORF_ERR_UNSUPPORTED when the driver offers
+ * no tensor-map encoder. */
+gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frames, const float* theta,
+                                 const float* means, const float* times, float inv_scale,
+                                 float* delta, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+
+/* Backward of the last gftorf_mlp_forward on this workspace (same
+ * arguments): d_theta (packed like theta) and d_means[N][3] (the path
+ * through the encoding, summed over frames) are OVERWRITTEN from
+ * d_delta[B][N][3]. */
+gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_frames, const float* theta,
+                                  const float* means, const float* times, float inv_scale,
+                                  const float* d_delta, float* d_theta, float* d_means,
+                                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* Copy an intermediate of the last gftorf_mlp_forward / _backward on this
+ * workspace into dst (device), rows m = b N + g, for inspection and tests:
+ * what = 0: the encoded input (BF16 bits, [B N][GFTORF_MLP_INPUT]);
+ * 1: hidden activation H_layer (BF16 bits, [B N][GFTORF_MLP_WIDTH]);
+ * 2: back-propagated pre-activation gradient dZ_layer of the last backward
+ *    (BF16 bits, [B N][GFTORF_MLP_WIDTH]);
+ * 3: gradient of the encoded input (FP32, [B N][GFTORF_MLP_INPUT]).
+ * layer in [0, GFTORF_MLP_DEPTH) for what = 1, 2. */
+gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames, int32_t what,
+                                int32_t layer, void* dst, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* Synchronises `stream`; GFTORF_OK or GFTORF_ERR_TIMEOUT if a bounded wait
+ * of the last MLP call ran out. */
+gftorf_status gftorf_mlp_read_status(void* workspace, size_t workspace_bytes, void* stream);
+
 /* Static description of a status code. */
 const char* gftorf_status_string(gftorf_status status);
 

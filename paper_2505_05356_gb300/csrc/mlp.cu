@@ -1,0 +1,836 @@
+// mlp.cu -- the deformation MLP of Sec. 4 ("MLP") on the 5th-generation
+// tensor cores: delta_x = MLP(gamma(x / d_u), gamma(t)), 8 hidden layers of
+// 256 with ReLU, a linear head to the 3 offset components, forward and
+// backward for B frames x N Gaussians (rows m = b N + g).
+//
+// Every matrix product is one BF16 GEMM kernel, D[M x N] = A[M x K] B[N x K]^T
+// with FP32 accumulation: operands K-major in global memory, brought into
+// shared memory by TMA (128-byte swizzle, a 4-stage mbarrier pipeline), one
+// elected thread issuing tcgen05.mma into a TMEM accumulator, four epilogue
+// warps draining TMEM with tcgen05.ld and applying the layer's epilogue:
+//   forward hidden layer   H = relu(D + b) -> H (row-major) and H^T
+//   forward head           delta = D + b (FP32)
+//   backward, hidden       dZ = D * (H_prev > 0) -> dZ and dZ^T
+//   backward, first layer  d(encoding) = D (FP32)
+//   weight gradient        dW_ext += D (split over rows, FP32 atomics)
+// The transposed copies make the weight-gradient GEMM K-major as well
+// (dW = dZ^T H: both operands have the rows of the batch as their reduction
+// dimension), and each transposed activation carries an extra row of ones so
+// that the same GEMM yields the bias gradient in the column after the
+// weights.  Waits on mbarriers are bounded (about 2 s): a wait that runs out
+// records GFTORF_ERR_TIMEOUT in the status word and the CTA winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "gftorf_internal.cuh"
+
+namespace gftorf {
+namespace {
+
+constexpr int kW = GFTORF_MLP_WIDTH;    // 256
+constexpr int kDepth = GFTORF_MLP_DEPTH;  // 8
+constexpr int kIn = GFTORF_MLP_INPUT;   // 128 (84 used)
+constexpr int kFreq = 10;
+constexpr int kHeadRows = 32;           // head padded to the MMA's N = 32
+constexpr int kExt = 16;                // ones row + padding after a transposed block
+constexpr int BM = 128, BK = 64, kStages = 4;
+
+enum Epi { EPI_HIDDEN = 0, EPI_HEAD = 1, EPI_MASK = 2, EPI_F32 = 3, EPI_ATOMIC = 4 };
+
+struct GemmArgs {
+  int kb_total;      // k-blocks (of 64) of the reduction
+  int kb_per_split;  // k-blocks per CTA along gridDim.z
+  int rows_valid;    // output rows that exist (epilogue guard)
+  int cols_valid;    // output columns that exist
+  const float* bias;
+  __nv_bfloat16* out_b;   // row-major bf16 output (ld = ldo)
+  __nv_bfloat16* out_t;   // transposed bf16 output (ld = ldt), or null
+  int ldo, ldt, ext_rows; // ext_rows: the transposed block's row count before the ones row
+  float* out_f;           // FP32 output (ld = ldf)
+  int ldf;
+  const __nv_bfloat16* mask;  // H of the layer below (ld = ldm)
+  int ldm;
+  int* status;
+};
+
+// ---- PTX wrappers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase with the given parity to complete.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (global_ns() - t0 > 2000000000ull) {
+      atomicExch(status, (int)GFTORF_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// K-major operand tile in shared memory, rows of 128 bytes with the 128-byte
+// swizzle (8-row groups 1024 bytes apart); the start address may step along K
+// inside the 128-byte row.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                             // leading offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                   // stride between 8-row groups
+  d |= (uint64_t)1 << 46;                             // descriptor version
+  d |= (uint64_t)2 << 61;                             // 128-byte swizzle
+  return d;
+}
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per lane)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void store_row_bf16(__nv_bfloat16* dst, const float* v) {
+  uint4 q[4];
+  uint32_t* w = reinterpret_cast<uint32_t*>(q);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = q[i];
+}
+
+// 32 columns [n, n + 32) of output row m
+template <int EPI>
+__device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float* v) {
+  if (EPI == EPI_HIDDEN || EPI == EPI_MASK) {
+    if (EPI == EPI_HIDDEN) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + __ldg(p.bias + n + j), 0.f);
+    } else {
+      const uint4* mk = reinterpret_cast<const uint4*>(p.mask + (size_t)m * p.ldm + n);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 u = __ldg(mk + q);
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (!(__bfloat162float(h[j]) > 0.f)) v[8 * q + j] = 0.f;
+      }
+    }
+    store_row_bf16(p.out_b + (size_t)m * p.ldo + n, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) p.out_t[(size_t)(n + j) * p.ldt + m] = __float2bfloat16_rn(v[j]);
+    if (p.ext_rows > 0 && n == 0) {  // the ones row (bias gradient) and its padding
+      p.out_t[(size_t)p.ext_rows * p.ldt + m] = __float2bfloat16_rn(1.f);
+#pragma unroll
+      for (int e = 1; e < kExt; ++e)
+        p.out_t[(size_t)(p.ext_rows + e) * p.ldt + m] = __float2bfloat16_rn(0.f);
+    }
+  } else if (EPI == EPI_HEAD) {
+    if (m < p.rows_valid)
+      for (int j = 0; j < 3; ++j) p.out_f[(size_t)m * 3 + j] = v[j] + __ldg(p.bias + j);
+  } else if (EPI == EPI_F32) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (n + j < p.cols_valid) p.out_f[(size_t)m * p.ldf + n + j] = v[j];
+  } else {  // EPI_ATOMIC
+    if (m < p.rows_valid) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (n + j < p.cols_valid) atomicAdd(p.out_f + (size_t)m * p.ldf + n + j, v[j]);
+    }
+  }
+}
+
+template <int BN>
+constexpr int smem_bytes() {
+  return kStages * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(192, 1)
+    umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
+  constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE = A_BYTES + B_BYTES;
+  constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem =
+      reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * STAGE);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * kStages,
+                 done = full0 + 16 * kStages;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kb0 = blockIdx.z * p.kb_per_split;
+  const int nkb = min(p.kb_per_split, p.kb_total - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(slot), TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (warp == 4) {
+    // TMA producer
+    if (lane == 0 && nkb > 0) {
+      int issued = 0;
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % kStages;
+        const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status)) break;
+        mbar_expect_tx(full0 + 8 * s, STAGE);
+        const uint32_t sa = sbase + s * STAGE;
+        tma_load_2d(sa, &tmA, full0 + 8 * s, (kb0 + i) * BK, m0);
+        tma_load_2d(sa + A_BYTES, &tmB, full0 + 8 * s, (kb0 + i) * BK, n0);
+        issued = i + 1;
+      }
+      // every load issued has landed before the CTA may exit
+      for (int i = issued - kStages < 0 ? 0 : issued - kStages; i < issued; ++i)
+        mbar_wait(full0 + 8 * (i % kStages), (uint32_t)(i / kStages) & 1u, p.status);
+    }
+  } else if (warp == 5) {
+    // MMA issuer
+    if (lane == 0 && nkb > 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % kStages;
+        const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+        if (!mbar_wait(full0 + 8 * s, ph, p.status)) break;
+        tc_fence_after();
+        const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          umma_bf16(tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
+                    (i > 0 || k > 0) ? 1u : 0u);
+        umma_commit(empty0 + 8 * s);
+      }
+      umma_commit(done);  // completes once every MMA issued above has
+    }
+  } else {
+    // epilogue: warp w owns TMEM lanes / output rows 32 w .. 32 w + 31
+    if (nkb > 0 && mbar_wait(done, 0, p.status)) {
+      tc_fence_after();
+      const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+        epilogue<EPI>(p, m, n0 + c * 32, v);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TCOLS);
+  }
+}
+
+// ---- element-wise kernels ----------------------------------------------------
+struct Times {
+  float t[kMaxFrames];
+};
+
+// fp32 packed parameters -> bf16 W and W^T of every layer (head padded to 32 rows)
+__global__ void mlp_prep_weights_kernel(const float* __restrict__ theta,
+                                        __nv_bfloat16* __restrict__ wb,
+                                        __nv_bfloat16* __restrict__ wt) {
+  // packed offsets: layer l (0..7) W at off_w(l), then b; head after
+  const int K0 = kIn;
+  const size_t total = (size_t)kW * K0 + (size_t)(kDepth - 1) * kW * kW + (size_t)kHeadRows * kW;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int l, o, i;
+    size_t src, dstb, dstt;
+    if (e < (size_t)kW * K0) {
+      l = 0;
+      o = (int)(e / K0), i = (int)(e % K0);
+      src = (size_t)o * K0 + i;
+      dstb = e;
+      dstt = (size_t)i * kW + o;
+    } else if (e < (size_t)kW * K0 + (size_t)(kDepth - 1) * kW * kW) {
+      const size_t r = e - (size_t)kW * K0;
+      l = 1 + (int)(r / ((size_t)kW * kW));
+      const size_t q = r % ((size_t)kW * kW);
+      o = (int)(q / kW), i = (int)(q % kW);
+      const size_t base = (size_t)kW * K0 + kW + (size_t)(l - 1) * ((size_t)kW * kW + kW);
+      src = base + q;
+      dstb = e;
+      dstt = (size_t)kW * K0 + (size_t)(l - 1) * kW * kW + (size_t)i * kW + o;
+    } else {
+      const size_t r = e - (size_t)kW * K0 - (size_t)(kDepth - 1) * kW * kW;
+      l = kDepth;
+      o = (int)(r / kW), i = (int)(r % kW);
+      const size_t base = (size_t)kW * K0 + kW + (size_t)(kDepth - 1) * ((size_t)kW * kW + kW);
+      src = o < 3 ? base + (size_t)o * kW + i : 0;
+      dstb = e;
+      dstt = (size_t)kW * K0 + (size_t)(kDepth - 1) * kW * kW + (size_t)i * kHeadRows + o;
+    }
+    const float w = (l == kDepth && o >= 3) ? 0.f : theta[src];
+    wb[dstb] = __float2bfloat16_rn(w);
+    wt[dstt] = __float2bfloat16_rn(w);
+  }
+}
+
+// positional encoding of row m = b N + g into enc[m][0..127] and encT[c][m]
+__global__ void mlp_encode_kernel(const float* __restrict__ means, Times tm, int N, int B,
+                                  float inv_scale, int M_pad, __nv_bfloat16* __restrict__ enc,
+                                  __nv_bfloat16* __restrict__ encT) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M_pad) return;
+  float e[kIn];
+#pragma unroll
+  for (int c = 0; c < kIn; ++c) e[c] = 0.f;
+  if (m < N * B) {
+    const int b = m / N, g = m - b * N;
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = means[(size_t)g * 3 + a] * inv_scale;
+    const float t = tm.t[b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) e[a] = x[a];
+    float f = 1.f;
+#pragma unroll
+    for (int l = 0; l < kFreq; ++l, f *= 2.f) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) sincospif(f * x[a], &e[3 + 6 * l + a], &e[6 + 6 * l + a]);
+    }
+    e[63] = t;
+    f = 1.f;
+#pragma unroll
+    for (int l = 0; l < kFreq; ++l, f *= 2.f) sincospif(f * t, &e[64 + 2 * l], &e[65 + 2 * l]);
+  }
+#pragma unroll
+  for (int q = 0; q < kIn / 32; ++q) store_row_bf16(enc + (size_t)m * kIn + 32 * q, e + 32 * q);
+#pragma unroll
+  for (int c = 0; c < kIn; ++c) encT[(size_t)c * M_pad + m] = __float2bfloat16_rn(e[c]);
+  encT[(size_t)kIn * M_pad + m] = __float2bfloat16_rn(1.f);
+#pragma unroll
+  for (int c = 1; c < kExt; ++c) encT[(size_t)(kIn + c) * M_pad + m] = __float2bfloat16_rn(0.f);
+}
+
+// dL/d(delta) fp32 [M][3] -> bf16 [M_pad][32] and its transpose [32][M_pad]
+__global__ void mlp_head_grad_kernel(const float* __restrict__ dd, int M, int M_pad,
+                                     __nv_bfloat16* __restrict__ dz,
+                                     __nv_bfloat16* __restrict__ dzt) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M_pad) return;
+  float v[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = 0.f;
+  if (m < M) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[j] = dd[(size_t)m * 3 + j];
+  }
+  store_row_bf16(dz + (size_t)m * kHeadRows, v);
+#pragma unroll
+  for (int j = 0; j < kHeadRows; ++j) dzt[(size_t)j * M_pad + m] = __float2bfloat16_rn(v[j]);
+}
+
+// d(encoding) -> d(means), summed over the frames in order
+__global__ void mlp_encode_bwd_kernel(const float* __restrict__ means,
+                                      const float* __restrict__ denc, int N, int B,
+                                      float inv_scale, float* __restrict__ dmeans) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  float x[3], acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = means[(size_t)g * 3 + a] * inv_scale;
+  for (int b = 0; b < B; ++b) {
+    const float* d = denc + ((size_t)b * N + g) * kIn;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float s = d[a], f = 1.f;
+#pragma unroll
+      for (int l = 0; l < kFreq; ++l, f *= 2.f) {
+        float sn, cs;
+        sincospif(f * x[a], &sn, &cs);
+        s += f * 3.14159265358979323846f * (cs * d[3 + 6 * l + a] - sn * d[6 + 6 * l + a]);
+      }
+      acc[a] += s;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dmeans[(size_t)g * 3 + a] = acc[a] * inv_scale;
+}
+
+// extended weight gradients [rows][K + ext] -> packed d_theta (W then b)
+__global__ void mlp_unpack_grads_kernel(const float* __restrict__ dwx, float* __restrict__ dth) {
+  const size_t total = (size_t)kW * (kIn + 1) + (size_t)(kDepth - 1) * kW * (kW + 1) + 3 * (kW + 1);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    // locate layer
+    size_t r = e, src_base = 0;
+    int K = kIn, rows = kW, l = 0;
+    for (;;) {
+      const size_t n = (size_t)rows * (K + 1);
+      if (r < n) break;
+      r -= n;
+      src_base += (size_t)(l == kDepth ? kHeadRows : kW) * (K + kExt);
+      ++l;
+      K = kW;
+      rows = l == kDepth ? 3 : kW;
+    }
+    const int ld = K + kExt;
+    float v;
+    if (r < (size_t)rows * K) {
+      const int o = (int)(r / K), i = (int)(r % K);
+      v = dwx[src_base + (size_t)o * ld + i];
+    } else {
+      const int o = (int)(r - (size_t)rows * K);
+      v = dwx[src_base + (size_t)o * ld + K];
+    }
+    dth[e] = v;
+  }
+}
+
+// ---- host side -----------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// bf16 matrix [rows][cols] with row stride ld elements; boxes of 64 columns x box_rows
+bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+              uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 2) % 16 != 0) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int EPI>
+bool gemm(const CUtensorMap& a, const CUtensorMap& b, const GemmArgs& args, int m_tiles,
+          int n_tiles, int splits, cudaStream_t st) {
+  static bool configured = false;
+  constexpr int smem = smem_bytes<BN>();
+  if (!configured) {
+    if (cudaFuncSetAttribute(umma_gemm_kernel<BN, EPI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return false;
+    configured = true;
+  }
+  umma_gemm_kernel<BN, EPI><<<dim3(m_tiles, n_tiles, splits), 192, smem, st>>>(a, b, args);
+  count_launches(1);
+  return true;
+}
+
+struct MlpLayout {
+  int N, B, M, M_pad;
+  size_t off_status, off_wb, off_wt, off_enc, off_encT, off_h, off_ht, off_dz, off_dzt0,
+      off_dzt1, off_dzh, off_dzht, off_denc, off_dwx, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t dwx_floats() {
+  return (size_t)kW * (kIn + kExt) + (size_t)(kDepth - 1) * kW * (kW + kExt) +
+         (size_t)kHeadRows * (kW + kExt);
+}
+size_t wb_elems() {
+  return (size_t)kW * kIn + (size_t)(kDepth - 1) * kW * kW + (size_t)kHeadRows * kW;
+}
+
+MlpLayout mlp_layout(int N, int B) {
+  MlpLayout L;
+  memset(&L, 0, sizeof(L));
+  L.N = N, L.B = B, L.M = N * B;
+  L.M_pad = (L.M + BM - 1) / BM * BM;
+  if (L.M_pad == 0) L.M_pad = BM;
+  const size_t Mp = (size_t)L.M_pad;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at_ = o;
+    o = align256(o + bytes);
+    return at_;
+  };
+  L.off_status = take(256);
+  L.off_wb = take(wb_elems() * 2);
+  L.off_wt = take(wb_elems() * 2);
+  L.off_enc = take(Mp * kIn * 2);
+  L.off_encT = take((size_t)(kIn + kExt) * Mp * 2);
+  L.off_h = take((size_t)kDepth * Mp * kW * 2);
+  L.off_ht = take((size_t)kDepth * (kW + kExt) * Mp * 2);
+  L.off_dz = take((size_t)kDepth * Mp * kW * 2);  // dZ of every layer (kept for export)
+  L.off_dzt0 = take((size_t)kW * Mp * 2);
+  L.off_dzt1 = take((size_t)kW * Mp * 2);
+  L.off_dzh = take(Mp * kHeadRows * 2);
+  L.off_dzht = take((size_t)kHeadRows * Mp * 2);
+  L.off_denc = take(Mp * kIn * 4);
+  L.off_dwx = take(dwx_floats() * 4);
+  L.total = o;
+  return L;
+}
+
+bool mlp_args_ok(int N, int B) {
+  return N >= 0 && B >= 1 && B <= kMaxFrames && (int64_t)N * B < (int64_t)1 << 30;
+}
+
+template <typename T>
+T* ptr(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + off);
+}
+
+// bf16 weights of layer l (l = kDepth: head) and their transposes
+size_t wb_off(int l) {
+  return l == 0 ? 0 : (size_t)kW * kIn + (size_t)(l - 1) * kW * kW;
+}
+size_t bias_off(int l) {  // in the packed fp32 vector
+  if (l == 0) return (size_t)kW * kIn;
+  return (size_t)kW * kIn + kW + (size_t)(l - 1) * ((size_t)kW * kW + kW) + (size_t)kW * kW;
+}
+size_t head_bias_off() {
+  return (size_t)kW * kIn + kW + (size_t)(kDepth - 1) * ((size_t)kW * kW + kW) + 3 * kW;
+}
+size_t dwx_off(int l) {  // floats
+  if (l == 0) return 0;
+  return (size_t)kW * (kIn + kExt) + (size_t)(l - 1) * kW * (kW + kExt);
+}
+
+}  // namespace
+}  // namespace gftorf
+
+using namespace gftorf;
+
+extern "C" size_t gftorf_mlp_workspace_size(int32_t n_gaussians, int32_t n_frames) {
+  if (!mlp_args_ok(n_gaussians, n_frames)) return 0;
+  return mlp_layout(n_gaussians, n_frames).total;
+}
+
+extern "C" size_t gftorf_mlp_param_count(void) {
+  return (size_t)kW * kIn + kW + (size_t)(kDepth - 1) * ((size_t)kW * kW + kW) + 3 * kW + 3;
+}
+
+extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frames,
+                                            const float* theta, const float* means,
+                                            const float* times, float inv_scale, float* delta,
+                                            void* workspace, size_t workspace_bytes,
+                                            void* stream) {
+  if (!mlp_args_ok(n_gaussians, n_frames) || !theta || !times ||
+      (n_gaussians > 0 && (!means || !delta)) || !(inv_scale > 0.f))
+    return GFTORF_ERR_ARG;
+  const MlpLayout L = mlp_layout(n_gaussians, n_frames);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 ||
+      workspace_bytes < L.total)
+    return GFTORF_ERR_WORKSPACE;
+  for (int b = 0; b < n_frames; ++b)
+    if (!std::isfinite(times[b])) return GFTORF_ERR_ARG;
+  if (!encode_fn()) return GFTORF_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* ws = workspace;
+  const int Mp = L.M_pad;
+  int* status = ptr<int>(ws, L.off_status);
+  cudaMemsetAsync(status, 0, 256, st);  // the status word of this forward and its backward
+  if (L.M == 0) return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+  auto* wb = ptr<__nv_bfloat16>(ws, L.off_wb);
+  auto* wt = ptr<__nv_bfloat16>(ws, L.off_wt);
+  mlp_prep_weights_kernel<<<4 * 152, 256, 0, st>>>(theta, wb, wt);
+  Times tm;
+  memset(&tm, 0, sizeof(tm));
+  for (int b = 0; b < n_frames; ++b) tm.t[b] = times[b];
+  auto* enc = ptr<__nv_bfloat16>(ws, L.off_enc);
+  auto* encT = ptr<__nv_bfloat16>(ws, L.off_encT);
+  mlp_encode_kernel<<<(Mp + 127) / 128, 128, 0, st>>>(means, tm, n_gaussians, n_frames,
+                                                      inv_scale, Mp, enc, encT);
+  count_launches(2);
+  auto* H = ptr<__nv_bfloat16>(ws, L.off_h);
+  auto* HT = ptr<__nv_bfloat16>(ws, L.off_ht);
+  const int mt = Mp / BM;
+  for (int l = 0; l < kDepth; ++l) {
+    const int K = l == 0 ? kIn : kW;
+    const __nv_bfloat16* in = l == 0 ? enc : H + (size_t)(l - 1) * Mp * kW;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, in, Mp, K, K, BM) || !make_map(&mb, wb + wb_off(l), kW, K, K, 256))
+      return GFTORF_ERR_CUDA;
+    GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kb_total = K / BK, a.kb_per_split = K / BK;
+    a.rows_valid = Mp, a.cols_valid = kW;
+    a.bias = theta + bias_off(l);
+    a.out_b = H + (size_t)l * Mp * kW, a.ldo = kW;
+    a.out_t = HT + (size_t)l * (kW + kExt) * Mp, a.ldt = Mp, a.ext_rows = kW;
+    a.status = status;
+    if (!gemm<256, EPI_HIDDEN>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
+  }
+  {
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, H + (size_t)(kDepth - 1) * Mp * kW, Mp, kW, kW, BM) ||
+        !make_map(&mb, wb + wb_off(kDepth), kHeadRows, kW, kW, kHeadRows))
+      return GFTORF_ERR_CUDA;
+    GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kb_total = kW / BK, a.kb_per_split = kW / BK;
+    a.rows_valid = L.M, a.cols_valid = 3;
+    a.bias = theta + head_bias_off();
+    a.out_f = delta;
+    a.status = status;
+    if (!gemm<32, EPI_HEAD>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+}
+
+extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_frames,
+                                             const float* theta, const float* means,
+                                             const float* times, float inv_scale,
+                                             const float* d_delta, float* d_theta,
+                                             float* d_means, void* workspace,
+                                             size_t workspace_bytes, void* stream) {
+  if (!mlp_args_ok(n_gaussians, n_frames) || !theta || !times || !d_theta ||
+      (n_gaussians > 0 && (!means || !d_means || !d_delta)) || !(inv_scale > 0.f))
+    return GFTORF_ERR_ARG;
+  const MlpLayout L = mlp_layout(n_gaussians, n_frames);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 ||
+      workspace_bytes < L.total)
+    return GFTORF_ERR_WORKSPACE;
+  if (!encode_fn()) return GFTORF_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* ws = workspace;
+  const int Mp = L.M_pad;
+  int* status = ptr<int>(ws, L.off_status);
+  float* dwx = ptr<float>(ws, L.off_dwx);
+  cudaMemsetAsync(dwx, 0, dwx_floats() * 4, st);
+  if (L.M == 0) {
+    mlp_unpack_grads_kernel<<<4 * 152, 256, 0, st>>>(dwx, d_theta);
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+  }
+  auto* wt = ptr<__nv_bfloat16>(ws, L.off_wt);
+  auto* encT = ptr<__nv_bfloat16>(ws, L.off_encT);
+  auto* H = ptr<__nv_bfloat16>(ws, L.off_h);
+  auto* HT = ptr<__nv_bfloat16>(ws, L.off_ht);
+  auto* dzh = ptr<__nv_bfloat16>(ws, L.off_dzh);
+  auto* dzht = ptr<__nv_bfloat16>(ws, L.off_dzht);
+  auto dz = [&](int l) { return ptr<__nv_bfloat16>(ws, L.off_dz) + (size_t)l * Mp * kW; };
+  __nv_bfloat16* dzt[2] = {ptr<__nv_bfloat16>(ws, L.off_dzt0),
+                           ptr<__nv_bfloat16>(ws, L.off_dzt1)};
+  float* denc = ptr<float>(ws, L.off_denc);
+  const int mt = Mp / BM;
+  const int kb_rows = Mp / BK;      // k-blocks of a reduction over the batch rows
+  const int per_split = 64;         // 4096 rows per CTA in the weight-gradient GEMMs
+  const int splits = (kb_rows + per_split - 1) / per_split;
+
+  mlp_head_grad_kernel<<<(Mp + 127) / 128, 128, 0, st>>>(d_delta, L.M, Mp, dzh, dzht);
+  count_launches(1);
+  // head: dW_head += dZh^T H_7 (bias in the ones column)
+  {
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, dzht, kHeadRows, Mp, Mp, BM) ||
+        !make_map(&mb, HT + (size_t)(kDepth - 1) * (kW + kExt) * Mp, kW + kExt, Mp, Mp, 256))
+      return GFTORF_ERR_CUDA;
+    GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kb_total = kb_rows, a.kb_per_split = per_split;
+    a.rows_valid = 3, a.cols_valid = kW + 1;
+    a.out_f = dwx + dwx_off(kDepth), a.ldf = kW + kExt;
+    a.status = status;
+    if (!gemm<256, EPI_ATOMIC>(ma, mb, a, 1, 2, splits, st)) return GFTORF_ERR_CUDA;
+  }
+  // dH_7 = dZh W_head, dZ_7 = dH_7 * (H_7 > 0)
+  int cur = 0;
+  {
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, dzh, Mp, kHeadRows, kHeadRows, BM) ||
+        !make_map(&mb, wt + wb_off(kDepth), kW, kHeadRows, kHeadRows, 256))
+      return GFTORF_ERR_CUDA;
+    GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kb_total = 1, a.kb_per_split = 1;
+    a.rows_valid = Mp, a.cols_valid = kW;
+    a.out_b = dz(kDepth - 1), a.ldo = kW, a.out_t = dzt[cur], a.ldt = Mp;
+    a.mask = H + (size_t)(kDepth - 1) * Mp * kW, a.ldm = kW;
+    a.status = status;
+    if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
+  }
+  for (int l = kDepth - 1; l >= 0; --l) {
+    const int K = l == 0 ? kIn : kW;
+    // dW_l += dZ_l^T H_{l-1} (or the encoding)
+    {
+      const __nv_bfloat16* bt = l == 0 ? encT : HT + (size_t)(l - 1) * (kW + kExt) * Mp;
+      CUtensorMap ma, mb;
+      if (!make_map(&ma, dzt[cur], kW, Mp, Mp, BM) ||
+          !make_map(&mb, bt, K + kExt, Mp, Mp, 256))
+        return GFTORF_ERR_CUDA;
+      GemmArgs a;
+      memset(&a, 0, sizeof(a));
+      a.kb_total = kb_rows, a.kb_per_split = per_split;
+      a.rows_valid = kW, a.cols_valid = K + 1;
+      a.out_f = dwx + dwx_off(l), a.ldf = K + kExt;
+      a.status = status;
+      if (!gemm<256, EPI_ATOMIC>(ma, mb, a, kW / BM, (K + kExt + 255) / 256, splits, st))
+        return GFTORF_ERR_CUDA;
+    }
+    // dH_{l-1} = dZ_l W_l  (l = 0: the encoding's gradient, FP32)
+    {
+      CUtensorMap ma, mb;
+      if (!make_map(&ma, dz(l), Mp, kW, kW, BM) || !make_map(&mb, wt + wb_off(l), K, kW, kW, 256))
+        return GFTORF_ERR_CUDA;
+      GemmArgs a;
+      memset(&a, 0, sizeof(a));
+      a.kb_total = kW / BK, a.kb_per_split = kW / BK;
+      a.rows_valid = Mp, a.cols_valid = K;
+      a.status = status;
+      if (l == 0) {
+        a.out_f = denc, a.ldf = kIn;
+        if (!gemm<256, EPI_F32>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
+      } else {
+        a.out_b = dz(l - 1), a.ldo = kW, a.out_t = dzt[cur ^ 1], a.ldt = Mp;
+        a.mask = H + (size_t)(l - 1) * Mp * kW, a.ldm = kW;
+        if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
+        cur ^= 1;
+      }
+    }
+  }
+  mlp_unpack_grads_kernel<<<4 * 152, 256, 0, st>>>(dwx, d_theta);
+  mlp_encode_bwd_kernel<<<(n_gaussians + 127) / 128, 128, 0, st>>>(means, denc, n_gaussians,
+                                                                   n_frames, inv_scale, d_means);
+  count_launches(2);
+  (void)times;
+  return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+}
+
+extern "C" gftorf_status gftorf_mlp_read_status(void* workspace, size_t workspace_bytes,
+                                                void* stream) {
+  if (!workspace || workspace_bytes < 256) return GFTORF_ERR_WORKSPACE;
+  int s = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&s, workspace, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GFTORF_ERR_CUDA;
+  return (gftorf_status)s;
+}
+
+extern "C" gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames, int32_t what,
+                                           int32_t layer, void* dst, void* workspace,
+                                           size_t workspace_bytes, void* stream) {
+  if (!mlp_args_ok(n_gaussians, n_frames) || !dst) return GFTORF_ERR_ARG;
+  const MlpLayout L = mlp_layout(n_gaussians, n_frames);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 ||
+      workspace_bytes < L.total)
+    return GFTORF_ERR_WORKSPACE;
+  const size_t Mp = (size_t)L.M_pad, M = (size_t)L.M;
+  size_t off, bytes;
+  switch (what) {
+    case 0: off = L.off_enc, bytes = M * kIn * 2; break;
+    case 1:
+    case 2:
+      if (layer < 0 || layer >= kDepth) return GFTORF_ERR_ARG;
+      off = (what == 1 ? L.off_h : L.off_dz) + (size_t)layer * Mp * kW * 2;
+      bytes = M * kW * 2;
+      break;
+    case 3: off = L.off_denc, bytes = M * kIn * 4; break;
+    default: return GFTORF_ERR_ARG;
+  }
+  if (bytes == 0) return GFTORF_OK;
+  const cudaError_t e =
+      cudaMemcpyAsync(dst, static_cast<unsigned char*>(workspace) + off, bytes,
+                      cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+}

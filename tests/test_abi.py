@@ -146,3 +146,31 @@ def test_training_calls_reject_bad_arguments_on_host(lib):
     assert lib.gftorf_adam_step(groups, 0, 1.5, 0.999, 1e-15, st, None) == gftorf.ERR_ARG
     # nothing to update: returns before touching the device
     assert lib.gftorf_adam_step(groups, 0, 0.9, 0.999, 1e-15, st, None) == gftorf.OK
+
+
+def test_mlp_calls_reject_bad_arguments_on_host(lib):
+    from paper_2505_05356_gb300 import mlp
+    L = mlp._lib()
+    assert L.gftorf_mlp_param_count() == 256 * 128 + 256 + 7 * (256 * 256 + 256) + 3 * 256 + 3
+    assert L.gftorf_mlp_workspace_size(-1, 1) == 0
+    assert L.gftorf_mlp_workspace_size(10, 0) == 0
+    assert L.gftorf_mlp_workspace_size(10, 65) == 0
+    small = L.gftorf_mlp_workspace_size(1000, 2)
+    assert small > 0 and small % 256 == 0
+    assert L.gftorf_mlp_workspace_size(2000, 2) > small
+    t = (ctypes.c_float * 2)(0.0, 1.0)
+    ws = ctypes.c_void_p(4096)
+    # missing pointers, bad scale, short or misaligned workspace: before any device work
+    assert L.gftorf_mlp_forward(10, 2, None, 256, t, 0.2, 256, ws, small, None) == gftorf.ERR_ARG
+    assert L.gftorf_mlp_forward(10, 2, 256, 256, t, 0.0, 256, ws, small, None) == gftorf.ERR_ARG
+    assert L.gftorf_mlp_forward(1000, 2, 256, 256, t, 0.2, 256, ws, small - 1,
+                                None) == gftorf.ERR_WORKSPACE
+    assert L.gftorf_mlp_forward(1000, 2, 256, 256, t, 0.2, 256, ctypes.c_void_p(4100), small,
+                                None) == gftorf.ERR_WORKSPACE
+    t[1] = float("nan")
+    assert L.gftorf_mlp_forward(1000, 2, 256, 256, t, 0.2, 256, ws, small,
+                                None) == gftorf.ERR_ARG
+    assert L.gftorf_mlp_backward(10, 2, 256, 256, t, 0.2, None, 256, 256, ws, small,
+                                 None) == gftorf.ERR_ARG
+    assert L.gftorf_mlp_export(1000, 2, 9, 0, 256, ws, small, None) == gftorf.ERR_ARG
+    assert L.gftorf_mlp_export(1000, 2, 1, 8, 256, ws, small, None) == gftorf.ERR_ARG

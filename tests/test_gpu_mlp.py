@@ -1,0 +1,184 @@
+"""GPU parity of the tensor-core deformation MLP (tcgen05 GEMMs) against the
+FP64 oracle with the same BF16 operand rounding (oracle/mlp.py).
+
+Layer by layer (tight): each kernel's output is compared with the oracle's
+layer applied to the kernel's own inputs (exported from the workspace).  The
+oracle sums exactly, the tensor cores in FP32, so an output that lands next to
+a BF16 rounding boundary may round the other way: such elements must be rare
+(< 1e-3 of a layer) and one BF16 ulp apart, or within the FP32 sum's error
+bound (K 2^-24 times the sum of the terms' magnitudes) of zero at the ReLU;
+FP32 outputs (head, weight and encoding gradients)
+agree to 1e-4 relative.
+
+Whole network (loose, derived): a flipped activation shifts every sum of the
+next layer a little and so flips a few more; over 8 layers ~1 % of the
+activations end one ulp apart (measured), which moves the output by ~1e-3 and
+the deepest weight gradients by ~1e-2 relative -- the difference between two
+BF16 evaluations that differ only in summation order.  Bars: output 2e-3,
+gradients 2.5e-2 per layer (norm-wise).  The oracle encodes the same
+single-precision scaled positions (the top frequency multiplies their
+rounding by 2^9 pi)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as omlp
+from paper_2505_05356_gb300 import gftorf, mlp, scenes
+
+pytestmark = pytest.mark.gpu
+
+ULP = 2.0 ** -7  # one BF16 ulp relative to the value, upper bound
+
+
+def _case(N, B, seed, head_std=0.05):
+    rng = np.random.default_rng(seed)
+    theta = scenes.init_mlp_params(seed, head_std=head_std)
+    means = rng.uniform(-2.5, 5.0, (N, 3)).astype(np.float32)
+    times = list(np.linspace(0.0, 1.0, B).astype(np.float32))
+    return theta, means, times
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _bf16_close(got, ref, mag, frac=1e-3):
+    """Elementwise equal except rare one-ulp rounding flips, and values
+    within the FP32 sum's error bound of zero at the ReLU: a sum of K = 256
+    products carries at most K 2^-24 sum|terms| <= 2e-5 mag (mag: the sum of
+    the terms' magnitudes, per element)."""
+    diff = got != ref
+    if not diff.any():
+        return True, (0.0,)
+    big = np.maximum(np.abs(got), np.abs(ref))[diff]
+    d = np.abs(got - ref)[diff]
+    ok = (big <= 2e-5 * mag[diff]) | (d <= ULP * big)
+    worst = (float(diff.mean()), int((~ok).sum()), float(d[~ok].max()) if (~ok).any() else 0.0)
+    return bool(np.all(ok) and diff.mean() <= frac), worst
+
+
+def _run(N, B, seed):
+    theta, means, times = _case(N, B, seed)
+    inv = np.float32(1.0 / mlp.unambiguous_range(30e6))
+    net = mlp.DeformationMLP(N, B, float(inv))
+    th = torch.as_tensor(theta, device="cuda")
+    mu = torch.as_tensor(means, device="cuda")
+    delta = net.forward(th, mu, times)
+    dd = np.random.default_rng(seed + 1).standard_normal((B, N, 3)).astype(np.float32)
+    d_theta, d_means = net.backward(th, mu, times, torch.as_tensor(dd, device="cuda"))
+    torch.cuda.synchronize()
+    net.check()
+    return theta, means, times, inv, net, delta, dd, d_theta, d_means
+
+
+@pytest.mark.parametrize("N,B", [(300, 2), (3000, 3), (77, 1)])
+def test_mlp_layer_by_layer(N, B):
+    theta, means, times, inv, net, delta, dd, d_theta, d_means = _run(N, B, N + B)
+    layers = omlp.unpack(theta.astype(np.float64))
+    r = omlp.to_bf16
+    # encoding (single-precision scaled positions; sin(pi k) exactly 0 on the GPU)
+    enc_g = net.export("enc").double().cpu().numpy()
+    enc_o = r(omlp.encode(means, np.asarray(times, np.float64), inv, single=True))
+    assert np.abs(enc_g - enc_o).max() <= 1e-6
+    H = [net.export("H", l).double().cpu().numpy() for l in range(8)]
+    x = enc_g
+    for l in range(8):
+        W, b = layers[l]
+        ref = r(np.maximum(x @ r(W).T + b, 0.0))
+        ok, frac = _bf16_close(H[l], ref, np.abs(x) @ np.abs(r(W)).T + np.abs(b))
+        assert ok, (l, frac)
+        x = H[l]
+    Wh, bh = layers[8]
+    ref = x @ r(Wh).T + bh
+    assert _rel(delta.double().cpu().numpy().reshape(-1, 3), ref) < 1e-5
+    # backward, each GEMM from the kernels' own operands
+    dZ = [net.export("dZ", l).double().cpu().numpy() for l in range(8)]
+    dzh = r(dd.reshape(-1, 3).astype(np.float64))
+    ok, frac = _bf16_close(dZ[7], r((dzh @ r(Wh)) * (H[7] > 0)), np.abs(dzh) @ np.abs(r(Wh)))
+    assert ok, ("dZ7", frac)
+    gt = omlp.unpack(d_theta.double().cpu().numpy())
+    assert _rel(gt[8][0], dzh.T @ H[7]) < 1e-4 and _rel(gt[8][1], dzh.sum(0)) < 1e-4
+    for l in range(7, -1, -1):
+        inp = H[l - 1] if l > 0 else enc_g
+        assert _rel(gt[l][0], dZ[l].T @ inp) < 1e-4, ("dW", l)
+        assert _rel(gt[l][1], dZ[l].sum(0)) < 1e-4, ("db", l)
+        dh = dZ[l] @ r(layers[l][0])
+        if l > 0:
+            ok, frac = _bf16_close(dZ[l - 1], r(dh * (H[l - 1] > 0)),
+                                   np.abs(dZ[l]) @ np.abs(r(layers[l][0])))
+            assert ok, ("dZ", l - 1, frac)
+        else:
+            denc = net.export("d_enc").double().cpu().numpy()
+            assert _rel(denc, dh) < 1e-4
+            dm = omlp.encode_backward(denc, means, times, inv, single=True)
+            assert _rel(d_means.double().cpu().numpy(), dm) < 1e-4
+
+
+@pytest.mark.parametrize("N,B", [(300, 2), (3000, 3)])
+def test_mlp_whole_network_matches_oracle(N, B):
+    theta, means, times, inv, net, delta, dd, d_theta, d_means = _run(N, B, 100 + N)
+    enc = omlp.encode(means, np.asarray(times, np.float64), inv, single=True)
+    d_o, acts = omlp.forward(theta.astype(np.float64), enc, bf16=True)
+    g_o, denc = omlp.backward(theta.astype(np.float64), acts, dd.reshape(-1, 3), bf16=True)
+    assert _rel(delta.double().cpu().numpy().reshape(-1, 3), d_o) < 2e-3
+    for l, ((W, b), (Wo, bo)) in enumerate(zip(omlp.unpack(d_theta.double().cpu().numpy()),
+                                              omlp.unpack(g_o))):
+        assert _rel(W, Wo) < 2.5e-2 and _rel(b, bo) < 2.5e-2, l
+    dm = omlp.encode_backward(denc, means, times, inv, single=True)
+    assert _rel(d_means.double().cpu().numpy(), dm) < 2.5e-2
+
+
+def test_mlp_zero_gaussians_and_status():
+    net = mlp.DeformationMLP(0, 2, 0.2)
+    theta = torch.as_tensor(scenes.init_mlp_params(1), device="cuda")
+    mu = torch.zeros((0, 3), device="cuda")
+    delta = net.forward(theta, mu, [0.0, 1.0])
+    d_theta, d_means = net.backward(theta, mu, [0.0, 1.0], torch.zeros((2, 0, 3), device="cuda"))
+    torch.cuda.synchronize()
+    assert delta.shape == (2, 0, 3) and d_means.shape == (0, 3)
+    assert torch.all(d_theta == 0)
+    assert net.read_status() == gftorf.OK
+
+
+def test_mlp_drives_the_renderer_end_to_end():
+    """delta from the MLP as the renderer's displacement; the renderer's
+    dL/d(delta) back through the MLP; compared with the oracles chained the
+    same way."""
+    from oracle import oracle as ora
+    sc = scenes.make_scene("batch_300k", 21, n=1500, width=64, height=48, frames=2)
+    sc.delta = None
+    theta = scenes.init_mlp_params(3, head_std=0.02)
+    inv = np.float32(1.0 / mlp.unambiguous_range(30e6))
+    net = mlp.DeformationMLP(sc.n, sc.frames, float(inv))
+    th = torch.as_tensor(theta, device="cuda")
+    p = gftorf.params_from_scene(sc)
+    times = [float(t) for t in sc.times]
+    p["delta"] = net.forward(th, p["means"], times)
+    r = gftorf.Renderer(sc.n, sc.frames, sc.width, sc.height, 1, 4)
+    fr, se, co = (gftorf.frames_from_scene(sc), gftorf.sensor_from_scene(sc),
+                  gftorf.consts_from_scene(sc))
+    bg = torch.as_tensor(sc.bg, device="cuda")
+    r.fit_capacity(p, fr, se, co, bg)
+    r.preprocess(p, fr, se, co)
+    out = r.render_fwd(bg)
+    # the oracle renders with the GPU's delta (its own MLP is checked above)
+    sc.delta = p["delta"].double().cpu().numpy()
+    q_o, _, amb, _ = ora.render(sc, ora.EPS_F32)
+    keep = (amb & ora.AMB_VALUE) == 0
+    err = np.abs(out.double().cpu().numpy() - q_o).transpose(1, 0, 2, 3)[:, keep]
+    assert err.max() <= 1e-5 * np.abs(q_o).max()
+    dout = scenes.random_dout(sc, 5)
+    dout[np.broadcast_to((amb != 0)[:, None], dout.shape)] = 0.0
+    g = r.render_bwd(p, bg, torch.as_tensor(dout, device="cuda"))
+    d_theta, d_means = net.backward(th, p["means"], times, g["delta"])
+    torch.cuda.synchronize()
+    go = ora.backward(sc, dout.astype(np.float64))
+    assert _rel(g["delta"].double().cpu().numpy(), go["delta"]) < 1e-3
+    # the MLP backward from the oracle's dL/d(delta) through the oracle MLP
+    enc = omlp.encode(sc.means, np.asarray(times), inv, single=True)
+    _, acts = omlp.forward(theta.astype(np.float64), enc, bf16=True)
+    g_th, denc = omlp.backward(theta.astype(np.float64), acts, go["delta"].reshape(-1, 3),
+                               bf16=True)
+    assert _rel(d_theta.double().cpu().numpy(), g_th) < 2.5e-2
+    dm_o = omlp.encode_backward(denc, sc.means, times, inv, single=True) + go["means"]
+    assert _rel(d_means.double().cpu().numpy() + g["means"].double().cpu().numpy(), dm_o) < 2.5e-2
