@@ -74,12 +74,23 @@ def to_bf16(x):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def encode(means, times, inv_scale):
-    """Encoded inputs (B * N, 128), row b N + g."""
+def _scaled(means, inv_scale, single):
+    if single:
+        # the scaled positions as a single-precision implementation forms them
+        # (one rounded product): the 2^9 pi of the top frequency turns their
+        # rounding into phase differences far above a BF16 ulp, so the check
+        # of such an implementation encodes the same single-precision inputs
+        return (np.asarray(means, np.float32) * np.float32(inv_scale)).astype(np.float64)
+    return np.asarray(means, np.float64) * inv_scale
+
+
+def encode(means, times, inv_scale, single=False):
+    """Encoded inputs (B * N, 128), row b N + g; single=True encodes the
+    single-precision scaled positions."""
     means = np.asarray(means, np.float64)
     times = np.asarray(times, np.float64)
     N, B = means.shape[0], times.shape[0]
-    x = means * inv_scale
+    x = _scaled(means, inv_scale, single)
     cols = [x]
     for l in range(N_FREQ):
         cols.append(np.sin(2.0 ** l * math.pi * x))
@@ -98,11 +109,11 @@ def encode(means, times, inv_scale):
     return np.concatenate(rows, 0)
 
 
-def encode_backward(d_enc, means, times, inv_scale):
+def encode_backward(d_enc, means, times, inv_scale, single=False):
     """dL/d(means) (N, 3), summed over the frames, from dL/d(encoded input)."""
     means = np.asarray(means, np.float64)
     N, B = means.shape[0], len(times)
-    x = means * inv_scale
+    x = _scaled(means, inv_scale, single)
     g = np.zeros((N, 3))
     for b in range(B):
         d = np.asarray(d_enc[b * N:(b + 1) * N], np.float64)

@@ -5,7 +5,8 @@
 //
 // Every matrix product is one BF16 GEMM kernel, D[M x N] = A[M x K] B[N x K]^T
 // with FP32 accumulation: operands K-major in global memory, brought into
-// shared memory by TMA (128-byte swizzle, a 4-stage mbarrier pipeline), one
+// shared memory by TMA (128-byte swizzle, a 2-stage mbarrier pipeline, two CTAs
+// per SM so that one's epilogue overlaps the other's loads and MMAs), one
 // elected thread issuing tcgen05.mma into a TMEM accumulator, four epilogue
 // warps draining TMEM with tcgen05.ld and applying the layer's epilogue:
 //   forward hidden layer   H = relu(D + b) -> H (row-major) and H^T
@@ -38,7 +39,7 @@ constexpr int kIn = GFTORF_MLP_INPUT;   // 128 (84 used)
 constexpr int kFreq = 10;
 constexpr int kHeadRows = 32;           // head padded to the MMA's N = 32
 constexpr int kExt = 16;                // ones row + padding after a transposed block
-constexpr int BM = 128, BK = 64, kStages = 4;
+constexpr int BM = 128, BK = 64, kStages = 2;  // 2 stages: two CTAs (and their epilogues) overlap per SM
 
 enum Epi { EPI_HIDDEN = 0, EPI_HEAD = 1, EPI_MASK = 2, EPI_F32 = 3, EPI_ATOMIC = 4 };
 
@@ -231,7 +232,7 @@ constexpr int smem_bytes() {
 }
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(192, 2)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
   constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE = A_BYTES + B_BYTES;
