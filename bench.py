@@ -400,6 +400,9 @@ def run_ours(args):
     fitres = None
     if not args.skip_fit and rank == 0:
         fitres = fit_loop_bench(args, tile, ppt, mode)
+    mlpres = None
+    if not args.skip_mlp and rank == 0:
+        mlpres = mlp_bench(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -436,6 +439,7 @@ def run_ours(args):
             "e2e": e2e,
             "per_frame_plain": plain,
             "optimization_loop": fitres,
+            "deformation_mlp": mlpres,
             "cpu_baseline": cpu,
             "clocks": clk,
             "autotune": None if tuned is None else tuned["table"],
@@ -543,6 +547,62 @@ def fit_loop_bench(args, tile, ppt, mode):
             "speedup": round(pms / ms, 2), "kernels_per_iteration": int(kernels_per_it),
             "iterations_run": its, "loss_after_warmup": loss_start, "loss_last": loss_end,
             "plain_status": gftorf.STATUS.get(code1)}
+
+
+# ---------------------------------------------------------------------------
+# deformation MLP on the tensor cores: fwd + bwd of all Gaussians at one
+# timestep (one fitting iteration's MLP work) and at the batch's 16 timesteps
+# ---------------------------------------------------------------------------
+MLP_FLOPS_PER_ROW = 2.0 * (84 * 256 + 7 * 256 * 256 + 3 * 256)  # forward; backward 2x
+
+
+def mlp_bench(args, n=300_000):
+    import torch
+
+    from paper_2505_05356_gb300 import mlp, scenes
+
+    peaks, _ = _peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    theta = torch.as_tensor(scenes.init_mlp_params(0, head_std=0.05), device="cuda")
+    rng = np.random.default_rng(0)
+    mu = torch.as_tensor(rng.uniform(-2.0, 4.0, (n, 3)).astype(np.float32), device="cuda")
+    out = {}
+    for B in (1, 16):
+        net = mlp.DeformationMLP(n, B, 1.0 / mlp.unambiguous_range(30e6))
+        times = list(np.linspace(0.0, 1.0, B))
+        dd = torch.randn((B, n, 3), device="cuda")
+        for _ in range(2):
+            net.forward(theta, mu, times)
+            net.backward(theta, mu, times, dd)
+        torch.cuda.synchronize()
+        k = 5 if B == 1 else 2
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tf = tb = 0.0
+        for _ in range(k):
+            ev[0].record()
+            net.forward(theta, mu, times)
+            ev[1].record()
+            net.backward(theta, mu, times, dd)
+            ev[2].record()
+            torch.cuda.synchronize()
+            tf += ev[0].elapsed_time(ev[1]) / k
+            tb += ev[1].elapsed_time(ev[2]) / k
+        net.check()
+        rows = n * B
+        flops = 3.0 * MLP_FLOPS_PER_ROW * rows
+        tfl = flops / ((tf + tb) / 1e3) / 1e12
+        out["rows_%d" % rows] = {
+            "frames": B, "fwd_ms": round(tf, 3), "bwd_ms": round(tb, 3),
+            "tflops": round(tfl, 1),
+            "roofline": {"bound": "tensor", "achieved": round(tfl, 1), "peak": peak,
+                         "unit": "TFLOP/s", "frac": round(tfl / peak, 4),
+                         "peak_source": "measured bf16 (burst)"}}
+        del net
+        torch.cuda.empty_cache()
+    out["network"] = ("positional encoding (10 freq) 84 -> 8 x 256 ReLU -> 3, BF16 tcgen05 "
+                      "GEMMs with FP32 accumulation; algorithmic FLOPs 3 x %.0f per row "
+                      "(forward + weight and input gradients)" % MLP_FLOPS_PER_ROW)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -669,6 +729,8 @@ def main():
     ap.add_argument("--skip-fit", action="store_true",
                     help="skip the optimisation-loop measurement (iterations/s)")
     ap.add_argument("--fit-iters", type=int, default=20)
+    ap.add_argument("--skip-mlp", action="store_true",
+                    help="skip the deformation-MLP measurement (tensor cores)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--frames", type=int, default=0, help="override frames per batch")
     ap.add_argument("--n", type=int, default=0, help="override the Gaussian count")
