@@ -655,11 +655,16 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
 
 
 def _calibrate(sc, seconds):
-    """Pixels per sample so that one oracle sample takes about `seconds`."""
-    _, spent, det = oracle_sample(sc, 64)
-    per_px = max(det["fwd_pixels_s"] + det["bwd_pixels_s"], 1e-4) / 64
-    fixed = det["project_s"] + det["chain_s"]
-    return int(min(sc.width * sc.height, max(64, (seconds - fixed) / per_px)))
+    """Pixels per sample so that one oracle sample takes about `seconds`: a
+    64-pixel probe, then a probe at a quarter of the target, which sets the
+    per-pixel cost free of fixed overheads."""
+    n = 64
+    for frac in (0.25, 1.0):
+        _, spent, det = oracle_sample(sc, n)
+        per_px = max(det["fwd_pixels_s"] + det["bwd_pixels_s"], 1e-6) / n
+        fixed = det["project_s"] + det["chain_s"]
+        n = int(min(sc.width * sc.height, max(64, (frac * seconds - fixed) / per_px)))
+    return n
 
 
 def cpu_baseline(sc, seconds):
@@ -731,7 +736,7 @@ def main():
     ap.add_argument("--fit-iters", type=int, default=20)
     ap.add_argument("--skip-mlp", action="store_true",
                     help="skip the deformation-MLP measurement (tensor cores)")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--frames", type=int, default=0, help="override frames per batch")
     ap.add_argument("--n", type=int, default=0, help="override the Gaussian count")
     ap.add_argument("--extra-channels", default="",

@@ -11,14 +11,17 @@
 // warps draining TMEM with tcgen05.ld and applying the layer's epilogue:
 //   forward hidden layer   H = relu(D + b) -> H (row-major) and H^T
 //   forward head           delta = D + b (FP32)
-//   backward, hidden       dZ = D * (H_prev > 0) -> dZ and dZ^T
+//   backward, hidden       dZ = D * (H_prev > 0) -> dZ and dZ^T (the ReLU
+//                          masks kept as bits by the forward)
 //   backward, first layer  d(encoding) = D (FP32)
-//   weight gradient        dW_ext += D (split over rows, FP32 atomics)
+//   weight gradient        partial dW over a share of the rows (the 256
+//                          output rows as two M = 128 accumulators sharing
+//                          each B tile, so both operands are read once),
+//                          then a reduction over the shares
 // The transposed copies make the weight-gradient GEMM K-major as well
 // (dW = dZ^T H: both operands have the rows of the batch as their reduction
-// dimension), and each transposed activation carries an extra row of ones so
-// that the same GEMM yields the bias gradient in the column after the
-// weights.  Waits on mbarriers are bounded (about 2 s): a wait that runs out
+// dimension); the bias gradient (column sums of dZ) is reduced in the
+// epilogue that writes dZ.  Waits on mbarriers are bounded (about 2 s): a wait that runs out
 // records GFTORF_ERR_TIMEOUT in the status word and the CTA winds down.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -38,10 +41,11 @@ constexpr int kDepth = GFTORF_MLP_DEPTH;  // 8
 constexpr int kIn = GFTORF_MLP_INPUT;   // 128 (84 used)
 constexpr int kFreq = 10;
 constexpr int kHeadRows = 32;           // head padded to the MMA's N = 32
-constexpr int kExt = 16;                // ones row + padding after a transposed block
-constexpr int BM = 128, BK = 64, kStages = 2;  // 2 stages: two CTAs (and their epilogues) overlap per SM
+constexpr int kExt = 16;                // bias column (+ padding) after each dW block
+constexpr int BM = 128, BK = 64;
 
-enum Epi { EPI_HIDDEN = 0, EPI_HEAD = 1, EPI_MASK = 2, EPI_F32 = 3, EPI_ATOMIC = 4 };
+enum Epi { EPI_HIDDEN = 0, EPI_HEAD = 1, EPI_MASK = 2, EPI_F32 = 3, EPI_ATOMIC = 4, EPI_PARTIAL = 5 };
+constexpr int kMaxSplits = 192;  // row splits of a weight-gradient GEMM
 
 struct GemmArgs {
   int kb_total;      // k-blocks (of 64) of the reduction
@@ -51,11 +55,13 @@ struct GemmArgs {
   const float* bias;
   __nv_bfloat16* out_b;   // row-major bf16 output (ld = ldo)
   __nv_bfloat16* out_t;   // transposed bf16 output (ld = ldt), or null
-  int ldo, ldt, ext_rows; // ext_rows: the transposed block's row count before the ones row
+  int ldo, ldt;
   float* out_f;           // FP32 output (ld = ldf)
   int ldf;
-  const __nv_bfloat16* mask;  // H of the layer below (ld = ldm)
-  int ldm;
+  uint32_t* mbits;            // ReLU masks, one bit per unit, [rows][8] words:
+                              // written by EPI_HIDDEN, read by EPI_MASK
+  float* dbias;               // EPI_MASK: column sums of the stored dZ added at dbias[n ldb]
+  int ldb;
   int* status;
 };
 
@@ -185,30 +191,42 @@ __device__ __forceinline__ void store_row_bf16(__nv_bfloat16* dst, const float* 
 
 // 32 columns [n, n + 32) of output row m
 template <int EPI>
-__device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float* v) {
+__device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float* v, float* s_db) {
   if (EPI == EPI_HIDDEN || EPI == EPI_MASK) {
     if (EPI == EPI_HIDDEN) {
+      uint32_t bits = 0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + __ldg(p.bias + n + j), 0.f);
-    } else {
-      const uint4* mk = reinterpret_cast<const uint4*>(p.mask + (size_t)m * p.ldm + n);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 u = __ldg(mk + q);
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (!(__bfloat162float(h[j]) > 0.f)) v[8 * q + j] = 0.f;
+      for (int j = 0; j < 32; ++j) {
+        v[j] = fmaxf(v[j] + __ldg(p.bias + n + j), 0.f);
+        bits |= (__bfloat162float(__float2bfloat16_rn(v[j])) > 0.f ? 1u : 0u) << j;
       }
+      p.mbits[(size_t)m * (kW / 32) + n / 32] = bits;
+    } else {
+      const uint32_t bits = __ldg(p.mbits + (size_t)m * (kW / 32) + n / 32);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (!((bits >> j) & 1u)) v[j] = 0.f;
     }
     store_row_bf16(p.out_b + (size_t)m * p.ldo + n, v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) p.out_t[(size_t)(n + j) * p.ldt + m] = __float2bfloat16_rn(v[j]);
-    if (p.ext_rows > 0 && n == 0) {  // the ones row (bias gradient) and its padding
-      p.out_t[(size_t)p.ext_rows * p.ldt + m] = __float2bfloat16_rn(1.f);
+    if (EPI == EPI_MASK) {
+      // bias gradient: the warp's column sums of the stored (rounded) dZ by
+      // recursive halving (lane L ends with column n + L), one shared atomic
 #pragma unroll
-      for (int e = 1; e < kExt; ++e)
-        p.out_t[(size_t)(p.ext_rows + e) * p.ldt + m] = __float2bfloat16_rn(0.f);
+      for (int j = 0; j < 32; ++j) v[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+      const int lane = threadIdx.x & 31;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+          const float keep = up ? v[i + off] : v[i];
+          const float send = up ? v[i] : v[i + off];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      atomicAdd(s_db + n + lane, v[0]);
     }
   } else if (EPI == EPI_HEAD) {
     if (m < p.rows_valid)
@@ -217,6 +235,13 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float*
 #pragma unroll
     for (int j = 0; j < 32; ++j)
       if (n + j < p.cols_valid) p.out_f[(size_t)m * p.ldf + n + j] = v[j];
+  } else if (EPI == EPI_PARTIAL) {  // this CTA's partial sum over its rows of the batch
+    if (m < p.rows_valid && n < p.cols_valid) {
+      float4* d = reinterpret_cast<float4*>(
+          p.out_f + ((size_t)blockIdx.z * p.rows_valid + m) * p.ldf + n);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
   } else {  // EPI_ATOMIC
     if (m < p.rows_valid) {
 #pragma unroll
@@ -226,22 +251,32 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float*
   }
 }
 
-template <int BN>
-constexpr int smem_bytes() {
-  return kStages * (BM * BK * 2 + BN * BK * 2) + 1024 + 256;
-}
+// MT: M = 128 accumulators per CTA sharing each B tile (A tile of 128 MT rows).
+// MT = 1: 2 pipeline stages and two CTAs per SM, so that one's epilogue
+// overlaps the other's loads and MMAs; MT = 2 fills TMEM (512 columns): one
+// CTA per SM with 3 stages.
+template <int BN, int MT>
+struct GemmShape {
+  static constexpr int kStages = MT == 2 ? 3 : 2;
+  static constexpr int A_BYTES = MT * BM * BK * 2, B_BYTES = BN * BK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr uint32_t TCOLS = MT * BN < 32 ? 32 : MT * BN;
+  static constexpr int SMEM = kStages * STAGE + 1024 + 256 + 1024;  // + bias column sums
+};
 
-template <int BN, int EPI>
-__global__ void __launch_bounds__(192, 2)
+template <int BN, int EPI, int MT>
+__global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
-  constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE = A_BYTES + B_BYTES;
-  constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
+  using S = GemmShape<BN, MT>;
+  constexpr int kStages = S::kStages, A_BYTES = S::A_BYTES, STAGE = S::STAGE;
+  constexpr uint32_t TCOLS = S::TCOLS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * STAGE);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  float* s_db = reinterpret_cast<float*>(smem + kStages * STAGE + 256);  // [256]
   const uint32_t sbase = smem_u32(smem);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * kStages,
                  done = full0 + 16 * kStages;
@@ -257,6 +292,10 @@ __global__ void __launch_bounds__(192, 2)
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (EPI == EPI_MASK && threadIdx.x < 128) {
+    s_db[threadIdx.x] = 0.f;
+    s_db[threadIdx.x + 128] = 0.f;
   }
   if (warp == 0) tmem_alloc(smem_u32(slot), TCOLS);
   tc_fence_before();
@@ -274,7 +313,7 @@ __global__ void __launch_bounds__(192, 2)
         if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status)) break;
         mbar_expect_tx(full0 + 8 * s, STAGE);
         const uint32_t sa = sbase + s * STAGE;
-        tma_load_2d(sa, &tmA, full0 + 8 * s, (kb0 + i) * BK, m0);
+        tma_load_2d(sa, &tmA, full0 + 8 * s, (kb0 + i) * BK, m0 * MT);
         tma_load_2d(sa + A_BYTES, &tmB, full0 + 8 * s, (kb0 + i) * BK, n0);
         issued = i + 1;
       }
@@ -294,8 +333,10 @@ __global__ void __launch_bounds__(192, 2)
         const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k)
-          umma_bf16(tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
-                    (i > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+          for (int t = 0; t < MT; ++t)
+            umma_bf16(tmem + (uint32_t)(t * BN), sw128_desc(sa + t * BM * 128 + 32 * k),
+                      sw128_desc(sb + 32 * k), idesc, (i > 0 || k > 0) ? 1u : 0u);
         umma_commit(empty0 + 8 * s);
       }
       umma_commit(done);  // completes once every MMA issued above has
@@ -304,12 +345,22 @@ __global__ void __launch_bounds__(192, 2)
     // epilogue: warp w owns TMEM lanes / output rows 32 w .. 32 w + 31
     if (nkb > 0 && mbar_wait(done, 0, p.status)) {
       tc_fence_after();
-      const int m = m0 + warp * 32 + lane;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-        epilogue<EPI>(p, m, n0 + c * 32, v);
+      for (int t = 0; t < MT; ++t) {
+        const int m = (m0 * MT + t * BM) + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * BN + c * 32), v);
+          epilogue<EPI>(p, m, n0 + c * 32, v, s_db);
+        }
+      }
+    }
+    if (EPI == EPI_MASK) {  // the CTA's bias-gradient column sums, one global atomic each
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (nkb > 0) {
+        atomicAdd(p.dbias + (size_t)threadIdx.x * p.ldb, s_db[threadIdx.x]);
+        atomicAdd(p.dbias + (size_t)(threadIdx.x + 128) * p.ldb, s_db[threadIdx.x + 128]);
       }
     }
   }
@@ -399,17 +450,15 @@ __global__ void mlp_encode_kernel(const float* __restrict__ means, Times tm, int
   for (int q = 0; q < kIn / 32; ++q) store_row_bf16(enc + (size_t)m * kIn + 32 * q, e + 32 * q);
 #pragma unroll
   for (int c = 0; c < kIn; ++c) encT[(size_t)c * M_pad + m] = __float2bfloat16_rn(e[c]);
-  encT[(size_t)kIn * M_pad + m] = __float2bfloat16_rn(1.f);
-#pragma unroll
-  for (int c = 1; c < kExt; ++c) encT[(size_t)(kIn + c) * M_pad + m] = __float2bfloat16_rn(0.f);
 }
 
 // dL/d(delta) fp32 [M][3] -> bf16 [M_pad][32] and its transpose [32][M_pad]
-__global__ void mlp_head_grad_kernel(const float* __restrict__ dd, int M, int M_pad,
-                                     __nv_bfloat16* __restrict__ dz,
-                                     __nv_bfloat16* __restrict__ dzt) {
+// (and the head's bias gradient, the column sums of the rounded values)
+__global__ void __launch_bounds__(128)
+    mlp_head_grad_kernel(const float* __restrict__ dd, int M, int M_pad,
+                         __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt,
+                         float* __restrict__ dbias, int ldb) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M_pad) return;
   float v[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = 0.f;
@@ -417,9 +466,18 @@ __global__ void mlp_head_grad_kernel(const float* __restrict__ dd, int M, int M_
 #pragma unroll
     for (int j = 0; j < 3; ++j) v[j] = dd[(size_t)m * 3 + j];
   }
-  store_row_bf16(dz + (size_t)m * kHeadRows, v);
+  if (m < M_pad) {
+    store_row_bf16(dz + (size_t)m * kHeadRows, v);
 #pragma unroll
-  for (int j = 0; j < kHeadRows; ++j) dzt[(size_t)j * M_pad + m] = __float2bfloat16_rn(v[j]);
+    for (int j = 0; j < kHeadRows; ++j) dzt[(size_t)j * M_pad + m] = __float2bfloat16_rn(v[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float b = __bfloat162float(__float2bfloat16_rn(v[j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if ((threadIdx.x & 31) == 0 && b != 0.f) atomicAdd(dbias + (size_t)j * ldb, b);
+  }
 }
 
 // d(encoding) -> d(means), summed over the frames in order
@@ -479,6 +537,18 @@ __global__ void mlp_unpack_grads_kernel(const float* __restrict__ dwx, float* __
   }
 }
 
+// sum of the row-split partials [splits][256][K] -> dW block [256][ld]
+__global__ void mlp_reduce_dw_kernel(const float* __restrict__ part, int splits, int K,
+                                     float* __restrict__ dw, int ld) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kW * K) return;
+  const size_t stride = (size_t)kW * K;
+  float s = 0.f;
+  for (int z = 0; z < splits; ++z) s += part[(size_t)z * stride + e];
+  const int o = e / K, i = e - o * K;
+  dw[(size_t)o * ld + i] = s;
+}
+
 // ---- host side -----------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -494,7 +564,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// bf16 matrix [rows][cols] with row stride ld elements; boxes of 64 columns x box_rows
+// bf16 matrix [rows][cols] with row stride ld elements; boxes of 64 columns x
+// box_rows with the 128-byte swizzle
 bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
               uint32_t box_rows) {
   auto fn = encode_fn();
@@ -508,26 +579,26 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, 
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int MT = 1>
 bool gemm(const CUtensorMap& a, const CUtensorMap& b, const GemmArgs& args, int m_tiles,
           int n_tiles, int splits, cudaStream_t st) {
   static bool configured = false;
-  constexpr int smem = smem_bytes<BN>();
+  constexpr int smem = GemmShape<BN, MT>::SMEM;
   if (!configured) {
-    if (cudaFuncSetAttribute(umma_gemm_kernel<BN, EPI>,
+    if (cudaFuncSetAttribute(umma_gemm_kernel<BN, EPI, MT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return false;
     configured = true;
   }
-  umma_gemm_kernel<BN, EPI><<<dim3(m_tiles, n_tiles, splits), 192, smem, st>>>(a, b, args);
+  umma_gemm_kernel<BN, EPI, MT><<<dim3(m_tiles, n_tiles, splits), 192, smem, st>>>(a, b, args);
   count_launches(1);
   return true;
 }
 
 struct MlpLayout {
   int N, B, M, M_pad;
-  size_t off_status, off_wb, off_wt, off_enc, off_encT, off_h, off_ht, off_dz, off_dzt0,
-      off_dzt1, off_dzh, off_dzht, off_denc, off_dwx, total;
+  size_t off_status, off_wb, off_wt, off_enc, off_encT, off_h, off_ht, off_bits, off_dz,
+      off_dzt0, off_dzt1, off_dzh, off_dzht, off_denc, off_dwx, off_part, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -557,9 +628,10 @@ MlpLayout mlp_layout(int N, int B) {
   L.off_wb = take(wb_elems() * 2);
   L.off_wt = take(wb_elems() * 2);
   L.off_enc = take(Mp * kIn * 2);
-  L.off_encT = take((size_t)(kIn + kExt) * Mp * 2);
+  L.off_encT = take((size_t)kIn * Mp * 2);
   L.off_h = take((size_t)kDepth * Mp * kW * 2);
-  L.off_ht = take((size_t)kDepth * (kW + kExt) * Mp * 2);
+  L.off_ht = take((size_t)kDepth * kW * Mp * 2);
+  L.off_bits = take((size_t)kDepth * Mp * (kW / 32) * 4);
   L.off_dz = take((size_t)kDepth * Mp * kW * 2);  // dZ of every layer (kept for export)
   L.off_dzt0 = take((size_t)kW * Mp * 2);
   L.off_dzt1 = take((size_t)kW * Mp * 2);
@@ -567,6 +639,7 @@ MlpLayout mlp_layout(int N, int B) {
   L.off_dzht = take((size_t)kHeadRows * Mp * 2);
   L.off_denc = take(Mp * kIn * 4);
   L.off_dwx = take(dwx_floats() * 4);
+  L.off_part = take((size_t)kMaxSplits * kW * kW * 4);
   L.total = o;
   return L;
 }
@@ -657,7 +730,8 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
     a.rows_valid = Mp, a.cols_valid = kW;
     a.bias = theta + bias_off(l);
     a.out_b = H + (size_t)l * Mp * kW, a.ldo = kW;
-    a.out_t = HT + (size_t)l * (kW + kExt) * Mp, a.ldt = Mp, a.ext_rows = kW;
+    a.out_t = HT + (size_t)l * kW * Mp, a.ldt = Mp;
+    a.mbits = ptr<uint32_t>(ws, L.off_bits) + (size_t)l * Mp * (kW / 32);
     a.status = status;
     if (!gemm<256, EPI_HIDDEN>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
@@ -705,8 +779,8 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
   }
   auto* wt = ptr<__nv_bfloat16>(ws, L.off_wt);
   auto* encT = ptr<__nv_bfloat16>(ws, L.off_encT);
-  auto* H = ptr<__nv_bfloat16>(ws, L.off_h);
   auto* HT = ptr<__nv_bfloat16>(ws, L.off_ht);
+  auto* bits = ptr<uint32_t>(ws, L.off_bits);
   auto* dzh = ptr<__nv_bfloat16>(ws, L.off_dzh);
   auto* dzht = ptr<__nv_bfloat16>(ws, L.off_dzht);
   auto dz = [&](int l) { return ptr<__nv_bfloat16>(ws, L.off_dz) + (size_t)l * Mp * kW; };
@@ -715,24 +789,36 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
   float* denc = ptr<float>(ws, L.off_denc);
   const int mt = Mp / BM;
   const int kb_rows = Mp / BK;      // k-blocks of a reduction over the batch rows
-  const int per_split = 64;         // 4096 rows per CTA in the weight-gradient GEMMs
-  const int splits = (kb_rows + per_split - 1) / per_split;
+  // weight-gradient GEMMs: one CTA per SM (TMEM-bound), the rows split evenly
+  int sms = 148;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int per_split = max(8, (kb_rows + min(sms, kMaxSplits) - 1) / min(sms, kMaxSplits));
+  const int splits = (kb_rows + per_split - 1) / per_split;  // <= kMaxSplits
+  float* part = ptr<float>(ws, L.off_part);
 
-  mlp_head_grad_kernel<<<(Mp + 127) / 128, 128, 0, st>>>(d_delta, L.M, Mp, dzh, dzht);
+  // bias gradient of a layer: column K of its dW block
+  auto dbias_of = [&](int l) { return dwx + dwx_off(l) + (l == 0 ? kIn : kW); };
+  auto ldb_of = [&](int l) { return (l == 0 ? kIn : kW) + kExt; };
+  mlp_head_grad_kernel<<<(Mp + 127) / 128, 128, 0, st>>>(d_delta, L.M, Mp, dzh, dzht,
+                                                         dbias_of(kDepth), kW + kExt);
   count_launches(1);
-  // head: dW_head += dZh^T H_7 (bias in the ones column)
+  // head: dW_head += dZh^T H_7
   {
     CUtensorMap ma, mb;
     if (!make_map(&ma, dzht, kHeadRows, Mp, Mp, BM) ||
-        !make_map(&mb, HT + (size_t)(kDepth - 1) * (kW + kExt) * Mp, kW + kExt, Mp, Mp, 256))
+        !make_map(&mb, HT + (size_t)(kDepth - 1) * kW * Mp, kW, Mp, Mp, 256))
       return GFTORF_ERR_CUDA;
     GemmArgs a;
     memset(&a, 0, sizeof(a));
     a.kb_total = kb_rows, a.kb_per_split = per_split;
-    a.rows_valid = 3, a.cols_valid = kW + 1;
+    a.rows_valid = 3, a.cols_valid = kW;
     a.out_f = dwx + dwx_off(kDepth), a.ldf = kW + kExt;
     a.status = status;
-    if (!gemm<256, EPI_ATOMIC>(ma, mb, a, 1, 2, splits, st)) return GFTORF_ERR_CUDA;
+    if (!gemm<256, EPI_ATOMIC>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
   }
   // dH_7 = dZh W_head, dZ_7 = dH_7 * (H_7 > 0)
   int cur = 0;
@@ -746,27 +832,29 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     a.kb_total = 1, a.kb_per_split = 1;
     a.rows_valid = Mp, a.cols_valid = kW;
     a.out_b = dz(kDepth - 1), a.ldo = kW, a.out_t = dzt[cur], a.ldt = Mp;
-    a.mask = H + (size_t)(kDepth - 1) * Mp * kW, a.ldm = kW;
+    a.mbits = bits + (size_t)(kDepth - 1) * Mp * (kW / 32);
+    a.dbias = dbias_of(kDepth - 1), a.ldb = ldb_of(kDepth - 1);
     a.status = status;
     if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
   for (int l = kDepth - 1; l >= 0; --l) {
     const int K = l == 0 ? kIn : kW;
-    // dW_l += dZ_l^T H_{l-1} (or the encoding)
+    // dW_l += dZ_l^T H_{l-1} (or the encoding): all 256 output rows per CTA
     {
-      const __nv_bfloat16* bt = l == 0 ? encT : HT + (size_t)(l - 1) * (kW + kExt) * Mp;
+      const __nv_bfloat16* bt = l == 0 ? encT : HT + (size_t)(l - 1) * kW * Mp;
       CUtensorMap ma, mb;
-      if (!make_map(&ma, dzt[cur], kW, Mp, Mp, BM) ||
-          !make_map(&mb, bt, K + kExt, Mp, Mp, 256))
+      if (!make_map(&ma, dzt[cur], kW, Mp, Mp, 2 * BM) || !make_map(&mb, bt, K, Mp, Mp, 256))
         return GFTORF_ERR_CUDA;
       GemmArgs a;
       memset(&a, 0, sizeof(a));
       a.kb_total = kb_rows, a.kb_per_split = per_split;
-      a.rows_valid = kW, a.cols_valid = K + 1;
-      a.out_f = dwx + dwx_off(l), a.ldf = K + kExt;
+      a.rows_valid = kW, a.cols_valid = K;
+      a.out_f = part, a.ldf = K;
       a.status = status;
-      if (!gemm<256, EPI_ATOMIC>(ma, mb, a, kW / BM, (K + kExt + 255) / 256, splits, st))
-        return GFTORF_ERR_CUDA;
+      if (!gemm<256, EPI_PARTIAL, 2>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
+      mlp_reduce_dw_kernel<<<(kW * K + 255) / 256, 256, 0, st>>>(part, splits, K,
+                                                                 dwx + dwx_off(l), K + kExt);
+      count_launches(1);
     }
     // dH_{l-1} = dZ_l W_l  (l = 0: the encoding's gradient, FP32)
     {
@@ -783,7 +871,8 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
         if (!gemm<256, EPI_F32>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
       } else {
         a.out_b = dz(l - 1), a.ldo = kW, a.out_t = dzt[cur ^ 1], a.ldt = Mp;
-        a.mask = H + (size_t)(l - 1) * Mp * kW, a.ldm = kW;
+        a.mbits = bits + (size_t)(l - 1) * Mp * (kW / 32);
+        a.dbias = dbias_of(l - 1), a.ldb = ldb_of(l - 1);
         if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
         cur ^= 1;
       }
