@@ -402,7 +402,7 @@ def run_ours(args):
         fitres = fit_loop_bench(args, tile, ppt, mode)
     mlpres = None
     if not args.skip_mlp and rank == 0:
-        mlpres = mlp_bench(args)
+        mlpres = mlp_bench(args, frames=tuple(int(v) for v in args.mlp_frames.split(",") if v))
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -556,7 +556,7 @@ def fit_loop_bench(args, tile, ppt, mode):
 MLP_FLOPS_PER_ROW = 2.0 * (84 * 256 + 7 * 256 * 256 + 3 * 256)  # forward; backward 2x
 
 
-def mlp_bench(args, n=300_000):
+def mlp_bench(args, n=300_000, frames=(1, 16)):
     import torch
 
     from paper_2505_05356_gb300 import mlp, scenes
@@ -567,7 +567,7 @@ def mlp_bench(args, n=300_000):
     rng = np.random.default_rng(0)
     mu = torch.as_tensor(rng.uniform(-2.0, 4.0, (n, 3)).astype(np.float32), device="cuda")
     out = {}
-    for B in (1, 16):
+    for B in frames:
         net = mlp.DeformationMLP(n, B, 1.0 / mlp.unambiguous_range(30e6))
         times = list(np.linspace(0.0, 1.0, B))
         dd = torch.randn((B, n, 3), device="cuda")
@@ -575,7 +575,7 @@ def mlp_bench(args, n=300_000):
             net.forward(theta, mu, times)
             net.backward(theta, mu, times, dd)
         torch.cuda.synchronize()
-        k = 5 if B == 1 else 2
+        k = args.mlp_iters if args.mlp_iters else (5 if B == 1 else 2)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         tf = tb = 0.0
         for _ in range(k):
@@ -736,6 +736,12 @@ def main():
     ap.add_argument("--fit-iters", type=int, default=20)
     ap.add_argument("--skip-mlp", action="store_true",
                     help="skip the deformation-MLP measurement (tensor cores)")
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="run only the deformation-MLP measurement (profiling)")
+    ap.add_argument("--mlp-frames", default="1,16",
+                    help="timesteps of 300k Gaussians per MLP measurement, comma list")
+    ap.add_argument("--mlp-iters", type=int, default=0,
+                    help="timed MLP forward+backward passes (0: 5 at one frame, else 2)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--frames", type=int, default=0, help="override frames per batch")
     ap.add_argument("--n", type=int, default=0, help="override the Gaussian count")
@@ -748,7 +754,12 @@ def main():
                     help="view-dependent reflectivity from SH of this degree (0-3); "
                          "default: scalar reflectivity")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mlp_only:
+        import torch
+        torch.cuda.set_device(0)
+        frames = tuple(int(v) for v in args.mlp_frames.split(",") if v)
+        print(json.dumps({"deformation_mlp": mlp_bench(args, frames=frames)}), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
