@@ -234,6 +234,7 @@ gftorf_status gftorf_preprocess(const gftorf_dims* dims,
                                 const gftorf_sensor* sensor,
                                 const gftorf_consts* consts, void* workspace,
                                 size_t workspace_bytes, void* stream) {
+  gftorf::TraceRange trace_("gftorf_preprocess");
   if (!dims_ok(dims) || !g || !frames || !sensor || !consts) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
   if (!params_ok(L, g)) return GFTORF_ERR_ARG;
@@ -304,6 +305,7 @@ gftorf_status gftorf_preprocess(const gftorf_dims* dims,
 
 gftorf_status gftorf_bin(const gftorf_dims* dims, void* workspace,
                          size_t workspace_bytes, void* stream) {
+  gftorf::TraceRange trace_("gftorf_bin");
   if (!dims_ok(dims)) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
   gftorf_status s = check_ws(L, workspace, workspace_bytes);
@@ -315,6 +317,7 @@ gftorf_status gftorf_bin(const gftorf_dims* dims, void* workspace,
 gftorf_status gftorf_composite_fwd(const gftorf_dims* dims, const void* bg,
                                    void* out, void* workspace,
                                    size_t workspace_bytes, void* stream) {
+  gftorf::TraceRange trace_("gftorf_composite_fwd");
   if (!dims_ok(dims) || !bg || !out) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
   gftorf_status s = check_ws(L, workspace, workspace_bytes);
@@ -332,6 +335,7 @@ gftorf_status gftorf_composite_fwd(const gftorf_dims* dims, const void* bg,
 gftorf_status gftorf_render_fwd(const gftorf_dims* dims, const void* bg,
                                 void* out, void* workspace,
                                 size_t workspace_bytes, void* stream) {
+  gftorf::TraceRange trace_("gftorf_render_fwd");
   if (!dims_ok(dims) || !bg || !out) return GFTORF_ERR_ARG;
   gftorf_status s = gftorf_bin(dims, workspace, workspace_bytes, stream);
   if (s != GFTORF_OK) return s;
@@ -342,6 +346,7 @@ gftorf_status gftorf_zero_grad_buffers(const gftorf_dims* dims,
                                        const gftorf_gradients* grads,
                                        void* workspace, size_t workspace_bytes,
                                        void* stream) {
+  gftorf::TraceRange trace_("gftorf_zero_grad_buffers");
   if (!dims_ok(dims) || !grads) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
   gftorf_status s = check_ws(L, workspace, workspace_bytes);
@@ -358,6 +363,7 @@ gftorf_status gftorf_composite_bwd(const gftorf_dims* dims, const void* bg,
                                    const gftorf_gradients* grads,
                                    void* workspace, size_t workspace_bytes,
                                    void* stream) {
+  gftorf::TraceRange trace_("gftorf_composite_bwd");
   if (!dims_ok(dims) || !bg || !dL_dout || !grads) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
   gftorf_status s = check_ws(L, workspace, workspace_bytes);
@@ -380,6 +386,7 @@ gftorf_status gftorf_preprocess_bwd(const gftorf_dims* dims,
                                     const gftorf_gradients* grads,
                                     void* workspace, size_t workspace_bytes,
                                     void* stream) {
+  gftorf::TraceRange trace_("gftorf_preprocess_bwd");
   if (!dims_ok(dims) || !g || !grads) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
   if (!params_ok(L, g)) return GFTORF_ERR_ARG;
@@ -399,6 +406,7 @@ gftorf_status gftorf_render_bwd(const gftorf_dims* dims,
                                 const void* dL_dout,
                                 const gftorf_gradients* grads, void* workspace,
                                 size_t workspace_bytes, void* stream) {
+  gftorf::TraceRange trace_("gftorf_render_bwd");
   if (!dims_ok(dims) || !g || !bg || !dL_dout || !grads) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
   if (!params_ok(L, g)) return GFTORF_ERR_ARG;
@@ -417,6 +425,7 @@ gftorf_status gftorf_sort_footprints(const gftorf_dims* dims, const float* u,
                                      uint32_t* values, uint32_t* ranges,
                                      int64_t* count, void* workspace,
                                      size_t workspace_bytes, void* stream) {
+  gftorf::TraceRange trace_("gftorf_sort_footprints");
   if (!dims_ok(dims)) return GFTORF_ERR_ARG;
   const Layout L = make_layout(dims);
   if (L.N > 0 && (!u || !v || !radius || !z)) return GFTORF_ERR_ARG;

@@ -8,7 +8,18 @@
 
 #include "../../include/gftorf.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace gftorf {
+
+// NVTX range over one C-ABI call (a no-op unless a profiler is attached):
+// the stages show up by name in timeline tools.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 constexpr int kMaxF = GFTORF_MAX_FREQ;
 constexpr int kMaxP = GFTORF_MAX_OFFSETS;

@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -62,6 +63,8 @@ struct GemmArgs {
                               // written by EPI_HIDDEN, read by EPI_MASK
   float* dbias;               // EPI_MASK: column sums of the stored dZ added at dbias[n ldb]
   int ldb;
+  int inject_no_loads;        // test hook: the producer issues nothing (waits run out)
+  unsigned long long wait_ns; // limit of one mbarrier wait
   int* status;
 };
 
@@ -92,13 +95,14 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 // Bounded wait for the phase with the given parity to complete.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status,
+                          unsigned long long limit_ns = 2000000000ull) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try(bar, parity)) return true;
-    if (global_ns() - t0 > 2000000000ull) {
+    if (global_ns() - t0 > limit_ns) {
       atomicExch(status, (int)GFTORF_ERR_TIMEOUT);
       return false;
     }
@@ -305,12 +309,12 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
 
   if (warp == 4) {
     // TMA producer
-    if (lane == 0 && nkb > 0) {
+    if (lane == 0 && nkb > 0 && !p.inject_no_loads) {
       int issued = 0;
       for (int i = 0; i < nkb; ++i) {
         const int s = i % kStages;
         const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status)) break;
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status, p.wait_ns)) break;
         mbar_expect_tx(full0 + 8 * s, STAGE);
         const uint32_t sa = sbase + s * STAGE;
         tma_load_2d(sa, &tmA, full0 + 8 * s, (kb0 + i) * BK, m0 * MT);
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
       }
       // every load issued has landed before the CTA may exit
       for (int i = issued - kStages < 0 ? 0 : issued - kStages; i < issued; ++i)
-        mbar_wait(full0 + 8 * (i % kStages), (uint32_t)(i / kStages) & 1u, p.status);
+        mbar_wait(full0 + 8 * (i % kStages), (uint32_t)(i / kStages) & 1u, p.status, p.wait_ns);
     }
   } else if (warp == 5) {
     // MMA issuer
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
       for (int i = 0; i < nkb; ++i) {
         const int s = i % kStages;
         const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-        if (!mbar_wait(full0 + 8 * s, ph, p.status)) break;
+        if (!mbar_wait(full0 + 8 * s, ph, p.status, p.wait_ns)) break;
         tc_fence_after();
         const uint32_t sa = sbase + s * STAGE, sb = sa + A_BYTES;
 #pragma unroll
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
     }
   } else {
     // epilogue: warp w owns TMEM lanes / output rows 32 w .. 32 w + 31
-    if (nkb > 0 && mbar_wait(done, 0, p.status)) {
+    if (nkb > 0 && mbar_wait(done, 0, p.status, p.wait_ns)) {
       tc_fence_after();
 #pragma unroll 1
       for (int t = 0; t < MT; ++t) {
@@ -648,6 +652,10 @@ bool mlp_args_ok(int N, int B) {
   return N >= 0 && B >= 1 && B <= kMaxFrames && (int64_t)N * B < (int64_t)1 << 30;
 }
 
+// fault-injection hook for tests (gftorf_mlp_debug_inject): 1 = the GEMMs'
+// load warps issue nothing, so the MMA and epilogue waits run out
+std::atomic<int> g_inject{0};
+
 template <typename T>
 T* ptr(void* ws, size_t off) {
   return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + off);
@@ -688,6 +696,7 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
                                             const float* times, float inv_scale, float* delta,
                                             void* workspace, size_t workspace_bytes,
                                             void* stream) {
+  gftorf::TraceRange trace_("gftorf_mlp_forward");
   if (!mlp_args_ok(n_gaussians, n_frames) || !theta || !times ||
       (n_gaussians > 0 && (!means || !delta)) || !(inv_scale > 0.f))
     return GFTORF_ERR_ARG;
@@ -733,6 +742,8 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
     a.out_t = HT + (size_t)l * kW * Mp, a.ldt = Mp;
     a.mbits = ptr<uint32_t>(ws, L.off_bits) + (size_t)l * Mp * (kW / 32);
     a.status = status;
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
     if (!gemm<256, EPI_HIDDEN>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
   {
@@ -747,6 +758,8 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
     a.bias = theta + head_bias_off();
     a.out_f = delta;
     a.status = status;
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
     if (!gemm<32, EPI_HEAD>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
@@ -758,6 +771,7 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
                                              const float* d_delta, float* d_theta,
                                              float* d_means, void* workspace,
                                              size_t workspace_bytes, void* stream) {
+  gftorf::TraceRange trace_("gftorf_mlp_backward");
   if (!mlp_args_ok(n_gaussians, n_frames) || !theta || !times || !d_theta ||
       (n_gaussians > 0 && (!means || !d_means || !d_delta)) || !(inv_scale > 0.f))
     return GFTORF_ERR_ARG;
@@ -818,6 +832,8 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     a.rows_valid = 3, a.cols_valid = kW;
     a.out_f = dwx + dwx_off(kDepth), a.ldf = kW + kExt;
     a.status = status;
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
     if (!gemm<256, EPI_ATOMIC>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
   }
   // dH_7 = dZh W_head, dZ_7 = dH_7 * (H_7 > 0)
@@ -835,6 +851,8 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     a.mbits = bits + (size_t)(kDepth - 1) * Mp * (kW / 32);
     a.dbias = dbias_of(kDepth - 1), a.ldb = ldb_of(kDepth - 1);
     a.status = status;
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
     if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
   for (int l = kDepth - 1; l >= 0; --l) {
@@ -851,6 +869,8 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
       a.rows_valid = kW, a.cols_valid = K;
       a.out_f = part, a.ldf = K;
       a.status = status;
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
       if (!gemm<256, EPI_PARTIAL, 2>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
       mlp_reduce_dw_kernel<<<(kW * K + 255) / 256, 256, 0, st>>>(part, splits, K,
                                                                  dwx + dwx_off(l), K + kExt);
@@ -866,6 +886,8 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
       a.kb_total = kW / BK, a.kb_per_split = kW / BK;
       a.rows_valid = Mp, a.cols_valid = K;
       a.status = status;
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
       if (l == 0) {
         a.out_f = denc, a.ldf = kIn;
         if (!gemm<256, EPI_F32>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
@@ -923,4 +945,8 @@ extern "C" gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames
       cudaMemcpyAsync(dst, static_cast<unsigned char*>(workspace) + off, bytes,
                       cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+}
+
+extern "C" void gftorf_mlp_debug_inject(int32_t mode) {
+  g_inject.store(mode == 1 ? 1 : 0, std::memory_order_relaxed);
 }

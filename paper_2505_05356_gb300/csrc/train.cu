@@ -143,6 +143,7 @@ using namespace gftorf;
 
 extern "C" gftorf_status gftorf_train_begin(gftorf_train_state* state, float* bg, int64_t n_bg,
                                             uint64_t seed, void* stream) {
+  gftorf::TraceRange trace_("gftorf_train_begin");
   if (!state || n_bg < 0 || n_bg > kBgMax) return GFTORF_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(state) & 7) != 0) return GFTORF_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -154,6 +155,7 @@ extern "C" gftorf_status gftorf_train_begin(gftorf_train_state* state, float* bg
 extern "C" gftorf_status gftorf_l2_loss(const gftorf_dims* dims, const float* out,
                                         const float* target, float* dL_dout,
                                         gftorf_train_state* state, void* stream) {
+  gftorf::TraceRange trace_("gftorf_l2_loss");
   if (!train_dims_ok(dims) || dims->dtype != GFTORF_F32 || !out || !target || !dL_dout ||
       !state)
     return GFTORF_ERR_ARG;
@@ -175,6 +177,7 @@ extern "C" gftorf_status gftorf_l2_loss(const gftorf_dims* dims, const float* ou
 extern "C" gftorf_status gftorf_adam_step(const gftorf_adam_group* groups, int n_groups,
                                           float beta1, float beta2, float eps,
                                           const gftorf_train_state* state, void* stream) {
+  gftorf::TraceRange trace_("gftorf_adam_step");
   if (!groups || n_groups < 0 || n_groups > GFTORF_MAX_ADAM_GROUPS || !state)
     return GFTORF_ERR_ARG;
   if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f))

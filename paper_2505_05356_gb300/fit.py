@@ -98,6 +98,30 @@ class FitLoop:
             else:
                 self.iteration()
 
+    # --- checkpoint / resume ---------------------------------------------------
+    def state_dict(self) -> Dict[str, object]:
+        """Everything a resumed fit needs (host copies): the parameters, Adam's
+        moments, the device iteration state (count and loss; the background
+        of an iteration is a function of the seed and the count), the seed,
+        learning rates and bounds.  torch.save-able."""
+        torch.cuda.synchronize()
+        host = lambda d: {k: v.detach().cpu().clone() for k, v in d.items() if v is not None}
+        return {"params": host(self.p), "m": host(self.opt.m), "v": host(self.opt.v),
+                "state": self.state.cpu().clone(), "seed": self.seed,
+                "lrs": dict(self.lrs), "bounds": dict(self.opt.bounds)}
+
+    def load_state_dict(self, sd: Dict[str, object]):
+        """Restore into this loop's existing device buffers (a captured graph
+        stays valid)."""
+        for name, dst in (("params", self.p), ("m", self.opt.m), ("v", self.opt.v)):
+            for k, t in sd[name].items():
+                dst[k].copy_(t.to(dst[k].device))
+        self.state.copy_(sd["state"].to(self.state.device))
+        self.seed = int(sd["seed"])
+        self.lrs.update(sd["lrs"])
+        self.opt.lrs.update(sd["lrs"])
+        self.opt.bounds.update(sd["bounds"])
+
     @property
     def step(self) -> int:
         return gftorf.train_step_count(self.state)

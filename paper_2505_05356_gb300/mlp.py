@@ -44,6 +44,8 @@ def _lib():
         L.gftorf_mlp_export.restype = ctypes.c_int
         L.gftorf_mlp_export.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32, vp, vp, sz, vp]
+        L.gftorf_mlp_debug_inject.restype = None
+        L.gftorf_mlp_debug_inject.argtypes = [ctypes.c_int32]
         L.gftorf_mlp_read_status.restype = ctypes.c_int
         L.gftorf_mlp_read_status.argtypes = [vp, sz, vp]
         L._mlp_typed = True
@@ -133,3 +135,10 @@ class DeformationMLP:
         code = self.read_status()
         if code != gftorf.OK:
             raise gftorf.GftorfError(code, "device status")
+
+
+def debug_inject(mode: int):
+    """Fault injection for failure-path tests: 1 = the GEMMs' load warps issue
+    nothing, so their bounded waits run out (GFTORF_ERR_TIMEOUT, no GPU
+    fault); 0 = normal."""
+    _lib().gftorf_mlp_debug_inject(int(mode))

@@ -182,3 +182,26 @@ def test_mlp_drives_the_renderer_end_to_end():
     assert _rel(d_theta.double().cpu().numpy(), g_th) < 2.5e-2
     dm_o = omlp.encode_backward(denc, sc.means, times, inv, single=True) + go["means"]
     assert _rel(d_means.double().cpu().numpy() + g["means"].double().cpu().numpy(), dm_o) < 2.5e-2
+
+
+def test_bounded_waits_report_timeout_and_leave_the_context_usable():
+    """With the load warps told to issue nothing, every GEMM's waits run out
+    (50 ms each under injection): the status word reports the timeout, the
+    kernels return, and the next call on the same context is correct."""
+    N, B = 100, 1
+    theta, means, times = _case(N, B, 41)
+    inv = np.float32(0.2)
+    net = mlp.DeformationMLP(N, B, float(inv))
+    th = torch.as_tensor(theta, device="cuda")
+    mu = torch.as_tensor(means, device="cuda")
+    mlp.debug_inject(1)
+    try:
+        net.forward(th, mu, times)
+        assert net.read_status() == gftorf.ERR_TIMEOUT
+    finally:
+        mlp.debug_inject(0)
+    delta = net.forward(th, mu, times)
+    assert net.read_status() == gftorf.OK
+    enc = omlp.encode(means, np.asarray(times, np.float64), inv, single=True)
+    d_o, _ = omlp.forward(theta.astype(np.float64), enc, bf16=True)
+    assert _rel(delta.double().cpu().numpy().reshape(-1, 3), d_o) < 2e-3

@@ -169,3 +169,34 @@ def test_fit_reduces_the_loss():
     loop.run(30)
     loop.check()
     assert loop.loss() < 0.98 * first
+
+
+def test_checkpoint_resume_continues_the_same_fit(tmp_path):
+    """A fit checkpointed after 3 iterations and resumed in a fresh loop (from
+    the file) draws the same next background and renders a bit-identical
+    forward in the next iteration."""
+    gt, init, target = _fit_setup(seed=9)
+
+    def make():
+        p = gftorf.params_from_scene(init)
+        return fit.FitLoop(p, gftorf.frames_from_scene(init), gftorf.sensor_from_scene(init),
+                           gftorf.consts_from_scene(init), torch.as_tensor(target, device="cuda"),
+                           seed=13, headroom=2.0)
+
+    a = make()
+    a.run(3)
+    path = tmp_path / "fit.pt"
+    torch.save(a.state_dict(), path)
+    a.run(1)
+    torch.cuda.synchronize()
+    b = make()
+    b.capture()  # resume into a captured loop: the graph's buffers are reused
+    b.load_state_dict(torch.load(path))
+    assert b.step == 3
+    b.run(1)
+    torch.cuda.synchronize()
+    assert b.step == a.step == 4
+    np.testing.assert_array_equal(b.bg.cpu().numpy(), a.bg.cpu().numpy())
+    np.testing.assert_array_equal(b.out.cpu().numpy(), a.out.cpu().numpy())
+    a.check()
+    b.check()
