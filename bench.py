@@ -604,12 +604,26 @@ def mlp_bench(args, n=300_000, frames=(1, 16)):
             tf += ev[0].elapsed_time(ev[1]) / k
             tb += ev[1].elapsed_time(ev[2]) / k
         net.check()
+        # inference forward (fused kernel, activations on chip)
+        net.infer(theta, mu, times)
+        torch.cuda.synchronize()
+        ti = 0.0
+        for _ in range(k):
+            ev[0].record()
+            net.infer(theta, mu, times)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ti += ev[0].elapsed_time(ev[1]) / k
+        net.check()
         rows = n * B
+        tfi = MLP_FLOPS_PER_ROW * rows / (ti / 1e3) / 1e12
         flops = 3.0 * MLP_FLOPS_PER_ROW * rows
         tfl = flops / ((tf + tb) / 1e3) / 1e12
         out["rows_%d" % rows] = {
             "frames": B, "fwd_ms": round(tf, 3), "bwd_ms": round(tb, 3),
             "tflops": round(tfl, 1),
+            "infer_fused": {"ms": round(ti, 3), "tflops": round(tfi, 1),
+                            "frac": round(tfi / peak, 4)},
             "roofline": {"bound": "tensor", "achieved": round(tfl, 1), "peak": peak,
                          "unit": "TFLOP/s", "frac": round(tfl / peak, 4),
                          "peak_source": "measured bf16 (burst)"}}

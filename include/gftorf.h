@@ -437,6 +437,17 @@ gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_frames, const f
                                   const float* d_delta, float* d_theta, float* d_means,
                                   void* workspace, size_t workspace_bytes, void* stream);
 
+/* Inference forward of the same network (rendering a fitted scene): all
+ * layers of a 128-row tile in one CTA, the activations kept in shared memory
+ * (bit-identical outputs to gftorf_mlp_forward, nothing kept for a
+ * backward).  Workspace: gftorf_mlp_infer_workspace_size() bytes (weights
+ * only), 256-byte aligned; same other arguments as gftorf_mlp_forward. */
+size_t gftorf_mlp_infer_workspace_size(void);
+gftorf_status gftorf_mlp_infer(int32_t n_gaussians, int32_t n_frames, const float* theta,
+                               const float* means, const float* times, float inv_scale,
+                               float* delta, void* workspace, size_t workspace_bytes,
+                               void* stream);
+
 /* Copy an intermediate of the last gftorf_mlp_forward / _backward on this
  * workspace into dst (device), rows m = b N + g, for inspection and tests:
  * what = 0: the encoded input (BF16 bits, [B N][GFTORF_MLP_INPUT]);

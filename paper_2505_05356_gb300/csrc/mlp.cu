@@ -381,6 +381,15 @@ struct Times {
   float t[kMaxFrames];
 };
 
+// offsets in the packed parameter vector, [W_0, b_0, W_1, b_1, ..., W_head, b_head]
+__host__ __device__ constexpr size_t bias_off_dev(int l) {
+  return l == 0 ? (size_t)kW * kIn
+                : (size_t)kW * kIn + kW + (size_t)(l - 1) * ((size_t)kW * kW + kW) + (size_t)kW * kW;
+}
+__host__ __device__ constexpr size_t head_bias_off_dev() {
+  return (size_t)kW * kIn + kW + (size_t)(kDepth - 1) * ((size_t)kW * kW + kW) + 3 * kW;
+}
+
 // fp32 packed parameters -> bf16 W and W^T of every layer (head padded to 32 rows)
 __global__ void mlp_prep_weights_kernel(const float* __restrict__ theta,
                                         __nv_bfloat16* __restrict__ wb,
@@ -422,16 +431,12 @@ __global__ void mlp_prep_weights_kernel(const float* __restrict__ theta,
   }
 }
 
-// positional encoding of row m = b N + g into enc[m][0..127] and encT[c][m]
-__global__ void mlp_encode_kernel(const float* __restrict__ means, Times tm, int N, int B,
-                                  float inv_scale, int M_pad, __nv_bfloat16* __restrict__ enc,
-                                  __nv_bfloat16* __restrict__ encT) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M_pad) return;
-  float e[kIn];
+// positional encoding of row m = b N + g (zeros for m >= M)
+__device__ __forceinline__ void encode_row(const float* __restrict__ means, const Times& tm, int N,
+                                           int M, float inv_scale, int m, float* e) {
 #pragma unroll
   for (int c = 0; c < kIn; ++c) e[c] = 0.f;
-  if (m < N * B) {
+  if (m < M) {
     const int b = m / N, g = m - b * N;
     float x[3];
 #pragma unroll
@@ -450,6 +455,16 @@ __global__ void mlp_encode_kernel(const float* __restrict__ means, Times tm, int
 #pragma unroll
     for (int l = 0; l < kFreq; ++l, f *= 2.f) sincospif(f * t, &e[64 + 2 * l], &e[65 + 2 * l]);
   }
+}
+
+// positional encoding of row m = b N + g into enc[m][0..127] and encT[c][m]
+__global__ void mlp_encode_kernel(const float* __restrict__ means, Times tm, int N, int B,
+                                  float inv_scale, int M_pad, __nv_bfloat16* __restrict__ enc,
+                                  __nv_bfloat16* __restrict__ encT) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M_pad) return;
+  float e[kIn];
+  encode_row(means, tm, N, N * B, inv_scale, m, e);
 #pragma unroll
   for (int q = 0; q < kIn / 32; ++q) store_row_bf16(enc + (size_t)m * kIn + 32 * q, e + 32 * q);
 #pragma unroll
@@ -551,6 +566,189 @@ __global__ void mlp_reduce_dw_kernel(const float* __restrict__ part, int splits,
   for (int z = 0; z < splits; ++z) s += part[(size_t)z * stride + e];
   const int o = e / K, i = e - o * K;
   dw[(size_t)o * ld + i] = s;
+}
+
+// ---- fused forward (inference): all layers of a 128-row tile in one CTA -------
+// The activations never leave shared memory: the epilogue warps write each
+// layer's output (bias, ReLU, BF16) straight into the 128 x 256 operand tile
+// of the next layer, in the swizzled K-major layout of the MMA descriptors,
+// while a TMA warp streams the layers' weights through a 3-stage ring.  The
+// arithmetic and its order are those of the layer-by-layer forward, so the
+// outputs agree bit for bit; nothing is kept for a backward.
+constexpr int kFusedStages = 3;
+constexpr int kActBytes = BM * kW * 2;     // 64 KB
+constexpr int kWStageBytes = kW * BK * 2;  // 32 KB (a 256-row k-block of W)
+constexpr int kFusedSmem = kActBytes + kFusedStages * kWStageBytes + 1024 + 256;
+
+struct FusedMaps {
+  CUtensorMap w[kDepth + 1];  // bf16 W of the hidden layers (256 rows), head (32 rows)
+};
+
+// byte offset of element (r, c) of the activation tile: 64-column blocks of
+// 16 KB, rows 128 bytes apart in 1024-byte 8-row atoms, 16-byte chunk j of
+// row r at chunk j ^ (r & 7) (the 128-byte swizzle)
+__device__ __forceinline__ uint32_t act_off(int r, int c) {
+  const int kb = c >> 6, cc = c & 63;
+  return (uint32_t)(kb * 16384 + (r >> 3) * 1024 + (r & 7) * 128 +
+                    ((((cc >> 3) ^ (r & 7)) << 4) | ((cc & 7) << 1)));
+}
+__device__ __forceinline__ void store_act32(uint8_t* act, int r, int c, const float* v) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint4 u;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * q + 2 * i], v[8 * q + 2 * i + 1]);
+      w[i] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    *reinterpret_cast<uint4*>(act + act_off(r, c + 8 * q)) = u;
+  }
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1)
+    mlp_fused_fwd_kernel(const __grid_constant__ FusedMaps maps, const float* __restrict__ theta,
+                         const float* __restrict__ means, Times tm, int N, int M, int n_tiles,
+                         float inv_scale, float* __restrict__ delta, int* status,
+                         unsigned long long wait_ns, int inject_no_loads) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem =
+      reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* act = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kActBytes + kFusedStages * kWStageBytes);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * kFusedStages + 2);
+  int* s_ok = reinterpret_cast<int*>(slot + 1);  // the epilogue's shared wait outcome
+  const uint32_t act_s = smem_u32(act), w_s = act_s + kActBytes;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * kFusedStages;
+  const uint32_t acc_ready = full0 + 16 * kFusedStages, act_ready = acc_ready + 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kFusedStages; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    mbar_init(acc_ready, 1);
+    mbar_init(act_ready, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(slot), (uint32_t)kW);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (warp == 4) {
+    // weights of every layer, k-block by k-block, for every tile of this CTA
+    if (lane == 0 && !inject_no_loads) {
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x)
+        for (int l = 0; ok && l <= kDepth; ++l) {
+          const int nkb = (l == 0 ? kIn : kW) / BK;
+          const uint32_t bytes = (uint32_t)(l == kDepth ? kHeadRows : kW) * BK * 2;
+          for (int kb = 0; kb < nkb; ++kb, ++it) {
+            const int s = it % kFusedStages;
+            if (!(ok = mbar_wait(empty0 + 8 * s, ((uint32_t)(it / kFusedStages) & 1u) ^ 1u,
+                                 status, wait_ns)))
+              break;
+            mbar_expect_tx(full0 + 8 * s, bytes);
+            tma_load_2d(w_s + s * kWStageBytes, &maps.w[l], full0 + 8 * s, kb * BK, 0);
+          }
+        }
+      // every load issued has landed before the CTA may exit
+      for (int i = it - kFusedStages < 0 ? 0 : it - kFusedStages; i < it; ++i)
+        mbar_wait(full0 + 8 * (i % kFusedStages), (uint32_t)(i / kFusedStages) & 1u, status,
+                  wait_ns);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      int it = 0;
+      uint32_t act_ph = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x)
+        for (int l = 0; ok && l <= kDepth; ++l) {
+          if (!(ok = mbar_wait(act_ready, act_ph, status, wait_ns))) break;
+          act_ph ^= 1u;
+          tc_fence_after();
+          const int nkb = (l == 0 ? kIn : kW) / BK;
+          const uint32_t idesc = l == kDepth ? idesc_bf16(BM, kHeadRows) : idesc_bf16(BM, kW);
+          for (int kb = 0; kb < nkb; ++kb, ++it) {
+            const int s = it % kFusedStages;
+            if (!(ok = mbar_wait(full0 + 8 * s, (uint32_t)(it / kFusedStages) & 1u, status,
+                                 wait_ns)))
+              break;
+            tc_fence_after();
+            const uint32_t sa = act_s + kb * 16384, sb = w_s + s * kWStageBytes;
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+              umma_bf16(tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
+                        (kb > 0 || k > 0) ? 1u : 0u);
+            umma_commit(empty0 + 8 * s);
+          }
+          umma_commit(acc_ready);
+        }
+    }
+  } else {
+    // epilogue warps: row r of every tile
+    const int r = warp * 32 + lane;
+    uint32_t acc_ph = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+      const int m = tile * BM + r;
+      {
+        float e[kIn];
+        encode_row(means, tm, N, M, inv_scale, m, e);
+#pragma unroll
+        for (int c = 0; c < kIn; c += 32) store_act32(act, r, c, e + c);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (threadIdx.x == 0) mbar_arrive(act_ready);
+      for (int l = 0; l <= kDepth; ++l) {
+        // one thread waits, the other epilogue threads follow the barrier, so
+        // that all 128 take the same branch (no split at the named barriers)
+        if (threadIdx.x == 0) *s_ok = mbar_wait(acc_ready, acc_ph, status, wait_ns) ? 1 : 0;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (!(ok = *s_ok != 0)) break;
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // all have read the flag
+        acc_ph ^= 1u;
+        tc_fence_after();
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        if (l < kDepth) {
+          const float* bias = theta + bias_off_dev(l);
+#pragma unroll 1
+          for (int c = 0; c < kW; c += 32) {
+            float v[32];
+            tmem_ld32(trow + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + __ldg(bias + c + j), 0.f);
+            store_act32(act, r, c, v);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          tc_fence_before();
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          if (threadIdx.x == 0) mbar_arrive(act_ready);
+        } else {
+          float v[32];
+          tmem_ld32(trow, v);
+          const float* bias = theta + head_bias_off_dev();
+          if (m < M)
+            for (int j = 0; j < 3; ++j) delta[(size_t)m * 3 + j] = v[j] + __ldg(bias + j);
+          tc_fence_before();
+          asm volatile("bar.sync 1, 128;" ::: "memory");  // TMEM drained before the next tile
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)kW);
+  }
 }
 
 // ---- host side -----------------------------------------------------------------
@@ -681,6 +879,10 @@ size_t dwx_off(int l) {  // floats
 }  // namespace gftorf
 
 using namespace gftorf;
+
+extern "C" size_t gftorf_mlp_infer_workspace_size(void) {
+  return 256 + align256(2 * wb_elems() * 2);  // status word, BF16 weights and transposes
+}
 
 extern "C" size_t gftorf_mlp_workspace_size(int32_t n_gaussians, int32_t n_frames) {
   if (!mlp_args_ok(n_gaussians, n_frames)) return 0;
@@ -949,4 +1151,53 @@ extern "C" gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames
 
 extern "C" void gftorf_mlp_debug_inject(int32_t mode) {
   g_inject.store(mode == 1 ? 1 : 0, std::memory_order_relaxed);
+}
+
+extern "C" gftorf_status gftorf_mlp_infer(int32_t n_gaussians, int32_t n_frames,
+                                          const float* theta, const float* means,
+                                          const float* times, float inv_scale, float* delta,
+                                          void* workspace, size_t workspace_bytes, void* stream) {
+  gftorf::TraceRange trace_("gftorf_mlp_infer");
+  if (!mlp_args_ok(n_gaussians, n_frames) || !theta || !times ||
+      (n_gaussians > 0 && (!means || !delta)) || !(inv_scale > 0.f))
+    return GFTORF_ERR_ARG;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 ||
+      workspace_bytes < gftorf_mlp_infer_workspace_size())
+    return GFTORF_ERR_WORKSPACE;
+  for (int b = 0; b < n_frames; ++b)
+    if (!std::isfinite(times[b])) return GFTORF_ERR_ARG;
+  if (!encode_fn()) return GFTORF_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* status = ptr<int>(workspace, 0);
+  cudaMemsetAsync(status, 0, 256, st);
+  const int M = n_gaussians * n_frames;
+  if (M == 0) return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+  auto* wb = ptr<__nv_bfloat16>(workspace, 256);
+  auto* wt = wb + wb_elems();
+  mlp_prep_weights_kernel<<<4 * 152, 256, 0, st>>>(theta, wb, wt);
+  FusedMaps maps;
+  for (int l = 0; l <= kDepth; ++l) {
+    const int K = l == 0 ? kIn : kW, rows = l == kDepth ? kHeadRows : kW;
+    if (!make_map(&maps.w[l], wb + wb_off(l), rows, K, K, rows)) return GFTORF_ERR_CUDA;
+  }
+  Times tm;
+  memset(&tm, 0, sizeof(tm));
+  for (int b = 0; b < n_frames; ++b) tm.t[b] = times[b];
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(mlp_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kFusedSmem) != cudaSuccess)
+      return GFTORF_ERR_CUDA;
+    configured = true;
+  }
+  int sms = 148, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tiles = (M + BM - 1) / BM;
+  const unsigned long long wait_ns = g_inject.load() ? 50000000ull : 2000000000ull;
+  mlp_fused_fwd_kernel<<<n_tiles < sms ? n_tiles : sms, 192, kFusedSmem, st>>>(
+      maps, theta, means, tm, n_gaussians, M, n_tiles, inv_scale, delta, status, wait_ns,
+      g_inject.load());
+  count_launches(2);
+  return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
 }

@@ -41,6 +41,12 @@ def _lib():
         L.gftorf_mlp_backward.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, vp,
                                           ctypes.POINTER(ctypes.c_float), ctypes.c_float, vp, vp,
                                           vp, vp, sz, vp]
+        L.gftorf_mlp_infer_workspace_size.restype = sz
+        L.gftorf_mlp_infer_workspace_size.argtypes = []
+        L.gftorf_mlp_infer.restype = ctypes.c_int
+        L.gftorf_mlp_infer.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, vp,
+                                       ctypes.POINTER(ctypes.c_float), ctypes.c_float, vp, vp,
+                                       sz, vp]
         L.gftorf_mlp_export.restype = ctypes.c_int
         L.gftorf_mlp_export.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32, vp, vp, sz, vp]
@@ -93,6 +99,21 @@ class DeformationMLP:
                                                   self.inv_scale, gftorf._ptr(delta),
                                                   self.ws_ptr, self.ws_bytes, gftorf._stream()),
                       "gftorf_mlp_forward")
+        return delta
+
+    def infer(self, theta: torch.Tensor, means: torch.Tensor, times: Sequence[float],
+              delta: torch.Tensor = None) -> torch.Tensor:
+        """Forward without keeping activations (one fused kernel; bit-identical
+        to forward())."""
+        self._check_f32(theta=theta, means=means)
+        if delta is None:
+            delta = torch.empty((self.B, self.N, 3), dtype=torch.float32, device=self.device)
+        self._keep_i = self._times(times)
+        gftorf._check(self.lib.gftorf_mlp_infer(self.N, self.B, gftorf._ptr(theta),
+                                                gftorf._ptr(means), self._keep_i, self.inv_scale,
+                                                gftorf._ptr(delta), self.ws_ptr, self.ws_bytes,
+                                                gftorf._stream()),
+                      "gftorf_mlp_infer")
         return delta
 
     def backward(self, theta, means, times, d_delta, d_theta=None,

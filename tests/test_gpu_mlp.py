@@ -205,3 +205,36 @@ def test_bounded_waits_report_timeout_and_leave_the_context_usable():
     enc = omlp.encode(means, np.asarray(times, np.float64), inv, single=True)
     d_o, _ = omlp.forward(theta.astype(np.float64), enc, bf16=True)
     assert _rel(delta.double().cpu().numpy().reshape(-1, 3), d_o) < 2e-3
+
+
+@pytest.mark.parametrize("N,B", [(300, 2), (3000, 3), (77, 1), (40000, 2)])
+def test_fused_inference_equals_layer_by_layer_forward(N, B):
+    """The fused kernel (activations in shared memory) performs the same
+    arithmetic in the same order: bit-identical offsets."""
+    theta, means, times = _case(N, B, 50 + N)
+    net = mlp.DeformationMLP(N, B, 0.2)
+    th = torch.as_tensor(theta, device="cuda")
+    mu = torch.as_tensor(means, device="cuda")
+    ref = net.forward(th, mu, times).clone()
+    got = net.infer(th, mu, times)
+    torch.cuda.synchronize()
+    assert net.read_status() == gftorf.OK
+    np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
+
+
+def test_fused_inference_bounded_waits():
+    N, B = 100, 1
+    theta, means, times = _case(N, B, 43)
+    net = mlp.DeformationMLP(N, B, 0.2)
+    th = torch.as_tensor(theta, device="cuda")
+    mu = torch.as_tensor(means, device="cuda")
+    mlp.debug_inject(1)
+    try:
+        net.infer(th, mu, times)
+        assert net.read_status() == gftorf.ERR_TIMEOUT
+    finally:
+        mlp.debug_inject(0)
+    ref = net.forward(th, mu, times).clone()
+    got = net.infer(th, mu, times)
+    assert net.read_status() == gftorf.OK
+    np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
