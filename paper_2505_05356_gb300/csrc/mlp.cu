@@ -568,23 +568,27 @@ __global__ void mlp_reduce_dw_kernel(const float* __restrict__ part, int splits,
   dw[(size_t)o * ld + i] = s;
 }
 
-// ---- fused forward (inference): all layers of a 128-row tile in one CTA -------
+// ---- fused forward (inference): all layers of 128-row tiles in one CTA -------
 // The activations never leave shared memory: the epilogue warps write each
 // layer's output (bias, ReLU, BF16) straight into the 128 x 256 operand tile
 // of the next layer, in the swizzled K-major layout of the MMA descriptors,
-// while a TMA warp streams the layers' weights through a 3-stage ring.  The
-// arithmetic and its order are those of the layer-by-layer forward, so the
-// outputs agree bit for bit; nothing is kept for a backward.
+// while a TMA warp streams the layers' weights through a 3-stage ring.  A CTA
+// works on two tiles at once (two activation tiles, two TMEM accumulators),
+// alternating (layer, tile) items so that the epilogue of one tile runs while
+// the tensor core computes the other.  The arithmetic and its order are those
+// of the layer-by-layer forward, so the outputs agree bit for bit; nothing is
+// kept for a backward.
 constexpr int kFusedStages = 3;
-constexpr int kActBytes = BM * kW * 2;     // 64 KB
+constexpr int kPair = 2;                   // tiles in flight per CTA
+constexpr int kActBytes = BM * kW * 2;     // 64 KB per tile
 constexpr int kWStageBytes = kW * BK * 2;  // 32 KB (a 256-row k-block of W)
-constexpr int kFusedSmem = kActBytes + kFusedStages * kWStageBytes + 1024 + 256;
+constexpr int kFusedSmem = kPair * kActBytes + kFusedStages * kWStageBytes + 1024 + 256;
 
 struct FusedMaps {
   CUtensorMap w[kDepth + 1];  // bf16 W of the hidden layers (256 rows), head (32 rows)
 };
 
-// byte offset of element (r, c) of the activation tile: 64-column blocks of
+// byte offset of element (r, c) of an activation tile: 64-column blocks of
 // 16 KB, rows 128 bytes apart in 1024-byte 8-row atoms, 16-byte chunk j of
 // row r at chunk j ^ (r & 7) (the 128-byte swizzle)
 __device__ __forceinline__ uint32_t act_off(int r, int c) {
@@ -617,47 +621,52 @@ __global__ void __launch_bounds__(192, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* act = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kActBytes + kFusedStages * kWStageBytes);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * kFusedStages + 2);
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem + kPair * kActBytes + kFusedStages * kWStageBytes);
+  // bars: full[S], empty[S], acc_ready[kPair], act_ready[kPair]
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * kFusedStages + 2 * kPair);
   int* s_ok = reinterpret_cast<int*>(slot + 1);  // the epilogue's shared wait outcome
-  const uint32_t act_s = smem_u32(act), w_s = act_s + kActBytes;
+  const uint32_t act_s = smem_u32(smem), w_s = act_s + kPair * kActBytes;
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * kFusedStages;
-  const uint32_t acc_ready = full0 + 16 * kFusedStages, act_ready = acc_ready + 8;
+  const uint32_t acc0 = full0 + 16 * kFusedStages, actr0 = acc0 + 8 * kPair;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_pairs = (n_tiles + kPair - 1) / kPair;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kFusedStages; ++i) {
       mbar_init(full0 + 8 * i, 1);
       mbar_init(empty0 + 8 * i, 1);
     }
-    mbar_init(acc_ready, 1);
-    mbar_init(act_ready, 1);
+    for (int t = 0; t < kPair; ++t) {
+      mbar_init(acc0 + 8 * t, 1);
+      mbar_init(actr0 + 8 * t, 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(smem_u32(slot), (uint32_t)kW);
+  if (warp == 0) tmem_alloc(smem_u32(slot), (uint32_t)(kPair * kW));
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
 
   if (warp == 4) {
-    // weights of every layer, k-block by k-block, for every tile of this CTA
+    // weights of every (layer, tile) item, k-block by k-block
     if (lane == 0 && !inject_no_loads) {
       int it = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x)
-        for (int l = 0; ok && l <= kDepth; ++l) {
-          const int nkb = (l == 0 ? kIn : kW) / BK;
-          const uint32_t bytes = (uint32_t)(l == kDepth ? kHeadRows : kW) * BK * 2;
-          for (int kb = 0; kb < nkb; ++kb, ++it) {
-            const int s = it % kFusedStages;
-            if (!(ok = mbar_wait(empty0 + 8 * s, ((uint32_t)(it / kFusedStages) & 1u) ^ 1u,
-                                 status, wait_ns)))
-              break;
-            mbar_expect_tx(full0 + 8 * s, bytes);
-            tma_load_2d(w_s + s * kWStageBytes, &maps.w[l], full0 + 8 * s, kb * BK, 0);
+      for (int pr = blockIdx.x; ok && pr < n_pairs; pr += gridDim.x)
+        for (int l = 0; ok && l <= kDepth; ++l)
+          for (int t = 0; ok && t < kPair; ++t) {
+            const int nkb = (l == 0 ? kIn : kW) / BK;
+            const uint32_t bytes = (uint32_t)(l == kDepth ? kHeadRows : kW) * BK * 2;
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+              const int s = it % kFusedStages;
+              if (!(ok = mbar_wait(empty0 + 8 * s, ((uint32_t)(it / kFusedStages) & 1u) ^ 1u,
+                                   status, wait_ns)))
+                break;
+              mbar_expect_tx(full0 + 8 * s, bytes);
+              tma_load_2d(w_s + s * kWStageBytes, &maps.w[l], full0 + 8 * s, kb * BK, 0);
+            }
           }
-        }
       // every load issued has landed before the CTA may exit
       for (int i = it - kFusedStages < 0 ? 0 : it - kFusedStages; i < it; ++i)
         mbar_wait(full0 + 8 * (i % kFusedStages), (uint32_t)(i / kFusedStages) & 1u, status,
@@ -666,88 +675,94 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 5) {
     if (lane == 0) {
       int it = 0;
-      uint32_t act_ph = 0;
+      uint32_t act_ph[kPair] = {0, 0};
       bool ok = true;
-      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x)
-        for (int l = 0; ok && l <= kDepth; ++l) {
-          if (!(ok = mbar_wait(act_ready, act_ph, status, wait_ns))) break;
-          act_ph ^= 1u;
-          tc_fence_after();
-          const int nkb = (l == 0 ? kIn : kW) / BK;
-          const uint32_t idesc = l == kDepth ? idesc_bf16(BM, kHeadRows) : idesc_bf16(BM, kW);
-          for (int kb = 0; kb < nkb; ++kb, ++it) {
-            const int s = it % kFusedStages;
-            if (!(ok = mbar_wait(full0 + 8 * s, (uint32_t)(it / kFusedStages) & 1u, status,
-                                 wait_ns)))
-              break;
+      for (int pr = blockIdx.x; ok && pr < n_pairs; pr += gridDim.x)
+        for (int l = 0; ok && l <= kDepth; ++l)
+          for (int t = 0; ok && t < kPair; ++t) {
+            if (!(ok = mbar_wait(actr0 + 8 * t, act_ph[t], status, wait_ns))) break;
+            act_ph[t] ^= 1u;
             tc_fence_after();
-            const uint32_t sa = act_s + kb * 16384, sb = w_s + s * kWStageBytes;
+            const int nkb = (l == 0 ? kIn : kW) / BK;
+            const uint32_t idesc = l == kDepth ? idesc_bf16(BM, kHeadRows) : idesc_bf16(BM, kW);
+            const uint32_t d = tmem + (uint32_t)(t * kW);
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+              const int s = it % kFusedStages;
+              if (!(ok = mbar_wait(full0 + 8 * s, (uint32_t)(it / kFusedStages) & 1u, status,
+                                   wait_ns)))
+                break;
+              tc_fence_after();
+              const uint32_t sa = act_s + t * kActBytes + kb * 16384, sb = w_s + s * kWStageBytes;
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k)
-              umma_bf16(tmem, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
-                        (kb > 0 || k > 0) ? 1u : 0u);
-            umma_commit(empty0 + 8 * s);
+              for (int k = 0; k < BK / 16; ++k)
+                umma_bf16(d, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
+                          (kb > 0 || k > 0) ? 1u : 0u);
+              umma_commit(empty0 + 8 * s);
+            }
+            umma_commit(acc0 + 8 * t);
           }
-          umma_commit(acc_ready);
-        }
     }
   } else {
     // epilogue warps: row r of every tile
     const int r = warp * 32 + lane;
-    uint32_t acc_ph = 0;
+    uint32_t acc_ph[kPair] = {0, 0};
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
-      const int m = tile * BM + r;
-      {
+    for (int pr = blockIdx.x; ok && pr < n_pairs; pr += gridDim.x) {
+      for (int t = 0; t < kPair; ++t) {
         float e[kIn];
-        encode_row(means, tm, N, M, inv_scale, m, e);
+        encode_row(means, tm, N, M, inv_scale, (pr * kPair + t) * BM + r, e);
+        uint8_t* act = smem + t * kActBytes;
 #pragma unroll
         for (int c = 0; c < kIn; c += 32) store_act32(act, r, c, e + c);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (threadIdx.x == 0) mbar_arrive(act_ready);
-      for (int l = 0; l <= kDepth; ++l) {
-        // one thread waits, the other epilogue threads follow the barrier, so
-        // that all 128 take the same branch (no split at the named barriers)
-        if (threadIdx.x == 0) *s_ok = mbar_wait(acc_ready, acc_ph, status, wait_ns) ? 1 : 0;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (!(ok = *s_ok != 0)) break;
-        asm volatile("bar.sync 1, 128;" ::: "memory");  // all have read the flag
-        acc_ph ^= 1u;
-        tc_fence_after();
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        if (l < kDepth) {
-          const float* bias = theta + bias_off_dev(l);
-#pragma unroll 1
-          for (int c = 0; c < kW; c += 32) {
-            float v[32];
-            tmem_ld32(trow + (uint32_t)c, v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + __ldg(bias + c + j), 0.f);
-            store_act32(act, r, c, v);
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          tc_fence_before();
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-          if (threadIdx.x == 0) mbar_arrive(act_ready);
-        } else {
-          float v[32];
-          tmem_ld32(trow, v);
-          const float* bias = theta + head_bias_off_dev();
-          if (m < M)
-            for (int j = 0; j < 3; ++j) delta[(size_t)m * 3 + j] = v[j] + __ldg(bias + j);
-          tc_fence_before();
-          asm volatile("bar.sync 1, 128;" ::: "memory");  // TMEM drained before the next tile
-        }
+        if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
       }
+      for (int l = 0; ok && l <= kDepth; ++l)
+        for (int t = 0; t < kPair; ++t) {
+          // one thread waits, the other epilogue threads follow the barrier, so
+          // that all 128 take the same branch (no split at the named barriers)
+          if (threadIdx.x == 0)
+            *s_ok = mbar_wait(acc0 + 8 * t, acc_ph[t], status, wait_ns) ? 1 : 0;
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          if (!(ok = *s_ok != 0)) break;
+          asm volatile("bar.sync 1, 128;" ::: "memory");  // all have read the flag
+          acc_ph[t] ^= 1u;
+          tc_fence_after();
+          const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kW);
+          uint8_t* act = smem + t * kActBytes;
+          if (l < kDepth) {
+            const float* bias = theta + bias_off_dev(l);
+#pragma unroll 1
+            for (int c = 0; c < kW; c += 32) {
+              float v[32];
+              tmem_ld32(trow + (uint32_t)c, v);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + __ldg(bias + c + j), 0.f);
+              store_act32(act, r, c, v);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
+          } else {
+            float v[32];
+            tmem_ld32(trow, v);
+            const float* bias = theta + head_bias_off_dev();
+            const int m = (pr * kPair + t) * BM + r;
+            if (m < M)
+              for (int j = 0; j < 3; ++j) delta[(size_t)m * 3 + j] = v[j] + __ldg(bias + j);
+            tc_fence_before();
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // TMEM drained before the next pair
+          }
+        }
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, (uint32_t)kW);
+    tmem_dealloc(tmem, (uint32_t)(kPair * kW));
   }
 }
 
@@ -1194,8 +1209,9 @@ extern "C" gftorf_status gftorf_mlp_infer(int32_t n_gaussians, int32_t n_frames,
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int n_tiles = (M + BM - 1) / BM;
+  const int n_pairs = (n_tiles + kPair - 1) / kPair;
   const unsigned long long wait_ns = g_inject.load() ? 50000000ull : 2000000000ull;
-  mlp_fused_fwd_kernel<<<n_tiles < sms ? n_tiles : sms, 192, kFusedSmem, st>>>(
+  mlp_fused_fwd_kernel<<<n_pairs < sms ? n_pairs : sms, 192, kFusedSmem, st>>>(
       maps, theta, means, tm, n_gaussians, M, n_tiles, inv_scale, delta, status, wait_ns,
       g_inject.load());
   count_launches(2);
