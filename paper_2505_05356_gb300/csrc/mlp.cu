@@ -613,7 +613,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(192, 1)
+// warps 0-7: epilogue (warp w: TMEM lanes / rows 32 (w % 4) .. + 31, columns
+// 128 (w / 4) .. + 127); warp 8: TMA; warp 9: MMA
+constexpr int kFusedEpiWarps = 8;
+constexpr int kFusedThreads = 32 * (kFusedEpiWarps + 2);
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
     mlp_fused_fwd_kernel(const __grid_constant__ FusedMaps maps, const float* __restrict__ theta,
                          const float* __restrict__ means, Times tm, int N, int M, int n_tiles,
                          float inv_scale, float* __restrict__ delta, int* status,
@@ -648,7 +653,7 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_after();
   const uint32_t tmem = *slot;
 
-  if (warp == 4) {
+  if (warp == kFusedEpiWarps) {
     // weights of every (layer, tile) item, k-block by k-block
     if (lane == 0 && !inject_no_loads) {
       int it = 0;
@@ -672,7 +677,7 @@ __global__ void __launch_bounds__(192, 1)
         mbar_wait(full0 + 8 * (i % kFusedStages), (uint32_t)(i / kFusedStages) & 1u, status,
                   wait_ns);
     }
-  } else if (warp == 5) {
+  } else if (warp == kFusedEpiWarps + 1) {
     if (lane == 0) {
       int it = 0;
       uint32_t act_ph[kPair] = {0, 0};
@@ -703,19 +708,22 @@ __global__ void __launch_bounds__(192, 1)
           }
     }
   } else {
-    // epilogue warps: row r of every tile
-    const int r = warp * 32 + lane;
+    // epilogue warps: row r of every tile, one half of the columns
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
     uint32_t acc_ph[kPair] = {0, 0};
     bool ok = true;
     for (int pr = blockIdx.x; ok && pr < n_pairs; pr += gridDim.x) {
       for (int t = 0; t < kPair; ++t) {
-        float e[kIn];
-        encode_row(means, tm, N, M, inv_scale, (pr * kPair + t) * BM + r, e);
-        uint8_t* act = smem + t * kActBytes;
+        if (half == 0) {
+          float e[kIn];
+          encode_row(means, tm, N, M, inv_scale, (pr * kPair + t) * BM + r, e);
+          uint8_t* act = smem + t * kActBytes;
 #pragma unroll
-        for (int c = 0; c < kIn; c += 32) store_act32(act, r, c, e + c);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+          for (int c = 0; c < kIn; c += 32) store_act32(act, r, c, e + c);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
         if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
       }
       for (int l = 0; ok && l <= kDepth; ++l)
@@ -724,36 +732,45 @@ __global__ void __launch_bounds__(192, 1)
           // that all 128 take the same branch (no split at the named barriers)
           if (threadIdx.x == 0)
             *s_ok = mbar_wait(acc0 + 8 * t, acc_ph[t], status, wait_ns) ? 1 : 0;
-          asm volatile("bar.sync 1, 128;" ::: "memory");
+          asm volatile("bar.sync 1, 256;" ::: "memory");
           if (!(ok = *s_ok != 0)) break;
-          asm volatile("bar.sync 1, 128;" ::: "memory");  // all have read the flag
+          asm volatile("bar.sync 1, 256;" ::: "memory");  // all have read the flag
           acc_ph[t] ^= 1u;
           tc_fence_after();
-          const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kW);
+          const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * kW);
           uint8_t* act = smem + t * kActBytes;
           if (l < kDepth) {
             const float* bias = theta + bias_off_dev(l);
 #pragma unroll 1
-            for (int c = 0; c < kW; c += 32) {
+            for (int c = half * (kW / 2); c < (half + 1) * (kW / 2); c += 32) {
               float v[32];
               tmem_ld32(trow + (uint32_t)c, v);
+              const float4* b4 = reinterpret_cast<const float4*>(bias + c);
 #pragma unroll
-              for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + __ldg(bias + c + j), 0.f);
+              for (int j = 0; j < 8; ++j) {
+                const float4 b = __ldg(b4 + j);
+                v[4 * j] = fmaxf(v[4 * j] + b.x, 0.f);
+                v[4 * j + 1] = fmaxf(v[4 * j + 1] + b.y, 0.f);
+                v[4 * j + 2] = fmaxf(v[4 * j + 2] + b.z, 0.f);
+                v[4 * j + 3] = fmaxf(v[4 * j + 3] + b.w, 0.f);
+              }
               store_act32(act, r, c, v);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, 256;" ::: "memory");
             if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
           } else {
-            float v[32];
-            tmem_ld32(trow, v);
-            const float* bias = theta + head_bias_off_dev();
-            const int m = (pr * kPair + t) * BM + r;
-            if (m < M)
-              for (int j = 0; j < 3; ++j) delta[(size_t)m * 3 + j] = v[j] + __ldg(bias + j);
+            if (half == 0) {
+              float v[32];
+              tmem_ld32(trow, v);
+              const float* bias = theta + head_bias_off_dev();
+              const int m = (pr * kPair + t) * BM + r;
+              if (m < M)
+                for (int j = 0; j < 3; ++j) delta[(size_t)m * 3 + j] = v[j] + __ldg(bias + j);
+            }
             tc_fence_before();
-            asm volatile("bar.sync 1, 128;" ::: "memory");  // TMEM drained before the next pair
+            asm volatile("bar.sync 1, 256;" ::: "memory");  // TMEM drained before the next pair
           }
         }
     }
@@ -1211,7 +1228,7 @@ extern "C" gftorf_status gftorf_mlp_infer(int32_t n_gaussians, int32_t n_frames,
   const int n_tiles = (M + BM - 1) / BM;
   const int n_pairs = (n_tiles + kPair - 1) / kPair;
   const unsigned long long wait_ns = g_inject.load() ? 50000000ull : 2000000000ull;
-  mlp_fused_fwd_kernel<<<n_pairs < sms ? n_pairs : sms, 192, kFusedSmem, st>>>(
+  mlp_fused_fwd_kernel<<<n_pairs < sms ? n_pairs : sms, kFusedThreads, kFusedSmem, st>>>(
       maps, theta, means, tm, n_gaussians, M, n_tiles, inv_scale, delta, status, wait_ns,
       g_inject.load());
   count_launches(2);
