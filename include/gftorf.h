@@ -460,11 +460,13 @@ gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames, int32_t w
                                 int32_t layer, void* dst, void* workspace,
                                 size_t workspace_bytes, void* stream);
 
-/* Fault injection for tests of the failure path (no GPU fault): mode 1 makes
- * the MLP GEMMs' load warps issue no copies, so every CTA's bounded waits (about
- * 2 s each) run out, record GFTORF_ERR_TIMEOUT in the MLP status word and the
- * kernels return with the context usable (outputs undefined); mode 0 restores
- * normal operation.  Process-wide; for small problems only. */
+/* Test hooks, process-wide.  Mode 1 (fault injection without a GPU fault):
+ * the MLP kernels' load warps issue no copies, so every CTA's bounded waits
+ * (50 ms each in this mode, about 2 s otherwise) run out, record
+ * GFTORF_ERR_TIMEOUT in the MLP status word and the kernels return with the
+ * context usable (outputs undefined); for small problems only.  Mode 2: the
+ * training forward runs one GEMM per layer instead of the fused kernel (the
+ * two are bit-identical; for cross-checks).  Mode 0: normal operation. */
 void gftorf_mlp_debug_inject(int32_t mode);
 
 /* Synchronises `stream`; GFTORF_OK or GFTORF_ERR_TIMEOUT if a bounded wait

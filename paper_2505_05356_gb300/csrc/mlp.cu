@@ -618,11 +618,23 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 constexpr int kFusedEpiWarps = 8;
 constexpr int kFusedThreads = 32 * (kFusedEpiWarps + 2);
 
+// What a training forward keeps for the backward (TRAIN): the encoded input
+// and every hidden activation transposed ([columns][Mp], BF16), and the ReLU
+// masks as bits ([layer][Mp][8] words) -- the same values the layer-by-layer
+// forward stores.
+struct FusedKeep {
+  __nv_bfloat16* encT;
+  __nv_bfloat16* HT;
+  uint32_t* bits;
+  int Mp;
+};
+
+template <bool TRAIN>
 __global__ void __launch_bounds__(kFusedThreads, 1)
     mlp_fused_fwd_kernel(const __grid_constant__ FusedMaps maps, const float* __restrict__ theta,
                          const float* __restrict__ means, Times tm, int N, int M, int n_tiles,
                          float inv_scale, float* __restrict__ delta, int* status,
-                         unsigned long long wait_ns, int inject_no_loads) {
+                         unsigned long long wait_ns, int inject_no_loads, FusedKeep keep) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -717,10 +729,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
       for (int t = 0; t < kPair; ++t) {
         if (half == 0) {
           float e[kIn];
-          encode_row(means, tm, N, M, inv_scale, (pr * kPair + t) * BM + r, e);
+          const int m = (pr * kPair + t) * BM + r;
+          encode_row(means, tm, N, M, inv_scale, m, e);
           uint8_t* act = smem + t * kActBytes;
 #pragma unroll
           for (int c = 0; c < kIn; c += 32) store_act32(act, r, c, e + c);
+          if (TRAIN && m < keep.Mp) {
+#pragma unroll
+            for (int c = 0; c < kIn; ++c)
+              keep.encT[(size_t)c * keep.Mp + m] = __float2bfloat16_rn(e[c]);
+          }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -755,6 +773,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 v[4 * j + 3] = fmaxf(v[4 * j + 3] + b.w, 0.f);
               }
               store_act32(act, r, c, v);
+              const int m = (pr * kPair + t) * BM + r;
+              if (TRAIN && m < keep.Mp) {
+                __nv_bfloat16* ht = keep.HT + (size_t)l * kW * keep.Mp;
+                uint32_t bits = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
+                  ht[(size_t)(c + j) * keep.Mp + m] = h;
+                  bits |= (__bfloat162float(h) > 0.f ? 1u : 0u) << j;
+                }
+                keep.bits[((size_t)l * keep.Mp + m) * (kW / 32) + c / 32] = bits;
+              }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
@@ -780,6 +810,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, (uint32_t)(kPair * kW));
+  }
+}
+
+// [rows][Mp] BF16 -> [M][rows] (export of the kept transposed activations)
+__global__ void mlp_untranspose_kernel(const __nv_bfloat16* __restrict__ src, int rows, int Mp,
+                                       int M, __nv_bfloat16* __restrict__ dst) {
+  const size_t total = (size_t)M * rows;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t m = e / rows, c = e - m * rows;
+    dst[e] = src[c * Mp + m];
   }
 }
 
@@ -882,9 +923,22 @@ bool mlp_args_ok(int N, int B) {
   return N >= 0 && B >= 1 && B <= kMaxFrames && (int64_t)N * B < (int64_t)1 << 30;
 }
 
-// fault-injection hook for tests (gftorf_mlp_debug_inject): 1 = the GEMMs'
-// load warps issue nothing, so the MMA and epilogue waits run out
+// test hooks (gftorf_mlp_debug_inject): 1 = the GEMMs' load warps issue
+// nothing, so the MMA and epilogue waits run out; 2 = the training forward
+// runs layer by layer (one GEMM per layer) instead of fused
 std::atomic<int> g_inject{0};
+
+bool fused_configured() {
+  static int ok = -1;
+  if (ok < 0)
+    ok = cudaFuncSetAttribute(mlp_fused_fwd_kernel<false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) ==
+                 cudaSuccess &&
+         cudaFuncSetAttribute(mlp_fused_fwd_kernel<true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) ==
+                 cudaSuccess;
+  return ok == 1;
+}
 
 template <typename T>
 T* ptr(void* ws, size_t off) {
@@ -955,12 +1009,34 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
   for (int b = 0; b < n_frames; ++b) tm.t[b] = times[b];
   auto* enc = ptr<__nv_bfloat16>(ws, L.off_enc);
   auto* encT = ptr<__nv_bfloat16>(ws, L.off_encT);
-  mlp_encode_kernel<<<(Mp + 127) / 128, 128, 0, st>>>(means, tm, n_gaussians, n_frames,
-                                                      inv_scale, Mp, enc, encT);
-  count_launches(2);
   auto* H = ptr<__nv_bfloat16>(ws, L.off_h);
   auto* HT = ptr<__nv_bfloat16>(ws, L.off_ht);
   const int mt = Mp / BM;
+  if (g_inject.load() != 2) {
+    // fused: all layers per pair of 128-row tiles, keeping the transposed
+    // activations and the ReLU masks for the backward
+    if (!fused_configured()) return GFTORF_ERR_CUDA;
+    FusedMaps maps;
+    for (int l = 0; l <= kDepth; ++l) {
+      const int K = l == 0 ? kIn : kW, rows = l == kDepth ? kHeadRows : kW;
+      if (!make_map(&maps.w[l], wb + wb_off(l), rows, K, K, rows)) return GFTORF_ERR_CUDA;
+    }
+    FusedKeep keep;
+    keep.encT = encT, keep.HT = HT, keep.bits = ptr<uint32_t>(ws, L.off_bits), keep.Mp = Mp;
+    int sms = 148, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int n_pairs = (mt + kPair - 1) / kPair;
+    const int inj = g_inject.load();
+    mlp_fused_fwd_kernel<true><<<n_pairs < sms ? n_pairs : sms, kFusedThreads, kFusedSmem, st>>>(
+        maps, theta, means, tm, n_gaussians, L.M, mt, inv_scale, delta, status,
+        inj == 1 ? 50000000ull : 2000000000ull, inj == 1, keep);
+    count_launches(2);
+    return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+  }
+  mlp_encode_kernel<<<(Mp + 127) / 128, 128, 0, st>>>(means, tm, n_gaussians, n_frames,
+                                                      inv_scale, Mp, enc, encT);
+  count_launches(2);
   for (int l = 0; l < kDepth; ++l) {
     const int K = l == 0 ? kIn : kW;
     const __nv_bfloat16* in = l == 0 ? enc : H + (size_t)(l - 1) * Mp * kW;
@@ -976,7 +1052,7 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
     a.out_t = HT + (size_t)l * kW * Mp, a.ldt = Mp;
     a.mbits = ptr<uint32_t>(ws, L.off_bits) + (size_t)l * Mp * (kW / 32);
     a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
     a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
     if (!gemm<256, EPI_HIDDEN>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
@@ -992,7 +1068,7 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
     a.bias = theta + head_bias_off();
     a.out_f = delta;
     a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
     a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
     if (!gemm<32, EPI_HEAD>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
@@ -1066,7 +1142,7 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     a.rows_valid = 3, a.cols_valid = kW;
     a.out_f = dwx + dwx_off(kDepth), a.ldf = kW + kExt;
     a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
     a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
     if (!gemm<256, EPI_ATOMIC>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
   }
@@ -1085,7 +1161,7 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     a.mbits = bits + (size_t)(kDepth - 1) * Mp * (kW / 32);
     a.dbias = dbias_of(kDepth - 1), a.ldb = ldb_of(kDepth - 1);
     a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
     a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
     if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
@@ -1103,7 +1179,7 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
       a.rows_valid = kW, a.cols_valid = K;
       a.out_f = part, a.ldf = K;
       a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
     a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
       if (!gemm<256, EPI_PARTIAL, 2>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
       mlp_reduce_dw_kernel<<<(kW * K + 255) / 256, 256, 0, st>>>(part, splits, K,
@@ -1120,7 +1196,7 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
       a.kb_total = kW / BK, a.kb_per_split = kW / BK;
       a.rows_valid = Mp, a.cols_valid = K;
       a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed);
+    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
     a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
       if (l == 0) {
         a.out_f = denc, a.ldf = kIn;
@@ -1163,12 +1239,22 @@ extern "C" gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames
     return GFTORF_ERR_WORKSPACE;
   const size_t Mp = (size_t)L.M_pad, M = (size_t)L.M;
   size_t off, bytes;
+  if (what == 0 || what == 1) {  // from the kept transposed copies
+    if (what == 1 && (layer < 0 || layer >= kDepth)) return GFTORF_ERR_ARG;
+    if (M == 0) return GFTORF_OK;
+    const int rows = what == 0 ? kIn : kW;
+    const __nv_bfloat16* src =
+        what == 0 ? ptr<__nv_bfloat16>(workspace, L.off_encT)
+                  : ptr<__nv_bfloat16>(workspace, L.off_ht) + (size_t)layer * kW * Mp;
+    mlp_untranspose_kernel<<<4 * 152, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        src, rows, (int)Mp, (int)M, static_cast<__nv_bfloat16*>(dst));
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
+  }
   switch (what) {
-    case 0: off = L.off_enc, bytes = M * kIn * 2; break;
-    case 1:
     case 2:
       if (layer < 0 || layer >= kDepth) return GFTORF_ERR_ARG;
-      off = (what == 1 ? L.off_h : L.off_dz) + (size_t)layer * Mp * kW * 2;
+      off = L.off_dz + (size_t)layer * Mp * kW * 2;
       bytes = M * kW * 2;
       break;
     case 3: off = L.off_denc, bytes = M * kIn * 4; break;
@@ -1182,7 +1268,7 @@ extern "C" gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames
 }
 
 extern "C" void gftorf_mlp_debug_inject(int32_t mode) {
-  g_inject.store(mode == 1 ? 1 : 0, std::memory_order_relaxed);
+  g_inject.store(mode == 1 || mode == 2 ? mode : 0, std::memory_order_relaxed);
 }
 
 extern "C" gftorf_status gftorf_mlp_infer(int32_t n_gaussians, int32_t n_frames,
@@ -1215,22 +1301,18 @@ extern "C" gftorf_status gftorf_mlp_infer(int32_t n_gaussians, int32_t n_frames,
   Times tm;
   memset(&tm, 0, sizeof(tm));
   for (int b = 0; b < n_frames; ++b) tm.t[b] = times[b];
-  static bool configured = false;
-  if (!configured) {
-    if (cudaFuncSetAttribute(mlp_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kFusedSmem) != cudaSuccess)
-      return GFTORF_ERR_CUDA;
-    configured = true;
-  }
+  if (!fused_configured()) return GFTORF_ERR_CUDA;
   int sms = 148, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int n_tiles = (M + BM - 1) / BM;
   const int n_pairs = (n_tiles + kPair - 1) / kPair;
-  const unsigned long long wait_ns = g_inject.load() ? 50000000ull : 2000000000ull;
-  mlp_fused_fwd_kernel<<<n_pairs < sms ? n_pairs : sms, kFusedThreads, kFusedSmem, st>>>(
+  const unsigned long long wait_ns = g_inject.load() == 1 ? 50000000ull : 2000000000ull;
+  FusedKeep none;
+  memset(&none, 0, sizeof(none));
+  mlp_fused_fwd_kernel<false><<<n_pairs < sms ? n_pairs : sms, kFusedThreads, kFusedSmem, st>>>(
       maps, theta, means, tm, n_gaussians, M, n_tiles, inv_scale, delta, status, wait_ns,
-      g_inject.load());
+      g_inject.load() == 1, none);
   count_launches(2);
   return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
 }

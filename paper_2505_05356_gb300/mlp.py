@@ -159,7 +159,7 @@ class DeformationMLP:
 
 
 def debug_inject(mode: int):
-    """Fault injection for failure-path tests: 1 = the GEMMs' load warps issue
-    nothing, so their bounded waits run out (GFTORF_ERR_TIMEOUT, no GPU
-    fault); 0 = normal."""
+    """Test hooks: 1 = the kernels' load warps issue nothing, so their bounded
+    waits run out (GFTORF_ERR_TIMEOUT, no GPU fault); 2 = the training
+    forward runs one GEMM per layer instead of fused; 0 = normal."""
     _lib().gftorf_mlp_debug_inject(int(mode))

@@ -215,11 +215,54 @@ def test_fused_inference_equals_layer_by_layer_forward(N, B):
     net = mlp.DeformationMLP(N, B, 0.2)
     th = torch.as_tensor(theta, device="cuda")
     mu = torch.as_tensor(means, device="cuda")
-    ref = net.forward(th, mu, times).clone()
+    mlp.debug_inject(2)  # the reference: one GEMM per layer
+    try:
+        ref = net.forward(th, mu, times).clone()
+    finally:
+        mlp.debug_inject(0)
     got = net.infer(th, mu, times)
     torch.cuda.synchronize()
     assert net.read_status() == gftorf.OK
     np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
+
+
+@pytest.mark.parametrize("N,B", [(300, 2), (3000, 3)])
+def test_fused_training_forward_keeps_what_the_layerwise_one_keeps(N, B):
+    """The fused training forward stores the same transposed activations,
+    encoding and ReLU masks as the one-GEMM-per-layer forward, so the same
+    backward follows."""
+    theta, means, times = _case(N, B, 60 + N)
+    net = mlp.DeformationMLP(N, B, 0.2)
+    th = torch.as_tensor(theta, device="cuda")
+    mu = torch.as_tensor(means, device="cuda")
+    dd = torch.as_tensor(np.random.default_rng(4).standard_normal((B, N, 3)).astype(np.float32),
+                         device="cuda")
+
+    def run():
+        d = net.forward(th, mu, times).clone()
+        keep = [net.export("enc").clone()] + [net.export("H", l).clone() for l in range(8)]
+        g, m = net.backward(th, mu, times, dd)
+        dz = [net.export("dZ", l).clone() for l in range(8)]
+        torch.cuda.synchronize()
+        return d, keep, g.clone(), m.clone(), dz
+
+    mlp.debug_inject(2)
+    try:
+        ref = run()
+    finally:
+        mlp.debug_inject(0)
+    got = run()
+    assert net.read_status() == gftorf.OK
+    np.testing.assert_array_equal(got[0].cpu().numpy(), ref[0].cpu().numpy())
+    for a, b in zip(got[1], ref[1]):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    for a, b in zip(got[4], ref[4]):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    # the bias and head gradients sum with atomics: equal up to summation order
+    for (W, b_), (Wr, br) in zip(omlp.unpack(got[2].double().cpu().numpy()),
+                                 omlp.unpack(ref[2].double().cpu().numpy())):
+        assert _rel(W, Wr) < 1e-6 and _rel(b_, br) < 1e-6
+    assert _rel(got[3].double().cpu().numpy(), ref[3].double().cpu().numpy()) < 1e-6
 
 
 def test_fused_inference_bounded_waits():
