@@ -411,8 +411,9 @@ gftorf_status gftorf_adam_step(const gftorf_adam_group* groups, int n_groups, fl
  * gradients rounded to BF16); biases, the output and the encoding's gradient
  * stay FP32.  The workspace (caller-owned device memory, 256-byte aligned,
  * gftorf_mlp_workspace_size bytes) keeps the activations from the forward
- * for the backward.  n_frames in [1, GFTORF_MAX_FRAMES]; times: HOST
- * array of n_frames values. */
+ * for the backward.  n_frames in [1, GFTORF_MAX_FRAMES], n_gaussians x
+ * n_frames below 2^27 (GFTORF_ERR_ARG otherwise; workspace size 0); times:
+ * HOST array of n_frames values. */
 #define GFTORF_MLP_WIDTH 256
 #define GFTORF_MLP_DEPTH 8
 #define GFTORF_MLP_INPUT 128
@@ -465,8 +466,10 @@ gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames, int32_t w
  * (50 ms each in this mode, about 2 s otherwise) run out, record
  * GFTORF_ERR_TIMEOUT in the MLP status word and the kernels return with the
  * context usable (outputs undefined); for small problems only.  Mode 2: the
- * training forward runs one GEMM per layer instead of the fused kernel (the
- * two are bit-identical; for cross-checks).  Mode 0: normal operation. */
+ * training forward and the backward's chain of dZ run one GEMM per layer
+ * instead of the fused kernels (activations, masks and dZ bit-identical,
+ * bias-gradient sums in another order; for cross-checks).  Mode 0: normal
+ * operation. */
 void gftorf_mlp_debug_inject(int32_t mode);
 
 /* Synchronises `stream`; GFTORF_OK or GFTORF_ERR_TIMEOUT if a bounded wait

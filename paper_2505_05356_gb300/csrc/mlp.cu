@@ -55,8 +55,7 @@ struct GemmArgs {
   int cols_valid;    // output columns that exist
   const float* bias;
   __nv_bfloat16* out_b;   // row-major bf16 output (ld = ldo)
-  __nv_bfloat16* out_t;   // transposed bf16 output (ld = ldt), or null
-  int ldo, ldt;
+  int ldo;
   float* out_f;           // FP32 output (ld = ldf)
   int ldf;
   uint32_t* mbits;            // ReLU masks, one bit per unit, [rows][8] words:
@@ -116,6 +115,25 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
       : "memory");
 }
+// tile from shared memory to global memory (bulk async-group of this thread)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0,
+                                             int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(src), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// this thread's bulk stores have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// ... and have completed
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -143,10 +161,23 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                             // 128-byte swizzle
   return d;
 }
-// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
+// MN-major operand tile (the M or N index contiguous): 64-element chunks of
+// the MN index, each 8192 bytes (64 K-rows of 128 bytes, the 128-byte swizzle
+// over 8-row groups 1024 bytes apart), as a TMA box of 64 x 64 lands them;
+// the start address steps along K by whole 8-row groups.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)(8192 >> 4) << 16;                   // between 64-element MN chunks
+  d |= (uint64_t)(1024 >> 4) << 32;                   // between 8-row K groups
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32; A and B K-major
+// unless mn_a / mn_b (MN-major)
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n, int mn_a = 0, int mn_b = 0) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)mn_a << 15) | ((uint32_t)mn_b << 16) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                           uint32_t accumulate) {
@@ -212,8 +243,6 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float*
         if (!((bits >> j) & 1u)) v[j] = 0.f;
     }
     store_row_bf16(p.out_b + (size_t)m * p.ldo + n, v);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) p.out_t[(size_t)(n + j) * p.ldt + m] = __float2bfloat16_rn(v[j]);
     if (EPI == EPI_MASK) {
       // bias gradient: the warp's column sums of the stored (rounded) dZ by
       // recursive halving (lane L ends with column n + L), one shared atomic
@@ -259,6 +288,10 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float*
 // MT = 1: 2 pipeline stages and two CTAs per SM, so that one's epilogue
 // overlaps the other's loads and MMAs; MT = 2 fills TMEM (512 columns): one
 // CTA per SM with 3 stages.
+// MNA / MNB: the operand is read MN-major from a row-major [rows][cols]
+// array whose rows are the reduction index (the weight gradients dZ^T H read
+// straight from the row-major dZ and H): TMA boxes of 64 columns x 64 rows,
+// one per 64 output rows (A) or columns (B), 8 KB each.
 template <int BN, int MT>
 struct GemmShape {
   static constexpr int kStages = MT == 2 ? 3 : 2;
@@ -268,7 +301,7 @@ struct GemmShape {
   static constexpr int SMEM = kStages * STAGE + 1024 + 256 + 1024;  // + bias column sums
 };
 
-template <int BN, int EPI, int MT>
+template <int BN, int EPI, int MT, int MNA, int MNB>
 __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, const GemmArgs p) {
@@ -317,8 +350,21 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
         if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.status, p.wait_ns)) break;
         mbar_expect_tx(full0 + 8 * s, STAGE);
         const uint32_t sa = sbase + s * STAGE;
-        tma_load_2d(sa, &tmA, full0 + 8 * s, (kb0 + i) * BK, m0 * MT);
-        tma_load_2d(sa + A_BYTES, &tmB, full0 + 8 * s, (kb0 + i) * BK, n0);
+        if (MNA) {
+#pragma unroll
+          for (int j = 0; j < 2 * MT; ++j)
+            tma_load_2d(sa + j * 8192, &tmA, full0 + 8 * s, m0 * MT + 64 * j, (kb0 + i) * BK);
+        } else {
+          tma_load_2d(sa, &tmA, full0 + 8 * s, (kb0 + i) * BK, m0 * MT);
+        }
+        if (MNB) {
+#pragma unroll
+          for (int j = 0; j < BN / 64; ++j)
+            tma_load_2d(sa + A_BYTES + j * 8192, &tmB, full0 + 8 * s, n0 + 64 * j,
+                        (kb0 + i) * BK);
+        } else {
+          tma_load_2d(sa + A_BYTES, &tmB, full0 + 8 * s, (kb0 + i) * BK, n0);
+        }
         issued = i + 1;
       }
       // every load issued has landed before the CTA may exit
@@ -328,7 +374,7 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
   } else if (warp == 5) {
     // MMA issuer
     if (lane == 0 && nkb > 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      constexpr uint32_t idesc = idesc_bf16(BM, BN, MNA, MNB);
       for (int i = 0; i < nkb; ++i) {
         const int s = i % kStages;
         const uint32_t ph = (uint32_t)(i / kStages) & 1u;
@@ -338,9 +384,13 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k)
 #pragma unroll
-          for (int t = 0; t < MT; ++t)
-            umma_bf16(tmem + (uint32_t)(t * BN), sw128_desc(sa + t * BM * 128 + 32 * k),
-                      sw128_desc(sb + 32 * k), idesc, (i > 0 || k > 0) ? 1u : 0u);
+          for (int t = 0; t < MT; ++t) {
+            // K step of 16: 32 bytes along a K-major row, two 8-row groups MN-major
+            const uint64_t da = MNA ? sw128_mn_desc(sa + t * 16384 + 2048 * k)
+                                    : sw128_desc(sa + t * BM * 128 + 32 * k);
+            const uint64_t db = MNB ? sw128_mn_desc(sb + 2048 * k) : sw128_desc(sb + 32 * k);
+            umma_bf16(tmem + (uint32_t)(t * BN), da, db, idesc, (i > 0 || k > 0) ? 1u : 0u);
+          }
         umma_commit(empty0 + 8 * s);
       }
       umma_commit(done);  // completes once every MMA issued above has
@@ -457,18 +507,15 @@ __device__ __forceinline__ void encode_row(const float* __restrict__ means, cons
   }
 }
 
-// positional encoding of row m = b N + g into enc[m][0..127] and encT[c][m]
+// positional encoding of row m = b N + g into enc[m][0..127]
 __global__ void mlp_encode_kernel(const float* __restrict__ means, Times tm, int N, int B,
-                                  float inv_scale, int M_pad, __nv_bfloat16* __restrict__ enc,
-                                  __nv_bfloat16* __restrict__ encT) {
+                                  float inv_scale, int M_pad, __nv_bfloat16* __restrict__ enc) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M_pad) return;
   float e[kIn];
   encode_row(means, tm, N, N * B, inv_scale, m, e);
 #pragma unroll
   for (int q = 0; q < kIn / 32; ++q) store_row_bf16(enc + (size_t)m * kIn + 32 * q, e + 32 * q);
-#pragma unroll
-  for (int c = 0; c < kIn; ++c) encT[(size_t)c * M_pad + m] = __float2bfloat16_rn(e[c]);
 }
 
 // dL/d(delta) fp32 [M][3] -> bf16 [M_pad][32] and its transpose [32][M_pad]
@@ -586,6 +633,8 @@ constexpr int kFusedSmem = kPair * kActBytes + kFusedStages * kWStageBytes + 102
 
 struct FusedMaps {
   CUtensorMap w[kDepth + 1];  // bf16 W of the hidden layers (256 rows), head (32 rows)
+  CUtensorMap enc;            // training forward: the encoding [Mp][128] (stores)
+  CUtensorMap act;            // H (forward) or dZ (backward) of all layers [8 Mp][256] (stores)
 };
 
 // byte offset of element (r, c) of an activation tile: 64-column blocks of
@@ -619,12 +668,12 @@ constexpr int kFusedEpiWarps = 8;
 constexpr int kFusedThreads = 32 * (kFusedEpiWarps + 2);
 
 // What a training forward keeps for the backward (TRAIN): the encoded input
-// and every hidden activation transposed ([columns][Mp], BF16), and the ReLU
-// masks as bits ([layer][Mp][8] words) -- the same values the layer-by-layer
-// forward stores.
+// and every hidden activation (row-major BF16, stored by TMA from the tile in
+// shared memory through maps.enc / maps.act), and the ReLU masks as bits
+// ([layer][Mp][8] words) -- the same values the layer-by-layer forward
+// stores.  The stores of tile t are issued (and waited for before the tile is
+// written again) by epilogue thread 32 t.
 struct FusedKeep {
-  __nv_bfloat16* encT;
-  __nv_bfloat16* HT;
   uint32_t* bits;
   int Mp;
 };
@@ -734,15 +783,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           uint8_t* act = smem + t * kActBytes;
 #pragma unroll
           for (int c = 0; c < kIn; c += 32) store_act32(act, r, c, e + c);
-          if (TRAIN && m < keep.Mp) {
-#pragma unroll
-            for (int c = 0; c < kIn; ++c)
-              keep.encT[(size_t)c * keep.Mp + m] = __float2bfloat16_rn(e[c]);
-          }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         asm volatile("bar.sync 1, 256;" ::: "memory");
         if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
+        if (TRAIN && threadIdx.x == 32 * t && pr * kPair + t < n_tiles) {
+          for (int kb = 0; kb < kIn / BK; ++kb)
+            tma_store_2d(&maps.enc, act_s + t * kActBytes + kb * 16384, kb * BK,
+                         (pr * kPair + t) * BM);
+          bulk_commit();
+        }
       }
       for (int l = 0; ok && l <= kDepth; ++l)
         for (int t = 0; t < kPair; ++t) {
@@ -750,6 +800,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           // that all 128 take the same branch (no split at the named barriers)
           if (threadIdx.x == 0)
             *s_ok = mbar_wait(acc0 + 8 * t, acc_ph[t], status, wait_ns) ? 1 : 0;
+          // the tile's last store has read it before it is written again
+          if (TRAIN && threadIdx.x == 32 * t) bulk_wait_read();
           asm volatile("bar.sync 1, 256;" ::: "memory");
           if (!(ok = *s_ok != 0)) break;
           asm volatile("bar.sync 1, 256;" ::: "memory");  // all have read the flag
@@ -775,14 +827,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
               store_act32(act, r, c, v);
               const int m = (pr * kPair + t) * BM + r;
               if (TRAIN && m < keep.Mp) {
-                __nv_bfloat16* ht = keep.HT + (size_t)l * kW * keep.Mp;
                 uint32_t bits = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
-                  ht[(size_t)(c + j) * keep.Mp + m] = h;
-                  bits |= (__bfloat162float(h) > 0.f ? 1u : 0u) << j;
-                }
+                for (int j = 0; j < 32; ++j)
+                  bits |= (__bfloat162float(__float2bfloat16_rn(v[j])) > 0.f ? 1u : 0u) << j;
                 keep.bits[((size_t)l * keep.Mp + m) * (kW / 32) + c / 32] = bits;
               }
             }
@@ -790,6 +838,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             tc_fence_before();
             asm volatile("bar.sync 1, 256;" ::: "memory");
             if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
+            if (TRAIN && threadIdx.x == 32 * t && pr * kPair + t < n_tiles) {
+              for (int kb = 0; kb < kW / BK; ++kb)
+                tma_store_2d(&maps.act, act_s + t * kActBytes + kb * 16384, kb * BK,
+                             l * keep.Mp + (pr * kPair + t) * BM);
+              bulk_commit();
+            }
           } else {
             if (half == 0) {
               float v[32];
@@ -804,6 +858,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           }
         }
     }
+    if (TRAIN && (threadIdx.x & 31) == 0) bulk_wait_all();  // the stores are done
   }
   tc_fence_before();
   __syncthreads();
@@ -813,14 +868,215 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   }
 }
 
-// [rows][Mp] BF16 -> [M][rows] (export of the kept transposed activations)
-__global__ void mlp_untranspose_kernel(const __nv_bfloat16* __restrict__ src, int rows, int Mp,
-                                       int M, __nv_bfloat16* __restrict__ dst) {
-  const size_t total = (size_t)M * rows;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t m = e / rows, c = e - m * rows;
-    dst[e] = src[c * Mp + m];
+// ---- fused backward: the dZ chain of 128-row tiles kept in shared memory ----
+// Step s = 0 forms dZ_7 = (dZ_head W_head) * mask_7 from dL/d(delta); steps
+// s = 1..7 form dZ_{7-s} = (dZ_{8-s} W_{8-s}) * mask_{7-s}; step 8 forms the
+// encoding's gradient dZ_0 W_0 (FP32).  Each dZ tile goes to shared memory as
+// the next step's operand and from there by TMA (maps.act, row-major) to
+// global memory for the weight gradients; its column sums (bias gradients)
+// accumulate per CTA.  The same operands and order as the one-GEMM-per-layer
+// backward: bit-identical dZ.
+constexpr int kBwdStages = 2;
+constexpr int kBwdSmem = kPair * kActBytes + kBwdStages * kWStageBytes + kDepth * kW * 4 + 1024 +
+                         256;
+
+struct FusedBwdArgs {
+  const float* dd;      // dL/d(delta) [M][3]
+  const uint32_t* bits; // ReLU masks [layer][Mp][8]
+  float* denc;          // [Mp][128] (out)
+  float* dbias[kDepth]; // bias-gradient column of each layer (out, accumulated)
+  int ldb[kDepth];
+  int M, Mp, n_tiles;
+};
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    mlp_fused_bwd_kernel(const __grid_constant__ FusedMaps maps, const FusedBwdArgs a,
+                         int* status, unsigned long long wait_ns, int inject_no_loads) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem =
+      reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  float* s_db = reinterpret_cast<float*>(smem + kPair * kActBytes + kBwdStages * kWStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_db + kDepth * kW);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * kBwdStages + 2 * kPair);
+  int* s_ok = reinterpret_cast<int*>(slot + 1);
+  const uint32_t act_s = smem_u32(smem), w_s = act_s + kPair * kActBytes;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * kBwdStages;
+  const uint32_t acc0 = full0 + 16 * kBwdStages, actr0 = acc0 + 8 * kPair;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_pairs = (a.n_tiles + kPair - 1) / kPair;
+  constexpr int kSteps = kDepth + 1;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kBwdStages; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    for (int t = 0; t < kPair; ++t) {
+      mbar_init(acc0 + 8 * t, 1);
+      mbar_init(actr0 + 8 * t, 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < kDepth * kW; i += blockDim.x) s_db[i] = 0.f;
+  if (warp == 0) tmem_alloc(smem_u32(slot), (uint32_t)(kPair * kW));
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (warp == kFusedEpiWarps) {
+    // W^T of the head (step 0) and of layers 7..0 (steps 1..8)
+    if (lane == 0 && !inject_no_loads) {
+      int it = 0;
+      bool ok = true;
+      for (int pr = blockIdx.x; ok && pr < n_pairs; pr += gridDim.x)
+        for (int st = 0; ok && st < kSteps; ++st)
+          for (int t = 0; ok && t < kPair; ++t) {
+            const int nkb = st == 0 ? 1 : kW / BK;
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+              const int s = it % kBwdStages;
+              if (!(ok = mbar_wait(empty0 + 8 * s, ((uint32_t)(it / kBwdStages) & 1u) ^ 1u,
+                                   status, wait_ns)))
+                break;
+              mbar_expect_tx(full0 + 8 * s, (uint32_t)kWStageBytes);
+              tma_load_2d(w_s + s * kWStageBytes, &maps.w[st == 0 ? kDepth : kDepth - st],
+                          full0 + 8 * s, kb * BK, 0);
+            }
+          }
+      for (int i = it - kBwdStages < 0 ? 0 : it - kBwdStages; i < it; ++i)
+        mbar_wait(full0 + 8 * (i % kBwdStages), (uint32_t)(i / kBwdStages) & 1u, status,
+                  wait_ns);
+    }
+  } else if (warp == kFusedEpiWarps + 1) {
+    if (lane == 0) {
+      int it = 0;
+      uint32_t act_ph[kPair] = {0, 0};
+      bool ok = true;
+      constexpr uint32_t idesc = idesc_bf16(BM, kW);
+      for (int pr = blockIdx.x; ok && pr < n_pairs; pr += gridDim.x)
+        for (int st = 0; ok && st < kSteps; ++st)
+          for (int t = 0; ok && t < kPair; ++t) {
+            if (!(ok = mbar_wait(actr0 + 8 * t, act_ph[t], status, wait_ns))) break;
+            act_ph[t] ^= 1u;
+            tc_fence_after();
+            const int nkb = st == 0 ? 1 : kW / BK;
+            const uint32_t d = tmem + (uint32_t)(t * kW);
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+              const int s = it % kBwdStages;
+              if (!(ok = mbar_wait(full0 + 8 * s, (uint32_t)(it / kBwdStages) & 1u, status,
+                                   wait_ns)))
+                break;
+              tc_fence_after();
+              const uint32_t sa = act_s + t * kActBytes + kb * 16384, sb = w_s + s * kWStageBytes;
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k)
+                umma_bf16(d, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc,
+                          (kb > 0 || k > 0) ? 1u : 0u);
+              umma_commit(empty0 + 8 * s);
+            }
+            umma_commit(acc0 + 8 * t);
+          }
+    }
+  } else {
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
+    uint32_t acc_ph[kPair] = {0, 0};
+    bool ok = true;
+    for (int pr = blockIdx.x; ok && pr < n_pairs; pr += gridDim.x) {
+      for (int t = 0; t < kPair; ++t) {
+        // step 0's operand: BF16 dL/d(delta) in columns 0..2 of k-block 0
+        const int m = (pr * kPair + t) * BM + r;
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        if (half == 0 && m < a.M)
+          for (int j = 0; j < 3; ++j) v[j] = a.dd[(size_t)m * 3 + j];
+        store_act32(smem + t * kActBytes, r, 32 * half, v);  // (free: waited at step 8)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
+      }
+      for (int st = 0; ok && st < kSteps; ++st)
+        for (int t = 0; t < kPair; ++t) {
+          if (threadIdx.x == 0)
+            *s_ok = mbar_wait(acc0 + 8 * t, acc_ph[t], status, wait_ns) ? 1 : 0;
+          // the tile's last store has read it before it is written again
+          if (threadIdx.x == 32 * t) bulk_wait_read();
+          asm volatile("bar.sync 1, 256;" ::: "memory");
+          if (!(ok = *s_ok != 0)) break;
+          asm volatile("bar.sync 1, 256;" ::: "memory");
+          acc_ph[t] ^= 1u;
+          tc_fence_after();
+          const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * kW);
+          const int m = (pr * kPair + t) * BM + r;
+          if (st < kDepth) {
+            const int j = kDepth - 1 - st;  // the layer whose dZ this step forms
+            uint8_t* act = smem + t * kActBytes;
+            const uint32_t* bits = a.bits + ((size_t)j * a.Mp + (m < a.Mp ? m : 0)) * (kW / 32);
+#pragma unroll 1
+            for (int c = half * (kW / 2); c < (half + 1) * (kW / 2); c += 32) {
+              float v[32];
+              tmem_ld32(trow + (uint32_t)c, v);
+              const uint32_t mk = m < a.Mp ? __ldg(bits + c / 32) : 0u;
+#pragma unroll
+              for (int k = 0; k < 32; ++k)
+                v[k] = ((mk >> k) & 1u) ? __bfloat162float(__float2bfloat16_rn(v[k])) : 0.f;
+              store_act32(act, r, c, v);
+              // column sums of the warp's rows (recursive halving; lane L: column c + L)
+#pragma unroll
+              for (int off = 16; off > 0; off >>= 1) {
+                const bool up = (lane & off) != 0;
+#pragma unroll
+                for (int i = 0; i < off; ++i) {
+                  const float keep = up ? v[i + off] : v[i];
+                  const float send = up ? v[i] : v[i + off];
+                  v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
+              }
+              atomicAdd(s_db + j * kW + c + lane, v[0]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
+            if (threadIdx.x == 32 * t && pr * kPair + t < a.n_tiles) {
+              for (int kb = 0; kb < kW / BK; ++kb)
+                tma_store_2d(&maps.act, act_s + t * kActBytes + kb * 16384, kb * BK,
+                             j * a.Mp + (pr * kPair + t) * BM);
+              bulk_commit();
+            }
+          } else {
+            if (half == 0) {
+#pragma unroll 1
+              for (int c = 0; c < kIn; c += 32) {
+                float v[32];
+                tmem_ld32(trow + (uint32_t)c, v);
+                if (m < a.Mp) {
+                  float4* d = reinterpret_cast<float4*>(a.denc + (size_t)m * kIn + c);
+#pragma unroll
+                  for (int k = 0; k < 8; ++k)
+                    d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                }
+              }
+            }
+            tc_fence_before();
+            asm volatile("bar.sync 1, 256;" ::: "memory");  // TMEM drained before the next pair
+          }
+        }
+    }
+    if ((threadIdx.x & 31) == 0) bulk_wait_all();  // the stores are done
+    // the CTA's bias-gradient sums, one global atomic per (layer, column)
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    if (ok)
+      for (int i = threadIdx.x; i < kDepth * kW; i += 256) {
+        const int j = i / kW, n = i - j * kW;
+        if (s_db[i] != 0.f) atomicAdd(a.dbias[j] + (size_t)n * a.ldb[j], s_db[i]);
+      }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)(kPair * kW));
   }
 }
 
@@ -854,26 +1110,27 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, 
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int EPI, int MT = 1>
+template <int BN, int EPI, int MT = 1, int MNA = 0, int MNB = 0>
 bool gemm(const CUtensorMap& a, const CUtensorMap& b, const GemmArgs& args, int m_tiles,
           int n_tiles, int splits, cudaStream_t st) {
   static bool configured = false;
   constexpr int smem = GemmShape<BN, MT>::SMEM;
   if (!configured) {
-    if (cudaFuncSetAttribute(umma_gemm_kernel<BN, EPI, MT>,
+    if (cudaFuncSetAttribute(umma_gemm_kernel<BN, EPI, MT, MNA, MNB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return false;
     configured = true;
   }
-  umma_gemm_kernel<BN, EPI, MT><<<dim3(m_tiles, n_tiles, splits), 192, smem, st>>>(a, b, args);
+  umma_gemm_kernel<BN, EPI, MT, MNA, MNB>
+      <<<dim3(m_tiles, n_tiles, splits), 192, smem, st>>>(a, b, args);
   count_launches(1);
   return true;
 }
 
 struct MlpLayout {
   int N, B, M, M_pad;
-  size_t off_status, off_wb, off_wt, off_enc, off_encT, off_h, off_ht, off_bits, off_dz,
-      off_dzt0, off_dzt1, off_dzh, off_dzht, off_denc, off_dwx, off_part, total;
+  size_t off_status, off_wb, off_wt, off_enc, off_h, off_bits, off_dz, off_dzh, off_dzht,
+      off_denc, off_dwx, off_part, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -902,14 +1159,10 @@ MlpLayout mlp_layout(int N, int B) {
   L.off_status = take(256);
   L.off_wb = take(wb_elems() * 2);
   L.off_wt = take(wb_elems() * 2);
-  L.off_enc = take(Mp * kIn * 2);
-  L.off_encT = take((size_t)kIn * Mp * 2);
-  L.off_h = take((size_t)kDepth * Mp * kW * 2);
-  L.off_ht = take((size_t)kDepth * kW * Mp * 2);
+  L.off_enc = take(Mp * kIn * 2);                   // [Mp][128]
+  L.off_h = take((size_t)kDepth * Mp * kW * 2);     // [layer][Mp][256]
   L.off_bits = take((size_t)kDepth * Mp * (kW / 32) * 4);
-  L.off_dz = take((size_t)kDepth * Mp * kW * 2);  // dZ of every layer (kept for export)
-  L.off_dzt0 = take((size_t)kW * Mp * 2);
-  L.off_dzt1 = take((size_t)kW * Mp * 2);
+  L.off_dz = take((size_t)kDepth * Mp * kW * 2);    // [layer][Mp][256]
   L.off_dzh = take(Mp * kHeadRows * 2);
   L.off_dzht = take((size_t)kHeadRows * Mp * 2);
   L.off_denc = take(Mp * kIn * 4);
@@ -919,13 +1172,16 @@ MlpLayout mlp_layout(int N, int B) {
   return L;
 }
 
+// rows: below 2^27 (the stores address layer l's rows at l Mp + m with
+// 32-bit TMA coordinates)
 bool mlp_args_ok(int N, int B) {
-  return N >= 0 && B >= 1 && B <= kMaxFrames && (int64_t)N * B < (int64_t)1 << 30;
+  return N >= 0 && B >= 1 && B <= kMaxFrames && (int64_t)N * B < (int64_t)1 << 27;
 }
 
 // test hooks (gftorf_mlp_debug_inject): 1 = the GEMMs' load warps issue
 // nothing, so the MMA and epilogue waits run out; 2 = the training forward
-// runs layer by layer (one GEMM per layer) instead of fused
+// and the backward's dZ chain run layer by layer (one GEMM per layer)
+// instead of fused
 std::atomic<int> g_inject{0};
 
 bool fused_configured() {
@@ -936,7 +1192,9 @@ bool fused_configured() {
                  cudaSuccess &&
          cudaFuncSetAttribute(mlp_fused_fwd_kernel<true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) ==
-                 cudaSuccess;
+                 cudaSuccess &&
+         cudaFuncSetAttribute(mlp_fused_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kBwdSmem) == cudaSuccess;
   return ok == 1;
 }
 
@@ -1008,12 +1266,10 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
   memset(&tm, 0, sizeof(tm));
   for (int b = 0; b < n_frames; ++b) tm.t[b] = times[b];
   auto* enc = ptr<__nv_bfloat16>(ws, L.off_enc);
-  auto* encT = ptr<__nv_bfloat16>(ws, L.off_encT);
   auto* H = ptr<__nv_bfloat16>(ws, L.off_h);
-  auto* HT = ptr<__nv_bfloat16>(ws, L.off_ht);
   const int mt = Mp / BM;
   if (g_inject.load() != 2) {
-    // fused: all layers per pair of 128-row tiles, keeping the transposed
+    // fused: all layers per pair of 128-row tiles, keeping the encoding, the
     // activations and the ReLU masks for the backward
     if (!fused_configured()) return GFTORF_ERR_CUDA;
     FusedMaps maps;
@@ -1021,8 +1277,11 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
       const int K = l == 0 ? kIn : kW, rows = l == kDepth ? kHeadRows : kW;
       if (!make_map(&maps.w[l], wb + wb_off(l), rows, K, K, rows)) return GFTORF_ERR_CUDA;
     }
+    if (!make_map(&maps.enc, enc, Mp, kIn, kIn, BM) ||
+        !make_map(&maps.act, H, (uint64_t)kDepth * Mp, kW, kW, BM))
+      return GFTORF_ERR_CUDA;
     FusedKeep keep;
-    keep.encT = encT, keep.HT = HT, keep.bits = ptr<uint32_t>(ws, L.off_bits), keep.Mp = Mp;
+    keep.bits = ptr<uint32_t>(ws, L.off_bits), keep.Mp = Mp;
     int sms = 148, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1035,7 +1294,7 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
     return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
   }
   mlp_encode_kernel<<<(Mp + 127) / 128, 128, 0, st>>>(means, tm, n_gaussians, n_frames,
-                                                      inv_scale, Mp, enc, encT);
+                                                      inv_scale, Mp, enc);
   count_launches(2);
   for (int l = 0; l < kDepth; ++l) {
     const int K = l == 0 ? kIn : kW;
@@ -1049,7 +1308,6 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
     a.rows_valid = Mp, a.cols_valid = kW;
     a.bias = theta + bias_off(l);
     a.out_b = H + (size_t)l * Mp * kW, a.ldo = kW;
-    a.out_t = HT + (size_t)l * kW * Mp, a.ldt = Mp;
     a.mbits = ptr<uint32_t>(ws, L.off_bits) + (size_t)l * Mp * (kW / 32);
     a.status = status;
     a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
@@ -1102,14 +1360,12 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
   }
   auto* wt = ptr<__nv_bfloat16>(ws, L.off_wt);
-  auto* encT = ptr<__nv_bfloat16>(ws, L.off_encT);
-  auto* HT = ptr<__nv_bfloat16>(ws, L.off_ht);
+  auto* enc = ptr<__nv_bfloat16>(ws, L.off_enc);
+  auto H = [&](int l) { return ptr<__nv_bfloat16>(ws, L.off_h) + (size_t)l * Mp * kW; };
   auto* bits = ptr<uint32_t>(ws, L.off_bits);
   auto* dzh = ptr<__nv_bfloat16>(ws, L.off_dzh);
   auto* dzht = ptr<__nv_bfloat16>(ws, L.off_dzht);
   auto dz = [&](int l) { return ptr<__nv_bfloat16>(ws, L.off_dz) + (size_t)l * Mp * kW; };
-  __nv_bfloat16* dzt[2] = {ptr<__nv_bfloat16>(ws, L.off_dzt0),
-                           ptr<__nv_bfloat16>(ws, L.off_dzt1)};
   float* denc = ptr<float>(ws, L.off_denc);
   const int mt = Mp / BM;
   const int kb_rows = Mp / BK;      // k-blocks of a reduction over the batch rows
@@ -1127,88 +1383,96 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
   // bias gradient of a layer: column K of its dW block
   auto dbias_of = [&](int l) { return dwx + dwx_off(l) + (l == 0 ? kIn : kW); };
   auto ldb_of = [&](int l) { return (l == 0 ? kIn : kW) + kExt; };
+  const bool inj_loads = g_inject.load(std::memory_order_relaxed) == 1;
+  const unsigned long long wait_ns = inj_loads ? 50000000ull : 2000000000ull;
   mlp_head_grad_kernel<<<(Mp + 127) / 128, 128, 0, st>>>(d_delta, L.M, Mp, dzh, dzht,
                                                          dbias_of(kDepth), kW + kExt);
   count_launches(1);
-  // head: dW_head += dZh^T H_7
+  // head: dW_head += dZh^T H_7 (H_7 read MN-major)
   {
     CUtensorMap ma, mb;
     if (!make_map(&ma, dzht, kHeadRows, Mp, Mp, BM) ||
-        !make_map(&mb, HT + (size_t)(kDepth - 1) * kW * Mp, kW, Mp, Mp, 256))
+        !make_map(&mb, H(kDepth - 1), Mp, kW, kW, BK))
       return GFTORF_ERR_CUDA;
     GemmArgs a;
     memset(&a, 0, sizeof(a));
     a.kb_total = kb_rows, a.kb_per_split = per_split;
     a.rows_valid = 3, a.cols_valid = kW;
     a.out_f = dwx + dwx_off(kDepth), a.ldf = kW + kExt;
-    a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
-    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
-    if (!gemm<256, EPI_ATOMIC>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
+    a.status = status, a.inject_no_loads = inj_loads, a.wait_ns = wait_ns;
+    if (!gemm<256, EPI_ATOMIC, 1, 0, 1>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
   }
-  // dH_7 = dZh W_head, dZ_7 = dH_7 * (H_7 > 0)
-  int cur = 0;
-  {
+  if (g_inject.load(std::memory_order_relaxed) != 2) {
+    // fused dZ chain: all layers per pair of 128-row tiles, dZ_l kept in
+    // shared memory as the next layer's operand and stored (row-major) for
+    // the weight gradients below
+    if (!fused_configured()) return GFTORF_ERR_CUDA;
+    FusedMaps maps;
+    if (!make_map(&maps.w[kDepth], wt + wb_off(kDepth), kW, kHeadRows, kHeadRows, 256))
+      return GFTORF_ERR_CUDA;
+    for (int l = 0; l < kDepth; ++l)
+      if (!make_map(&maps.w[l], wt + wb_off(l), l == 0 ? kIn : kW, kW, kW, 256))
+        return GFTORF_ERR_CUDA;
+    if (!make_map(&maps.act, dz(0), (uint64_t)kDepth * Mp, kW, kW, BM)) return GFTORF_ERR_CUDA;
+    FusedBwdArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.dd = d_delta, fa.bits = bits, fa.denc = denc;
+    for (int l = 0; l < kDepth; ++l) fa.dbias[l] = dbias_of(l), fa.ldb[l] = ldb_of(l);
+    fa.M = L.M, fa.Mp = Mp, fa.n_tiles = mt;
+    const int n_pairs = (mt + kPair - 1) / kPair;
+    mlp_fused_bwd_kernel<<<n_pairs < sms ? n_pairs : sms, kFusedThreads, kBwdSmem, st>>>(
+        maps, fa, status, wait_ns, inj_loads);
+    count_launches(1);
+  } else {
+    // dH_7 = dZh W_head, dZ_7 = dH_7 * (H_7 > 0); then dH_{l-1} = dZ_l W_l
+    // (l = 0: the encoding's gradient, FP32), one GEMM per layer
+    for (int l = kDepth; l >= 1; --l) {
+      const int K = l == kDepth ? kHeadRows : kW;
+      CUtensorMap ma, mb;
+      if (!make_map(&ma, l == kDepth ? dzh : dz(l), Mp, K, K, BM) ||
+          !make_map(&mb, wt + wb_off(l), l == 0 ? kIn : kW, K, K, 256))
+        return GFTORF_ERR_CUDA;
+      GemmArgs a;
+      memset(&a, 0, sizeof(a));
+      a.kb_total = l == kDepth ? 1 : kW / BK, a.kb_per_split = a.kb_total;
+      a.rows_valid = Mp, a.cols_valid = kW;
+      a.out_b = dz(l - 1), a.ldo = kW;
+      a.mbits = bits + (size_t)(l - 1) * Mp * (kW / 32);
+      a.dbias = dbias_of(l - 1), a.ldb = ldb_of(l - 1);
+      a.status = status, a.inject_no_loads = inj_loads, a.wait_ns = wait_ns;
+      if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
+    }
     CUtensorMap ma, mb;
-    if (!make_map(&ma, dzh, Mp, kHeadRows, kHeadRows, BM) ||
-        !make_map(&mb, wt + wb_off(kDepth), kW, kHeadRows, kHeadRows, 256))
+    if (!make_map(&ma, dz(0), Mp, kW, kW, BM) || !make_map(&mb, wt, kIn, kW, kW, 256))
       return GFTORF_ERR_CUDA;
     GemmArgs a;
     memset(&a, 0, sizeof(a));
-    a.kb_total = 1, a.kb_per_split = 1;
-    a.rows_valid = Mp, a.cols_valid = kW;
-    a.out_b = dz(kDepth - 1), a.ldo = kW, a.out_t = dzt[cur], a.ldt = Mp;
-    a.mbits = bits + (size_t)(kDepth - 1) * Mp * (kW / 32);
-    a.dbias = dbias_of(kDepth - 1), a.ldb = ldb_of(kDepth - 1);
-    a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
-    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
-    if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
+    a.kb_total = kW / BK, a.kb_per_split = kW / BK;
+    a.rows_valid = Mp, a.cols_valid = kIn;
+    a.out_f = denc, a.ldf = kIn;
+    a.status = status, a.inject_no_loads = inj_loads, a.wait_ns = wait_ns;
+    if (!gemm<256, EPI_F32>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
   }
+  // dW_l += dZ_l^T H_{l-1} (or the encoding): all 256 output rows per CTA,
+  // both operands read MN-major from the row-major dZ_l and H_{l-1}
   for (int l = kDepth - 1; l >= 0; --l) {
     const int K = l == 0 ? kIn : kW;
-    // dW_l += dZ_l^T H_{l-1} (or the encoding): all 256 output rows per CTA
-    {
-      const __nv_bfloat16* bt = l == 0 ? encT : HT + (size_t)(l - 1) * kW * Mp;
-      CUtensorMap ma, mb;
-      if (!make_map(&ma, dzt[cur], kW, Mp, Mp, 2 * BM) || !make_map(&mb, bt, K, Mp, Mp, 256))
-        return GFTORF_ERR_CUDA;
-      GemmArgs a;
-      memset(&a, 0, sizeof(a));
-      a.kb_total = kb_rows, a.kb_per_split = per_split;
-      a.rows_valid = kW, a.cols_valid = K;
-      a.out_f = part, a.ldf = K;
-      a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
-    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
-      if (!gemm<256, EPI_PARTIAL, 2>(ma, mb, a, 1, 1, splits, st)) return GFTORF_ERR_CUDA;
-      mlp_reduce_dw_kernel<<<(kW * K + 255) / 256, 256, 0, st>>>(part, splits, K,
-                                                                 dwx + dwx_off(l), K + kExt);
-      count_launches(1);
-    }
-    // dH_{l-1} = dZ_l W_l  (l = 0: the encoding's gradient, FP32)
-    {
-      CUtensorMap ma, mb;
-      if (!make_map(&ma, dz(l), Mp, kW, kW, BM) || !make_map(&mb, wt + wb_off(l), K, kW, kW, 256))
-        return GFTORF_ERR_CUDA;
-      GemmArgs a;
-      memset(&a, 0, sizeof(a));
-      a.kb_total = kW / BK, a.kb_per_split = kW / BK;
-      a.rows_valid = Mp, a.cols_valid = K;
-      a.status = status;
-    a.inject_no_loads = g_inject.load(std::memory_order_relaxed) == 1;
-    a.wait_ns = a.inject_no_loads ? 50000000ull : 2000000000ull;
-      if (l == 0) {
-        a.out_f = denc, a.ldf = kIn;
-        if (!gemm<256, EPI_F32>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
-      } else {
-        a.out_b = dz(l - 1), a.ldo = kW, a.out_t = dzt[cur ^ 1], a.ldt = Mp;
-        a.mbits = bits + (size_t)(l - 1) * Mp * (kW / 32);
-        a.dbias = dbias_of(l - 1), a.ldb = ldb_of(l - 1);
-        if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
-        cur ^= 1;
-      }
-    }
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, dz(l), Mp, kW, kW, BK) ||
+        !make_map(&mb, l == 0 ? enc : H(l - 1), Mp, K, K, BK))
+      return GFTORF_ERR_CUDA;
+    GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kb_total = kb_rows, a.kb_per_split = per_split;
+    a.rows_valid = kW, a.cols_valid = K;
+    a.out_f = part, a.ldf = K;
+    a.status = status, a.inject_no_loads = inj_loads, a.wait_ns = wait_ns;
+    if (!(l == 0 ? gemm<kIn, EPI_PARTIAL, 2, 1, 1>(ma, mb, a, 1, 1, splits, st)
+                 : gemm<kW, EPI_PARTIAL, 2, 1, 1>(ma, mb, a, 1, 1, splits, st)))
+      return GFTORF_ERR_CUDA;
+    mlp_reduce_dw_kernel<<<(kW * K + 255) / 256, 256, 0, st>>>(part, splits, K, dwx + dwx_off(l),
+                                                               K + kExt);
+    count_launches(1);
   }
   mlp_unpack_grads_kernel<<<4 * 152, 256, 0, st>>>(dwx, d_theta);
   mlp_encode_bwd_kernel<<<(n_gaussians + 127) / 128, 128, 0, st>>>(means, denc, n_gaussians,
@@ -1239,24 +1503,11 @@ extern "C" gftorf_status gftorf_mlp_export(int32_t n_gaussians, int32_t n_frames
     return GFTORF_ERR_WORKSPACE;
   const size_t Mp = (size_t)L.M_pad, M = (size_t)L.M;
   size_t off, bytes;
-  if (what == 0 || what == 1) {  // from the kept transposed copies
-    if (what == 1 && (layer < 0 || layer >= kDepth)) return GFTORF_ERR_ARG;
-    if (M == 0) return GFTORF_OK;
-    const int rows = what == 0 ? kIn : kW;
-    const __nv_bfloat16* src =
-        what == 0 ? ptr<__nv_bfloat16>(workspace, L.off_encT)
-                  : ptr<__nv_bfloat16>(workspace, L.off_ht) + (size_t)layer * kW * Mp;
-    mlp_untranspose_kernel<<<4 * 152, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        src, rows, (int)Mp, (int)M, static_cast<__nv_bfloat16*>(dst));
-    count_launches(1);
-    return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
-  }
+  if ((what == 1 || what == 2) && (layer < 0 || layer >= kDepth)) return GFTORF_ERR_ARG;
   switch (what) {
-    case 2:
-      if (layer < 0 || layer >= kDepth) return GFTORF_ERR_ARG;
-      off = L.off_dz + (size_t)layer * Mp * kW * 2;
-      bytes = M * kW * 2;
-      break;
+    case 0: off = L.off_enc, bytes = M * kIn * 2; break;
+    case 1: off = L.off_h + (size_t)layer * Mp * kW * 2, bytes = M * kW * 2; break;
+    case 2: off = L.off_dz + (size_t)layer * Mp * kW * 2, bytes = M * kW * 2; break;
     case 3: off = L.off_denc, bytes = M * kIn * 4; break;
     default: return GFTORF_ERR_ARG;
   }

@@ -155,6 +155,8 @@ def test_mlp_calls_reject_bad_arguments_on_host(lib):
     assert L.gftorf_mlp_workspace_size(-1, 1) == 0
     assert L.gftorf_mlp_workspace_size(10, 0) == 0
     assert L.gftorf_mlp_workspace_size(10, 65) == 0
+    assert L.gftorf_mlp_workspace_size(1 << 26, 2) == 0       # 2^27 rows
+    assert L.gftorf_mlp_workspace_size((1 << 26) - 1, 2) > 0
     small = L.gftorf_mlp_workspace_size(1000, 2)
     assert small > 0 and small % 256 == 0
     assert L.gftorf_mlp_workspace_size(2000, 2) > small

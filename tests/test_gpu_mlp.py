@@ -226,11 +226,13 @@ def test_fused_inference_equals_layer_by_layer_forward(N, B):
     np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
 
 
-@pytest.mark.parametrize("N,B", [(300, 2), (3000, 3)])
+@pytest.mark.parametrize("N,B", [(300, 2), (3000, 3), (77, 1), (40000, 2)])
 def test_fused_training_forward_keeps_what_the_layerwise_one_keeps(N, B):
     """The fused training forward stores the same transposed activations,
-    encoding and ReLU masks as the one-GEMM-per-layer forward, so the same
-    backward follows."""
+    encoding and ReLU masks as the one-GEMM-per-layer forward, and the fused
+    backward chain forms the same dZ of every layer and the same encoding
+    gradient (same operands, same MMA order): bit-identical.  (40000, 2):
+    more tile pairs than SMs, so CTAs loop; (77, 1): one ragged tile.)"""
     theta, means, times = _case(N, B, 60 + N)
     net = mlp.DeformationMLP(N, B, 0.2)
     th = torch.as_tensor(theta, device="cuda")
@@ -242,7 +244,7 @@ def test_fused_training_forward_keeps_what_the_layerwise_one_keeps(N, B):
         d = net.forward(th, mu, times).clone()
         keep = [net.export("enc").clone()] + [net.export("H", l).clone() for l in range(8)]
         g, m = net.backward(th, mu, times, dd)
-        dz = [net.export("dZ", l).clone() for l in range(8)]
+        dz = [net.export("dZ", l).clone() for l in range(8)] + [net.export("d_enc").clone()]
         torch.cuda.synchronize()
         return d, keep, g.clone(), m.clone(), dz
 
@@ -262,7 +264,33 @@ def test_fused_training_forward_keeps_what_the_layerwise_one_keeps(N, B):
     for (W, b_), (Wr, br) in zip(omlp.unpack(got[2].double().cpu().numpy()),
                                  omlp.unpack(ref[2].double().cpu().numpy())):
         assert _rel(W, Wr) < 1e-6 and _rel(b_, br) < 1e-6
-    assert _rel(got[3].double().cpu().numpy(), ref[3].double().cpu().numpy()) < 1e-6
+    np.testing.assert_array_equal(got[3].cpu().numpy(), ref[3].cpu().numpy())
+
+
+def test_fused_backward_bounded_waits():
+    """The fused backward's waits run out under injection: timeout in the
+    status word, the context stays usable, and the next backward matches."""
+    N, B = 100, 1
+    theta, means, times = _case(N, B, 45)
+    net = mlp.DeformationMLP(N, B, 0.2)
+    th = torch.as_tensor(theta, device="cuda")
+    mu = torch.as_tensor(means, device="cuda")
+    dd = torch.as_tensor(np.random.default_rng(5).standard_normal((B, N, 3)).astype(np.float32),
+                         device="cuda")
+    net.forward(th, mu, times)
+    g_ref, m_ref = (t.clone() for t in net.backward(th, mu, times, dd))
+    assert net.read_status() == gftorf.OK
+    mlp.debug_inject(1)
+    try:
+        net.backward(th, mu, times, dd)
+        assert net.read_status() == gftorf.ERR_TIMEOUT
+    finally:
+        mlp.debug_inject(0)
+    net.forward(th, mu, times)
+    g, m = net.backward(th, mu, times, dd)
+    assert net.read_status() == gftorf.OK
+    assert _rel(g.double().cpu().numpy(), g_ref.double().cpu().numpy()) < 1e-6
+    np.testing.assert_array_equal(m.cpu().numpy(), m_ref.cpu().numpy())
 
 
 def test_fused_inference_bounded_waits():
