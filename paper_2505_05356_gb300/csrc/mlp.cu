@@ -60,7 +60,8 @@ struct GemmArgs {
   int ldf;
   uint32_t* mbits;            // ReLU masks, one bit per unit, [rows][8] words:
                               // written by EPI_HIDDEN, read by EPI_MASK
-  float* dbias;               // EPI_MASK: column sums of the stored dZ added at dbias[n ldb]
+  float* dbias;               // EPI_PARTIAL with an MN-major A: A's column sums over the
+                              // CTA's rows (the bias gradient) added at dbias[n ldb]
   int ldb;
   int inject_no_loads;        // test hook: the producer issues nothing (waits run out)
   unsigned long long wait_ns; // limit of one mbarrier wait
@@ -77,6 +78,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -225,17 +229,22 @@ __device__ __forceinline__ void store_row_bf16(__nv_bfloat16* dst, const float* 
 }
 
 // 32 columns [n, n + 32) of output row m
+// bf16_rn(v) > 0 for v >= 0 (or -0): v above 2^-134, half the smallest BF16
+// subnormal (ties round to even, i.e. to zero)
+__device__ __forceinline__ uint32_t relu_bits(const float* v) {
+  uint32_t bits = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) bits |= (v[j] > 0x1p-134f ? 1u : 0u) << j;
+  return bits;
+}
+
 template <int EPI>
-__device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float* v, float* s_db) {
+__device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float* v) {
   if (EPI == EPI_HIDDEN || EPI == EPI_MASK) {
     if (EPI == EPI_HIDDEN) {
-      uint32_t bits = 0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        v[j] = fmaxf(v[j] + __ldg(p.bias + n + j), 0.f);
-        bits |= (__bfloat162float(__float2bfloat16_rn(v[j])) > 0.f ? 1u : 0u) << j;
-      }
-      p.mbits[(size_t)m * (kW / 32) + n / 32] = bits;
+      for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + __ldg(p.bias + n + j), 0.f);
+      p.mbits[(size_t)m * (kW / 32) + n / 32] = relu_bits(v);
     } else {
       const uint32_t bits = __ldg(p.mbits + (size_t)m * (kW / 32) + n / 32);
 #pragma unroll
@@ -243,24 +252,6 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, int m, int n, float*
         if (!((bits >> j) & 1u)) v[j] = 0.f;
     }
     store_row_bf16(p.out_b + (size_t)m * p.ldo + n, v);
-    if (EPI == EPI_MASK) {
-      // bias gradient: the warp's column sums of the stored (rounded) dZ by
-      // recursive halving (lane L ends with column n + L), one shared atomic
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
-      const int lane = threadIdx.x & 31;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < off; ++i) {
-          const float keep = up ? v[i + off] : v[i];
-          const float send = up ? v[i] : v[i + off];
-          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-      }
-      atomicAdd(s_db + n + lane, v[0]);
-    }
   } else if (EPI == EPI_HEAD) {
     if (m < p.rows_valid)
       for (int j = 0; j < 3; ++j) p.out_f[(size_t)m * 3 + j] = v[j] + __ldg(p.bias + j);
@@ -298,7 +289,7 @@ struct GemmShape {
   static constexpr int A_BYTES = MT * BM * BK * 2, B_BYTES = BN * BK * 2;
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr uint32_t TCOLS = MT * BN < 32 ? 32 : MT * BN;
-  static constexpr int SMEM = kStages * STAGE + 1024 + 256 + 1024;  // + bias column sums
+  static constexpr int SMEM = kStages * STAGE + 1024 + 256;
 };
 
 template <int BN, int EPI, int MT, int MNA, int MNB>
@@ -313,8 +304,11 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * STAGE);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
-  float* s_db = reinterpret_cast<float*>(smem + kStages * STAGE + 256);  // [256]
+  int* s_ok = reinterpret_cast<int*>(slot + 1);  // the column-sum warps' shared wait outcome
   const uint32_t sbase = smem_u32(smem);
+  // the epilogue warps sum A's columns from each stage while the MMAs run
+  // (the weight-gradient GEMMs are bound by HBM; their epilogue warps idle)
+  constexpr bool COLSUM = EPI == EPI_PARTIAL && MNA && MT == 2;
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * kStages,
                  done = full0 + 16 * kStages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -325,14 +319,10 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, COLSUM ? 2 : 1);  // (+ the column-sum warps)
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (EPI == EPI_MASK && threadIdx.x < 128) {
-    s_db[threadIdx.x] = 0.f;
-    s_db[threadIdx.x + 128] = 0.f;
   }
   if (warp == 0) tmem_alloc(smem_u32(slot), TCOLS);
   tc_fence_before();
@@ -396,8 +386,35 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
       umma_commit(done);  // completes once every MMA issued above has
     }
   } else {
+    float cs0 = 0.f, cs1 = 0.f;  // COLSUM: columns 2 tid, 2 tid + 1 of A
+    bool cs_ok = true;
+    if (COLSUM) {
+      // A's 64-column chunk tid / 32, 4-byte word (tid % 32) of each 128-byte
+      // row (chunk (tid % 32) / 4 of the row, under the swizzle)
+      const int tid = threadIdx.x;
+      const uint32_t col_off = (uint32_t)(tid >> 5) * 8192u + 4u * (uint32_t)(tid & 3);
+      const uint32_t chunk = (uint32_t)((tid & 31) >> 2);
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % kStages;
+        // one thread waits, the others follow the barrier (all take one branch)
+        if (threadIdx.x == 0)
+          *s_ok = mbar_wait(full0 + 8 * s, (uint32_t)(i / kStages) & 1u, p.status, p.wait_ns);
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (!(cs_ok = *s_ok != 0)) break;
+        const uint8_t* st = smem + s * STAGE + col_off;
+#pragma unroll 8
+        for (int r = 0; r < BK; ++r) {
+          const uint32_t w = *reinterpret_cast<const uint32_t*>(
+              st + (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (uint32_t)(r & 7)) << 4));
+          cs0 += __uint_as_float(w << 16);
+          cs1 += __uint_as_float(w & 0xFFFF0000u);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // all four warps have read stage s
+        if (threadIdx.x == 0) mbar_arrive(empty0 + 8 * s);
+      }
+    }
     // epilogue: warp w owns TMEM lanes / output rows 32 w .. 32 w + 31
-    if (nkb > 0 && mbar_wait(done, 0, p.status, p.wait_ns)) {
+    if (nkb > 0 && cs_ok && mbar_wait(done, 0, p.status, p.wait_ns)) {
       tc_fence_after();
 #pragma unroll 1
       for (int t = 0; t < MT; ++t) {
@@ -406,15 +423,12 @@ __global__ void __launch_bounds__(192, MT == 2 ? 1 : 2)
         for (int c = 0; c < BN / 32; ++c) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * BN + c * 32), v);
-          epilogue<EPI>(p, m, n0 + c * 32, v, s_db);
+          epilogue<EPI>(p, m, n0 + c * 32, v);
         }
       }
-    }
-    if (EPI == EPI_MASK) {  // the CTA's bias-gradient column sums, one global atomic each
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (nkb > 0) {
-        atomicAdd(p.dbias + (size_t)threadIdx.x * p.ldb, s_db[threadIdx.x]);
-        atomicAdd(p.dbias + (size_t)(threadIdx.x + 128) * p.ldb, s_db[threadIdx.x + 128]);
+      if (COLSUM) {
+        atomicAdd(p.dbias + (size_t)(2 * threadIdx.x) * p.ldb, cs0);
+        atomicAdd(p.dbias + (size_t)(2 * threadIdx.x + 1) * p.ldb, cs1);
       }
     }
   }
@@ -658,9 +672,6 @@ __device__ __forceinline__ void store_act32(uint8_t* act, int r, int c, const fl
     *reinterpret_cast<uint4*>(act + act_off(r, c + 8 * q)) = u;
   }
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 // warps 0-7: epilogue (warp w: TMEM lanes / rows 32 (w % 4) .. + 31, columns
 // 128 (w / 4) .. + 127); warp 8: TMA; warp 9: MMA
@@ -826,13 +837,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
               }
               store_act32(act, r, c, v);
               const int m = (pr * kPair + t) * BM + r;
-              if (TRAIN && m < keep.Mp) {
-                uint32_t bits = 0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                  bits |= (__bfloat162float(__float2bfloat16_rn(v[j])) > 0.f ? 1u : 0u) << j;
-                keep.bits[((size_t)l * keep.Mp + m) * (kW / 32) + c / 32] = bits;
-              }
+              if (TRAIN && m < keep.Mp)
+                keep.bits[((size_t)l * keep.Mp + m) * (kW / 32) + c / 32] = relu_bits(v);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
@@ -873,19 +879,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
 // s = 1..7 form dZ_{7-s} = (dZ_{8-s} W_{8-s}) * mask_{7-s}; step 8 forms the
 // encoding's gradient dZ_0 W_0 (FP32).  Each dZ tile goes to shared memory as
 // the next step's operand and from there by TMA (maps.act, row-major) to
-// global memory for the weight gradients; its column sums (bias gradients)
-// accumulate per CTA.  The same operands and order as the one-GEMM-per-layer
-// backward: bit-identical dZ.
-constexpr int kBwdStages = 2;
-constexpr int kBwdSmem = kPair * kActBytes + kBwdStages * kWStageBytes + kDepth * kW * 4 + 1024 +
-                         256;
+// global memory for the weight gradients (whose GEMMs also form the bias
+// gradients, the column sums).  The same operands and order as the
+// one-GEMM-per-layer backward: bit-identical dZ.
+constexpr int kBwdStages = kFusedStages;
+constexpr int kBwdSmem = kFusedSmem;
 
 struct FusedBwdArgs {
   const float* dd;      // dL/d(delta) [M][3]
   const uint32_t* bits; // ReLU masks [layer][Mp][8]
   float* denc;          // [Mp][128] (out)
-  float* dbias[kDepth]; // bias-gradient column of each layer (out, accumulated)
-  int ldb[kDepth];
   int M, Mp, n_tiles;
 };
 
@@ -895,8 +898,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  float* s_db = reinterpret_cast<float*>(smem + kPair * kActBytes + kBwdStages * kWStageBytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_db + kDepth * kW);
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem + kPair * kActBytes + kBwdStages * kWStageBytes);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * kBwdStages + 2 * kPair);
   int* s_ok = reinterpret_cast<int*>(slot + 1);
   const uint32_t act_s = smem_u32(smem), w_s = act_s + kPair * kActBytes;
@@ -916,7 +919,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = threadIdx.x; i < kDepth * kW; i += blockDim.x) s_db[i] = 0.f;
   if (warp == 0) tmem_alloc(smem_u32(slot), (uint32_t)(kPair * kW));
   tc_fence_before();
   __syncthreads();
@@ -1019,20 +1021,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
               const uint32_t mk = m < a.Mp ? __ldg(bits + c / 32) : 0u;
 #pragma unroll
               for (int k = 0; k < 32; ++k)
-                v[k] = ((mk >> k) & 1u) ? __bfloat162float(__float2bfloat16_rn(v[k])) : 0.f;
+                if (!((mk >> k) & 1u)) v[k] = 0.f;
               store_act32(act, r, c, v);
-              // column sums of the warp's rows (recursive halving; lane L: column c + L)
-#pragma unroll
-              for (int off = 16; off > 0; off >>= 1) {
-                const bool up = (lane & off) != 0;
-#pragma unroll
-                for (int i = 0; i < off; ++i) {
-                  const float keep = up ? v[i + off] : v[i];
-                  const float send = up ? v[i] : v[i + off];
-                  v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-                }
-              }
-              atomicAdd(s_db + j * kW + c + lane, v[0]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
@@ -1064,13 +1054,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         }
     }
     if ((threadIdx.x & 31) == 0) bulk_wait_all();  // the stores are done
-    // the CTA's bias-gradient sums, one global atomic per (layer, column)
-    asm volatile("bar.sync 1, 256;" ::: "memory");
-    if (ok)
-      for (int i = threadIdx.x; i < kDepth * kW; i += 256) {
-        const int j = i / kW, n = i - j * kW;
-        if (s_db[i] != 0.f) atomicAdd(a.dbias[j] + (size_t)n * a.ldb[j], s_db[i]);
-      }
   }
   tc_fence_before();
   __syncthreads();
@@ -1417,7 +1400,6 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     FusedBwdArgs fa;
     memset(&fa, 0, sizeof(fa));
     fa.dd = d_delta, fa.bits = bits, fa.denc = denc;
-    for (int l = 0; l < kDepth; ++l) fa.dbias[l] = dbias_of(l), fa.ldb[l] = ldb_of(l);
     fa.M = L.M, fa.Mp = Mp, fa.n_tiles = mt;
     const int n_pairs = (mt + kPair - 1) / kPair;
     mlp_fused_bwd_kernel<<<n_pairs < sms ? n_pairs : sms, kFusedThreads, kBwdSmem, st>>>(
@@ -1438,7 +1420,6 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
       a.rows_valid = Mp, a.cols_valid = kW;
       a.out_b = dz(l - 1), a.ldo = kW;
       a.mbits = bits + (size_t)(l - 1) * Mp * (kW / 32);
-      a.dbias = dbias_of(l - 1), a.ldb = ldb_of(l - 1);
       a.status = status, a.inject_no_loads = inj_loads, a.wait_ns = wait_ns;
       if (!gemm<256, EPI_MASK>(ma, mb, a, mt, 1, 1, st)) return GFTORF_ERR_CUDA;
     }
@@ -1466,6 +1447,7 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     a.kb_total = kb_rows, a.kb_per_split = per_split;
     a.rows_valid = kW, a.cols_valid = K;
     a.out_f = part, a.ldf = K;
+    a.dbias = dbias_of(l), a.ldb = ldb_of(l);  // the column sums of dZ_l
     a.status = status, a.inject_no_loads = inj_loads, a.wait_ns = wait_ns;
     if (!(l == 0 ? gemm<kIn, EPI_PARTIAL, 2, 1, 1>(ma, mb, a, 1, 1, splits, st)
                  : gemm<kW, EPI_PARTIAL, 2, 1, 1>(ma, mb, a, 1, 1, splits, st)))
