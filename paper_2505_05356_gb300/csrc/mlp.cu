@@ -560,31 +560,48 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// d(encoding) -> d(means), summed over the frames in order
-__global__ void mlp_encode_bwd_kernel(const float* __restrict__ means,
-                                      const float* __restrict__ denc, int N, int B,
-                                      float inv_scale, float* __restrict__ dmeans) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+// dL/d(means) from the encoding's gradient (the position part, columns
+// 0..62), summed over the frames: one warp per Gaussian.  The frames' rows
+// are summed first (coalesced, lanes over columns), then each lane applies
+// the derivative of its columns' encoding -- d sin(f pi x)/dx = f pi cos(f pi x),
+// d cos(f pi x)/dx = -f pi sin(f pi x) -- and the warp reduces per axis.
+__global__ void __launch_bounds__(256)
+    mlp_encode_bwd_kernel(const float* __restrict__ means, const float* __restrict__ denc, int N,
+                          int B, float inv_scale, float* __restrict__ dmeans) {
+  const int g = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (g >= N) return;
-  float x[3], acc[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) x[a] = means[(size_t)g * 3 + a] * inv_scale;
+  float d0 = 0.f, d1 = 0.f;  // columns lane and lane + 32, summed over the frames
   for (int b = 0; b < B; ++b) {
-    const float* d = denc + ((size_t)b * N + g) * kIn;
+    const float* row = denc + ((size_t)b * N + g) * kIn;
+    d0 += __ldg(row + lane);
+    if (lane < 31) d1 += __ldg(row + 32 + lane);
+  }
+  float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      float s = d[a], f = 1.f;
-#pragma unroll
-      for (int l = 0; l < kFreq; ++l, f *= 2.f) {
-        float sn, cs;
-        sincospif(f * x[a], &sn, &cs);
-        s += f * 3.14159265358979323846f * (cs * d[3 + 6 * l + a] - sn * d[6 + 6 * l + a]);
-      }
-      acc[a] += s;
+  for (int h = 0; h < 2; ++h) {
+    const int c = lane + 32 * h;
+    const float d = h ? d1 : d0;
+    if (c < 3) {
+      acc[c] += d;
+    } else if (c < 63) {
+      const int l = (c - 3) / 6, w = (c - 3) - 6 * l, a = w < 3 ? w : w - 3;
+      const float f = (float)(1 << l);
+      const float x = __ldg(means + (size_t)g * 3 + a) * inv_scale;
+      float sn, cs;
+      sincospif(f * x, &sn, &cs);
+      const float term = f * 3.14159265358979323846f * (w < 3 ? cs * d : -sn * d);
+      acc[0] += a == 0 ? term : 0.f;
+      acc[1] += a == 1 ? term : 0.f;
+      acc[2] += a == 2 ? term : 0.f;
     }
   }
 #pragma unroll
-  for (int a = 0; a < 3; ++a) dmeans[(size_t)g * 3 + a] = acc[a] * inv_scale;
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], off);
+  if (lane == 0)
+    for (int a = 0; a < 3; ++a) dmeans[(size_t)g * 3 + a] = acc[a] * inv_scale;
 }
 
 // extended weight gradients [rows][K + ext] -> packed d_theta (W then b)
@@ -1457,8 +1474,8 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
     count_launches(1);
   }
   mlp_unpack_grads_kernel<<<4 * 152, 256, 0, st>>>(dwx, d_theta);
-  mlp_encode_bwd_kernel<<<(n_gaussians + 127) / 128, 128, 0, st>>>(means, denc, n_gaussians,
-                                                                   n_frames, inv_scale, d_means);
+  mlp_encode_bwd_kernel<<<(n_gaussians + 7) / 8, 256, 0, st>>>(means, denc, n_gaussians,
+                                                               n_frames, inv_scale, d_means);
   count_launches(2);
   (void)times;
   return cudaGetLastError() == cudaSuccess ? GFTORF_OK : GFTORF_ERR_CUDA;
