@@ -159,12 +159,13 @@ def test_persistent_mode_bit_identical(ppt):
     np.testing.assert_array_equal(a["nlast"], b["nlast"])
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 32)])
-def test_pixels_per_thread_bit_identical(tile):
+@pytest.mark.parametrize("tile,freqs", [((16, 16), [30e6]), ((8, 8), [30e6]),
+                                        ((16, 32), [30e6]), ((16, 32), [30e6, 80e6])])
+def test_pixels_per_thread_bit_identical(tile, freqs):
     """1, 2 or 4 pixels per compositing thread: same forward bit for bit,
     same gradients up to atomic summation order."""
     sc = scenes.make_scene("batch_300k", 8, n=4000, width=72, height=56, frames=2,
-                           tile=tile)
+                           tile=tile, freqs_hz=freqs)
     dout = scenes.random_dout(sc, 5)
     ref = run_gpu(sc, dout, pixels_per_thread=1)
     for ppt in (2, 4):
