@@ -297,14 +297,20 @@ __device__ __forceinline__ void render_tile_fwd(
     for (int j = 0; j < cnt && done != ALL; ++j) {
       const Real* r = s_rec + j * RS;
       const Column<Real> col = column_of(r, fpx);
+      // the exponents of all PPT pixels first (independent chains), then
+      // each pixel's decisions
+      Real lg[PPT], oG[PPT];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        lg[k] = log2_oG(r, col, sub_rn(r[1], fpy[k]));
+        oG[k] = ex2_approx(lg[k]);
+      }
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (done & (1u << k)) continue;
         if (COUNT) ++evals;
-        const Real lg = log2_oG(r, col, sub_rn(r[1], fpy[k]));
-        const Real oG = ex2_approx(lg);
-        const Real alpha = oG < amax ? oG : amax;
-        if (lg > r[5] || alpha < amin) continue;
+        const Real alpha = oG[k] < amax ? oG[k] : amax;
+        if (lg[k] > r[5] || alpha < amin) continue;
         const Real tn = T[k] * (Real(1) - alpha);
         if (tn < tmin) {
           done |= 1u << k;
