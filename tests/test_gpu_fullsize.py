@@ -70,3 +70,60 @@ def test_full_size_sampled_pixels(tile, ppt, mode):
         g_ora = ora.backward(sc, dout.astype(np.float64))
         for k, (nrm, elem) in grads_close(g, g_ora).items():
             assert nrm <= 1e-3 and elem <= 1e-3, (k, nrm, elem)
+
+
+def test_mlp_full_size_sampled_rows():
+    """The deformation MLP at the benchmark's size (300k Gaussians x 16
+    timesteps = 4.8M rows) in the fused kernels bench.py times: offsets of
+    sampled rows against the BF16 oracle, the inference kernel bit-identical to
+    the training forward, and the gradients of a loss that only sees the
+    sampled rows (dL/d(delta) zero elsewhere), which the oracle computes
+    exactly from those rows alone.  Bars: the whole-network ones (output
+    2e-3, gradients 2.5e-2 per layer, norm-wise)."""
+    from oracle import mlp as omlp
+    from paper_2505_05356_gb300 import mlp
+
+    N, B, K = 300_000, 16, 384
+    theta = scenes.init_mlp_params(0, head_std=0.05)
+    rng = np.random.default_rng(21)
+    means = rng.uniform(-2.0, 4.0, (N, 3)).astype(np.float32)
+    times = list(np.linspace(0.0, 1.0, B).astype(np.float32))
+    inv = np.float32(1.0 / mlp.unambiguous_range(30e6))
+    rows = np.sort(rng.choice(N * B, K, replace=False))
+    dd = np.zeros((B * N, 3), np.float32)
+    dd[rows] = rng.standard_normal((K, 3)).astype(np.float32)
+
+    net = mlp.DeformationMLP(N, B, float(inv))
+    th = torch.as_tensor(theta, device="cuda")
+    mu = torch.as_tensor(means, device="cuda")
+    delta = net.forward(th, mu, times).clone()
+    d_theta, d_means = net.backward(th, mu, times, torch.as_tensor(dd.reshape(B, N, 3),
+                                                                   device="cuda"))
+    infer = net.infer(th, mu, times)
+    torch.cuda.synchronize()
+    net.check()
+    np.testing.assert_array_equal(infer.cpu().numpy(), delta.cpu().numpy())
+
+    # the oracle on the sampled rows only
+    b_of, g_of = rows // N, rows % N
+    enc = np.concatenate([omlp.encode(means[g:g + 1], np.asarray([times[b]], np.float64), inv,
+                                      single=True) for b, g in zip(b_of, g_of)])
+    d_o, acts = omlp.forward(theta.astype(np.float64), enc, bf16=True)
+    got = delta.double().cpu().numpy().reshape(-1, 3)[rows]
+    assert np.linalg.norm(got - d_o) / np.linalg.norm(d_o) < 2e-3
+    g_o, denc = omlp.backward(theta.astype(np.float64), acts, dd[rows].astype(np.float64),
+                              bf16=True)
+    for l, ((W, b), (Wo, bo)) in enumerate(zip(omlp.unpack(d_theta.double().cpu().numpy()),
+                                              omlp.unpack(g_o))):
+        assert np.linalg.norm(W - Wo) / np.linalg.norm(Wo) < 2.5e-2, l
+        assert np.linalg.norm(b - bo) / np.linalg.norm(bo) < 2.5e-2, l
+    # dL/d(means) of the sampled rows' Gaussians (all other rows contribute 0)
+    dm_o = np.zeros((N, 3))
+    for i, (b, g) in enumerate(zip(b_of, g_of)):
+        dm_o[g] += omlp.encode_backward(denc[i:i + 1], means[g:g + 1], [times[b]], inv,
+                                        single=True)[0]
+    gs = np.unique(g_of)
+    dm = d_means.double().cpu().numpy()
+    assert np.linalg.norm(dm[gs] - dm_o[gs]) / np.linalg.norm(dm_o[gs]) < 2.5e-2
+    others = np.setdiff1d(np.arange(N), gs)
+    assert np.all(dm[others] == 0.0)
