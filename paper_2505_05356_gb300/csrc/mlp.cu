@@ -3,26 +3,31 @@
 // 256 with ReLU, a linear head to the 3 offset components, forward and
 // backward for B frames x N Gaussians (rows m = b N + g).
 //
-// Every matrix product is one BF16 GEMM kernel, D[M x N] = A[M x K] B[N x K]^T
-// with FP32 accumulation: operands K-major in global memory, brought into
-// shared memory by TMA (128-byte swizzle, a 2-stage mbarrier pipeline, two CTAs
-// per SM so that one's epilogue overlaps the other's loads and MMAs), one
-// elected thread issuing tcgen05.mma into a TMEM accumulator, four epilogue
-// warps draining TMEM with tcgen05.ld and applying the layer's epilogue:
-//   forward hidden layer   H = relu(D + b) -> H (row-major) and H^T
-//   forward head           delta = D + b (FP32)
-//   backward, hidden       dZ = D * (H_prev > 0) -> dZ and dZ^T (the ReLU
-//                          masks kept as bits by the forward)
-//   backward, first layer  d(encoding) = D (FP32)
-//   weight gradient        partial dW over a share of the rows (the 256
-//                          output rows as two M = 128 accumulators sharing
-//                          each B tile, so both operands are read once),
-//                          then a reduction over the shares
-// The transposed copies make the weight-gradient GEMM K-major as well
-// (dW = dZ^T H: both operands have the rows of the batch as their reduction
-// dimension); the bias gradient (column sums of dZ) is reduced in the
-// epilogue that writes dZ.  Waits on mbarriers are bounded (about 2 s): a wait that runs out
-// records GFTORF_ERR_TIMEOUT in the status word and the CTA winds down.
+// Two kinds of kernel, both BF16 operands with FP32 accumulation in TMEM
+// (tcgen05.mma issued by one elected thread, operand tiles in shared memory
+// in the 128-byte swizzled layout, TMA loads completing on mbarriers):
+//  * fused all-layer kernels over pairs of 128-row tiles per CTA (one CTA per
+//    SM, the two tiles' accumulators filling TMEM, the epilogue of one tile
+//    overlapping the MMAs of the other; a TMA warp streams the weights, an
+//    MMA warp, 8 epilogue warps):
+//      forward        every layer's output (bias, ReLU, BF16) written back
+//                     into the tile as the next layer's operand; training:
+//                     each tile also TMA-stored row-major (H_l, the encoding)
+//                     and the ReLU masks as bits; inference: nothing kept
+//      dZ chain       dZ_7 = (dZ_head W_head) * mask_7, ..., dZ_0, then
+//                     d(encoding) = dZ_0 W_0 (FP32), each dZ tile TMA-stored
+//                     row-major
+//  * a tiled GEMM (TMA pipeline, 4 epilogue warps), for the weight gradients
+//    dW_l = dZ_l^T H_{l-1}: the batch rows are the reduction dimension, so
+//    both operands are read MN-major straight from the row-major dZ_l and
+//    H_{l-1} (transpose bits of the instruction descriptor), the 256 output
+//    rows as two M = 128 accumulators sharing each B tile, partial sums per
+//    share of rows reduced afterwards; its epilogue warps, idle during the
+//    main loop, sum dZ_l's columns (the bias gradient) from each stage.  The
+//    same GEMM with other epilogues runs the one-GEMM-per-layer forward and
+//    dZ chain, kept as a test mode the fused kernels are checked against.
+// Waits on mbarriers are bounded (about 2 s): a wait that runs out records
+// GFTORF_ERR_TIMEOUT in the status word and the CTA winds down.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>

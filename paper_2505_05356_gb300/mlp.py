@@ -161,5 +161,6 @@ class DeformationMLP:
 def debug_inject(mode: int):
     """Test hooks: 1 = the kernels' load warps issue nothing, so their bounded
     waits run out (GFTORF_ERR_TIMEOUT, no GPU fault); 2 = the training
-    forward runs one GEMM per layer instead of fused; 0 = normal."""
+    forward and the backward's dZ chain run one GEMM per layer instead of
+    fused; 0 = normal."""
     _lib().gftorf_mlp_debug_inject(int(mode))
