@@ -1,6 +1,8 @@
-"""Parity at the benchmark's full size (300k dynamic Gaussians, 640x480, 16
-timesteps) in the launch configurations bench.py times, on sampled pixels the
-oracle computes one by one, and gradients of a loss that only sees those
+"""Parity at full size -- the benchmark's workload (300k dynamic Gaussians,
+640x480, 16 timesteps) in the launch configurations bench.py times, and the
+other full-size workloads (100k Gaussians at 640x480; 500k Gaussians at
+640x576 with two modulation frequencies, 8 timesteps) -- on sampled pixels
+the oracle computes one by one, and gradients of a loss that only sees those
 pixels (exactly computable by the oracle)."""
 import numpy as np
 import pytest
@@ -16,8 +18,9 @@ K_PIX = 24  # sampled pixels per frame
 
 
 def _gpu(sc, tile, ppt, mode, dout=None):
-    r = gftorf.Renderer(sc.n, sc.frames, sc.width, sc.height, 1, 4, tile=tile,
-                        render_mode=mode, pixels_per_thread=ppt)
+    r = gftorf.Renderer(sc.n, sc.frames, sc.width, sc.height, len(sc.sensor.freqs_hz),
+                        len(sc.sensor.offsets_rad), tile=tile, render_mode=mode,
+                        pixels_per_thread=ppt)
     p = gftorf.params_from_scene(sc)
     fr, se, co = (gftorf.frames_from_scene(sc), gftorf.sensor_from_scene(sc),
                   gftorf.consts_from_scene(sc))
@@ -34,13 +37,22 @@ def _gpu(sc, tile, ppt, mode, dout=None):
     return out.double().cpu().numpy(), g, cnt
 
 
-@pytest.mark.parametrize("tile,ppt,mode", [((16, 16), 4, 0), ((8, 8), 2, 1), ((16, 32), 4, 0)])
-def test_full_size_sampled_pixels(tile, ppt, mode):
-    sc = scenes.make_scene("batch_300k", 0, tile=tile)
-    assert (sc.n, sc.frames, sc.width, sc.height) == (300_000, 16, 640, 480)
+FULL = [  # (workload, expected (n, frames, width, height), tile, ppt, mode, gradients)
+    ("batch_300k", (300_000, 16, 640, 480), (16, 16), 4, 0, True),
+    ("batch_300k", (300_000, 16, 640, 480), (8, 8), 2, 1, False),
+    ("batch_300k", (300_000, 16, 640, 480), (16, 32), 4, 0, False),
+    ("dynamic_100k", (100_000, 1, 640, 480), (16, 32), 4, 1, True),
+    ("twofreq_500k", (500_000, 8, 640, 576), (16, 32), 4, 1, True),
+]
+
+
+@pytest.mark.parametrize("name,size,tile,ppt,mode,full_grad", FULL)
+def test_full_size_sampled_pixels(name, size, tile, ppt, mode, full_grad):
+    sc = scenes.make_scene(name, 0, tile=tile)
+    assert (sc.n, sc.frames, sc.width, sc.height) == size
+    C = sc.n_channels
     pix = scenes.sample_pixels(sc, K_PIX, seed=9)
-    full_grad = tile == (16, 16)
-    dout = np.zeros((sc.frames, 5, sc.height, sc.width), np.float32)
+    dout = np.zeros((sc.frames, C, sc.height, sc.width), np.float32)
     rng = np.random.default_rng(10)
     refs = []
     for b in range(sc.frames):
@@ -48,17 +60,17 @@ def test_full_size_sampled_pixels(tile, ppt, mode):
                                            splats=ora.project(sc, b, ora.EPS_F32))
         refs.append((q, amb))
         keep = amb == 0
-        dout[b, :, pix[b, keep, 1], pix[b, keep, 0]] = rng.standard_normal((keep.sum(), 5))
+        dout[b, :, pix[b, keep, 1], pix[b, keep, 0]] = rng.standard_normal((keep.sum(), C))
     out, g, cnt = _gpu(sc, tile, ppt, mode, dout if full_grad else None)
-    assert cnt > 20_000_000  # tens of millions of (Gaussian, tile) instances
+    assert cnt > 2 * sc.n * sc.frames  # millions of (Gaussian, tile) instances per frame
     nflag, worst, kinds = 0, 0.0, {}
     for b in range(sc.frames):
         q, amb = refs[b]
         got = out[b][:, pix[b, :, 1], pix[b, :, 0]].T  # (K, C)
         keep = (amb & ora.AMB_VALUE) == 0
         nflag += int((~keep).sum())
-        for name, bit in ora.AMB.items():
-            kinds[name] = kinds.get(name, 0) + int(((amb & bit) != 0).sum())
+        for kind, bit in ora.AMB.items():
+            kinds[kind] = kinds.get(kind, 0) + int(((amb & bit) != 0).sum())
         scale = np.maximum(np.abs(q), np.sqrt((q ** 2).mean(axis=0, keepdims=True)) + 1e-30)
         err = np.abs(got - q) / scale
         worst = max(worst, float(err[keep].max()))
