@@ -361,6 +361,16 @@ typedef struct {
 gftorf_status gftorf_train_begin(gftorf_train_state* state, float* bg, int64_t n_bg,
                                  uint64_t seed, void* stream);
 
+/* The same for a shard of a batch whose frames are split over processes:
+ * bg[n_bg] receives values [bg_offset, bg_offset + n_bg) of the iteration's
+ * bg_stride values (k = (s - 1) bg_stride + bg_offset + i + 1), the slice the
+ * whole batch's draw would give these frames.  gftorf_train_begin is the
+ * case bg_offset = 0, bg_stride = n_bg.  GFTORF_ERR_ARG unless
+ * 0 <= bg_offset, bg_offset + n_bg <= bg_stride <= 2^40. */
+gftorf_status gftorf_train_begin_shard(gftorf_train_state* state, float* bg, int64_t n_bg,
+                                       uint64_t seed, int64_t bg_offset, int64_t bg_stride,
+                                       void* stream);
+
 /* Raw-sample L2 loss of a rendered batch (the L_q term of Eq. 9, without
  * SSIM): L = mean over frames, raw channels c < n_freq * n_offsets and
  * pixels of (out - target)^2.  out, target, dL_dout: device [B][C][H][W]
@@ -369,6 +379,14 @@ gftorf_status gftorf_train_begin(gftorf_train_state* state, float* bg, int64_t n
  * state->loss.  dims->dtype must be GFTORF_F32. */
 gftorf_status gftorf_l2_loss(const gftorf_dims* dims, const float* out, const float* target,
                              float* dL_dout, gftorf_train_state* state, void* stream);
+
+/* The same with the mean taken over `count` raw samples instead of this
+ * batch's M: for a shard of frames, count = the whole batch's raw samples,
+ * so that the shards' losses and gradients add up to the whole batch's.
+ * GFTORF_ERR_ARG unless count >= 1 and finite. */
+gftorf_status gftorf_l2_loss_scaled(const gftorf_dims* dims, const float* out,
+                                    const float* target, float* dL_dout,
+                                    gftorf_train_state* state, double count, void* stream);
 
 #define GFTORF_MAX_ADAM_GROUPS 12
 

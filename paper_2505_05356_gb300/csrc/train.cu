@@ -27,8 +27,11 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
+// values [offset, offset + n_bg) of the iteration's `stride` background
+// values (a shard of frames draws its own slice of the whole batch's)
 __global__ void __launch_bounds__(256)
-    train_begin_kernel(gftorf_train_state* st, float* bg, int n_bg, uint64_t seed) {
+    train_begin_kernel(gftorf_train_state* st, float* bg, int n_bg, uint64_t seed,
+                       uint64_t offset, uint64_t stride) {
   __shared__ int64_t s_step;
   if (threadIdx.x == 0) {
     s_step = st->step + 1;
@@ -37,7 +40,7 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   if (!bg) return;
-  const uint64_t base = (uint64_t)(s_step - 1) * (uint64_t)n_bg + 1;
+  const uint64_t base = (uint64_t)(s_step - 1) * stride + offset + 1;
   for (int i = threadIdx.x; i < n_bg; i += blockDim.x) {
     const uint32_t top = (uint32_t)(splitmix64_at(seed, base + i) >> 40);  // 24 bits
     // 2 u - 1 with u = top 2^-24: exact in single precision
@@ -141,29 +144,40 @@ int sm_count() {
 
 using namespace gftorf;
 
-extern "C" gftorf_status gftorf_train_begin(gftorf_train_state* state, float* bg, int64_t n_bg,
-                                            uint64_t seed, void* stream) {
+extern "C" gftorf_status gftorf_train_begin_shard(gftorf_train_state* state, float* bg,
+                                                  int64_t n_bg, uint64_t seed,
+                                                  int64_t bg_offset, int64_t bg_stride,
+                                                  void* stream) {
   gftorf::TraceRange trace_("gftorf_train_begin");
-  if (!state || n_bg < 0 || n_bg > kBgMax) return GFTORF_ERR_ARG;
+  if (!state || n_bg < 0 || n_bg > kBgMax || bg_offset < 0 || bg_offset + n_bg > bg_stride ||
+      bg_stride > ((int64_t)1 << 40))
+    return GFTORF_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(state) & 7) != 0) return GFTORF_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  train_begin_kernel<<<1, 256, 0, st>>>(state, n_bg ? bg : nullptr, (int)n_bg, seed);
+  train_begin_kernel<<<1, 256, 0, st>>>(state, n_bg ? bg : nullptr, (int)n_bg, seed,
+                                        (uint64_t)bg_offset, (uint64_t)bg_stride);
   count_launches(1);
   return last_status();
 }
 
-extern "C" gftorf_status gftorf_l2_loss(const gftorf_dims* dims, const float* out,
-                                        const float* target, float* dL_dout,
-                                        gftorf_train_state* state, void* stream) {
+extern "C" gftorf_status gftorf_train_begin(gftorf_train_state* state, float* bg, int64_t n_bg,
+                                            uint64_t seed, void* stream) {
+  return gftorf_train_begin_shard(state, bg, n_bg, seed, 0, n_bg > 0 ? n_bg : 0, stream);
+}
+
+extern "C" gftorf_status gftorf_l2_loss_scaled(const gftorf_dims* dims, const float* out,
+                                               const float* target, float* dL_dout,
+                                               gftorf_train_state* state, double count,
+                                               void* stream) {
   gftorf::TraceRange trace_("gftorf_l2_loss");
   if (!train_dims_ok(dims) || dims->dtype != GFTORF_F32 || !out || !target || !dL_dout ||
-      !state)
+      !state || !(count >= 1.0) || !std::isfinite(count))
     return GFTORF_ERR_ARG;
   const Layout L = train_layout(dims);
   const int64_t HW = (int64_t)L.W * L.H;
   const int64_t n_rows = (int64_t)L.B * L.C;
   const int FP = L.F * L.P;
-  const double M = (double)L.B * FP * (double)HW;
+  const double M = count;
   const bool vec = (HW & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(target) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(dL_dout) & 15) == 0;
@@ -172,6 +186,15 @@ extern "C" gftorf_status gftorf_l2_loss(const gftorf_dims* dims, const float* ou
                                                  HW, (float)(2.0 / M), 1.0 / M, vec ? 1 : 0);
   count_launches(1);
   return last_status();
+}
+
+extern "C" gftorf_status gftorf_l2_loss(const gftorf_dims* dims, const float* out,
+                                        const float* target, float* dL_dout,
+                                        gftorf_train_state* state, void* stream) {
+  if (!train_dims_ok(dims)) return GFTORF_ERR_ARG;
+  const Layout L = train_layout(dims);
+  const double M = (double)L.B * (L.F * L.P) * ((double)L.W * L.H);
+  return gftorf_l2_loss_scaled(dims, out, target, dL_dout, state, M, stream);
 }
 
 extern "C" gftorf_status gftorf_adam_step(const gftorf_adam_group* groups, int n_groups,

@@ -16,11 +16,19 @@ the linear parameters this renderer takes (the scale rate 5e-3 on
 log-scales times a typical scale of 0.05; the opacity rate 5e-2 on logits
 times 0.2, about the sigmoid's slope of 0.25 at opacity 0.5).  The
 projection box keeps opacity, scales and reflectivity valid.
+
+Frame shards (several processes, one GPU each): a loop over frames
+[frame_offset, frame_offset + B) of a batch of total_frames draws the
+background values the whole batch's draw gives those frames, normalises the
+loss by the whole batch's raw samples, and calls grad_hook on the parameter
+gradients between the backward and the update -- `shard.allreduce_sum_`
+sums them over the processes, so every process takes the same Adam step as
+the unsharded loop.
 """
 from __future__ import annotations
 
 import math
-from typing import Dict, Optional, Sequence
+from typing import Callable, Dict, Optional, Sequence
 
 import torch
 
@@ -45,8 +53,14 @@ class FitLoop:
                  n_freq: int = 1, n_offsets: int = 4, tile=(16, 16), pixels_per_thread=4,
                  render_mode=1, seed: int = 0, lrs: Optional[Dict[str, float]] = None,
                  bounds=None, headroom: float = 1.5, flags: int = 0,
-                 random_background: bool = True):
+                 random_background: bool = True, frame_offset: int = 0,
+                 total_frames: Optional[int] = None,
+                 grad_hook: Optional[Callable[[Dict[str, torch.Tensor]], None]] = None):
         B, C, H, W = targets.shape
+        total = B if total_frames is None else int(total_frames)
+        if frame_offset < 0 or frame_offset + B > total:
+            raise ValueError("frames [%d, %d) outside a batch of %d"
+                             % (frame_offset, frame_offset + B, total))
         n = params["means"].shape[0]
         self.r = gftorf.Renderer(n, B, W, H, n_freq, n_offsets, tile=tile,
                                  render_mode=render_mode, pixels_per_thread=pixels_per_thread,
@@ -66,37 +80,71 @@ class FitLoop:
         self.opt = gftorf.Adam(params, self.lrs, bounds if bounds is not None else BOUNDS)
         self.state = gftorf.new_train_state(targets.device)
         self.graph = None
+        self.update_graph = None
+        # the shard's place in the whole batch (the defaults: the batch itself)
+        self.bg_offset, self.bg_stride = frame_offset * C, total * C
+        self.loss_count = (None if total == B else
+                           float(total) * n_freq * n_offsets * H * W)
+        self.grad_hook = grad_hook
 
-    def iteration(self):
-        """Enqueue one iteration on the current stream."""
+    def param_grads(self) -> Dict[str, torch.Tensor]:
+        """The gradients the update reads (what a grad_hook receives)."""
+        return {k: self.grads[k] for k in self.opt.names}
+
+    def forward_backward(self):
+        """Enqueue an iteration up to the parameter gradients."""
         r = self.r
-        gftorf.train_begin(self.state, self.bg if self.random_background else None, self.seed)
+        gftorf.train_begin(self.state, self.bg if self.random_background else None, self.seed,
+                           self.bg_offset, self.bg_stride)
         r.preprocess(self.p, self.frames, self.sensor, self.consts)
         r.bin()
         r.composite_fwd(self.bg, self.out)
-        gftorf.l2_loss(r, self.out, self.targets, self.dout, self.state)
+        gftorf.l2_loss(r, self.out, self.targets, self.dout, self.state, count=self.loss_count)
         r.zero_grad_buffers(self.grads)
         r.composite_bwd(self.bg, self.dout, self.grads)
         r.preprocess_bwd(self.p, self.grads)
+
+    def update(self):
+        """Enqueue the Adam step from the current gradients."""
         self.opt.step(self.grads, self.state)
 
+    def iteration(self):
+        """Enqueue one iteration on the current stream (with grad_hook
+        between the backward and the update)."""
+        self.forward_backward()
+        if self.grad_hook is not None:
+            self.grad_hook(self.param_grads())
+        self.update()
+
     def capture(self):
-        """Record one iteration as a CUDA graph (runs nothing)."""
+        """Record one iteration as a CUDA graph (runs nothing); with a
+        grad_hook two graphs, the hook running between their replays."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
+        if self.grad_hook is None:
+            with torch.cuda.graph(self.graph, stream=s):
+                self.iteration()
+            return self.graph
         with torch.cuda.graph(self.graph, stream=s):
-            self.iteration()
+            self.forward_backward()
+        self.update_graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.update_graph, stream=s):
+            self.update()
         return self.graph
 
     def run(self, k: int):
         """k iterations: graph replays when captured, else eager launches."""
         for _ in range(k):
-            if self.graph is not None:
+            if self.graph is None:
+                self.iteration()
+            elif self.update_graph is None:
                 self.graph.replay()
             else:
-                self.iteration()
+                self.graph.replay()
+                self.grad_hook(self.param_grads())
+                self.update_graph.replay()
 
     # --- checkpoint / resume ---------------------------------------------------
     def state_dict(self) -> Dict[str, object]:
@@ -127,7 +175,8 @@ class FitLoop:
         return gftorf.train_step_count(self.state)
 
     def loss(self) -> float:
-        """Loss of the last iteration (synchronises)."""
+        """Loss of the last iteration (synchronises); a shard's part of the
+        batch's loss (the parts add up to it)."""
         return gftorf.train_loss(self.state)
 
     def check(self):

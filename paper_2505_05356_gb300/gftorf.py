@@ -130,7 +130,10 @@ def load(build_if_missing: bool = True):
     L.gftorf_kernel_launches.restype = ctypes.c_int64
     L.gftorf_kernel_launches.argtypes = []
     L.gftorf_train_begin.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_uint64, vp]
+    L.gftorf_train_begin_shard.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_uint64,
+                                           ctypes.c_int64, ctypes.c_int64, vp]
     L.gftorf_l2_loss.argtypes = [_P(Dims), vp, vp, vp, vp, vp]
+    L.gftorf_l2_loss_scaled.argtypes = [_P(Dims), vp, vp, vp, vp, ctypes.c_double, vp]
     L.gftorf_adam_step.argtypes = [_P(AdamGroup), ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, vp, vp]
     for name in ("gftorf_preprocess", "gftorf_render_fwd", "gftorf_render_bwd",
@@ -138,7 +141,8 @@ def load(build_if_missing: bool = True):
                  "gftorf_export_pixel_state", "gftorf_read_device_status",
                  "gftorf_bin", "gftorf_composite_fwd", "gftorf_zero_grad_buffers",
                  "gftorf_composite_bwd", "gftorf_preprocess_bwd", "gftorf_train_begin",
-                 "gftorf_l2_loss", "gftorf_adam_step"):
+                 "gftorf_train_begin_shard", "gftorf_l2_loss", "gftorf_l2_loss_scaled",
+                 "gftorf_adam_step"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -565,21 +569,33 @@ def train_loss(state: torch.Tensor) -> float:
     return float(state.view(torch.float64)[1].item())
 
 
-def train_begin(state: torch.Tensor, bg: Optional[torch.Tensor], seed: int):
-    """Device-side iteration start: step += 1, loss = 0, fresh random bg."""
+def train_begin(state: torch.Tensor, bg: Optional[torch.Tensor], seed: int,
+                bg_offset: int = 0, bg_stride: Optional[int] = None):
+    """Device-side iteration start: step += 1, loss = 0, fresh random bg.
+    With bg_offset / bg_stride (a shard of a batch's frames): bg gets values
+    [bg_offset, bg_offset + bg.numel()) of the batch's bg_stride values."""
     L = load()
     n = 0 if bg is None else bg.numel()
     if bg is not None and (bg.dtype != torch.float32 or not bg.is_contiguous()):
         raise ValueError("bg must be contiguous float32")
-    _check(L.gftorf_train_begin(_ptr(state), _ptr(bg), n, seed & ((1 << 64) - 1), _stream()),
+    stride = n if bg_stride is None else int(bg_stride)
+    _check(L.gftorf_train_begin_shard(_ptr(state), _ptr(bg), n, seed & ((1 << 64) - 1),
+                                      int(bg_offset), stride, _stream()),
            "gftorf_train_begin")
 
 
-def l2_loss(renderer: "Renderer", out, target, dout, state):
+def l2_loss(renderer: "Renderer", out, target, dout, state, count: Optional[float] = None):
     """dL/dout of the raw-sample L2 loss (written into dout); adds L to the
-    state's loss."""
-    _check(renderer.lib.gftorf_l2_loss(ctypes.byref(renderer.dims), _ptr(out), _ptr(target),
-                                       _ptr(dout), _ptr(state), _stream()), "gftorf_l2_loss")
+    state's loss.  count: the number of raw samples the mean is over (default:
+    this batch's; a shard of frames passes the whole batch's)."""
+    if count is None:
+        code = renderer.lib.gftorf_l2_loss(ctypes.byref(renderer.dims), _ptr(out), _ptr(target),
+                                           _ptr(dout), _ptr(state), _stream())
+    else:
+        code = renderer.lib.gftorf_l2_loss_scaled(ctypes.byref(renderer.dims), _ptr(out),
+                                                  _ptr(target), _ptr(dout), _ptr(state),
+                                                  float(count), _stream())
+    _check(code, "gftorf_l2_loss")
 
 
 class Adam:

@@ -148,6 +148,21 @@ def test_training_calls_reject_bad_arguments_on_host(lib):
     assert lib.gftorf_adam_step(groups, 0, 0.9, 0.999, 1e-15, st, None) == gftorf.OK
 
 
+def test_shard_training_calls_reject_bad_arguments_on_host(lib):
+    """The shard variants of the fitting calls check their arguments before
+    any launch (a fake, aligned state pointer is never touched)."""
+    st = ctypes.c_void_p(4096)
+    for n, off, stride in ((4, -1, 8), (4, 5, 8), (4, 0, 3), (4, 0, 1 << 41), (-1, 0, 8)):
+        assert lib.gftorf_train_begin_shard(st, ctypes.c_void_p(8192), n, 1, off, stride,
+                                            None) == gftorf.ERR_ARG, (n, off, stride)
+    assert lib.gftorf_train_begin_shard(None, None, 0, 1, 0, 0, None) == gftorf.ERR_ARG
+    d = _dims()
+    buf = ctypes.c_void_p(8192)
+    for count in (0.0, -3.0, float("inf"), float("nan")):
+        assert lib.gftorf_l2_loss_scaled(ctypes.byref(d), buf, buf, buf, st, count,
+                                         None) == gftorf.ERR_ARG, count
+
+
 def test_mlp_calls_reject_bad_arguments_on_host(lib):
     from paper_2505_05356_gb300 import mlp
     L = mlp._lib()

@@ -200,3 +200,84 @@ def test_checkpoint_resume_continues_the_same_fit(tmp_path):
     np.testing.assert_array_equal(b.out.cpu().numpy(), a.out.cpu().numpy())
     a.check()
     b.check()
+
+
+def test_background_shards_are_slices_of_the_batch_draw():
+    """A shard of frames draws exactly its slice of the whole batch's
+    background stream, every iteration (bit for bit, against the oracle's
+    stream of the whole batch)."""
+    B, C, seed = 6, 5, 99
+    full = otrain.background_sample(seed, 3, B * C).reshape(3, B, C)
+    for a, b in ((0, 2), (2, 5), (5, 6)):
+        st = gftorf.new_train_state()
+        bg = torch.empty((b - a, C), device="cuda")
+        for s in range(3):
+            gftorf.train_begin(st, bg, seed, bg_offset=a * C, bg_stride=B * C)
+            np.testing.assert_array_equal(bg.cpu().numpy().astype(np.float64), full[s, a:b])
+
+
+def test_frame_shards_add_up_to_the_whole_batch():
+    """One fitting iteration of a 4-frame batch run as two 2-frame shards (one
+    after the other on this GPU, as two processes would run them): the
+    shards' background slices, losses and parameter gradients add up to the
+    whole batch's, and after the gradient sum (the all-reduce of a sharded
+    fit) both shards take the same Adam step."""
+    gt, init, target = _fit_setup(seed=9)
+    B = init.frames
+    fr, se, co = (gftorf.frames_from_scene(init), gftorf.sensor_from_scene(init),
+                  gftorf.consts_from_scene(init))
+    tgt = torch.as_tensor(target, device="cuda")
+
+    def loop(a, b):
+        p = gftorf.params_from_scene(init)
+        return fit.FitLoop(p, fr[a:b], se, co, tgt[a:b].contiguous(), seed=13, headroom=2.0,
+                           frame_offset=a, total_frames=B), p
+
+    whole, pw = loop(0, B)
+    parts = [loop(0, 2), loop(2, B)]
+    whole.forward_backward()
+    for lp, _ in parts:
+        lp.forward_backward()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(torch.cat([lp.bg for lp, _ in parts]).cpu().numpy(),
+                                  whole.bg.cpu().numpy())
+    assert sum(lp.loss() for lp, _ in parts) == pytest.approx(whole.loss(), rel=1e-6)
+    gsum = {k: sum(lp.param_grads()[k] for lp, _ in parts) for k in whole.param_grads()}
+    for k, g in whole.param_grads().items():
+        ref = g.double().cpu().numpy()
+        got = gsum[k].double().cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), k
+    for lp, _ in parts:  # the all-reduce's result on every process
+        for k, g in lp.param_grads().items():
+            g.copy_(gsum[k])
+        lp.update()
+    torch.cuda.synchronize()
+    for k in FIT_LRS:
+        np.testing.assert_array_equal(parts[0][1][k].cpu().numpy(), parts[1][1][k].cpu().numpy())
+
+
+def test_grad_hook_runs_between_two_graphs():
+    """With a grad_hook the iteration is captured as two graphs with the hook
+    between their replays; an identity hook leaves the fit as without one."""
+    gt, init, target = _fit_setup(seed=10)
+
+    def make(hook):
+        p = gftorf.params_from_scene(init)
+        return fit.FitLoop(p, gftorf.frames_from_scene(init), gftorf.sensor_from_scene(init),
+                           gftorf.consts_from_scene(init), torch.as_tensor(target, device="cuda"),
+                           seed=3, headroom=2.0, grad_hook=hook), p
+
+    calls = []
+    hooked, p1 = make(lambda g: calls.append(sorted(g)))
+    hooked.capture()
+    hooked.run(3)
+    plain, p2 = make(None)
+    plain.capture()
+    plain.run(3)
+    torch.cuda.synchronize()
+    assert len(calls) == 3 and calls[0] == sorted(FIT_LRS)
+    assert hooked.step == plain.step == 3
+    assert hooked.loss() == pytest.approx(plain.loss(), rel=1e-5)
+    for k in FIT_LRS:
+        np.testing.assert_allclose(p1[k].cpu().numpy(), p2[k].cpu().numpy(), rtol=1e-4,
+                                   atol=1e-4 * FIT_LRS[k])
