@@ -34,7 +34,7 @@ METRIC = "fwd+bwd raw C-ToF frames/sec at 640x480, 300k Gaussians; % HBM/FP32 ro
 UNIT = "frames/s"
 WORKLOAD = "batch_300k"
 
-# Algorithmic work per unit ("Roofline"): FP32 lane operations per
+# Algorithmic work per unit: FP32 lane operations per
 # evaluated (pixel, Gaussian) pair of the compositing kernels, and bytes per
 # Gaussian-frame / per instance of the memory-bound stages.
 OPS_PER_PAIR_FWD = 20
