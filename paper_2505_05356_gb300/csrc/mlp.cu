@@ -721,6 +721,22 @@ __device__ __forceinline__ void store_act32(uint8_t* act, int r, int c, const fl
   }
 }
 
+// the same with the ReLU folded into the conversion: each BF16 value is
+// bf16_rn(v) clamped at zero, which equals bf16_rn(max(v, 0))
+__device__ __forceinline__ void store_act32_relu(uint8_t* act, int r, int c, const float* v) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint4 u;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;"
+          : "=r"(w[i])
+          : "f"(v[8 * q + 2 * i + 1]), "f"(v[8 * q + 2 * i]));
+    *reinterpret_cast<uint4*>(act + act_off(r, c + 8 * q)) = u;
+  }
+}
+
 // warps 0-7: epilogue (warp w: TMEM lanes / rows 32 (w % 4) .. + 31, columns
 // 128 (w / 4) .. + 127); warp 8: TMA; warp 9: MMA
 constexpr int kFusedEpiWarps = 8;
@@ -882,12 +898,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                   const float4 b = __ldg(b4 + j);
-                  v[4 * j] = fmaxf(v[4 * j] + b.x, 0.f);
-                  v[4 * j + 1] = fmaxf(v[4 * j + 1] + b.y, 0.f);
-                  v[4 * j + 2] = fmaxf(v[4 * j + 2] + b.z, 0.f);
-                  v[4 * j + 3] = fmaxf(v[4 * j + 3] + b.w, 0.f);
+                  v[4 * j] += b.x;
+                  v[4 * j + 1] += b.y;
+                  v[4 * j + 2] += b.z;
+                  v[4 * j + 3] += b.w;
                 }
-                store_act32(act, r, c, v);
+                store_act32_relu(act, r, c, v);  // (the mask bits below: v > 2^-134
+                                                 // before or after the ReLU alike)
                 const int m = (pr * kPair + t) * BM + r;
                 if (TRAIN && m < keep.Mp)
                   keep.bits[((size_t)l * keep.Mp + m) * (kW / 32) + c / 32] = relu_bits(v);
