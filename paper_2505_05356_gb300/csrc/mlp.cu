@@ -1052,11 +1052,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     const int q = warp & 3, half = warp >> 2;
     const int r = q * 32 + lane;
     uint32_t acc_ph[kPair] = {0, 0};
+    // the ReLU mask words of this thread's row and column half, one step
+    // ahead: a tile's next layer is loaded while this one is processed
+    uint4 nb[kPair];
+    auto load_bits = [&](int layer, int m) {
+      return m < a.Mp ? __ldg(reinterpret_cast<const uint4*>(
+                                  a.bits + ((size_t)layer * a.Mp + m) * (kW / 32)) +
+                              half)
+                      : make_uint4(0u, 0u, 0u, 0u);
+    };
     bool ok = true;
     for (int pr = blockIdx.x; ok && pr < n_pairs; pr += gridDim.x) {
+#pragma unroll
       for (int t = 0; t < kPair; ++t) {
         // step 0's operand: BF16 dL/d(delta) in columns 0..2 of k-block 0
         const int m = (pr * kPair + t) * BM + r;
+        nb[t] = load_bits(kDepth - 1, m);
         float v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = 0.f;
@@ -1068,6 +1079,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         if (threadIdx.x == 0) mbar_arrive(actr0 + 8 * t);
       }
       for (int st = 0; ok && st < kSteps; ++st)
+#pragma unroll
         for (int t = 0; t < kPair; ++t) {
           if (threadIdx.x == 0)
             *s_ok = mbar_wait(acc0 + 8 * t, acc_ph[t], status, wait_ns) ? 1 : 0;
@@ -1083,11 +1095,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           if (st < kDepth) {
             const int j = kDepth - 1 - st;  // the layer whose dZ this step forms
             uint8_t* act = smem + t * kActBytes;
-            const uint32_t* bits = a.bits + ((size_t)j * a.Mp + (m < a.Mp ? m : 0)) * (kW / 32);
+            const uint4 mk = nb[t];
+            if (j > 0) nb[t] = load_bits(j - 1, m);
 #pragma unroll 1
-            for (int c0 = half * (kW / 2); c0 < (half + 1) * (kW / 2); c0 += 64) {
-              const uint32_t mk0 = m < a.Mp ? __ldg(bits + c0 / 32) : 0u;
-              const uint32_t mk1 = m < a.Mp ? __ldg(bits + c0 / 32 + 1) : 0u;
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int c0 = half * (kW / 2) + 64 * h2;
+              const uint32_t mk0 = h2 ? mk.z : mk.x, mk1 = h2 ? mk.w : mk.y;
               float vv[64];
               tmem_ld64(trow + (uint32_t)c0, vv);
 #pragma unroll
