@@ -878,8 +878,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           // the tile's last store has read it before it is written again
           if (TRAIN && threadIdx.x == 32 * t) bulk_wait_read();
           asm volatile("bar.sync 1, 256;" ::: "memory");
+          // (every step ends at a named barrier that all epilogue threads reach
+          // after reading the flag, so thread 0 rewrites it only afterwards)
           if (!(ok = *s_ok != 0)) break;
-          asm volatile("bar.sync 1, 256;" ::: "memory");  // all have read the flag
           acc_ph[t] ^= 1u;
           tc_fence_after();
           const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * kW);
@@ -1086,8 +1087,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           // the tile's last store has read it before it is written again
           if (threadIdx.x == 32 * t) bulk_wait_read();
           asm volatile("bar.sync 1, 256;" ::: "memory");
-          if (!(ok = *s_ok != 0)) break;
-          asm volatile("bar.sync 1, 256;" ::: "memory");
+          if (!(ok = *s_ok != 0)) break;  // (rewritten only after the step's last barrier)
           acc_ph[t] ^= 1u;
           tc_fence_after();
           const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * kW);
