@@ -372,22 +372,38 @@ __global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 1 : (SH ? 3 : 4))
   Real gmu[3] = {0, 0, 0}, gc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   Real gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0, gamp = 0;
   const Real dil = (Real)tab->dilation;
+  // frame b + 1's rectangle and 2D-gradient row (7 + NF values, the row
+  // stride) are loaded while frame b is processed; they are used only where
+  // the rectangle says visible, as before
+  constexpr int RW = 7 + NF;
+  uint2 rr_next = rect[g];
+  Real row_next[RW];
+#pragma unroll
+  for (int i = 0; i < RW; ++i) row_next[i] = g2d[(size_t)g * g2d_stride + i];
   for (int b = 0; b < B; ++b) {
     const size_t bg = (size_t)b * N + g;
     Real* gdelta = D.delta ? static_cast<Real*>(D.delta) + bg * 3 : nullptr;
-    const uint2 rr = rect[bg];
-    const Real* gr = g2d + bg * g2d_stride;
+    const uint2 rr = rr_next;
+    Real row[RW];
+#pragma unroll
+    for (int i = 0; i < RW; ++i) row[i] = row_next[i];
+    if (b + 1 < B) {
+      const size_t bn = bg + (size_t)N;
+      rr_next = rect[bn];
+#pragma unroll
+      for (int i = 0; i < RW; ++i) row_next[i] = g2d[bn * g2d_stride + i];
+    }
     Real gu = 0, gv = 0, ga = 0, gb = 0, gcn = 0, gop = 0, gdist = 0, gf[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) gf[f] = 0;
     bool any = false;
     if (rr.x != rr.y || rr.x != 0) {  // visible in this frame
-      gu = gr[0], gv = gr[1], ga = gr[2], gb = gr[3], gcn = gr[4], gop = gr[5];
-      gdist = gr[6 + NF];  // through the mean depth's d_k
+      gu = row[0], gv = row[1], ga = row[2], gb = row[3], gcn = row[4], gop = row[5];
+      gdist = row[6 + NF];  // through the mean depth's d_k
       any = gu != 0 || gv != 0 || ga != 0 || gb != 0 || gcn != 0 || gop != 0 || gdist != 0;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        gf[f] = gr[6 + f];
+        gf[f] = row[6 + f];
         any |= gf[f] != 0;
       }
     }
