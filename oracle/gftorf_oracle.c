@@ -501,6 +501,27 @@ void ora_render_pixels(int n, const double* splats, const double* frame,
   }
 }
 
+int ora_pixel_steps(int n, const double* splats, const double* sensor,
+                    const double* consts, const double* eps, int x, int y,
+                    int max_steps, double* alpha, double* trans, double* tfinal) {
+  const int tw = (int)consts[ORA_CO_TW], th = (int)consts[ORA_CO_TH];
+  cand_t* cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)max_candidates(n));
+  step_t* steps = (step_t*)malloc(sizeof(step_t) * (size_t)max_candidates(n));
+  int m = collect_candidates(n, splats, x / tw, y / th, cand);
+  double acc[ORA_MAX_FEAT + 1], T;
+  int flags = 0;
+  int k = composite_pixel(splats, cand, m, x + 0.5, y + 0.5, sensor, consts, eps, acc, &T,
+                          &flags, steps);
+  for (int i = 0; i < k && i < max_steps; ++i) {
+    alpha[i] = steps[i].alpha;
+    trans[i] = steps[i].T;
+  }
+  *tfinal = T;
+  free(steps);
+  free(cand);
+  return k;
+}
+
 void ora_render_frame(int n, const double* splats, const double* frame,
                       const double* sensor, const double* consts,
                       const double* bg, const double* eps, double* out,

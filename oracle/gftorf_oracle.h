@@ -139,6 +139,13 @@ void ora_render_pixels(int n, const double* splats, const double* frame,
                        const int32_t* pix, double* out, double* tfinal,
                        int32_t* ambig, int32_t* ncontrib);
 
+/* Instrumentation of one pixel (x, y): the composited Gaussians' alpha_k and
+ * transmittance T_k before them (one-way), front to back, up to max_steps of
+ * them; *tfinal = T_N.  Returns the number composited. */
+int ora_pixel_steps(int n, const double* splats, const double* sensor,
+                    const double* consts, const double* eps, int x, int y,
+                    int max_steps, double* alpha, double* trans, double* tfinal);
+
 /* Full frame: out[C*H*W] (channel-major), tfinal[H*W], ambig[H*W],
  * ncontrib[H*W]. */
 void ora_render_frame(int n, const double* splats, const double* frame,

@@ -58,6 +58,9 @@ def lib():
         L.ora_sh_basis.restype = ctypes.c_double
         L.ora_render_pixels.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _d,
                                         ctypes.c_int, _i32, _d, _d, _i32, _i32]
+        L.ora_pixel_steps.argtypes = [ctypes.c_int, _d, _d, _d, _d, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, _d, _d, _d]
+        L.ora_pixel_steps.restype = ctypes.c_int
         L.ora_render_frame.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _d,
                                        _d, _d, _i32, _i32]
         L.ora_backward_2d.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _d, _d, _d]
@@ -211,6 +214,21 @@ def render_pixels(scene, b: int, pix: np.ndarray, splats=None, eps=EPS_NONE):
                             k, _p(pix, _i32), _p(out), _p(tf), _p(amb, _i32),
                             _p(nc, _i32))
     return out, tf, amb, nc
+
+
+def pixel_steps(scene, b: int, x: int, y: int, splats=None, max_steps: int = 100000):
+    """Instrumented pixel (x, y) of frame b: (alpha_k, T_k) of the composited
+    Gaussians front to back (T_k one-way, before Gaussian k) and T_N."""
+    if splats is None:
+        splats = project(scene, b)
+    alpha = np.zeros(max_steps)
+    trans = np.zeros(max_steps)
+    tf = np.zeros(1)
+    k = lib().ora_pixel_steps(scene.n, _p(splats), _p(pack_sensor(scene)),
+                              _p(pack_consts(scene)), _p(np.asarray(EPS_NONE, np.float64)),
+                              int(x), int(y), max_steps, _p(alpha), _p(trans), _p(tf))
+    k = min(k, max_steps)
+    return alpha[:k], trans[:k], float(tf[0])
 
 
 def render(scene, eps=EPS_NONE, params: Params = None):

@@ -271,3 +271,25 @@ def test_async_frame_equals_channel_of_synchronous_quartet():
         np.testing.assert_array_equal(r1["out"][0, 0], rs["out"][0, j])
         np.testing.assert_array_equal(r1["out"][0, 1], rs["out"][0, 4])
     assert abs(offs[1] - math.pi / 2) < 1e-6
+
+
+def test_telescoping_coincident_gaussians_on_the_gpu():
+    """The golden telescoping case through the CUDA path's own outputs: N
+    coincident Gaussians of equal alpha with unit amplitude term A = s r / d^2
+    and zero background, so the ambient channel is sum_k alpha T_k^2 (the
+    golden geometric series) and the exported T_N is (1 - alpha)^N."""
+    import json
+    import os
+    from tests.oracle_scenes import at_pixel, tiny_scene
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                         "closed_forms.json")))
+    case = golden["telescoping"]["cases"][0]
+    cam = tiny_scene([[0, 0, 1]], 0.1).cameras[0]
+    p = at_pixel(cam, 10.5, 50.5, 2.0)
+    d = float(np.linalg.norm(p))
+    n = case["N"]
+    sc = tiny_scene([p] * n, 0.05, opacity=[case["alpha"]] * n, amplitude=[d * d] * n)
+    res = run_gpu(sc)
+    assert res["out"][0, 4, 50, 10] == pytest.approx(case["sum_weights"], rel=1e-5)
+    assert res["tfinal"][0, 50, 10] == pytest.approx(case["T_final"], rel=1e-5)
+    assert res["nlast"][0, 50, 10] >= n  # all N composited (list position past the last)

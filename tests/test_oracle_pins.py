@@ -738,3 +738,27 @@ def test_gradient_async_interpolated_matches_central_differences(seed):
             assert g[name].reshape(-1)[i] == pytest.approx(fd, rel=2e-5, abs=2e-6 * (1 + abs(fd)))
             checked += 1
     assert checked > 60
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_squared_transmittance_telescopes_for_any_scene(seed):
+    """The weights of the round trip telescope for any scene: with T_{k+1} =
+    T_k (1 - alpha_k), alpha_k (2 - alpha_k) T_k^2 = T_k^2 - T_{k+1}^2, so
+    sum_k alpha_k (2 - alpha_k) T_k^2 = 1 - T_N^2 (Eq. 4's T_k^2; the early
+    stop only ends the sum).  Checked on the oracle's instrumented walk of
+    pixels with dozens of contributors."""
+    from paper_2505_05356_gb300 import scenes
+    sc = scenes.make_scene("static_1k", seed, n=1500, width=48, height=40)
+    splats = ora.project(sc, 0)
+    rng = np.random.default_rng(seed)
+    deep = 0
+    for x, y in rng.integers(0, [48, 40], size=(40, 2)):
+        a, T, TN = ora.pixel_steps(sc, 0, x, y, splats=splats)
+        if len(a) == 0:
+            assert TN == 1.0
+            continue
+        deep += len(a) >= 20
+        np.testing.assert_allclose(T[1:], T[:-1] * (1 - a[:-1]), rtol=1e-15)
+        assert T[0] == 1.0 and TN == pytest.approx(T[-1] * (1 - a[-1]), rel=1e-15)
+        assert float(np.sum(a * (2 - a) * T * T)) == pytest.approx(1 - TN * TN, abs=1e-13)
+    assert deep >= 5
