@@ -647,7 +647,9 @@ def mlp_bench(args, n=300_000, frames=(1, 16)):
 # CPU oracle timing (baseline; bounded sample of the same workload)
 # ---------------------------------------------------------------------------
 def oracle_sample(sc, n_pix, frame=0, seed=5):
-    """Time the FP64 oracle's fwd+bwd on n_pix random pixels of one frame and
+    """Time the FP64 oracle's fwd+bwd on about n_pix pixels of one frame --
+    all pixels of randomly chosen tiles, so that the per-tile work (the
+    backward's candidate lists) and the per-pixel work scale alike -- and
     extrapolate to frames/s.  Returns (frames_per_s, seconds_spent, detail)."""
     from oracle import oracle as ora
     from paper_2505_05356_gb300 import scenes
@@ -658,8 +660,15 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
                        sc.sensor, sc.consts, sc.bg[frame:frame + 1], sc.sh)
     HW = sc.width * sc.height
     rng = np.random.default_rng(seed)
-    idx = rng.choice(HW, n_pix, replace=False)
-    pix = np.stack([idx % sc.width, idx // sc.width], 1).astype(np.int32)
+    TW, TH = sc.consts.tile_w, sc.consts.tile_h
+    tx_n, ty_n = -(-sc.width // TW), -(-sc.height // TH)
+    k = int(min(tx_n * ty_n, max(1, round(n_pix / (TW * TH)))))
+    tiles = rng.choice(tx_n * ty_n, k, replace=False)
+    xs, ys = np.meshgrid(np.arange(TW), np.arange(TH))
+    pix = np.concatenate([np.stack([xs.ravel() + (t % tx_n) * TW, ys.ravel() + (t // tx_n) * TH], 1)
+                          for t in tiles])
+    pix = pix[(pix[:, 0] < sc.width) & (pix[:, 1] < sc.height)].astype(np.int32)
+    n_pix = len(pix)
     P = ora.Params(one)
     t0 = time.perf_counter()
     sp = ora.project(one, 0, ora.EPS_NONE, P)
@@ -672,10 +681,18 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
     g2d = np.zeros((sc.n, 7 + nf))
     lib = ora.lib()
     fr, se, co = ora.pack_frame(one, 0), ora.pack_sensor(one), ora.pack_consts(one)
-    lib.ora_backward_2d(sc.n, ora._p(sp), ora._p(fr), ora._p(se), ora._p(co),
-                        ora._p(np.ascontiguousarray(one.bg[0], np.float64)), ora._p(dout),
-                        ora._p(g2d), None)
+    bg0 = np.ascontiguousarray(one.bg[0], np.float64)
+    lib.ora_backward_2d(sc.n, ora._p(sp), ora._p(fr), ora._p(se), ora._p(co), ora._p(bg0),
+                        ora._p(dout), ora._p(g2d), None)
     t3 = time.perf_counter()
+    # the 2D backward's per-frame part (its pass over every pixel for the
+    # nonzero dL/dQ) is not scaled with the sample: timed with no pixel set
+    g2d0 = np.zeros_like(g2d)
+    u0 = time.perf_counter()
+    lib.ora_backward_2d(sc.n, ora._p(sp), ora._p(fr), ora._p(se), ora._p(co), ora._p(bg0),
+                        ora._p(np.zeros_like(dout)), ora._p(g2d0), None)
+    bwd_fixed = min(time.perf_counter() - u0, t3 - t2)
+    t3c = time.perf_counter()
     grads = np.zeros((sc.n, ora.NPARAM))
     lib.ora_backward_params(sc.n, ora._p(P.means), ora._p(P.coeffs), ora._p(P.scales),
                             ora._p(P.quats), ora._p(P.opacity), ora._p(P.amplitude),
@@ -683,13 +700,15 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
                             ora._p(co),
                             ora._p(sp), ora._p(g2d), ora._p(grads))
     t4 = time.perf_counter()
+    chain = t4 - t3c
     touched = int(np.count_nonzero(np.any(g2d != 0, axis=1)))
     visible = int(np.count_nonzero(sp[:, ora.SP["VIS"]]))
-    per_frame = ((t1 - t0) + ((t2 - t1) + (t3 - t2)) * HW / n_pix +
-                 (t4 - t3) * (visible / max(touched, 1)))
+    per_frame = ((t1 - t0) + ((t2 - t1) + (t3 - t2 - bwd_fixed)) * HW / n_pix + bwd_fixed +
+                 chain * (visible / max(touched, 1)))
     detail = dict(project_s=t1 - t0, fwd_pixels_s=t2 - t1, bwd_pixels_s=t3 - t2,
-                  chain_s=t4 - t3, touched=touched, visible=visible)
-    return 1.0 / per_frame, t4 - t0, detail
+                  bwd_frame_s=bwd_fixed, chain_s=chain, touched=touched, visible=visible,
+                  pixels=n_pix, tiles=k)
+    return 1.0 / per_frame, (t4 - t0) - bwd_fixed, detail
 
 
 def _calibrate(sc, seconds):
@@ -699,7 +718,7 @@ def _calibrate(sc, seconds):
     n = 64
     for frac in (0.25, 1.0):
         _, spent, det = oracle_sample(sc, n)
-        per_px = max(det["fwd_pixels_s"] + det["bwd_pixels_s"], 1e-6) / n
+        per_px = max(det["fwd_pixels_s"] + det["bwd_pixels_s"], 1e-6) / det["pixels"]
         fixed = det["project_s"] + det["chain_s"]
         n = int(min(sc.width * sc.height, max(64, (frac * seconds - fixed) / per_px)))
     return n
@@ -708,12 +727,26 @@ def _calibrate(sc, seconds):
 def cpu_baseline(sc, seconds):
     from oracle import oracle as ora
     n_pix = _calibrate(sc, seconds)
+    threads = ora.num_threads()
     fps, spent, det = oracle_sample(sc, n_pix, seed=6)
-    return {"value": round(fps, 6), "unit": UNIT, "cores": ora.num_threads(), "kind": "oracle",
-            "sample": "frame 0 of the batch: projection of all %d Gaussians + fwd/bwd of %d "
-                      "random pixels (of %d) + chain rule of the %d touched Gaussians, "
-                      "extrapolated to a full frame (%.1f s of CPU work)"
-                      % (sc.n, n_pix, sc.width * sc.height, det["touched"], spent)}
+    # the same on one thread, on a proportionally smaller sample
+    n1 = max(64, n_pix // (8 * max(threads, 1)))
+    ora.set_threads(1)
+    try:
+        fps1, spent1, det1 = oracle_sample(sc, n1, seed=7)
+    finally:
+        ora.set_threads(threads)
+    return {"value": round(fps, 6), "unit": UNIT, "cores": threads, "nproc": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "frame 0 of the batch: projection of all %d Gaussians + fwd/bwd of the "
+                      "%d pixels of %d random tiles (of %d pixels) + chain rule of the %d "
+                      "touched Gaussians, extrapolated to a full frame (%.1f s of CPU work)"
+                      % (sc.n, det["pixels"], det["tiles"], sc.width * sc.height,
+                         det["touched"], spent),
+            "single_thread": {"value": round(fps1, 6), "unit": UNIT,
+                              "sample": "the same with the %d pixels of %d tile(s) on one "
+                                        "thread (%.1f s)"
+                                        % (det1["pixels"], det1["tiles"], spent1)}}
 
 
 def run_reference(args):
@@ -743,10 +776,11 @@ def run_reference(args):
         "config": {"workload": "%s: %d dynamic Gaussians, %dx%d, %d timesteps per batch"
                                % (WORKLOAD, sc.n, sc.width, sc.height, sc.frames)},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": ora.num_threads(),
-                         "kind": "oracle",
+                         "nproc": os.cpu_count(), "kind": "oracle",
                          "sample": "per step one frame: projection of all Gaussians + fwd/bwd of "
-                                   "%d random pixels + chain rule of the touched Gaussians, "
-                                   "extrapolated to the full frame" % n_pix},
+                                   "the pixels of random tiles (about %d pixels) + chain rule of "
+                                   "the touched Gaussians, extrapolated to the full frame"
+                                   % n_pix},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

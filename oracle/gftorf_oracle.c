@@ -33,6 +33,14 @@ int ora_num_threads(void) {
 #endif
 }
 
+void ora_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 static int n_feat(const double* sensor) { return 2 * (int)sensor[ORA_SE_F] + 1; }
 static int n_chan(const double* sensor, const double* consts) {
   const int F = (int)sensor[ORA_SE_F];

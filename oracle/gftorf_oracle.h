@@ -107,6 +107,8 @@ extern "C" {
 
 int ora_splat_len(void);
 int ora_num_threads(void);
+/* OpenMP threads of the following calls (n > 0; for timing). */
+void ora_set_threads(int n);
 
 /* Project all n Gaussians for one frame (Sec. 3; 3DGS EWA convention).
  * params: means[n*3], coeffs[n*9] (c1 xyz, c2 xyz, c3 xyz), scales[n*3],

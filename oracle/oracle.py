@@ -53,6 +53,7 @@ def lib():
         L = ctypes.CDLL(path)
         L.ora_splat_len.restype = ctypes.c_int
         L.ora_num_threads.restype = ctypes.c_int
+        L.ora_set_threads.argtypes = [ctypes.c_int]
         L.ora_project.argtypes = [ctypes.c_int] + [_d] * 13
         L.ora_sh_basis.argtypes = [ctypes.c_int] + [ctypes.c_double] * 3
         L.ora_sh_basis.restype = ctypes.c_double
@@ -76,6 +77,11 @@ def lib():
 
 def num_threads() -> int:
     return lib().ora_num_threads()
+
+
+def set_threads(n: int):
+    """OpenMP threads of the oracle's following calls."""
+    lib().ora_set_threads(int(n))
 
 
 def _p(a, t=_d):
