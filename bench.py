@@ -662,7 +662,7 @@ def oracle_sample(sc, n_pix, frame=0, seed=5):
     rng = np.random.default_rng(seed)
     TW, TH = sc.consts.tile_w, sc.consts.tile_h
     tx_n, ty_n = -(-sc.width // TW), -(-sc.height // TH)
-    k = int(min(tx_n * ty_n, max(1, round(n_pix / (TW * TH)))))
+    k = int(min(tx_n * ty_n, max(1, round(n_pix * tx_n * ty_n / HW))))  # tiles, on average
     tiles = rng.choice(tx_n * ty_n, k, replace=False)
     xs, ys = np.meshgrid(np.arange(TW), np.arange(TH))
     pix = np.concatenate([np.stack([xs.ravel() + (t % tx_n) * TW, ys.ravel() + (t // tx_n) * TH], 1)
