@@ -67,3 +67,15 @@ def test_allreduce_sum_two_gloo_ranks():
         assert g["means"] == [[3.0] * 3] * 5
         assert g["opacity"] == [0.0, 3.0, 6.0, 9.0]
         assert g["empty"] == []
+
+
+@pytest.mark.parametrize("offset,total", [(-1, 4), (3, 4), (0, 1)])
+def test_fit_loop_rejects_a_shard_outside_its_batch(offset, total):
+    """A loop over 2 frames at frame_offset in a batch of total_frames: the
+    range must lie inside the batch (checked before anything touches a GPU)."""
+    from paper_2505_05356_gb300 import fit
+    params = {"means": torch.zeros((10, 3))}
+    targets = torch.zeros((2, 5, 4, 4))
+    with pytest.raises(ValueError):
+        fit.FitLoop(params, [None, None], None, None, targets, frame_offset=offset,
+                    total_frames=total)
