@@ -565,14 +565,13 @@ void launch_footprints(const Layout& L, const float* u, const float* v,
 }
 
 void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {  // per-CTA tile counters may exceed the default 48 KB
-    cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    cudaFuncSetAttribute(tile_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr_set = true;
-  }
+  static PerDeviceOnce attr;
+  attr.run([] {  // per-CTA tile counters may exceed the default 48 KB
+    return cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024) == cudaSuccess &&
+           cudaFuncSetAttribute(tile_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024) == cudaSuccess;
+  });
   auto* hdr = at<Header>(ws, L.off_header);
   auto* zkey = at<uint32_t>(ws, L.off_zkey);
   auto* k0 = at<uint32_t>(ws, L.off_zkey2);

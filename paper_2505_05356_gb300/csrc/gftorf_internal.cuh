@@ -10,7 +10,53 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include <atomic>
+#include <mutex>
+
 namespace gftorf {
+
+// ---------------------------------------------------------------------------
+// per-device host state: function attributes and device properties belong to
+// a device's context, so a process driving several GPUs keeps one copy each
+// ---------------------------------------------------------------------------
+constexpr int kMaxDevices = 64;
+
+inline int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+  return d;
+}
+
+// Runs f() once per device (the current one); returns f's result on the
+// call that ran it and the cached result afterwards.  Devices beyond the
+// table run f() on every call.
+struct PerDeviceOnce {
+  std::once_flag flag[kMaxDevices];
+  bool ok[kMaxDevices] = {};
+  template <typename F>
+  bool run(F&& f) {
+    const int d = current_device();
+    if (d < 0) return f();
+    std::call_once(flag[d], [&] { ok[d] = f(); });
+    return ok[d];
+  }
+};
+
+// multiprocessor count of the current device, looked up once per device
+inline int sm_count() {
+  static std::atomic<int> cache[kMaxDevices];
+  const int d = current_device();
+  if (d >= 0) {
+    const int c = cache[d].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d < 0 ? 0 : d) != cudaSuccess ||
+      n <= 0)
+    n = 1;
+  if (d >= 0) cache[d].store(n, std::memory_order_relaxed);
+  return n;
+}
 
 // NVTX range over one C-ABI call (a no-op unless a profiler is attached):
 // the stages show up by name in timeline tools.

@@ -1183,14 +1183,14 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, 
 template <int BN, int EPI, int MT = 1, int MNA = 0, int MNB = 0>
 bool gemm(const CUtensorMap& a, const CUtensorMap& b, const GemmArgs& args, int m_tiles,
           int n_tiles, int splits, cudaStream_t st) {
-  static bool configured = false;
   constexpr int smem = GemmShape<BN, MT>::SMEM;
-  if (!configured) {
-    if (cudaFuncSetAttribute(umma_gemm_kernel<BN, EPI, MT, MNA, MNB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return false;
-    configured = true;
-  }
+  static PerDeviceOnce configured;
+  if (!configured.run([] {
+        return cudaFuncSetAttribute(umma_gemm_kernel<BN, EPI, MT, MNA, MNB>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem) == cudaSuccess;
+      }))
+    return false;
   umma_gemm_kernel<BN, EPI, MT, MNA, MNB>
       <<<dim3(m_tiles, n_tiles, splits), 192, smem, st>>>(a, b, args);
   count_launches(1);
@@ -1255,17 +1255,17 @@ bool mlp_args_ok(int N, int B) {
 std::atomic<int> g_inject{0};
 
 bool fused_configured() {
-  static int ok = -1;
-  if (ok < 0)
-    ok = cudaFuncSetAttribute(mlp_fused_fwd_kernel<false>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) ==
-                 cudaSuccess &&
-         cudaFuncSetAttribute(mlp_fused_fwd_kernel<true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) ==
-                 cudaSuccess &&
-         cudaFuncSetAttribute(mlp_fused_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kBwdSmem) == cudaSuccess;
-  return ok == 1;
+  static PerDeviceOnce once;
+  return once.run([] {
+    return cudaFuncSetAttribute(mlp_fused_fwd_kernel<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(mlp_fused_fwd_kernel<true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(mlp_fused_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kBwdSmem) == cudaSuccess;
+  });
 }
 
 template <typename T>
@@ -1352,9 +1352,7 @@ extern "C" gftorf_status gftorf_mlp_forward(int32_t n_gaussians, int32_t n_frame
       return GFTORF_ERR_CUDA;
     FusedKeep keep;
     keep.bits = ptr<uint32_t>(ws, L.off_bits), keep.Mp = Mp;
-    int sms = 148, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     const int n_pairs = (mt + kPair - 1) / kPair;
     const int inj = g_inject.load();
     mlp_fused_fwd_kernel<true><<<n_pairs < sms ? n_pairs : sms, kFusedThreads, kFusedSmem, st>>>(
@@ -1440,12 +1438,7 @@ extern "C" gftorf_status gftorf_mlp_backward(int32_t n_gaussians, int32_t n_fram
   const int mt = Mp / BM;
   const int kb_rows = Mp / BK;      // k-blocks of a reduction over the batch rows
   // weight-gradient GEMMs: one CTA per SM (TMEM-bound), the rows split evenly
-  int sms = 148;
-  {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  const int sms = sm_count();
   const int per_split = max(8, (kb_rows + min(sms, kMaxSplits) - 1) / min(sms, kMaxSplits));
   const int splits = (kb_rows + per_split - 1) / per_split;  // <= kMaxSplits
   float* part = ptr<float>(ws, L.off_part);
@@ -1622,9 +1615,7 @@ extern "C" gftorf_status gftorf_mlp_infer(int32_t n_gaussians, int32_t n_frames,
   memset(&tm, 0, sizeof(tm));
   for (int b = 0; b < n_frames; ++b) tm.t[b] = times[b];
   if (!fused_configured()) return GFTORF_ERR_CUDA;
-  int sms = 148, dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess)
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   const int n_tiles = (M + BM - 1) / BM;
   const int n_pairs = (n_tiles + kPair - 1) / kPair;
   const unsigned long long wait_ns = g_inject.load() == 1 ? 50000000ull : 2000000000ull;

@@ -13,10 +13,9 @@ Layout binning_layout(const gftorf_dims* d);
 
 namespace {
 
-// Largest scratch this entry point can use; every GPU that loads the library
-// reserves it for the life of the process.
+// Largest scratch this entry point can use; a device reserves it at the latest
+// at the first call made there, and keeps it for the life of the process.
 constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 

@@ -681,15 +681,9 @@ RenderGeom geom_of(const Layout& L) {
 
 template <typename KernelT>
 int persistent_grid(KernelT kernel, int threads, size_t smem) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-  return sms * (per_sm > 0 ? per_sm : 1);
+  return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 
 template <typename Real, int F, int PPT, bool DEPTH, bool COUNT>
@@ -699,11 +693,11 @@ void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
   const int threads = L.TW * L.TH / PPT;
   const size_t smem = (size_t)threads * (2 * RS * sizeof(Real) + sizeof(uint32_t));
   auto kernel = render_fwd_kernel<Real, F, PPT, DEPTH, COUNT>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr_set = true;
-  }
+  static PerDeviceOnce attr;
+  attr.run([&] {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024) == cudaSuccess;
+  });
   auto* hdr = at<Header>(ws, L.off_header);
   dim3 grid(L.NT, L.B);
   if (L.mode == 1) {
@@ -729,11 +723,11 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
   const size_t smem = (size_t)threads * (2 * RS + GS) * sizeof(Real) +
                       32 * sizeof(Real) + (size_t)threads * 2 * sizeof(uint32_t);
   auto kernel = render_bwd_kernel<Real, F, PPT, DEPTH>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr_set = true;
-  }
+  static PerDeviceOnce attr;
+  attr.run([&] {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024) == cudaSuccess;
+  });
   auto* hdr = at<Header>(ws, L.off_header);
   dim3 grid(L.NT, L.B);
   if (L.mode == 1) {

@@ -56,12 +56,25 @@ def forward_close(q_gpu, q_ora, amb, rel=1e-5, flag_mask=ora.AMB_VALUE):
     return worst <= rel, worst, int((~keep).sum())
 
 
-def grads_close(g_gpu, g_ora, rel=1e-3):
+def absent_groups(scene):
+    """Gradient groups the CUDA path does not return for `scene` because the
+    scene has no such parameter (static trajectories, no per-frame
+    displacement, scalar reflectivity)."""
+    out = set()
+    for k in ("coeffs", "delta", "amplitude", "sh"):
+        if getattr(scene, k, None) is None:
+            out.add(k)
+    return out
+
+
+def grads_close(g_gpu, g_ora, rel=1e-3, absent=()):
     """Per parameter group: norm-wise relative error and elementwise error
-    against max(|g|, RMS of the group).  Returns dict name -> (norm, elem)."""
+    against max(|g|, RMS of the group).  Returns dict name -> (norm, elem).
+    Every group of g_ora must be in g_gpu unless listed in `absent`."""
     out = {}
     for k, go in g_ora.items():
         if k not in g_gpu:
+            assert k in absent, "gradient group %r missing from the CUDA path's result" % k
             continue
         gg = g_gpu[k].reshape(-1)
         go = np.asarray(go, np.float64).reshape(-1)

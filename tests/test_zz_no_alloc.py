@@ -49,3 +49,21 @@ def test_noalloc_rejects_problems_larger_than_its_scratch():
     r = torch.ones((1, n), dtype=torch.int32, device="cuda")
     code, *_ = gftorf.sort_footprints_noalloc(u, u, r, u + 1, 64, 64, (16, 16), max_instances=16)
     assert code == gftorf.ERR_WORKSPACE
+
+
+def test_noalloc_overflow_leaves_empty_lists_after_a_call_that_fit():
+    """Capacity overflow is reported through *count (> max_instances) and
+    leaves every range empty, even though the shared array still holds the
+    previous call's lists and counters."""
+    W, H, tile = 160, 120, (16, 16)
+    u, v, r, z = _footprints(5, 2, 4000, W, H)
+    keys_ref, _, _ = gftorf.sort_footprints(u, v, r, z, W, H, tile)
+    m = keys_ref.numel()
+    code, *_ = gftorf.sort_footprints_noalloc(u, v, r, z, W, H, tile, max_instances=m + 10)
+    assert code == gftorf.OK
+    code, keys, vals, ranges, count = gftorf.sort_footprints_noalloc(
+        u, v, r, z, W, H, tile, max_instances=m // 3)
+    torch.cuda.synchronize()
+    assert code == gftorf.OK, gftorf.STATUS.get(code)
+    assert int(count.item()) == m > m // 3
+    assert int(ranges.view(torch.int32).abs().sum().item()) == 0
