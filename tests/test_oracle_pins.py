@@ -371,6 +371,31 @@ def _loss(sc, dout, params):
     return float(np.sum(out * dout)), amb
 
 
+def _check_bg_by_differences(sc, dout, g):
+    """dL/dbg against central differences of the oracle's own forward in a
+    scene with Gaussians on every frame: Eq. 4 scales the background by the
+    one-way T_N of each pixel (not T_N^2), and Eq. 5's mean depth has no
+    background, so its entry must not move the loss at all.  The output is
+    linear in bg (no decision depends on it), so the quotient is exact up to
+    rounding."""
+    bg0 = np.array(sc.bg, np.float64, copy=True)
+    gbg = g["bg"]
+    assert gbg.shape == bg0.shape
+    tf = ora.render(sc)[1]
+    assert tf.min() < 0.5  # T_N well below 1 somewhere: T_N and T_N^2 differ
+    h = 1e-3
+    for b in range(bg0.shape[0]):
+        for c in range(bg0.shape[1]):
+            vals = []
+            for sgn in (1, -1):
+                sc.bg = bg0.copy()
+                sc.bg[b, c] += sgn * h
+                vals.append(_loss(sc, dout, ora.Params(sc))[0])
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert gbg[b, c] == pytest.approx(fd, rel=1e-8, abs=1e-9 * (1 + abs(fd))), (b, c)
+    sc.bg = bg0
+
+
 @pytest.mark.parametrize("seed,freqs", [(0, (30e6,)), (1, (30e6, 80e6)), (2, (20e6,))])
 def test_gradient_matches_central_differences(seed, freqs):
     sc = _fd_scene(seed, freqs=freqs)
@@ -405,6 +430,7 @@ def test_gradient_matches_central_differences(seed, freqs):
             assert gflat[i] == pytest.approx(fd, rel=2e-5, abs=2e-6 * (1 + abs(fd))), (name, i)
             checked += 1
     assert checked > 150
+    _check_bg_by_differences(sc, dout, g)
 
 
 def test_s3_recursion_against_direct_derivative():
@@ -527,6 +553,8 @@ def test_gradient_with_phasor_and_depth_matches_central_differences(seed):
             assert g[name].reshape(-1)[i] == pytest.approx(fd, rel=2e-5, abs=2e-6 * (1 + abs(fd)))
             checked += 1
     assert checked > 80
+    _check_bg_by_differences(sc, dout, g)
+    assert np.all(g["bg"][:, C - 1] == 0.0)  # Eq. 5: no background in the mean depth
 
 
 # --------------------------------------------------------------------------
