@@ -178,18 +178,38 @@ def _dist():
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_ours(args):
+# the other full-size workloads, measured after the headline one and reported
+# as extra keys of the same line (100k Gaussians at 640x480, one frame per
+# step; 500k Gaussians at 640x576 with 30 and 80 MHz, 8 frames per step)
+EXTRA_WORKLOADS = ("dynamic_100k", "twofreq_500k")
+
+
+def workload_config(sc, name, args) -> dict:
+    """The workload a line measures (shared by both arms, no launch choices)."""
+    nF, nP = len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad)
+    vis = ", 30-100%% visible per frame" if name in ("batch_300k", "twofreq_500k") else ""
+    return {"workload": "%s: %d dynamic Gaussians (cubic trajectories), %dx%d, "
+                        "%d timesteps per batch, %s MHz x %d offsets + ambient%s" % (
+                            name, sc.n, sc.width, sc.height, sc.frames,
+                            "+".join("%g" % (f / 1e6) for f in sc.sensor.freqs_hz), nP, vis),
+            "frames_per_step": sc.frames, "channels": sc.n_channels,
+            "reflectivity": ("SH degree %d" % args.sh_degree
+                             if args.sh_degree >= 0 else "scalar"),
+            "capture": ("asynchronous (1 offset per frame, Eq. 7 motion)"
+                        if args.async_capture else "synchronous quartets")}
+
+
+def measure(sc, args, steps, warmup, world=1, seed=0, autotune=True, want_e2e=False,
+            want_plain=False, alu=None):
+    """Time the batched, graph-captured fwd+bwd step of scene `sc`: the step
+    rate, per-stage CUDA-event times, each stage against its roofline, and
+    optionally the end-to-end rate through the public API from pinned host
+    memory and the same work as per-frame plain launches."""
     import torch
     import torch.distributed as dist
 
     from paper_2505_05356_gb300 import gftorf, scenes
 
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    sc = scenes.make_scene(args.workload, seed=rank, **_overrides(args))
     B, N, W, H = sc.frames, sc.n, sc.width, sc.height
     nF, nP = len(sc.sensor.freqs_hz), len(sc.sensor.offsets_rad)
     xflags = gftorf.flags_from_scene(sc)
@@ -198,14 +218,14 @@ def run_ours(args):
     se = gftorf.sensor_from_scene(sc)
     co = gftorf.consts_from_scene(sc)
     bg = torch.as_tensor(sc.bg, device="cuda")
-    dout = torch.as_tensor(scenes.random_dout(sc, 100 + rank), device="cuda")
+    dout = torch.as_tensor(scenes.random_dout(sc, 100 + seed), device="cuda")
     tile = tuple(int(v) for v in args.tile.split("x"))
     ppt, mode = args.ppt, args.mode
     tuned = None
-    if args.autotune:
-        from paper_2505_05356_gb300 import autotune
-        tuned = autotune.autotune(N, B, W, H, nF, nP, p, fr, se, co, bg, dout, steps=2,
-                                  flags=xflags, n_sh=sc.n_sh)
+    if autotune:
+        from paper_2505_05356_gb300 import autotune as at
+        tuned = at.autotune(N, B, W, H, nF, nP, p, fr, se, co, bg, dout, steps=2,
+                            flags=xflags, n_sh=sc.n_sh)
         tile, ppt, mode = tuned["tile"], tuned["ppt"], tuned["mode"]
     r = gftorf.Renderer(N, B, W, H, nF, nP, tile=tile, render_mode=mode,
                         pixels_per_thread=ppt, flags=xflags, n_sh=sc.n_sh)
@@ -243,32 +263,29 @@ def run_ours(args):
         run = graph.replay
     else:
         run = step
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         run()
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         run()
     e1.record()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
     code, count = r.read_status()
     if code != gftorf.OK:
         raise RuntimeError("device status %s" % gftorf.STATUS.get(code))
     ms = max_over_ranks(ms, world, "cuda")
-    ms_per_step = ms / args.steps
-    value = world * B * args.steps / (ms / 1e3)
+    res = {"ms_per_step": ms / steps, "value": world * B * steps / (ms / 1e3),
+           "kernels_per_step": int(kernels_per_step), "tile": tile, "ppt": ppt, "mode": mode,
+           "tuned": tuned, "ws_bytes": r.ws_bytes, "C": r.C, "use_graph": use_graph}
 
     # --- per-stage timing (same stream, CUDA events, eager) ---
     stages = ["preprocess", "bin", "composite_fwd", "zero_grad_buffers", "composite_bwd",
@@ -277,15 +294,15 @@ def run_ours(args):
              lambda: r.zero_grad_buffers(grads), lambda: r.composite_bwd(bg, dout, grads),
              lambda: r.preprocess_bwd(p, grads)]
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(steps):
         ev[k][0].record()
         for i, c in enumerate(calls):
             c()
             ev[k][i + 1].record()
     torch.cuda.synchronize()
-    stage_ms = {s_: sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
+    stage_ms = {s_: sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)) / steps
                 for i, s_ in enumerate(stages)}
 
     # --- algorithmic work of this batch: evaluated (pixel, Gaussian) pairs
@@ -299,39 +316,51 @@ def run_ours(args):
     del rc
     torch.cuda.empty_cache()
     peaks, peak_kind = _peaks()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e9  # G FP32 lane-ops/s
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if alu is not None:
+        alu_peak = alu["ffma"] / 1e9  # G FP32 lane-ops/s, measured in this run
+        alu_src = "measured FFMA loop (gftorf_probe_throughput, this run)"
+    else:
+        n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        alu_peak = n_sm * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+        alu_src = "nominal: SMs x 128 FP32 lanes x max SM clock"
     vis = B * N  # upper bound of Gaussian-frames
     work = {
-        "composite_bwd": ("alu", pairs * OPS_PER_PAIR_BWD / 1e9, "Gop/s", alu_peak),
-        "composite_fwd": ("alu", pairs * OPS_PER_PAIR_FWD / 1e9, "Gop/s", alu_peak),
+        "composite_bwd": ("alu", pairs * OPS_PER_PAIR_BWD / 1e9, "Gop/s", alu_peak, alu_src),
+        "composite_fwd": ("alu", pairs * OPS_PER_PAIR_FWD / 1e9, "Gop/s", alu_peak, alu_src),
         # read 84 B of parameters + write a 48 B record, 8 B rect, 4 B key
         # (+ 4 B per SH coefficient read with the parameters)
-        "preprocess": ("hbm", vis * (84 + 60 + 4 * sc.n_sh) / 1e9, "GB/s", hbm_peak),
+        "preprocess": ("hbm", vis * (84 + 60 + 4 * sc.n_sh) / 1e9, "GB/s", hbm_peak, peak_kind),
         # instance values written once; depth keys 4 passes x 16 B
-        "bin": ("hbm", (instances * 4 + vis * 16 * 4) / 1e9, "GB/s", hbm_peak),
+        "bin": ("hbm", (instances * 4 + vis * 16 * 4) / 1e9, "GB/s", hbm_peak, peak_kind),
         "preprocess_bwd": ("hbm", (vis * (84 + 36 + 12) + N * 8 * sc.n_sh) / 1e9, "GB/s",
-                           hbm_peak),
-        "zero_grad_buffers": ("hbm", vis * 36 / 1e9, "GB/s", hbm_peak),
+                           hbm_peak, peak_kind),
+        "zero_grad_buffers": ("hbm", vis * 36 / 1e9, "GB/s", hbm_peak, peak_kind),
     }
-    dom = max(stage_ms, key=stage_ms.get)
-    bound, amount, unit, peak = work[dom]
-    achieved = amount / (stage_ms[dom] / 1e3)
-    roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 2),
-                "peak": round(peak, 2), "unit": unit, "frac": round(achieved / peak, 4),
-                "traffic": _traffic(dom, B), "peak_source": peak_kind}
     stage_rows = {}
     for s_ in stages:
-        b_, a_, u_, pk_ = work[s_]
+        b_, a_, u_, pk_, src_ = work[s_]
         ach = a_ / (stage_ms[s_] / 1e3) if stage_ms[s_] > 0 else 0.0
-        stage_rows[s_] = {"ms": round(stage_ms[s_], 4), "bound": b_, "achieved": round(ach, 1),
-                          "unit": u_, "frac": round(ach / pk_, 4)}
+        row = {"ms": round(stage_ms[s_], 4), "bound": b_, "achieved": round(ach, 1),
+               "unit": u_, "peak": round(pk_, 1), "frac": round(ach / pk_, 4)}
+        if b_ == "alu" and alu is not None:
+            # one ex2 per evaluated pair: the multi-function unit's share
+            ex2 = pairs / (stage_ms[s_] / 1e3) / 1e9
+            row["mufu"] = {"achieved": round(ex2, 1), "peak": round(alu["ex2"] / 1e9, 1),
+                           "unit": "G ex2/s", "frac": round(ex2 / (alu["ex2"] / 1e9), 4)}
+        stage_rows[s_] = row
+    dom = max(stage_ms, key=stage_ms.get)
+    b_, a_, u_, pk_, src_ = work[dom]
+    achieved = a_ / (stage_ms[dom] / 1e3)
+    roofline = {"kernel": dom, "bound": b_, "achieved": round(achieved, 2),
+                "peak": round(pk_, 2), "unit": u_, "frac": round(achieved / pk_, 4),
+                "traffic": _traffic(dom, B), "peak_source": src_}
+    if "mufu" in stage_rows[dom]:
+        roofline["mufu"] = stage_rows[dom]["mufu"]
+    res.update(stage_rows=stage_rows, roofline=roofline, instances=instances, pairs=pairs)
 
     # --- end to end through the public API with host buffers ---
-    e2e = None
-    if not args.skip_e2e:
+    if want_e2e:
         # end to end from pinned host memory: every step copies its inputs in
         # and its gradients out; the copies of neighbouring steps overlap the
         # compute (two buffer sets, two graphs, copy streams; pipeline.py)
@@ -371,18 +400,18 @@ def run_ours(args):
             dist.barrier()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record()
-        hs.run(host_in, host_out, args.steps, start=a0)
+        hs.run(host_in, host_out, steps, start=a0)
         a1.record()
         torch.cuda.synchronize()
         ems = max_over_ranks(a0.elapsed_time(a1), world, "cuda")
-        e2e = {"value": round(world * B * args.steps / (ems / 1e3), 2), "unit": UNIT,
-               "pipelined": "host->device of step i+1 and device->host of step i-1 overlap "
-                            "step i (two buffer sets, two CUDA graphs, copy streams)",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        res["e2e"] = {"value": round(world * B * steps / (ems / 1e3), 2), "unit": UNIT,
+                      "pipelined": "host->device of step i+1 and device->host of step i-1 "
+                                   "overlap step i (two buffer sets, two CUDA graphs, copy "
+                                   "streams)",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # --- per-frame plain launches (no batching, no graph), same work ---
-    plain = None
-    if not args.skip_plain and rank == 0:
+    if want_plain:
         r1 = gftorf.Renderer(N, 1, W, H, nF, nP, tile=tile, render_mode=0,
                              pixels_per_thread=ppt, flags=xflags, n_sh=sc.n_sh,
                              max_instances=max(1024, int(r.capacity / B * 1.6)))
@@ -407,23 +436,77 @@ def run_ours(args):
                 for k, v in gacc.items():
                     v.add_(g1[k])
 
-        for _ in range(max(2, args.warmup)):
+        for _ in range(max(2, warmup)):
             plain_step()
         torch.cuda.synchronize()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         q0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             plain_step()
         q1.record()
         torch.cuda.synchronize()
-        pms = q0.elapsed_time(q1) / args.steps
+        pms = q0.elapsed_time(q1) / steps
         code1, _ = r1.read_status()
-        plain = {"value": round(B / (pms / 1e3), 2), "unit": UNIT, "ms_per_step": round(pms, 3),
-                 "status": gftorf.STATUS.get(code1)}
+        res["plain"] = {"value": round(B / (pms / 1e3), 2), "unit": UNIT,
+                        "ms_per_step": round(pms, 3), "status": gftorf.STATUS.get(code1)}
+        del r1
+    del r, out, grads
+    torch.cuda.empty_cache()
+    return res
+
+
+def launch_config(m, args) -> dict:
+    """The launch choices a measurement ran with (autotuned unless asked)."""
+    return {"tile": "%dx%d" % tuple(m["tile"]), "pixels_per_thread": m["ppt"],
+            "render_mode": "persistent" if m["mode"] == 1 else "grid",
+            "autotuned": m["tuned"] is not None, "cuda_graph": m["use_graph"],
+            "kernels_per_step": m["kernels_per_step"]}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_05356_gb300 import gftorf, scenes
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    sc = scenes.make_scene(args.workload, seed=rank, **_overrides(args))
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    # the compositing kernels' denominators, measured on this GPU in this run
+    alu = gftorf.measure_alu_peaks()
+    m = measure(sc, args, args.steps, args.warmup, world=world, seed=rank,
+                autotune=args.autotune, want_e2e=not args.skip_e2e,
+                want_plain=not args.skip_plain and rank == 0, alu=alu)
+    clk = clocks.stop()
+
+    extras = {}
+    if rank == 0 and not args.skip_extra and not _overrides(args):
+        for name in EXTRA_WORKLOADS:
+            if name == args.workload:
+                continue
+            esc = scenes.make_scene(name, seed=0)
+            em = measure(esc, args, min(args.steps, 10), max(3, min(args.warmup, 5)),
+                         autotune=args.autotune, alu=alu)
+            extras[name] = {"metric": metric_of(esc), "value": round(em["value"], 2),
+                            "unit": UNIT, "ms_per_step": round(em["ms_per_step"], 4),
+                            "config": workload_config(esc, name, args),
+                            "launch": launch_config(em, args),
+                            "roofline": em["roofline"], "stages": em["stage_rows"],
+                            "instances_per_step": em["instances"],
+                            "pairs_per_step": em["pairs"],
+                            "autotune": None if em["tuned"] is None else em["tuned"]["table"]}
+    if world > 1:
+        dist.barrier()
 
     fitres = None
     if not args.skip_fit and rank == 0:
-        fitres = fit_loop_bench(args, tile, ppt, mode)
+        fitres = fit_loop_bench(args, m["tile"], m["ppt"], m["mode"])
     mlpres = None
     if not args.skip_mlp and rank == 0:
         mlpres = mlp_bench(args, frames=tuple(int(v) for v in args.mlp_frames.split(",") if v))
@@ -433,40 +516,36 @@ def run_ours(args):
         cpu = cpu_baseline(sc, args.cpu_seconds)
 
     if rank == 0:
+        launch = launch_config(m, args)
+        launch.update({"parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (%.0f MB workspace per step)"
+                             % (m["ws_bytes"] / 1e6),
+                       "instances_per_step": m["instances"], "pairs_per_step": m["pairs"]})
         line = {
-            "metric": metric_of(sc), "value": round(value, 2), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "metric": metric_of(sc), "value": round(m["value"], 2), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(m["ms_per_step"], 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; shaped like the paper's C-ToF scenes)",
-            "config": {"workload": "%s: %d dynamic Gaussians (cubic trajectories), %dx%d, "
-                                   "%d timesteps per batch, %s MHz x %d offsets + ambient, "
-                                   "30-100%% visible per frame" % (
-                                       args.workload, N, W, H, B,
-                                       "+".join("%g" % (f / 1e6) for f in sc.sensor.freqs_hz),
-                                       nP),
-                       "frames_per_step": B, "tile": "%dx%d" % tuple(tile),
-                       "channels": r.C,
-                       "reflectivity": ("SH degree %d" % args.sh_degree
-                                        if args.sh_degree >= 0 else "scalar"),
-                       "capture": ("asynchronous (1 offset per frame, Eq. 7 motion)"
-                                   if args.async_capture else "synchronous quartets"),
-                       "pixels_per_thread": ppt,
-                       "render_mode": "persistent" if mode == 1 else "grid",
-                       "autotuned": tuned is not None,
-                       "cuda_graph": use_graph, "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "l2": "inputs larger than L2 (%.0f MB workspace per step)" % (r.ws_bytes / 1e6),
-                       "instances_per_step": instances, "pairs_per_step": pairs},
-            "gpu_launches": int(kernels_per_step * args.steps),
-            "kernels_per_step": int(kernels_per_step),
-            "roofline": roofline,
-            "stages": stage_rows,
-            "e2e": e2e,
-            "per_frame_plain": plain,
+            "config": workload_config(sc, args.workload, args),
+            "launch": launch,
+            "gpu_launches": int(m["kernels_per_step"] * args.steps),
+            "kernels_per_step": int(m["kernels_per_step"]),
+            "roofline": m["roofline"],
+            "alu_peaks": {"ffma_g_lane_ops_s": round(alu["ffma"] / 1e9, 1),
+                          "ex2_g_lane_ops_s": round(alu["ex2"] / 1e9, 1),
+                          "how": "gftorf_probe_throughput: 8 x 256-thread CTAs per SM, 8 "
+                                 "independent chains per thread, best of 5 launches, CUDA "
+                                 "events; clocks as in 'clocks'"},
+            "stages": m["stage_rows"],
+            "e2e": m.get("e2e"),
+            "per_frame_plain": m.get("plain"),
+            "workloads": extras or None,
             "optimization_loop": fitres,
             "deformation_mlp": mlpres,
             "cpu_baseline": cpu,
             "clocks": clk,
-            "autotune": None if tuned is None else tuned["table"],
+            "autotune": None if m["tuned"] is None else m["tuned"]["table"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -773,8 +852,7 @@ def run_reference(args):
         "ms_per_step": round(1e3 * sc.frames / value, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded; shaped like the paper's C-ToF scenes)",
-        "config": {"workload": "%s: %d dynamic Gaussians, %dx%d, %d timesteps per batch"
-                               % (WORKLOAD, sc.n, sc.width, sc.height, sc.frames)},
+        "config": workload_config(sc, args.workload, args),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": ora.num_threads(),
                          "nproc": os.cpu_count(), "kind": "oracle",
                          "sample": "per step one frame: projection of all Gaussians + fwd/bwd of "
@@ -803,6 +881,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="skip the other full-size workloads (100k at 640x480; 500k, 2 freq)")
     ap.add_argument("--skip-fit", action="store_true",
                     help="skip the optimisation-loop measurement (iterations/s)")
     ap.add_argument("--fit-iters", type=int, default=20)

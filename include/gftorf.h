@@ -283,7 +283,11 @@ gftorf_status gftorf_sort_footprints(const gftorf_dims* dims, const float* u,
  * handed).  The paper has no counterpart; it is a packaging convenience.
  * Same arguments, results and bit-exact ordering as gftorf_sort_footprints.
  * Its scratch is a fixed 32 MiB device array inside the library, so:
- *   - every GPU that loads the library holds those 32 MiB until process exit;
+ *   - the 32 MiB are reserved on a device at the latest by the first call
+ *     made there (with lazy module loading, CUDA creates the array when the
+ *     library's device code first loads on that device, so a failure to get
+ *     the memory shows up as GFTORF_ERR_CUDA from that call) and stay
+ *     reserved until the process exits;
  *   - problems whose binning scratch (about 32 B per (frame, Gaussian) plus
  *     4 B per instance of dims->max_instances plus per-tile counters) does
  *     not fit return GFTORF_ERR_WORKSPACE before any work is enqueued;
@@ -336,6 +340,24 @@ int64_t gftorf_kernel_launches(void);
 gftorf_status gftorf_read_counters(const gftorf_dims* dims, void* workspace,
                                    size_t workspace_bytes, int64_t* counters,
                                    void* stream);
+
+/* Throughput probes: the rooflines of the compositing kernels (Eq. 4 forward,
+ * Eq. S3 backward) are FP32 issue (each evaluated (pixel, Gaussian) pair is a
+ * short chain of FP32 multiply-adds, compares and selects) and, for the one
+ * base-2 exponential per pair, the multi-function unit.  This enqueues one
+ * launch of 8 CTAs x 256 threads per SM, each thread running 8 independent
+ * chains of `iters` operations:
+ *   GFTORF_PROBE_FFMA: x <- x a + b (FP32 fused multiply-add);
+ *   GFTORF_PROBE_EX2:  x <- 2^-x (ex2.approx.ftz.f32, the instruction the
+ *                      compositing kernels use).
+ * *lane_ops (HOST int64) receives the lane operations the launch performs;
+ * time the launch with events on `stream` to get the rate.  sink: device
+ * float[1], never written in practice (it keeps the loops live).  iters must
+ * be a positive multiple of 16.  Not part of the method: measurement only. */
+#define GFTORF_PROBE_FFMA 0
+#define GFTORF_PROBE_EX2 1
+gftorf_status gftorf_probe_throughput(int32_t kind, int32_t iters, float* sink,
+                                      int64_t* lane_ops, void* stream);
 
 /* ---- Optimisation loop (Sec. 4: raw-quad L2 loss, Adam with betas (0.9,
  * 0.999) and epsilon 1e-15, a fresh random background every iteration) ----

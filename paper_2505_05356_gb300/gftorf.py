@@ -129,6 +129,9 @@ def load(build_if_missing: bool = True):
     L.gftorf_read_counters.restype = ctypes.c_int
     L.gftorf_kernel_launches.restype = ctypes.c_int64
     L.gftorf_kernel_launches.argtypes = []
+    L.gftorf_probe_throughput.argtypes = [ctypes.c_int32, ctypes.c_int32, vp,
+                                          _P(ctypes.c_int64), vp]
+    L.gftorf_probe_throughput.restype = ctypes.c_int
     L.gftorf_train_begin.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_uint64, vp]
     L.gftorf_train_begin_shard.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_uint64,
                                            ctypes.c_int64, ctypes.c_int64, vp]
@@ -500,6 +503,39 @@ def sort_footprints_noalloc(u, v, radius, z, width, height, tile=(16, 16), max_i
                                             _ptr(z), _ptr(keys), _ptr(vals), _ptr(ranges),
                                             _ptr(count), _stream())
     return code, keys, vals, ranges, count
+
+
+PROBE_FFMA, PROBE_EX2 = 0, 1
+
+
+def probe_throughput(kind: int, iters: int, sink: torch.Tensor) -> int:
+    """gftorf_probe_throughput: enqueue one throughput-probe launch on the
+    current stream; returns the lane operations it performs."""
+    ops = ctypes.c_int64(0)
+    _check(load().gftorf_probe_throughput(int(kind), int(iters), _ptr(sink), ctypes.byref(ops),
+                                          _stream()), "gftorf_probe_throughput")
+    return int(ops.value)
+
+
+def measure_alu_peaks(iters: int = 4096, reps: int = 5) -> Dict[str, float]:
+    """FP32 FMA and ex2 lane operations per second of this device (best of
+    `reps` launches, CUDA events on the current stream, after a warm-up)."""
+    sink = torch.zeros(1, device="cuda")
+    out = {}
+    for name, kind in (("ffma", PROBE_FFMA), ("ex2", PROBE_EX2)):
+        probe_throughput(kind, iters, sink)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ops = probe_throughput(kind, iters, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name] = ops / (best / 1e3)
+        out[name + "_ms"] = best
+    return out
 
 
 # --- autograd ------------------------------------------------------------------

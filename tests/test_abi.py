@@ -191,3 +191,13 @@ def test_mlp_calls_reject_bad_arguments_on_host(lib):
                                  None) == gftorf.ERR_ARG
     assert L.gftorf_mlp_export(1000, 2, 9, 0, 256, ws, small, None) == gftorf.ERR_ARG
     assert L.gftorf_mlp_export(1000, 2, 1, 8, 256, ws, small, None) == gftorf.ERR_ARG
+
+
+def test_throughput_probe_rejects_bad_arguments_on_host(lib):
+    ops = ctypes.c_int64(0)
+    fake = ctypes.c_void_p(256)  # never dereferenced: every call below fails its host checks
+    for kind, iters in ((2, 64), (-1, 64), (0, 0), (0, 17), (1, -16)):
+        assert lib.gftorf_probe_throughput(kind, iters, fake, ctypes.byref(ops), None) == \
+            gftorf.ERR_ARG, (kind, iters)
+    assert lib.gftorf_probe_throughput(0, 64, None, ctypes.byref(ops), None) == gftorf.ERR_ARG
+    assert lib.gftorf_probe_throughput(0, 64, fake, None, None) == gftorf.ERR_ARG
