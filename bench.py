@@ -312,7 +312,7 @@ def measure(sc, args, steps, warmup, world=1, seed=0, autotune=True, want_e2e=Fa
                          max_instances=r.capacity, n_sh=sc.n_sh)
     rc.preprocess(p, fr, se, co)
     rc.render_fwd(bg)
-    instances, pairs = rc.counters()
+    instances, pairs, pairs_warp = rc.counters(with_warp=True)
     del rc
     torch.cuda.empty_cache()
     peaks, peak_kind = _peaks()
@@ -357,7 +357,8 @@ def measure(sc, args, steps, warmup, world=1, seed=0, autotune=True, want_e2e=Fa
                 "traffic": _traffic(dom, B), "peak_source": src_}
     if "mufu" in stage_rows[dom]:
         roofline["mufu"] = stage_rows[dom]["mufu"]
-    res.update(stage_rows=stage_rows, roofline=roofline, instances=instances, pairs=pairs)
+    res.update(stage_rows=stage_rows, roofline=roofline, instances=instances, pairs=pairs,
+               pairs_warp=pairs_warp)
 
     # --- end to end through the public API with host buffers ---
     if want_e2e:
@@ -520,7 +521,8 @@ def run_ours(args):
         launch.update({"parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (%.0f MB workspace per step)"
                              % (m["ws_bytes"] / 1e6),
-                       "instances_per_step": m["instances"], "pairs_per_step": m["pairs"]})
+                       "instances_per_step": m["instances"], "pairs_per_step": m["pairs"],
+                       "pairs_reaching_warp_per_step": m["pairs_warp"]})
         line = {
             "metric": metric_of(sc), "value": round(m["value"], 2), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -335,8 +335,12 @@ gftorf_status gftorf_read_device_status(const gftorf_dims* dims,
 int64_t gftorf_kernel_launches(void);
 
 /* Synchronises `stream`; counters[0] = tile instances of the last binning,
- * counters[1] = (pixel, Gaussian) pairs the last forward evaluated (0 unless
- * dims->flags has GFTORF_FLAG_COUNT_PAIRS).  counters: HOST int64[2]. */
+ * counters[1] = (pixel, Gaussian) pairs the last forward evaluated: per
+ * pixel, the entries of its tile's list up to and including the one that
+ * stops it; counters[2] = the part of counters[1] in records that can reach
+ * alpha_min in the rows of the pixel's warp (the compositing kernels skip the
+ * others for the whole warp; the results do not depend on it).  Both are 0
+ * unless dims->flags has GFTORF_FLAG_COUNT_PAIRS.  counters: HOST int64[3]. */
 gftorf_status gftorf_read_counters(const gftorf_dims* dims, void* workspace,
                                    size_t workspace_bytes, int64_t* counters,
                                    void* stream);

@@ -43,9 +43,11 @@ bool dims_ok(const gftorf_dims* d) {
     return false;
   if (d->reserved != 0) return false;
   if (d->max_instances < 0 || d->max_instances > (int64_t)0xFFFFFFFFll) return false;
-  const int64_t tiles = (int64_t)((d->width + d->tile_w - 1) / d->tile_w) *
-                        ((d->height + d->tile_h - 1) / d->tile_h);
-  if (tiles > 50000) return false;  // per-CTA tile counters live in shared memory
+  // per-CTA tile counters ((tiles_x + 1) x (tiles_y + 1), 4 bytes each) live in
+  // shared memory
+  const int64_t corners = (int64_t)((d->width + d->tile_w - 1) / d->tile_w + 1) *
+                          ((d->height + d->tile_h - 1) / d->tile_h + 1);
+  if (corners > 50000) return false;
   return true;
 }
 
@@ -80,8 +82,8 @@ Layout make_layout(const gftorf_dims* d) {
   L.n_dblk = (L.N + kSortTile - 1) / kSortTile;
   L.n_chunk = (int)((d->max_instances + kChunk - 1) / kChunk) + L.B;
   L.n_scan = (int)(((size_t)L.B * L.N + kScanTile - 1) / kScanTile);
-  int nw = 8;
-  while (nw > 1 && (size_t)nw * L.NT * 4 > 96 * 1024) nw >>= 1;
+  int nw = 8;  // scatter warps: per-warp tile counters within 96 KB where possible
+  while (nw > 1 && (size_t)nw * (L.tiles_x + 1) * (L.tiles_y + 1) * 4 > 96 * 1024) nw >>= 1;
   L.scatter_warps = nw;
   L.cap = d->max_instances;
   const size_t BN = (size_t)L.B * L.N, HW = (size_t)L.W * L.H;
@@ -95,6 +97,7 @@ Layout make_layout(const gftorf_dims* d) {
   L.off_table = take(sizeof(Table) + sizeof(TableT<float>));
   L.off_rec = take(BN * L.rec_stride * L.real_size);
   L.off_rect = take(BN * sizeof(uint2));
+  L.off_srect = take(BN * sizeof(uint2));
   L.off_zkey = take(BN * 4);
   L.off_zkey2 = take(2 * BN * 4);
   L.off_ids = take(BN * 4);
@@ -163,6 +166,7 @@ Layout binning_layout(const gftorf_dims* d) {
   L.off_table = take(0);
   L.off_rec = take(0);
   L.off_rect = take(BN * sizeof(uint2));
+  L.off_srect = take(BN * sizeof(uint2));
   L.off_zkey = take(BN * 4);
   L.off_zkey2 = take(2 * BN * 4);
   L.off_ids = take(BN * 4);
@@ -188,7 +192,7 @@ using namespace gftorf;
 
 extern "C" {
 
-int32_t gftorf_version(void) { return 100; }
+int32_t gftorf_version(void) { return 101; }
 
 int64_t gftorf_kernel_launches(void) { return gftorf::launches_so_far(); }
 
@@ -207,6 +211,7 @@ gftorf_status gftorf_read_counters(const gftorf_dims* dims, void* workspace,
     return GFTORF_ERR_CUDA;
   counters[0] = h.count;
   counters[1] = (int64_t)h.pairs;
+  counters[2] = (int64_t)h.pairs_warp;
   return GFTORF_OK;
 }
 

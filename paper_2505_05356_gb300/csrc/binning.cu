@@ -8,11 +8,18 @@
 // BEFORE duplication -- they are a per-Gaussian key -- and whose high digit
 // (frame, tile) is one stable counting pass over the duplicated instances:
 //   1. depth sort: 4 passes of 8 bits over the per-frame depth keys
-//      (culled Gaussians carry 0xFFFFFFFF and end up last);
-//   2. per chunk of 4096 depth-ordered Gaussians, count covered tiles;
-//   3. exclusive scan over (frame, tile, chunk) -> tile ranges and bases;
-//   4. scatter: each warp walks its Gaussians in depth order and writes the
-//      Gaussian index at its tile's running cursor (stable by construction).
+//      (culled Gaussians carry 0xFFFFFFFF and end up last); the last pass
+//      also writes each Gaussian's tile rectangle in depth order;
+//   2. emission offsets: exclusive scan of the tiles each depth-ordered
+//      Gaussian covers; chunks of kChunk consecutive instances per frame;
+//   3. per chunk, tile counts: every Gaussian (or the part of its rectangle
+//      inside the chunk) adds +-1 at the corners of its tile rectangle in a
+//      difference array, whose 2D prefix sum is the count of each tile;
+//      exclusive scans over chunks and tiles give the tile ranges;
+//   4. scatter: per warp of a chunk the same corner counts give its cursors;
+//      then the warp walks its Gaussians in depth order, lanes spread over
+//      one Gaussian's tiles, each writing the Gaussian index at its tile's
+//      running cursor (stable by construction).
 // The 64-bit keys themselves are never needed by the compositing kernels;
 // gftorf_export_tile_lists materialises them from the ranges.
 #include "gftorf_internal.cuh"
@@ -77,6 +84,68 @@ __device__ __forceinline__ int warp_upper_rank(const uint32_t* __restrict__ e, i
     hi = min(hi, lo + step);
   }
   return lo;
+}
+
+// ---------------------------------------------------------------------------
+// tile counts of rectangles from their corners
+// ---------------------------------------------------------------------------
+// A rectangle [xa, xb) x [ya, yb) of tiles adds +1 at (xa, ya) and (xb, yb)
+// and -1 at (xb, ya) and (xa, yb) of a (tiles_y + 1) x (tiles_x + 1)
+// difference array D (row stride `cols` = tiles_x + 1, arithmetic mod 2^32);
+// the inclusive 2D prefix sum of D is then, at every tile, the number of
+// rectangles covering it.
+__device__ __forceinline__ void diff_add_rect(uint32_t* D, int cols, int xa, int ya, int xb,
+                                              int yb) {
+  if (xa >= xb || ya >= yb) return;
+  atomicAdd(&D[ya * cols + xa], 1u);
+  atomicAdd(&D[ya * cols + xb], 0xFFFFFFFFu);
+  atomicAdd(&D[yb * cols + xa], 0xFFFFFFFFu);
+  atomicAdd(&D[yb * cols + xb], 1u);
+}
+
+// The instances [lo, hi) (row-major indices, hi > lo) of a Gaussian whose
+// tile rectangle is w wide and starts at (x0, y0): at most three rectangles
+// (the tail of a first row, whole rows, the head of a last row).
+__device__ __forceinline__ void diff_add_span(uint32_t* D, int cols, int x0, int y0, int w,
+                                              int lo, int hi) {
+  const int ky0 = lo / w, kx0 = lo - ky0 * w;
+  const int last = hi - 1;
+  const int ky1 = last / w, kx1 = last - ky1 * w;
+  if (ky0 == ky1) {
+    diff_add_rect(D, cols, x0 + kx0, y0 + ky0, x0 + kx1 + 1, y0 + ky0 + 1);
+  } else if (kx0 == 0 && kx1 == w - 1) {
+    diff_add_rect(D, cols, x0, y0 + ky0, x0 + w, y0 + ky1 + 1);
+  } else {
+    diff_add_rect(D, cols, x0 + kx0, y0 + ky0, x0 + w, y0 + ky0 + 1);
+    diff_add_rect(D, cols, x0, y0 + ky0 + 1, x0 + w, y0 + ky1);
+    diff_add_rect(D, cols, x0, y0 + ky1, x0 + kx1 + 1, y0 + ky1 + 1);
+  }
+}
+
+// Inclusive 2D prefix sum of D (rows x cols) by threads [0, nthr) of a group
+// (a warp: WARP = true, else the whole CTA): a sequential scan per row, then
+// per column.
+template <bool WARP>
+__device__ __forceinline__ void prefix2d(uint32_t* D, int rows, int cols, int tid, int nthr) {
+  for (int y = tid; y < rows; y += nthr) {
+    uint32_t* row = D + y * cols;
+    uint32_t run = 0;
+    for (int x = 0; x < cols; ++x) {
+      run += row[x];
+      row[x] = run;
+    }
+  }
+  if (WARP)
+    __syncwarp();
+  else
+    __syncthreads();
+  for (int x = tid; x < cols; x += nthr) {
+    uint32_t run = 0;
+    for (int y = 0; y < rows; ++y) {
+      run += D[y * cols + x];
+      D[y * cols + x] = run;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -170,12 +239,15 @@ __global__ void __launch_bounds__(256) dsort_scan_digits_kernel(uint32_t* __rest
   cta_exclusive_scan<uint32_t>(dtot + (size_t)blockIdx.x * 256, 256, nullptr);
 }
 
+// rin/rout (last pass only, else null): the Gaussians' tile rectangles are
+// written in the sorted order as well
 __global__ void __launch_bounds__(kSortThreads)
     dsort_scatter_kernel(const uint32_t* __restrict__ kin,
                          const uint32_t* __restrict__ iin,
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ iout,
                          int N, int shift, const uint32_t* __restrict__ dh,
-                         const uint32_t* __restrict__ dtot, int n_dblk) {
+                         const uint32_t* __restrict__ dtot, int n_dblk,
+                         const uint2* __restrict__ rin, uint2* __restrict__ rout) {
   __shared__ uint32_t wc[kSortWarps][256];
   const int blk = blockIdx.x, b = blockIdx.y;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -225,6 +297,7 @@ __global__ void __launch_bounds__(kSortThreads)
       const uint32_t dst = wc[w][d] + loc[it];
       kout[fb + dst] = key[it];
       iout[fb + dst] = id[it];
+      if (rout) rout[fb + dst] = rin[fb + id[it]];
     }
   }
 }
@@ -236,9 +309,7 @@ __global__ void __launch_bounds__(kSortThreads)
 // e[g] <= k < e[g + 1]
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-    inst_count_kernel(const uint32_t* __restrict__ sorted_ids,
-                      const uint2* __restrict__ rect,
-                      const Header* __restrict__ hdr,
+    inst_count_kernel(const uint2* __restrict__ srect, const Header* __restrict__ hdr,
                       uint32_t* __restrict__ ecnt, int N) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
@@ -246,7 +317,7 @@ __global__ void __launch_bounds__(256)
   uint32_t c = 0;
   if (i < (int)hdr->vis[b]) {
     int x0, y0, x1, y1;
-    unpack_rect(rect[(size_t)b * N + sorted_ids[(size_t)b * N + i]], x0, y0, x1, y1);
+    unpack_rect(srect[(size_t)b * N + i], x0, y0, x1, y1);
     c = (uint32_t)((x1 - x0) * (y1 - y0));
   }
   ecnt[(size_t)b * N + i] = c;
@@ -349,46 +420,45 @@ __device__ __forceinline__ ChunkPos chunk_pos(const Header* hdr, int c) {
   return p;
 }
 
-// count the tiles hit by the instances [s, e) of one chunk
+// count the tiles hit by the instances [s, e) of one chunk: corners of each
+// Gaussian's part of the chunk in a difference array, then its 2D prefix sum
 __global__ void __launch_bounds__(256)
-    tile_count_kernel(const uint32_t* __restrict__ sorted_ids,
-                      const uint2* __restrict__ rect,
-                      const Header* __restrict__ hdr,
-                      const uint32_t* __restrict__ eoff,
-                      uint32_t* __restrict__ tcnt, int N, int NT, int tiles_x,
-                      int B) {
-  extern __shared__ uint32_t hist[];  // NT
+    tile_count_kernel(const uint2* __restrict__ srect, const Header* __restrict__ hdr,
+                      const uint32_t* __restrict__ eoff, uint32_t* __restrict__ tcnt, int N,
+                      int NT, int tiles_x, int tiles_y, int B) {
+  extern __shared__ uint32_t D[];  // (tiles_y + 1) x (tiles_x + 1)
   __shared__ int s_r0;
   const int c = blockIdx.x;
   if ((uint32_t)c >= hdr->coff[B]) return;
   const ChunkPos cp = chunk_pos(hdr, c);
   const int vis = (int)hdr->vis[cp.b];
   const uint32_t* eb = eoff + (size_t)cp.b * N;
-  for (int t = threadIdx.x; t < NT; t += blockDim.x) hist[t] = 0;
+  const int cols = tiles_x + 1, rows = tiles_y + 1;
+  for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) D[t] = 0;
   if (threadIdx.x < 32) {
     const int r0 = warp_upper_rank(eb, vis, cp.s, threadIdx.x);
     if (threadIdx.x == 0) s_r0 = r0;
   }
   __syncthreads();
-  const uint32_t* ids = sorted_ids + (size_t)cp.b * N;
-  const uint2* rc = rect + (size_t)cp.b * N;
+  const uint2* rc = srect + (size_t)cp.b * N;
   for (int r = s_r0 + threadIdx.x; r < vis; r += blockDim.x) {
     const uint32_t eo = eb[r];
     if (eo >= cp.e) break;
     int x0, y0, x1, y1;
-    unpack_rect(rc[ids[r]], x0, y0, x1, y1);
+    unpack_rect(rc[r], x0, y0, x1, y1);
     const int w = x1 - x0;
     const uint32_t n = (uint32_t)(w * (y1 - y0));
     const uint32_t lo = max(cp.s, eo) - eo, hi = min(cp.e, eo + n) - eo;
-    int ky = (int)(lo / (uint32_t)w), kx = (int)(lo - (uint32_t)ky * w);
-    for (uint32_t k = lo; k < hi; ++k) {
-      atomicAdd(&hist[(y0 + ky) * tiles_x + x0 + kx], 1u);
-      if (++kx == w) kx = 0, ++ky;
-    }
+    diff_add_span(D, cols, x0, y0, w, (int)lo, (int)hi);
   }
   __syncthreads();
+  prefix2d<false>(D, rows, cols, threadIdx.x, blockDim.x);
+  __syncthreads();
   uint32_t* out = tcnt + (size_t)c * NT;
-  for (int t = threadIdx.x; t < NT; t += blockDim.x) out[t] = hist[t];
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    out[t] = D[ty * cols + tx];
+  }
 }
 
 // per (frame, tile): exclusive prefix over the frame's chunks; tile totals.
@@ -441,20 +511,25 @@ __global__ void __launch_bounds__(1024)
   if (threadIdx.x == 0 && total > (uint64_t)cap) set_status(hdr, GFTORF_ERR_CAPACITY);
 }
 
-// Stable scatter of one chunk: warp w owns the instance sub-range
-// [s + w kChunk/nw, ...) and walks its Gaussians in depth order, one at a
-// time, lanes spread over the Gaussian's tiles of the sub-range; each tile's
-// cursor starts at tile base + chunk prefix + earlier warps' counts.
+// Stable scatter of one chunk.  Warp w owns the instance sub-range
+// [s + w kChunk/nw, ...).  Its per-tile counts come from the corners of its
+// Gaussians' parts (as in tile_count); each tile's cursor for warp w starts
+// at tile base + chunk prefix + earlier warps' counts.  Then the warp takes
+// its Gaussians 32 at a time (depth order) and walks them one by one, lanes
+// spread over the Gaussian's tiles of the sub-range (the tiles of one
+// Gaussian are distinct, so the lanes never share a cursor); the row-major
+// index in the rectangle is split into (row, column) with a float reciprocal
+// and an exact one-step correction.
 __global__ void __launch_bounds__(256)
     tile_scatter_kernel(const uint32_t* __restrict__ sorted_ids,
-                        const uint2* __restrict__ rect,
+                        const uint2* __restrict__ srect,
                         const Header* __restrict__ hdr,
                         const uint32_t* __restrict__ eoff,
                         const uint32_t* __restrict__ tcnt,
                         const uint32_t* __restrict__ toff,
                         uint32_t* __restrict__ values, int N, int NT,
-                        int tiles_x, int B, int64_t cap) {
-  extern __shared__ uint32_t cur[];  // [warps][NT]
+                        int tiles_x, int tiles_y, int B, int64_t cap) {
+  extern __shared__ uint32_t cur[];  // [warps][(tiles_y + 1) x (tiles_x + 1)]
   const int c = blockIdx.x;
   if ((uint32_t)c >= hdr->coff[B]) return;
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -462,14 +537,15 @@ __global__ void __launch_bounds__(256)
   const int vis = (int)hdr->vis[cp.b];
   const uint32_t* eb = eoff + (size_t)cp.b * N;
   const uint32_t* ids = sorted_ids + (size_t)cp.b * N;
-  const uint2* rc = rect + (size_t)cp.b * N;
-  for (int i = threadIdx.x; i < nw * NT; i += blockDim.x) cur[i] = 0;
+  const uint2* rc = srect + (size_t)cp.b * N;
+  const int cols = tiles_x + 1, rows = tiles_y + 1, A = rows * cols;
+  for (int i = threadIdx.x; i < nw * A; i += blockDim.x) cur[i] = 0;
   const uint32_t per = kChunk / nw;
   const uint32_t sw = cp.s + (uint32_t)w * per;
   const uint32_t ew = min(sw + per, cp.e);
   const bool active = sw < ew;
   const int rw = active ? warp_upper_rank(eb, vis, sw, lane) : 0;
-  uint32_t* my = cur + (size_t)w * NT;
+  uint32_t* D = cur + (size_t)w * A;
   __syncthreads();
   // phase 1: this warp's tile counts
   if (active) {
@@ -477,66 +553,84 @@ __global__ void __launch_bounds__(256)
       const uint32_t eo = eb[r];
       if (eo >= ew) break;
       int x0, y0, x1, y1;
-      unpack_rect(rc[ids[r]], x0, y0, x1, y1);
+      unpack_rect(rc[r], x0, y0, x1, y1);
       const int wd = x1 - x0;
       const uint32_t n = (uint32_t)(wd * (y1 - y0));
       const uint32_t lo = max(sw, eo) - eo, hi = min(ew, eo + n) - eo;
-      int ky = (int)(lo / (uint32_t)wd), kx = (int)(lo - (uint32_t)ky * wd);
-      for (uint32_t k = lo; k < hi; ++k) {
-        atomicAdd(&my[(y0 + ky) * tiles_x + x0 + kx], 1u);
-        if (++kx == wd) kx = 0, ++ky;
-      }
+      diff_add_span(D, cols, x0, y0, wd, (int)lo, (int)hi);
     }
+    __syncwarp();
+    prefix2d<true>(D, rows, cols, lane, 32);
   }
   __syncthreads();
   // phase 2: cursors
   const uint32_t* cc = tcnt + (size_t)c * NT;
   const uint32_t* to = toff + (size_t)cp.b * NT;
   for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    const int ty = t / tiles_x, idx = t + ty;  // ty * cols + (t - ty * tiles_x)
     uint32_t run = to[t] + cc[t];
     for (int ww = 0; ww < nw; ++ww) {
-      const uint32_t v = cur[(size_t)ww * NT + t];
-      cur[(size_t)ww * NT + t] = run;
+      const uint32_t v = cur[(size_t)ww * A + idx];
+      cur[(size_t)ww * A + idx] = run;
       run += v;
     }
   }
   __syncthreads();
   if (!active) return;
-  // phase 3: ordered writes
-  for (int base = rw;; base += 32) {
-    const int r = base + lane;
-    uint32_t eo = 0xFFFFFFFFu, g = 0;
+  // phase 3: Gaussians one at a time, lanes over its tiles
+  __shared__ int4 s_g[8][32];  // per warp and Gaussian of the batch: lo, n, width, index
+  __shared__ float s_inv[8][32];  // 1 / width
+  for (int rb = rw;; rb += 32) {
+    const int r = rb + lane;
+    uint32_t eo = 0, g = 0;
     uint2 pr = make_uint2(0, 0);
+    bool ok = false;
     if (r < vis) {
       eo = eb[r];
-      if (eo < ew) {
+      ok = eo < ew;
+      if (ok) {
         g = ids[r];
-        pr = rc[g];
+        pr = rc[r];
       }
     }
-    const unsigned take = __ballot_sync(0xffffffffu, r < vis && eo < ew);
-    const int cnt = __popc(take);  // a prefix of the lanes (offsets increase)
-    for (int j = 0; j < cnt; ++j) {
-      const uint32_t gj = __shfl_sync(0xffffffffu, g, j);
-      const uint32_t eoj = __shfl_sync(0xffffffffu, eo, j);
-      uint2 rj;
-      rj.x = __shfl_sync(0xffffffffu, pr.x, j);
-      rj.y = __shfl_sync(0xffffffffu, pr.y, j);
-      int x0, y0, x1, y1;
-      unpack_rect(rj, x0, y0, x1, y1);
-      const int wd = x1 - x0;
-      const uint32_t n = (uint32_t)(wd * (y1 - y0));
-      const uint32_t lo = max(sw, eoj) - eoj, hi = min(ew, eoj + n) - eoj;
-      for (uint32_t k = lo + lane; k < hi; k += 32) {
-        const int ky = (int)(k / (uint32_t)wd), kx = (int)(k - (uint32_t)ky * wd);
-        const int t = (y0 + ky) * tiles_x + x0 + kx;
-        const uint32_t p = my[t];
-        my[t] = p + 1;
-        if ((int64_t)p < cap) values[p] = gj;
+    const unsigned take = __ballot_sync(0xffffffffu, ok);
+    if (!take) break;
+    int x0, y0, x1, y1;
+    unpack_rect(pr, x0, y0, x1, y1);
+    const int wd = ok ? x1 - x0 : 1;
+    const uint32_t n_all = ok ? (uint32_t)(wd * (y1 - y0)) : 0u;
+    const uint32_t lo = ok ? max(sw, eo) - eo : 0u;
+    const uint32_t n = ok ? min(ew, eo + n_all) - eo - lo : 0u;
+    s_g[w][lane] = make_int4((int)lo, (int)n, wd, (int)g);
+    s_inv[w][lane] = __frcp_rn((float)wd);
+    __syncwarp();
+    const int cnt = __popc(take);
+    const int xy = x0 | (y0 << 16);  // the rectangle's corner, broadcast by shuffle
+    for (int jj = 0; jj < cnt; ++jj) {
+      const int4 q = s_g[w][jj];
+      const float inv = s_inv[w][jj];
+      const int xyj = __shfl_sync(0xffffffffu, xy, jj);
+      for (int k = lane; k < q.y; k += 32) {
+        const int local = q.x + k;
+        int ky = (int)((float)local * inv);
+        int kx = local - ky * q.z;
+        if (kx < 0) {
+          --ky;
+          kx += q.z;
+        } else if (kx >= q.z) {
+          ++ky;
+          kx -= q.z;
+        }
+        const int idx = ((xyj >> 16) + ky) * cols + (xyj & 0xFFFF) + kx;
+        if ((unsigned)idx < (unsigned)A) {
+          const uint32_t p = D[idx];
+          D[idx] = p + 1;
+          if ((int64_t)p < cap) values[p] = (uint32_t)q.w;
+        }
       }
       __syncwarp();
     }
-    if (cnt < 32) break;
+    if (take != 0xffffffffu) break;
   }
 }
 
@@ -567,6 +661,7 @@ void launch_footprints(const Layout& L, const float* u, const float* v,
 void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   static PerDeviceOnce attr;
   attr.run([] {  // per-CTA tile counters may exceed the default 48 KB
+    // (at most 50000 counters of 4 bytes per CTA: see the dims checks)
     return cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024) == cudaSuccess &&
            cudaFuncSetAttribute(tile_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -581,6 +676,7 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   auto* dh = at<uint32_t>(ws, L.off_dhist);
   auto* dtot = at<uint32_t>(ws, L.off_dtot);
   auto* rect = at<const uint2>(ws, L.off_rect);
+  auto* srect = at<uint2>(ws, L.off_srect);
   auto* ecnt = at<uint32_t>(ws, L.off_ecnt);
   auto* bsum = at<uint64_t>(ws, L.off_bsum);
   auto* tcnt = at<uint32_t>(ws, L.off_tcnt);
@@ -604,26 +700,30 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
     dsort_scan_rows_kernel<<<(L.B * 256 + 7) / 8, 256, 0, st>>>(dh, dtot, L.B * 256, L.n_dblk);
     dsort_scan_digits_kernel<<<L.B, 256, 0, st>>>(dtot);
     dsort_scatter_kernel<<<g, kSortThreads, 0, st>>>(kin, iin, kout[pass & 1], iout[pass & 1],
-                                                     L.N, shift, dh, dtot, L.n_dblk);
+                                                     L.N, shift, dh, dtot, L.n_dblk,
+                                                     pass == 3 ? rect : nullptr,
+                                                     pass == 3 ? srect : nullptr);
     kin = kout[pass & 1];
     iin = iout[pass & 1];
   }
   // 2. emission offsets of the depth-ordered Gaussians, chunk table
   const int64_t S = (int64_t)L.B * L.N;
-  inst_count_kernel<<<dim3((L.N + 255) / 256, L.B), 256, 0, st>>>(sorted, rect, hdr, ecnt, L.N);
+  inst_count_kernel<<<dim3((L.N + 255) / 256, L.B), 256, 0, st>>>(srect, hdr, ecnt, L.N);
   scan_reduce_kernel<<<L.n_scan, 256, 0, st>>>(ecnt, S, bsum);
   scan_top_kernel<<<1, 1024, 0, st>>>(bsum, L.n_scan);
   scan_down_kernel<<<L.n_scan, 256, 0, st>>>(ecnt, S, bsum);
   chunk_table_kernel<<<1, 32, 0, st>>>(ecnt, bsum, L.n_scan, hdr, L.B, L.N, L.cap, L.n_chunk);
   // 3. per-chunk tile counts, per-frame column scan, tile ranges
-  tile_count_kernel<<<L.n_chunk, 256, (size_t)L.NT * 4, st>>>(sorted, rect, hdr, ecnt, tcnt,
-                                                              L.N, L.NT, L.tiles_x, L.B);
+  const size_t corners = (size_t)(L.tiles_x + 1) * (L.tiles_y + 1) * 4;
+  tile_count_kernel<<<L.n_chunk, 256, corners, st>>>(srect, hdr, ecnt, tcnt, L.N, L.NT,
+                                                     L.tiles_x, L.tiles_y, L.B);
   tile_colscan_kernel<<<dim3((L.NT + 31) / 32, L.B), 256, 0, st>>>(tcnt, ttot, hdr, L.NT);
   tile_scan_kernel<<<1, 1024, 0, st>>>(ttot, ranges, hdr, (int64_t)L.B * L.NT, L.cap);
   // 4. stable scatter
   const int nw = L.scatter_warps;
-  tile_scatter_kernel<<<L.n_chunk, nw * 32, (size_t)nw * L.NT * 4, st>>>(
-      sorted, rect, hdr, ecnt, tcnt, ttot, values, L.N, L.NT, L.tiles_x, L.B, L.cap);
+  tile_scatter_kernel<<<L.n_chunk, nw * 32, (size_t)nw * corners, st>>>(
+      sorted, srect, hdr, ecnt, tcnt, ttot, values, L.N, L.NT, L.tiles_x, L.tiles_y, L.B,
+      L.cap);
   count_launches(16 + 9);
 }
 

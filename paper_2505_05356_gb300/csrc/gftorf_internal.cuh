@@ -117,6 +117,8 @@ struct Header {
   int32_t pad0;
   int64_t count;           // tile instances of the batch
   unsigned long long pairs;  // evaluated (pixel, Gaussian) pairs (when counted)
+  unsigned long long pairs_warp;  // of those, the ones in records that reach the
+                                  // warp's rows (the rest are skipped per warp)
   uint32_t queue[4];       // persistent work-queue heads (fwd, bwd)
   uint32_t vis[kMaxFrames];  // visible Gaussians per frame
   uint32_t fstart[kMaxFrames + 1];  // first instance of each frame
@@ -139,7 +141,7 @@ struct Layout {
   int n_scan;      // CTAs of the emission-offset scan
   int scatter_warps;
   int64_t cap;
-  size_t off_header, off_table, off_rec, off_rect, off_zkey, off_zkey2,
+  size_t off_header, off_table, off_rec, off_rect, off_srect, off_zkey, off_zkey2,
       off_ids, off_ids2, off_dhist, off_dtot, off_ecnt, off_bsum, off_tcnt, off_toff,
       off_ranges,
       off_values, off_tfinal, off_nlast, off_g2d, total;

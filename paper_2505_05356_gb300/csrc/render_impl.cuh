@@ -162,6 +162,10 @@ __device__ __forceinline__ bool tile_hit(const Real* r, Real cx0, Real cx1, Real
   return m <= K * Real(1.001) + Real(1e-3);
 }
 
+// Per-warp masks of staged records: at most 512 threads per CTA, so at most
+// 16 warps and 16 words of 32 records each.
+constexpr int kMaskWords = 16;
+
 // Block-wide stable compaction: returns this thread's slot among the kept
 // ones (valid when keep) and the number kept; s_cnt holds >= 32 ints.
 __device__ __forceinline__ int block_compact(bool keep, int* s_cnt, int& pos) {
@@ -234,7 +238,7 @@ __device__ __forceinline__ void render_tile_fwd(
     const Real* __restrict__ rec, const Real* __restrict__ bg,
     Real* __restrict__ out, Real* __restrict__ tfinal,
     uint32_t* __restrict__ nlast, Real* s_rec, Real* s_stage, uint32_t* s_idx,
-    int* s_cnt, Header* __restrict__ hdr) {
+    int* s_cnt, unsigned* s_mask, Header* __restrict__ hdr) {
   constexpr int NF = 2 * F + 1;
   constexpr int RS = rec_stride<Real, F>();
   constexpr unsigned ALL = (1u << PPT) - 1u;
@@ -271,6 +275,11 @@ __device__ __forceinline__ void render_tile_fwd(
   const Real cx0 = (Real)(tc.tx * rg.TW) + Real(0.5), cx1 = cx0 + (Real)(rg.TW - 1);
   const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
   const Real log2_amin = log2(amin);
+  // this warp's rows of the tile (it spans whole rows: 32 is a multiple of TW)
+  const int lane = tid & 31, wid = tid >> 5;
+  const Real wy0 = cy0 + (Real)(((wid << 5) / rg.TW) * PPT);
+  const Real wy1 = cy0 + (Real)(((wid << 5) + 31) / rg.TW * PPT + PPT - 1);
+  uint32_t wevals = 0;  // pairs of records that reach the warp's rows (COUNT only)
   for (uint32_t base = range.x; base < range.y; base += nthr) {
     if (__syncthreads_count(done == ALL) == nthr) break;
     // stage the batch, then keep only the records that can reach alpha_min
@@ -294,42 +303,72 @@ __device__ __forceinline__ void render_tile_fwd(
       s_idx[pos] = i;
     }
     __syncthreads();
-    for (int j = 0; j < cnt && done != ALL; ++j) {
-      const Real* r = s_rec + j * RS;
-      const Column<Real> col = column_of(r, fpx);
-      // the exponents of all PPT pixels first (independent chains), then
-      // each pixel's decisions
-      Real lg[PPT], oG[PPT];
+    // records that can reach alpha_min at a pixel centre of this warp's rows
+    // (the tile test on the warp's rectangle): bit j of word q is record
+    // 32 q + j; the others are skipped by every pixel of the warp
+    const int nq = (cnt + 31) >> 5;
+    for (int q = 0; q < nq; ++q) {
+      const int j = (q << 5) + lane;
+      const bool hit = j < cnt && (!rg.cull || tile_hit<Real>(s_rec + j * RS, cx0, cx1, wy0, wy1,
+                                                               log2_amin));
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) s_mask[wid * kMaskWords + q] = m;
+    }
+    __syncwarp();
+    for (int q = 0; q < nq && done != ALL; ++q) {
+      unsigned m = s_mask[wid * kMaskWords + q];
+      // the pair-counting instantiation walks every record (its count is the
+      // tile lists' candidate pairs) and counts the warp's records apart
+      unsigned walk = COUNT ? (q + 1 < nq || (cnt & 31) == 0 ? 0xffffffffu
+                                                             : (1u << (cnt & 31)) - 1u)
+                            : m;
+      while (walk && done != ALL) {
+        const int bit = __ffs(walk) - 1;
+        walk &= walk - 1;
+        const int j = (q << 5) + bit;
+        const Real* r = s_rec + j * RS;
+        const Column<Real> col = column_of(r, fpx);
+        // the exponents of all PPT pixels first (independent chains), then
+        // each pixel's decisions
+        Real lg[PPT], oG[PPT];
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        lg[k] = log2_oG(r, col, sub_rn(r[1], fpy[k]));
-        oG[k] = ex2_approx(lg[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        if (done & (1u << k)) continue;
-        if (COUNT) ++evals;
-        const Real alpha = oG[k] < amax ? oG[k] : amax;
-        if (lg[k] > r[5] || alpha < amin) continue;
-        const Real tn = T[k] * (Real(1) - alpha);
-        if (tn < tmin) {
-          done |= 1u << k;
-          continue;
+        for (int k = 0; k < PPT; ++k) {
+          lg[k] = log2_oG(r, col, sub_rn(r[1], fpy[k]));
+          oG[k] = ex2_approx(lg[k]);
         }
-        const Real w = alpha * T[k] * T[k];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) acc[k][f] += w * r[6 + f];
-        if (DEPTH) accD[k] += alpha * T[k] * r[7 + NF];  // Eq. 5: one-way T
-        T[k] = tn;
-        last[k] = s_idx[j] + 1;
+        for (int k = 0; k < PPT; ++k) {
+          if (done & (1u << k)) continue;
+          if (COUNT) {
+            ++evals;
+            wevals += (m >> bit) & 1u;
+          }
+          const Real alpha = oG[k] < amax ? oG[k] : amax;
+          if (lg[k] > r[5] || alpha < amin) continue;
+          const Real tn = T[k] * (Real(1) - alpha);
+          if (tn < tmin) {
+            done |= 1u << k;
+            continue;
+          }
+          const Real w = alpha * T[k] * T[k];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) acc[k][f] += w * r[6 + f];
+          if (DEPTH) accD[k] += alpha * T[k] * r[7 + NF];  // Eq. 5: one-way T
+          T[k] = tn;
+          last[k] = s_idx[j] + 1;
+        }
       }
     }
   }
   if (COUNT) {
-    unsigned long long e = evals;
+    unsigned long long e = evals, ew = wevals;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      ew += __shfl_xor_sync(0xffffffffu, ew, o);
+    }
     if ((tid & 31) == 0 && e) atomicAdd(&hdr->pairs, e);
+    if ((tid & 31) == 0 && ew) atomicAdd(&hdr->pairs_warp, ew);
   }
   const size_t HW = (size_t)rg.W * rg.H;
   const Real* bgb = bg + (size_t)tc.b * rg.C;
@@ -372,12 +411,13 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT, false>::value)
   Real* s_stage = s_rec + (size_t)blockDim.x * RS;
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_stage + (size_t)blockDim.x * RS);
   __shared__ int s_cnt[32];
+  __shared__ unsigned s_mask[kMaskWords * kMaskWords];  // [warp][word]
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
     render_tile_fwd<Real, F, PPT, DEPTH, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                          values, rec, bg, out, tfinal, nlast, s_rec, s_stage,
-                                         s_idx, s_cnt, hdr);
+                                         s_idx, s_cnt, s_mask, hdr);
     return;
   }
   __shared__ uint32_t s_item;
@@ -389,7 +429,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT, false>::value)
     if (item >= items) break;
     render_tile_fwd<Real, F, PPT, DEPTH, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                          values, rec, bg, out, tfinal, nlast, s_rec, s_stage,
-                                         s_idx, s_cnt, hdr);
+                                         s_idx, s_cnt, s_mask, hdr);
   }
 }
 
@@ -404,7 +444,7 @@ __device__ __forceinline__ void render_tile_bwd(
     const Real* __restrict__ dout, const Real* __restrict__ tfinal,
     const uint32_t* __restrict__ nlast, Real* __restrict__ g2d, int g2d_stride,
     Real* __restrict__ dbg, Real* s_rec, Real* s_grad, uint32_t* s_id,
-    Real* s_red, uint32_t* s_idx, int* s_cnt, Real* s_stage) {
+    Real* s_red, uint32_t* s_idx, int* s_cnt, Real* s_stage, unsigned* s_mask) {
   constexpr int NF = 2 * F + 1;
   constexpr int GS = 6 + NF + (DEPTH ? 1 : 0);
   constexpr int RS = rec_stride<Real, F>();
@@ -511,6 +551,9 @@ __device__ __forceinline__ void render_tile_bwd(
   const Real cx0 = (Real)(tc.tx * rg.TW) + Real(0.5), cx1 = cx0 + (Real)(rg.TW - 1);
   const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
   const Real log2_amin = log2(amin);
+  // this warp's rows of the tile (it spans whole rows: 32 is a multiple of TW)
+  const Real wy0 = cy0 + (Real)(((wid << 5) / rg.TW) * PPT);
+  const Real wy1 = cy0 + (Real)(((wid << 5) + 31) / rg.TW * PPT + PPT - 1);
   for (int hi = maxn; hi > 0; hi -= nthr) {
     const int lo = max(0, hi - nthr);
     const int cnt = hi - lo;
@@ -550,7 +593,23 @@ __device__ __forceinline__ void render_tile_bwd(
     int warp_hi = thread_hi;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) warp_hi = max(warp_hi, __shfl_xor_sync(0xffffffffu, warp_hi, o));
-    for (int j = warp_hi - 1; j >= 0; --j) {
+    // records below warp_hi that can reach alpha_min in this warp's rows (the
+    // forward's warp test, so the same records): bit j of word q is 32 q + j
+    const int nq = (warp_hi + 31) >> 5;
+    for (int q = 0; q < nq; ++q) {
+      const int j = (q << 5) + lane;
+      const bool hit = j < warp_hi && (!rg.cull || tile_hit<Real>(s_rec + j * RS, cx0, cx1, wy0,
+                                                                   wy1, log2_amin));
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) s_mask[wid * kMaskWords + q] = m;
+    }
+    __syncwarp();
+    for (int q = nq - 1; q >= 0; --q) {
+     unsigned m = s_mask[wid * kMaskWords + q];
+     while (m) {
+      const int bit = 31 - __clz(m);
+      m &= ~(1u << bit);
+      const int j = (q << 5) + bit;
       const Real* r = s_rec + j * RS;
       Real c[GS];
 #pragma unroll
@@ -612,6 +671,7 @@ __device__ __forceinline__ void render_tile_bwd(
         Fold<GS, 16>::run(c, lane);
         if (red_slot >= 0 && c[0] != Real(0)) atomicAdd(&s_grad[j * GS + red_slot], c[0]);
       }
+     }
     }
     __syncthreads();
     for (int k = tid; k < nk * GS; k += nthr) {
@@ -648,13 +708,14 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT, true>::value)
   uint32_t* s_idx = s_id + nthr;
   Real* s_stage = reinterpret_cast<Real*>(s_idx + nthr);
   __shared__ int s_cnt[32];
+  __shared__ unsigned s_mask[kMaskWords * kMaskWords];  // [warp][word]
   const uint32_t items = (uint32_t)rg.B * rg.NT;
   if (!persistent) {
     const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
     render_tile_bwd<Real, F, PPT, DEPTH>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                   values, rec, bg, dout, tfinal, nlast, g2d,
                                   g2d_stride, dbg, s_rec, s_grad, s_id, s_red, s_idx, s_cnt,
-                                  s_stage);
+                                  s_stage, s_mask);
     return;
   }
   __shared__ uint32_t s_item;
@@ -667,7 +728,7 @@ __global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT, true>::value)
     render_tile_bwd<Real, F, PPT, DEPTH>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
                                   values, rec, bg, dout, tfinal, nlast, g2d,
                                   g2d_stride, dbg, s_rec, s_grad, s_id, s_red, s_idx, s_cnt,
-                                  s_stage);
+                                  s_stage, s_mask);
   }
 }
 

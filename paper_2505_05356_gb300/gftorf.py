@@ -399,12 +399,15 @@ class Renderer:
                                                   self.ws_bytes, ctypes.byref(cnt), _stream())
         return code, int(cnt.value)
 
-    def counters(self):
-        """(instances, evaluated pairs) of the last binning / forward; pairs
-        are counted only with FLAG_COUNT_PAIRS.  Synchronises."""
-        buf = (ctypes.c_int64 * 2)()
+    def counters(self, with_warp=False):
+        """(instances, evaluated pairs) of the last binning / forward, and with
+        with_warp the evaluated pairs in records that reach the pixel's warp;
+        pairs are counted only with FLAG_COUNT_PAIRS.  Synchronises."""
+        buf = (ctypes.c_int64 * 3)()
         _check(self.lib.gftorf_read_counters(ctypes.byref(self.dims), self.ws_ptr, self.ws_bytes,
                                              buf, _stream()), "gftorf_read_counters")
+        if with_warp:
+            return int(buf[0]), int(buf[1]), int(buf[2])
         return int(buf[0]), int(buf[1])
 
     def check(self):

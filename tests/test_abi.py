@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.gftorf_version() == 100
+    assert lib.gftorf_version() == 101
     for code, text in gftorf.STATUS.items():
         assert lib.gftorf_status_string(code).decode() == text
 
