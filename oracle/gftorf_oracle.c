@@ -394,24 +394,91 @@ typedef struct {
   int clamped;
 } step_t;
 
+/* A decision of the walk that a single-precision implementation may take
+ * the other way, because the oracle's value lies within the margin of the
+ * threshold: its kind (an ORA_AMB_* bit) and the Gaussian it concerns (for
+ * ORA_AMB_ORDER also g2, the composited Gaussian of nearly equal depth just
+ * before it).  A walk can be re-run with a set of them forced the other way. */
+typedef struct {
+  int g, kind, g2;
+} flip_t;
+
+static int is_forced(const flip_t* f, int nf, int g, int kind) {
+  for (int i = 0; i < nf; ++i)
+    if (f[i].g == g && f[i].kind == kind) return 1;
+  return 0;
+}
+
+/* record a near-threshold decision (not already forced in this walk) */
+static void note_flip(flip_t* out, int* nout, int max_out, const flip_t* force, int nforce,
+                      int g, int kind, int g2) {
+  if (!out || is_forced(force, nforce, g, kind)) return;
+  for (int i = 0; i < *nout; ++i)
+    if (out[i].g == g && out[i].kind == kind) return;
+  if (*nout < max_out) {
+    out[*nout].g = g;
+    out[*nout].kind = kind;
+    out[*nout].g2 = g2;
+    ++*nout;
+  }
+}
+
 /* Front-to-back walk of one pixel.  Returns the number of composited
  * Gaussians (steps[] filled if non-NULL), the accumulators acc[2F+1]
  * (sum alpha T^2 feature), acc[2F+1] = sum alpha T d (mean depth, one-way T)
- * and the final one-way transmittance. */
-static int composite_pixel(const double* splats, const cand_t* cand, int m,
-                           double px, double py, const double* sensor,
-                           const double* consts, const double* eps,
-                           double* acc, double* T_out, int* ambig,
-                           step_t* steps) {
+ * and the final one-way transmittance.
+ * force[nforce]: decisions taken the other way in this walk -- a tile
+ * membership (include a Gaussian outside the nominal rectangle or drop one
+ * inside it), the power > 0 skip, the alpha_min skip, the T_min stop, or the
+ * order of two composited Gaussians of nearly equal depth (swapped).
+ * near[*nnear] (if non-NULL): the decisions of this walk within margin of
+ * their thresholds, other than the forced ones. */
+static int composite_walk(const double* splats, const cand_t* cand, int m,
+                          double px, double py, const double* sensor,
+                          const double* consts, const double* eps,
+                          const flip_t* force, int nforce, flip_t* near, int* nnear,
+                          int max_near, double* acc, double* T_out, int* ambig,
+                          step_t* steps) {
   const int nf = n_feat(sensor);
   const double amax = consts[ORA_CO_AMAX], amin = consts[ORA_CO_AMIN];
   const double tmin = consts[ORA_CO_TMIN];
   double T = 1.0;
   int k = 0, flags = 0;
   double prev_z = -INFINITY;
+  int prev_g = -1;
+  /* forced order swaps: positions of the two Gaussians exchange */
+  int swap_a[8], swap_b[8], nswap = 0;
+  for (int i = 0; i < nforce && nswap < 8; ++i) {
+    if (force[i].kind != ORA_AMB_ORDER) continue;
+    int pa = -1, pb = -1;
+    for (int j = 0; j < m; ++j) {
+      if (cand[j].g == force[i].g2) pa = j;
+      if (cand[j].g == force[i].g) pb = j;
+    }
+    if (pa >= 0 && pb >= 0) {
+      swap_a[nswap] = pa;
+      swap_b[nswap] = pb;
+      ++nswap;
+    }
+  }
+  if (nnear) *nnear = 0;
   for (int f = 0; f <= nf; ++f) acc[f] = 0.0;
-  for (int i = 0; i < m; ++i) {
-    const double* sp = splats + (size_t)cand[i].g * ORA_SP_LEN;
+  for (int i0 = 0; i0 < m; ++i0) {
+    int i = i0;
+    for (int q = 0; q < nswap; ++q) {
+      if (i0 == swap_a[q]) i = swap_b[q];
+      else if (i0 == swap_b[q]) i = swap_a[q];
+    }
+    const int g = cand[i].g;
+#define ORA_POS(j0, jout)                                \
+  do {                                                   \
+    jout = (j0);                                         \
+    for (int q_ = 0; q_ < nswap; ++q_) {                 \
+      if ((j0) == swap_a[q_]) jout = swap_b[q_];         \
+      else if ((j0) == swap_b[q_]) jout = swap_a[q_];    \
+    }                                                    \
+  } while (0)
+    const double* sp = splats + (size_t)g * ORA_SP_LEN;
     double dx = sp[ORA_SP_U] - px, dy = sp[ORA_SP_V] - py;
     double a = sp[ORA_SP_CA], b = sp[ORA_SP_CB], c = sp[ORA_SP_CC];
     double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
@@ -420,27 +487,69 @@ static int composite_pixel(const double* splats, const cand_t* cand, int m,
     double oG = sp[ORA_SP_OPA] * G;
     double alpha = fmin(amax, oG);
     int would = alpha >= amin * (1.0 - eps[ORA_EPS_ALPHA]);
-    if (!cand[i].nominal) {
-      if (would) flags |= ORA_AMB_RECT;
+    int member = cand[i].nominal;
+    if (!member) {
+      if (would) {
+        flags |= ORA_AMB_RECT;
+        note_flip(near, nnear, max_near, force, nforce, g, ORA_AMB_RECT, -1);
+      }
+      if (!is_forced(force, nforce, g, ORA_AMB_RECT)) continue;
+    } else if (is_forced(force, nforce, g, ORA_AMB_RECT)) {
       continue;
     }
-    if (would && fabs(power) <= eps[ORA_EPS_ALPHA] * mag) flags |= ORA_AMB_POWER;
-    if (power > 0.0) continue;
-    if (fabs(alpha - amin) <= eps[ORA_EPS_ALPHA] * amin) flags |= ORA_AMB_ALPHA_MIN;
-    if (alpha < amin) continue;
+    if (would && fabs(power) <= eps[ORA_EPS_ALPHA] * mag) {
+      flags |= ORA_AMB_POWER;
+      note_flip(near, nnear, max_near, force, nforce, g, ORA_AMB_POWER, -1);
+    }
+    if ((power > 0.0) != is_forced(force, nforce, g, ORA_AMB_POWER)) continue;
+    if (fabs(alpha - amin) <= eps[ORA_EPS_ALPHA] * amin) {
+      flags |= ORA_AMB_ALPHA_MIN;
+      note_flip(near, nnear, max_near, force, nforce, g, ORA_AMB_ALPHA_MIN, -1);
+    }
+    if ((alpha < amin) != is_forced(force, nforce, g, ORA_AMB_ALPHA_MIN)) continue;
     if (fabs(oG - amax) <= eps[ORA_EPS_ALPHA] * amax) flags |= ORA_AMB_CLAMP;
-    if (cand[i].uncertain) flags |= ORA_AMB_RECT;
-    if (cand[i].z - prev_z <= eps[ORA_EPS_Z] * fabs(cand[i].z)) flags |= ORA_AMB_ORDER;
+    if (member && cand[i].uncertain) {
+      flags |= ORA_AMB_RECT;
+      note_flip(near, nnear, max_near, force, nforce, g, ORA_AMB_RECT, -1);
+    }
+    if (fabs(cand[i].z - prev_z) <= eps[ORA_EPS_Z] * fabs(cand[i].z)) {
+      flags |= ORA_AMB_ORDER;
+      note_flip(near, nnear, max_near, force, nforce, g, ORA_AMB_ORDER, prev_g);
+    }
     prev_z = cand[i].z;
+    prev_g = g;
     double t_next = T * (1.0 - alpha);
-    if (fabs(t_next - tmin) <= eps[ORA_EPS_T] * (double)(k + 4) * tmin)
+    if (fabs(t_next - tmin) <= eps[ORA_EPS_T] * (double)(k + 4) * tmin) {
       flags |= ORA_AMB_TMIN;
-    if (t_next < tmin) break; /* early stop; this Gaussian is not composited */
+      note_flip(near, nnear, max_near, force, nforce, g, ORA_AMB_TMIN, -1);
+    }
+    /* early stop; this Gaussian is not composited */
+    if ((t_next < tmin) != is_forced(force, nforce, g, ORA_AMB_TMIN)) {
+      /* Gaussians of nearly equal depth just behind the stopping one: single
+       * precision may order one of them first and composite it before
+       * stopping, so each that could composite here is an order decision
+       * (the alternative swaps the two) */
+      for (int j0 = i0 + 1; j0 < m; ++j0) {
+        int j;
+        ORA_POS(j0, j);
+        if (cand[j].z - cand[i].z > eps[ORA_EPS_Z] * fabs(cand[j].z)) break;
+        if (!cand[j].nominal) continue;
+        const double* sj = splats + (size_t)cand[j].g * ORA_SP_LEN;
+        const double ex = sj[ORA_SP_U] - px, ey = sj[ORA_SP_V] - py;
+        const double pw = -0.5 * (sj[ORA_SP_CA] * ex * ex + sj[ORA_SP_CC] * ey * ey) -
+                          sj[ORA_SP_CB] * ex * ey;
+        const double aj = fmin(amax, sj[ORA_SP_OPA] * exp(pw));
+        if (pw > 0.0 || aj < amin * (1.0 - eps[ORA_EPS_ALPHA])) continue;
+        flags |= ORA_AMB_ORDER;
+        note_flip(near, nnear, max_near, force, nforce, cand[j].g, ORA_AMB_ORDER, g);
+      }
+      break;
+    }
     double w = alpha * T * T;  /* squared transmittance: round trip */
     for (int f = 0; f < nf; ++f) acc[f] += w * sp[ORA_SP_FEAT + f];
     acc[nf] += alpha * T * sp[ORA_SP_D]; /* Eq. 5: one-way transmittance */
     if (steps) {
-      steps[k].g = cand[i].g;
+      steps[k].g = g;
       steps[k].alpha = alpha;
       steps[k].T = T;
       steps[k].G = G;
@@ -451,9 +560,89 @@ static int composite_pixel(const double* splats, const cand_t* cand, int m,
     T = t_next;
     ++k;
   }
+#undef ORA_POS
   *T_out = T;
   if (ambig) *ambig = flags;
   return k;
+}
+
+static int composite_pixel(const double* splats, const cand_t* cand, int m,
+                           double px, double py, const double* sensor,
+                           const double* consts, const double* eps,
+                           double* acc, double* T_out, int* ambig,
+                           step_t* steps) {
+  return composite_walk(splats, cand, m, px, py, sensor, consts, eps, NULL, 0, NULL, NULL, 0,
+                        acc, T_out, ambig, steps);
+}
+
+/* Every result the walk of pixel (px, py) takes when single precision
+ * decides some of its near-threshold decisions the other way: the nominal
+ * walk first, then walks with one, two or three of them forced the other way
+ * (breadth first; each walk's own near-threshold decisions extend the
+ * search, since a flipped decision changes T for the rest of the walk).
+ * At most max_out distinct results; acc_out[max_out][2F+2], T_out[max_out].
+ * Returns the number of distinct results; *capped = 1 if the search stopped
+ * at max_out. */
+#define ORA_ALT_DEPTH 3
+static int pixel_alternatives(const double* splats, const cand_t* cand, int m, double px,
+                              double py, const double* sensor, const double* consts,
+                              const double* eps, int max_out, double* acc_out, double* T_out,
+                              int* capped) {
+  enum { kMaxSets = 64, kMaxNear = 16 };
+  flip_t sets[kMaxSets][ORA_ALT_DEPTH];
+  int setn[kMaxSets];
+  int nsets = 1;
+  setn[0] = 0;
+  int nout = 0;
+  *capped = 0;
+  const int stride = ORA_MAX_FEAT + 1;
+  for (int s = 0; s < nsets; ++s) {
+    if (nout == max_out) {
+      *capped = 1;
+      break;
+    }
+    flip_t near[kMaxNear];
+    int nnear = 0;
+    double* acc = acc_out + (size_t)nout * stride;
+    for (int f = 0; f < stride; ++f) acc[f] = 0.0; /* the walk fills 2F+2 of them */
+    composite_walk(splats, cand, m, px, py, sensor, consts, eps, sets[s], setn[s], near, &nnear,
+                   kMaxNear, acc, T_out + nout, NULL, NULL);
+    /* keep the result unless an earlier walk gave exactly the same one (two
+     * swaps of the same pair restore the order) */
+    int same = 0;
+    for (int o = 0; o < nout && !same; ++o) {
+      same = T_out[o] == T_out[nout];
+      for (int f = 0; f < stride && same; ++f) same = acc_out[(size_t)o * stride + f] == acc[f];
+    }
+    if (!same) ++nout;
+    if (setn[s] == ORA_ALT_DEPTH) continue;
+    for (int a = 0; a < nnear; ++a) {
+      /* the set sets[s] + near[a], unless an equal set is queued already */
+      int dup = 0;
+      for (int t = 0; t < nsets && !dup; ++t) {
+        if (setn[t] != setn[s] + 1) continue;
+        int all = 1;
+        for (int u = 0; u < setn[t] && all; ++u) {
+          const flip_t* x = &sets[t][u];
+          int found = x->g == near[a].g && x->kind == near[a].kind;
+          for (int v = 0; v < setn[s] && !found; ++v)
+            found = x->g == sets[s][v].g && x->kind == sets[s][v].kind;
+          all = found;
+        }
+        dup = all;
+      }
+      if (dup) continue;
+      if (nsets == kMaxSets) {
+        *capped = 1;
+        break;
+      }
+      for (int u = 0; u < setn[s]; ++u) sets[nsets][u] = sets[s][u];
+      sets[nsets][setn[s]] = near[a];
+      setn[nsets] = setn[s] + 1;
+      ++nsets;
+    }
+  }
+  return nout;
 }
 
 /* raw samples from the accumulators: Q_fj = cos(phi_j) S_f + sin(phi_j) C_f
@@ -562,6 +751,79 @@ void ora_render_frame(int n, const double* splats, const double* frame,
     }
     free(cand);
   }
+}
+
+int64_t ora_render_tiles(int n, const double* splats, const double* frame,
+                         const double* sensor, const double* consts, const double* bg,
+                         const double* eps, int ntiles, const int32_t* tiles, double* out,
+                         double* tfinal, int32_t* ambig, int32_t* pix, int max_alt,
+                         int64_t alt_cap, double* alt_out, int64_t* alt_pix,
+                         int64_t* n_alt, int64_t* n_capped) {
+  const int W = (int)frame[ORA_FR_W], H = (int)frame[ORA_FR_H];
+  const int tw = (int)consts[ORA_CO_TW], th = (int)consts[ORA_CO_TH];
+  const int C = n_chan(sensor, consts);
+  const int value_flags = ORA_AMB_ALPHA_MIN | ORA_AMB_TMIN | ORA_AMB_ORDER | ORA_AMB_RECT |
+                          ORA_AMB_POWER;
+  /* pixel offsets of the tiles (tile by tile, row-major, inside the image) */
+  int64_t* first = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ntiles + 1));
+  first[0] = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    const int x0 = tiles[2 * t] * tw, y0 = tiles[2 * t + 1] * th;
+    const int wx = x0 >= W ? 0 : (x0 + tw <= W ? tw : W - x0);
+    const int wy = y0 >= H ? 0 : (y0 + th <= H ? th : H - y0);
+    first[t + 1] = first[t] + (int64_t)wx * wy;
+  }
+  int64_t next_alt = 0, capped_px = 0;
+  const int stride = ORA_MAX_FEAT + 1;
+#pragma omp parallel
+  {
+    cand_t* cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)max_candidates(n));
+    double* accs = (double*)malloc(sizeof(double) * (size_t)(max_alt > 0 ? max_alt : 1) * stride);
+    double* Ts = (double*)malloc(sizeof(double) * (size_t)(max_alt > 0 ? max_alt : 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int t = 0; t < ntiles; ++t) {
+      const int tx = tiles[2 * t], ty = tiles[2 * t + 1];
+      const int m = collect_candidates(n, splats, tx, ty, cand);
+      int64_t p = first[t];
+      for (int y = ty * th; y < (ty + 1) * th && y < H; ++y)
+        for (int x = tx * tw; x < (tx + 1) * tw && x < W; ++x, ++p) {
+          double acc[ORA_MAX_FEAT + 1], T;
+          int flags = 0;
+          composite_pixel(splats, cand, m, x + 0.5, y + 0.5, sensor, consts, eps, acc, &T,
+                          &flags, NULL);
+          samples_from_acc(acc, T, bg, frame, sensor, consts, out + (size_t)p * C, 1);
+          tfinal[p] = T;
+          ambig[p] = flags;
+          pix[2 * p] = x;
+          pix[2 * p + 1] = y;
+          if (max_alt <= 1 || !(flags & value_flags)) continue;
+          int capped = 0;
+          const int k = pixel_alternatives(splats, cand, m, x + 0.5, y + 0.5, sensor, consts,
+                                           eps, max_alt, accs, Ts, &capped);
+          int64_t at;
+#pragma omp atomic capture
+          { at = next_alt; next_alt += k; }
+          if (capped) {
+#pragma omp atomic
+            ++capped_px;
+          }
+          for (int i = 0; i < k; ++i) {
+            if (at + i >= alt_cap) break;
+            samples_from_acc(accs + (size_t)i * stride, Ts[i], bg, frame, sensor, consts,
+                             alt_out + (size_t)(at + i) * C, 1);
+            alt_pix[at + i] = p;
+          }
+        }
+    }
+    free(Ts);
+    free(accs);
+    free(cand);
+  }
+  *n_alt = next_alt;
+  *n_capped = capped_px;
+  const int64_t total = first[ntiles];
+  free(first);
+  return total;
 }
 
 static void atomic_add(double* p, double v) {

@@ -155,6 +155,24 @@ void ora_render_frame(int n, const double* splats, const double* frame,
                       const double* bg, const double* eps, double* out,
                       double* tfinal, int32_t* ambig, int32_t* ncontrib);
 
+/* Whole tiles of one frame, and every valid result of their ambiguous
+ * pixels.  tiles[ntiles*2] = (tx, ty); pixels are taken tile by tile,
+ * row-major, inside the image: pix[npix*2] = (x, y), out[npix*C] (samples as
+ * in ora_render_pixels), tfinal[npix], ambig[npix].  For every pixel with a
+ * value-changing ambiguity flag, the walk is re-run with its near-threshold
+ * decisions (alpha floor, power > 0 skip, T_min stop, near-equal depth order,
+ * uncertain tile membership) taken the other way -- up to three at once,
+ * each re-run's own near-threshold decisions included, at most max_alt walks
+ * per pixel, the first the nominal one -- and each walk's samples go to
+ * alt_out[i*C] with alt_pix[i] = its pixel's index, for i < alt_cap.
+ * *n_alt = walks produced (may exceed alt_cap: then the rest are dropped);
+ * *n_capped = pixels whose search stopped at max_alt.  Returns npix. */
+int64_t ora_render_tiles(int n, const double* splats, const double* frame,
+                         const double* sensor, const double* consts, const double* bg,
+                         const double* eps, int ntiles, const int32_t* tiles, double* out,
+                         double* tfinal, int32_t* ambig, int32_t* pix, int max_alt,
+                         int64_t alt_cap, double* alt_out, int64_t* alt_pix,
+                         int64_t* n_alt, int64_t* n_capped);
 /* Gradient of L = sum dout * out for one frame w.r.t. the per-Gaussian 2D
  * record (u, v, conic a, b, c, opacity, features[2F+1], distance d) -- the
  * Eq. S3 recursion for the squared-transmittance channels and the 3DGS

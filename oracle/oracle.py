@@ -66,6 +66,11 @@ def lib():
                                        _d, _d, _i32, _i32]
         L.ora_backward_2d.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _d, _d, _d]
         L.ora_backward_params.argtypes = [ctypes.c_int] + [_d] * 14
+        _i64 = ctypes.POINTER(ctypes.c_int64)
+        L.ora_render_tiles.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _d, ctypes.c_int, _i32,
+                                       _d, _d, _i32, _i32, ctypes.c_int, ctypes.c_int64, _d,
+                                       _i64, _i64, _i64]
+        L.ora_render_tiles.restype = ctypes.c_int64
         L.ora_bin_f32.argtypes = [ctypes.c_int, ctypes.c_int, _f32, _f32, _i32,
                                   _f32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int64, _u64, _u32, _u32]
@@ -220,6 +225,48 @@ def render_pixels(scene, b: int, pix: np.ndarray, splats=None, eps=EPS_NONE):
                             k, _p(pix, _i32), _p(out), _p(tf), _p(amb, _i32),
                             _p(nc, _i32))
     return out, tf, amb, nc
+
+
+def render_tiles(scene, b: int, tiles, splats=None, eps=EPS_F32, max_alt: int = 32,
+                 alt_per_pixel: int = 8):
+    """Whole tiles of frame b (tiles: (k, 2) of (tx, ty)) and every valid
+    result of their ambiguous pixels.  Returns dict(pix (npix, 2) (x, y),
+    out (npix, C), tfinal, ambig, alts {pixel index: (k, C) results, the
+    nominal one first}, capped = pixels whose search hit max_alt)."""
+    if splats is None:
+        splats = project(scene, b, eps)
+    tiles = np.ascontiguousarray(np.asarray(tiles, np.int32).reshape(-1, 2))
+    k = scene.consts
+    npix_max = len(tiles) * int(k.tile_w) * int(k.tile_h)
+    C = n_channels(scene)
+    out = np.zeros((npix_max, C))
+    tf = np.zeros(npix_max)
+    amb = np.zeros(npix_max, np.int32)
+    pix = np.zeros((npix_max, 2), np.int32)
+    cap = max(1, npix_max * alt_per_pixel)
+    _i64 = ctypes.POINTER(ctypes.c_int64)
+    while True:
+        alt_out = np.zeros((cap, C))
+        alt_pix = np.zeros(cap, np.int64)
+        n_alt = np.zeros(1, np.int64)
+        n_capped = np.zeros(1, np.int64)
+        npix = lib().ora_render_tiles(scene.n, _p(splats), _p(pack_frame(scene, b)),
+                                      _p(pack_sensor(scene)), _p(pack_consts(scene)),
+                                      _p(_f64(scene.bg[b])), _p(np.asarray(eps, np.float64)),
+                                      len(tiles), _p(tiles, _i32), _p(out), _p(tf),
+                                      _p(amb, _i32), _p(pix, _i32), int(max_alt), cap,
+                                      _p(alt_out), _p(alt_pix, _i64), _p(n_alt, _i64),
+                                      _p(n_capped, _i64))
+        if n_alt[0] <= cap:
+            break
+        cap = int(n_alt[0])
+    alts = {}
+    m = int(n_alt[0])
+    for i in range(m):
+        alts.setdefault(int(alt_pix[i]), []).append(alt_out[i])
+    alts = {p_: np.stack(v) for p_, v in alts.items()}
+    return dict(pix=pix[:npix], out=out[:npix], tfinal=tf[:npix], ambig=amb[:npix],
+                alts=alts, capped=int(n_capped[0]))
 
 
 def pixel_steps(scene, b: int, x: int, y: int, splats=None, max_steps: int = 100000):

@@ -99,6 +99,37 @@ __device__ __forceinline__ void sh_grad(const Real* c, Real x, Real y, Real z, R
   g[0] = gx, g[1] = gy, g[2] = gz;
 }
 
+// sum_c R[c] x[c] + t, compensated: each product's rounding error is exact
+// (fma(a, b, -ab)) and each sum's by Knuth's two-sum, and the collected error
+// is added once at the end, so the result is within about one rounding of the
+// exact value.  A general rigid camera then moves a footprint centre no more
+// than the identity camera does (where p = x is exact).
+// (every step with its own rounding: the compiler must not contract them)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename Real>
+__device__ __forceinline__ Real dot3_plus(const Real* R, const Real* x, Real t) {
+  Real s = t, err = Real(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Real pr = mul_rn(R[c], x[c]);
+    const Real pe = fma_rn(R[c], x[c], -pr);
+    const Real sn = add_rn(s, pr);
+    const Real bb = sub_rn(sn, s);
+    const Real se = add_rn(sub_rn(s, sub_rn(sn, bb)), sub_rn(pr, bb));
+    s = sn;
+    err = add_rn(err, add_rn(pe, se));
+  }
+  return add_rn(s, err);
+}
+
 template <typename Real>
 struct Params {
   Real mu[3], c[9], s[3], q[4], o, amp;
@@ -182,9 +213,10 @@ __device__ __forceinline__ void geometry(const Params<Real>& P,
     Q.x[a] = x;
   }
 #pragma unroll
-  for (int r = 0; r < 3; ++r)
-    Q.p[r] = (Real)fr.R[3 * r] * Q.x[0] + (Real)fr.R[3 * r + 1] * Q.x[1] +
-             (Real)fr.R[3 * r + 2] * Q.x[2] + (Real)fr.t[r];
+  for (int r = 0; r < 3; ++r) {
+    const Real Rr[3] = {(Real)fr.R[3 * r], (Real)fr.R[3 * r + 1], (Real)fr.R[3 * r + 2]};
+    Q.p[r] = dot3_plus<Real>(Rr, Q.x, (Real)fr.t[r]);
+  }
   Q.iz = Real(1) / Q.p[2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) Q.e[a] = Q.x[a] - (Real)fr.o[a];

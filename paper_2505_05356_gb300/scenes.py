@@ -286,6 +286,20 @@ def sample_pixels(scene: Scene, k: int, seed: int = 2) -> np.ndarray:
     return out
 
 
+def sample_tiles(scene: Scene, k: int, seed: int = 2) -> np.ndarray:
+    """k distinct tiles (tx, ty) of the scene's tile grid per frame, int32,
+    shape (B, k, 2)."""
+    rng = np.random.default_rng(seed)
+    tw, th = scene.consts.tile_w, scene.consts.tile_h
+    nx, ny = -(-scene.width // tw), -(-scene.height // th)
+    out = np.zeros((scene.frames, k, 2), np.int32)
+    for b in range(scene.frames):
+        idx = rng.choice(nx * ny, size=k, replace=False)
+        out[b, :, 0] = idx % nx
+        out[b, :, 1] = idx // nx
+    return out
+
+
 def make_fit_scenes(seed: int = 4, n_backdrop: int = 270_000, n_rod: int = 30_000,
                     n_init: int = 300_000, frames: int = 60, width: int = 640,
                     height: int = 480):

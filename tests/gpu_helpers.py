@@ -56,6 +56,38 @@ def forward_close(q_gpu, q_ora, amb, rel=1e-5, flag_mask=ora.AMB_VALUE):
     return worst <= rel, worst, int((~keep).sum())
 
 
+def match_alternatives(q_gpu, alts, sigma, rel=1e-5):
+    """Smallest, over the valid oracle results `alts` (k, C) of one pixel, of
+    the largest per-channel error |q_gpu - alt| / max(|alt|, sigma_c).  The
+    pixel is correct when this is <= rel: single precision took each of its
+    near-threshold decisions one of the two ways, and the result matches the
+    oracle walk that took the same ones."""
+    err = np.abs(q_gpu[None, :] - alts) / np.maximum(np.abs(alts), sigma[None, :])
+    return float(err.max(axis=1).min())
+
+
+def ambiguous_pixels_match(scene, b, q_gpu, q_ora, amb, rel=1e-5):
+    """Every pixel of frame b with a value-changing ambiguity flag equals one
+    of the oracle's valid results for it (the walk re-run with its
+    near-threshold decisions taken the other way).  q_gpu, q_ora: (C, H, W);
+    amb: (H, W).  Returns (flagged, worst best-match error, capped searches)."""
+    C = q_ora.shape[0]
+    sigma = np.sqrt((q_ora.reshape(C, -1) ** 2).mean(axis=1)) + 1e-300
+    flagged = np.argwhere((amb & ora.AMB_VALUE) != 0)  # (y, x)
+    if len(flagged) == 0:
+        return 0, 0.0, 0
+    k = scene.consts
+    tiles = np.unique(np.stack([flagged[:, 1] // k.tile_w, flagged[:, 0] // k.tile_h], 1), axis=0)
+    r = ora.render_tiles(scene, b, tiles, eps=ora.EPS_F32)
+    index = {(int(x), int(y)): i for i, (x, y) in enumerate(r["pix"])}
+    worst = 0.0
+    for y, x in flagged:
+        i = index[(int(x), int(y))]
+        alts = r["alts"].get(i, r["out"][i:i + 1])
+        worst = max(worst, match_alternatives(q_gpu[:, y, x], alts, sigma, rel))
+    return len(flagged), worst, r["capped"]
+
+
 def absent_groups(scene):
     """Gradient groups the CUDA path does not return for `scene` because the
     scene has no such parameter (static trajectories, no per-frame

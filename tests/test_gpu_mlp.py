@@ -10,6 +10,11 @@ bound (K 2^-24 times the sum of the terms' magnitudes) of zero at the ReLU;
 FP32 outputs (head, weight and encoding gradients)
 agree to 1e-4 relative.
 
+Against the plain FP64 network (the paper's MLP computes in FP32; BF16
+operands are this path's precision choice): offsets within 3u sqrt(9),
+u = 2^-8, and gradients within twice the BF16 arithmetic's own distance from
+the network (ReLU masks flip near zero) -- test_mlp_against_the_fp64_network.
+
 Whole network (loose, derived): a flipped activation shifts every sum of the
 next layer a little and so flips a few more; over 8 layers ~1 % of the
 activations end one ulp apart (measured), which moves the output by ~1e-3 and
@@ -126,6 +131,40 @@ def test_mlp_whole_network_matches_oracle(N, B):
         assert _rel(W, Wo) < 2.5e-2 and _rel(b, bo) < 2.5e-2, l
     dm = omlp.encode_backward(denc, means, times, inv, single=True)
     assert _rel(d_means.double().cpu().numpy(), dm) < 2.5e-2
+
+
+def test_mlp_against_the_fp64_network():
+    """The CUDA MLP against the plain FP64 network (Sec. 4: the paper's MLP
+    is an FP32 network; this path computes with BF16 operands and FP32
+    accumulation).  Bars from BF16's unit roundoff u = 2^-8: each of the 9
+    GEMMs rounds its two operands and its output (<= 3u per term; random-sign
+    sums keep that relative to the result) and independent layers add in
+    quadrature, so the offsets stay within 3u sqrt(9) of the network.  The
+    gradients also see ReLU masks that flip where rounding moves a
+    pre-activation across zero; such a flip changes a whole dZ element, so
+    their distance from the network is the BF16 arithmetic's own (computed
+    here by the oracle with BF16 operands, independently of the GPU); the
+    CUDA path must stay within twice it, plus the output bar."""
+    N, B = 3000, 3
+    theta, means, times, inv, net, delta, dd, d_theta, d_means = _run(N, B, 300)
+    th64 = theta.astype(np.float64)
+    enc = omlp.encode(means, np.asarray(times, np.float64), inv)  # exact scaled positions
+    d64, a64 = omlp.forward(th64, enc, bf16=False)
+    g64, de64 = omlp.backward(th64, a64, dd.reshape(-1, 3).astype(np.float64), bf16=False)
+    d16, a16 = omlp.forward(th64, enc, bf16=True)
+    g16, de16 = omlp.backward(th64, a16, dd.reshape(-1, 3).astype(np.float64), bf16=True)
+    u = 2.0 ** -8
+    out_bar = 3 * u * np.sqrt(9)
+    assert _rel(delta.double().cpu().numpy().reshape(-1, 3), d64) <= out_bar
+    for l, ((W, b), (W16, b16), (Wo, bo)) in enumerate(
+            zip(omlp.unpack(d_theta.double().cpu().numpy()), omlp.unpack(g16),
+                omlp.unpack(g64))):
+        assert _rel(W, Wo) <= 2 * _rel(W16, Wo) + out_bar, ("W", l, _rel(W, Wo), _rel(W16, Wo))
+        assert _rel(b, bo) <= 2 * _rel(b16, bo) + out_bar, ("b", l, _rel(b, bo), _rel(b16, bo))
+    dm64 = omlp.encode_backward(de64, means, times, inv)
+    dm16 = omlp.encode_backward(de16, means, times, inv)
+    dm = d_means.double().cpu().numpy()
+    assert _rel(dm, dm64) <= 2 * _rel(dm16, dm64) + out_bar
 
 
 def test_mlp_zero_gaussians_and_status():

@@ -4,8 +4,9 @@ Bars: tile lists and sort order bit-exact; forward raw samples within 1e-5 of
 max(|Q|, channel RMS); gradients within 1e-3 (norm-wise per parameter group
 and elementwise against max(|g|, group RMS)).  Pixels where single precision
 may take one of the method's discrete decisions (alpha floor, early stop,
-depth order, tile membership) the other way are ambiguous: they are counted,
-must stay rare, and are compared loosely.
+depth order, tile membership) the other way have several valid results: each
+must equal, at the same 1e-5 bar, one of the oracle's walks with those
+decisions taken either way.
 """
 import numpy as np
 import pytest
@@ -13,7 +14,8 @@ import torch
 
 from oracle import oracle as ora
 from paper_2505_05356_gb300 import gftorf, scenes
-from tests.gpu_helpers import absent_groups, forward_close, grads_close, run_gpu
+from tests.gpu_helpers import (absent_groups, ambiguous_pixels_match, forward_close,
+                               grads_close, run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -47,15 +49,6 @@ SMALL = [
                           freqs_hz=[30e6, 80e6], z_range=(0.5, 6.0))),
 ]
 
-# Forward bar of the moved-camera cases.  With R = I the camera transform is
-# exact in FP32; a general rigid transform p = R x + t rounds three more
-# products and sums per coordinate (~3e-7 m at 2 m), which moves a
-# footprint's centre by ~1e-5 px at the image border.  Where a small, steep
-# footprint dominates a pixel this reaches 1.7e-5 of the sample (the same with
-# scalar and SH reflectivity); the bar there is 3e-5.
-FWD_REL_POSED = 3e-5
-
-
 def _ids(case):
     name, kw = case
     return name + "-" + "-".join("%s=%s" % (k, v) for k, v in sorted(kw.items()))
@@ -68,18 +61,15 @@ def test_forward_matches_oracle(case):
     q_ora, tf_ora, amb, nc = ora.render(sc, ora.EPS_F32)
     res = run_gpu(sc)
     assert res["status"][0] == gftorf.OK
-    rel = FWD_REL_POSED if "pose" in kw else 1e-5
-    ok, worst, nflag = forward_close(res["out"], q_ora, amb, rel=rel)
-    assert nflag <= 0.01 * amb.size + 2, nflag
+    ok, worst, nflag = forward_close(res["out"], q_ora, amb, rel=1e-5)
     assert ok, worst
     keep = (amb & ora.AMB_VALUE) == 0
     np.testing.assert_allclose(res["tfinal"][keep], tf_ora[keep], rtol=2e-5, atol=1e-9)
-    # ambiguous pixels: still finite and close to one of the valid results
-    bad = ~keep
-    if bad.any():
-        scale = np.abs(q_ora).max()
-        assert np.all(np.isfinite(res["out"]))
-        assert np.abs(res["out"] - q_ora).transpose(1, 0, 2, 3)[:, bad].max() <= 0.25 * scale
+    # ambiguous pixels: each equals one of the oracle's valid results
+    for b in range(sc.frames):
+        n_b, worst_b, capped = ambiguous_pixels_match(sc, b, res["out"][b], q_ora[b], amb[b])
+        assert capped == 0
+        assert worst_b <= 1e-5, (b, n_b, worst_b)
 
 
 @pytest.mark.parametrize("case", SMALL, ids=[_ids(c) for c in SMALL])

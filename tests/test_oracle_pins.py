@@ -790,3 +790,94 @@ def test_squared_transmittance_telescopes_for_any_scene(seed):
         assert T[0] == 1.0 and TN == pytest.approx(T[-1] * (1 - a[-1]), rel=1e-15)
         assert float(np.sum(a * (2 - a) * T * T)) == pytest.approx(1 - TN * TN, abs=1e-13)
     assert deep >= 5
+
+
+# --------------------------------------------------------------------------
+# every valid result of an ambiguous pixel (the walk re-run with its
+# near-threshold decisions taken the other way)
+# --------------------------------------------------------------------------
+
+def _alts_at(sc, x, y):
+    k = sc.consts
+    r = ora.render_tiles(sc, 0, [(x // k.tile_w, y // k.tile_h)], eps=ora.EPS_F32)
+    i = int(np.flatnonzero((r["pix"][:, 0] == x) & (r["pix"][:, 1] == y))[0])
+    return r, i
+
+
+def _quads(sp, weights, T, bg, offsets):
+    """Eq. 4 written out: Q_j = sum_k w_k (A sin psi_k cos phi_j + A cos psi_k
+    sin phi_j) + bg_j T, ambient = sum_k w_k A_k + bg_amb T."""
+    S = ora.SP
+    q = [sum(w * (sp[g, S["FEAT"]] * np.cos(ph) + sp[g, S["FEAT"] + 1] * np.sin(ph))
+             for g, w in weights) + bg[j] * T for j, ph in enumerate(offsets)]
+    q.append(sum(w * sp[g, S["FEAT"] + 2] for g, w in weights) + bg[len(offsets)] * T)
+    return np.array(q)
+
+
+def test_alternatives_of_a_near_depth_tie_are_both_orders():
+    """Two Gaussians on one pixel (0.1 px off its centre, so no power > 0
+    question arises) at depths 2 relative 2.5e-7 apart (closer than single
+    precision resolves): the pixel is flagged, and its valid results are
+    exactly the two compositing orders, alpha_a then alpha_b and the reverse
+    (weights alpha T^2, T the product of (1 - alpha))."""
+    cam = tiny_scene([[0, 0, 1]], 0.1).cameras[0]
+    pa = np.array(at_pixel(cam, 20.6, 30.4, 2.0))
+    pb = pa * (1 + 2.5e-7)
+    bg = np.array([0.3, -0.2, 0.1, 0.4, 0.25])
+    sc = tiny_scene([pa, pb], 0.05, opacity=[0.6, 0.3], bg=bg)
+    r, i = _alts_at(sc, 20, 30)
+    assert r["ambig"][i] & ora.AMB["ORDER"]
+    alts = r["alts"][i]
+    assert alts.shape[0] == 2
+    sp = ora.project(sc, 0)
+    S = ora.SP
+    al = [min(0.99, sp[g, S["OPA"]] * np.exp(-0.5 * (sp[g, S["CA"]] * (sp[g, S["U"]] - 20.5) ** 2 +
+                                                       sp[g, S["CC"]] * (sp[g, S["V"]] - 30.5) ** 2)
+                                                - sp[g, S["CB"]] * (sp[g, S["U"]] - 20.5) *
+                                                (sp[g, S["V"]] - 30.5)))
+          for g in (0, 1)]
+    offs = sc.sensor.offsets_rad
+    T = (1 - al[0]) * (1 - al[1])
+    ab = _quads(sp, [(0, al[0]), (1, al[1] * (1 - al[0]) ** 2)], T, bg, offs)
+    ba = _quads(sp, [(1, al[1]), (0, al[0] * (1 - al[1]) ** 2)], T, bg, offs)
+    np.testing.assert_allclose(alts[0], ab, rtol=1e-12, atol=1e-14)  # nominal first: a in front
+    np.testing.assert_allclose(alts[1], ba, rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(alts[0], r["out"][i])
+
+
+def test_alternatives_at_the_alpha_floor_composite_or_skip():
+    """A Gaussian of opacity alpha_min 0.004 px from the pixel centre (its
+    alpha there is below alpha_min by ~5e-6 relative) behind an ordinary one:
+    the pixel is flagged, and its valid results are without it (the nominal
+    walk) and with it."""
+    cam = tiny_scene([[0, 0, 1]], 0.1).cameras[0]
+    pa = np.array(at_pixel(cam, 12.7, 9.4, 1.5))
+    pb = np.array(at_pixel(cam, 12.504, 9.5, 2.5))
+    bg = np.array([0.3, -0.2, 0.1, 0.4, 0.25])
+    sc = tiny_scene([pa, pb], 0.05, opacity=[0.5, 1.0 / 255.0], bg=bg)
+    r, i = _alts_at(sc, 12, 9)
+    assert r["ambig"][i] & ora.AMB["ALPHA_MIN"]
+    alts = r["alts"][i]
+    sp = ora.project(sc, 0)
+    S = ora.SP
+
+    def alpha(g):
+        dx, dy = sp[g, S["U"]] - 12.5, sp[g, S["V"]] - 9.5
+        return sp[g, S["OPA"]] * np.exp(-0.5 * (sp[g, S["CA"]] * dx * dx + sp[g, S["CC"]] * dy * dy)
+                                        - sp[g, S["CB"]] * dx * dy)
+    a0, a1 = alpha(0), alpha(1)
+    offs = sc.sensor.offsets_rad
+    without = _quads(sp, [(0, a0)], 1 - a0, bg, offs)
+    with_ = _quads(sp, [(0, a0), (1, a1 * (1 - a0) ** 2)], (1 - a0) * (1 - a1), bg, offs)
+    got = sorted(alts.tolist(), key=lambda q: q[0])
+    want = sorted([without.tolist(), with_.tolist()], key=lambda q: q[0])
+    assert len(got) == 2
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(alts[0], without, rtol=1e-12, atol=1e-14)  # nominal: skipped
+
+
+def test_no_alternatives_without_a_near_threshold_decision():
+    sc = tiny_scene([at_pixel(tiny_scene([[0, 0, 1]], 0.1).cameras[0], 30.7, 30.4, 2.0)], 0.05,
+                    opacity=[0.7])
+    r, i = _alts_at(sc, 30, 30)
+    assert r["ambig"][i] == 0 and i not in r["alts"]
