@@ -95,7 +95,7 @@ typedef enum { GFTORF_F32 = 0, GFTORF_F64 = 1 } gftorf_dtype;
 
 /* Static problem shape.  One workspace serves one dims value. */
 typedef struct {
-  int32_t n_gaussians;   /* N >= 0                                          */
+  int32_t n_gaussians;   /* N in [0, 2^30)                                  */
   int32_t n_frames;      /* B in [1, GFTORF_MAX_FRAMES]                     */
   int32_t width, height; /* image size in pixels, >= 1                      */
   int32_t tile_w, tile_h;/* one of 8x8, 16x16, 16x32 (w x h)                */

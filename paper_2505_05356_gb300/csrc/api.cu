@@ -26,7 +26,9 @@ bool tile_ok(int tw, int th) {
 
 bool dims_ok(const gftorf_dims* d) {
   if (!d) return false;
-  if (d->n_gaussians < 0 || d->n_frames < 1 || d->n_frames > kMaxFrames) return false;
+  // (depth-sort counts share a 32-bit status word with two flag bits)
+  if (d->n_gaussians < 0 || d->n_gaussians >= (1 << 30)) return false;
+  if (d->n_frames < 1 || d->n_frames > kMaxFrames) return false;
   if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384) return false;
   if (!tile_ok(d->tile_w, d->tile_h)) return false;
   if (d->n_freq < 1 || d->n_freq > kMaxF || d->n_offsets < 1 || d->n_offsets > kMaxP)
@@ -102,8 +104,8 @@ Layout make_layout(const gftorf_dims* d) {
   L.off_zkey2 = take(2 * BN * 4);
   L.off_ids = take(BN * 4);
   L.off_ids2 = take(BN * 4);
-  L.off_dhist = take((size_t)L.B * 256 * (L.n_dblk > 0 ? L.n_dblk : 1) * 4);
-  L.off_dtot = take((size_t)L.B * 256 * 4);
+  L.off_dhist = take(lb_bytes(L));
+  L.off_dtot = take((size_t)L.B * 1024 * 4);
   L.off_ecnt = take((size_t)L.B * L.N * 4 + 4);
   L.off_bsum = take((size_t)(L.n_scan + 1) * 8);
   L.off_tcnt = take((size_t)L.n_chunk * L.NT * 4);
@@ -171,8 +173,8 @@ Layout binning_layout(const gftorf_dims* d) {
   L.off_zkey2 = take(2 * BN * 4);
   L.off_ids = take(BN * 4);
   L.off_ids2 = take(BN * 4);
-  L.off_dhist = take((size_t)L.B * 256 * (L.n_dblk > 0 ? L.n_dblk : 1) * 4);
-  L.off_dtot = take((size_t)L.B * 256 * 4);
+  L.off_dhist = take(lb_bytes(L));
+  L.off_dtot = take((size_t)L.B * 1024 * 4);
   L.off_ecnt = take(BN * 4 + 4);
   L.off_bsum = take((size_t)(L.n_scan + 1) * 8);
   L.off_tcnt = take((size_t)L.n_chunk * L.NT * 4);

@@ -184,75 +184,66 @@ __global__ void footprint_kernel(const float* __restrict__ u,
 }
 
 // ---------------------------------------------------------------------------
-// depth sort: stable LSD radix sort, 8-bit digits, one segment per frame
+// depth sort: stable LSD radix sort, 8-bit digits, one segment per frame.
+// The per-frame digit totals of all four passes come from one reading of the
+// keys (they do not depend on the order); each pass is then one kernel that
+// ranks a tile of keys in shared memory and finds the tile's offset for each
+// digit from the tiles before it (decoupled look-back: every tile publishes
+// its digit counts, then the running prefix once it knows it).
 // ---------------------------------------------------------------------------
+constexpr uint32_t kLbPrefix = 0x80000000u;  // status word: inclusive prefix
+constexpr uint32_t kLbAggregate = 0x40000000u;  // status word: this tile's count only
+constexpr uint32_t kLbCount = 0x3FFFFFFFu;
+constexpr int kLbSpinLimit = 1 << 22;  // bounded wait on a predecessor tile
+
 __global__ void __launch_bounds__(kSortThreads)
-    dsort_hist_kernel(const uint32_t* __restrict__ kin, int N, int shift,
-                      uint32_t* __restrict__ dh, int n_dblk) {
-  __shared__ uint32_t h[256];
+    dsort_hist_kernel(const uint32_t* __restrict__ keys, int N, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[4][256];
   const int blk = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
-  h[tid] = 0;
-  const uint32_t* k = kin + (size_t)b * N;
-  uint32_t d[kSortItems];
-#pragma unroll
-  for (int it = 0; it < kSortItems; ++it) {  // all loads in flight first
-    const int pos = blk * kSortTile + it * kSortThreads + tid;
-    d[it] = pos < N ? (k[pos] >> shift) & 255u : 256u + (tid & 31);
-  }
+  for (int i = tid; i < 4 * 256; i += kSortThreads) (&h[0][0])[i] = 0;
   __syncthreads();
+  const uint32_t* k = keys + (size_t)b * N;
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    const uint32_t peers = __match_any_sync(0xffffffffu, d[it]);
-    if (d[it] < 256u && __popc(peers & lanemask_lt()) == 0)
-      atomicAdd(&h[d[it]], (uint32_t)__popc(peers));
+    const int pos = blk * kSortTile + it * kSortThreads + tid;
+    if (pos < N) {
+      const uint32_t key = k[pos];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
+    }
   }
   __syncthreads();
-  dh[((size_t)b * 256 + tid) * n_dblk + blk] = h[tid];
-}
-
-// Offsets for the scatter, in two short steps: each (frame, digit) row of
-// per-tile counts is scanned by one warp (in place, row total kept), then each
-// frame's 256 row totals by one CTA; offset = digit base + row prefix.
-__global__ void __launch_bounds__(256)
-    dsort_scan_rows_kernel(uint32_t* __restrict__ dh, uint32_t* __restrict__ dtot,
-                           int rows, int n_dblk) {
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (row >= rows) return;
-  uint32_t* a = dh + (size_t)row * n_dblk;
-  uint32_t carry = 0;
-  for (int base = 0; base < n_dblk; base += 32) {
-    const int i = base + lane;
-    const uint32_t v = i < n_dblk ? a[i] : 0u;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (i < n_dblk) a[i] = carry + x - v;
-    carry += __shfl_sync(0xffffffffu, x, 31);
+  for (int i = tid; i < 4 * 256; i += kSortThreads) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(&ghist[(size_t)b * 1024 + i], c);
   }
-  if (lane == 0) dtot[row] = carry;
 }
 
-__global__ void __launch_bounds__(256) dsort_scan_digits_kernel(uint32_t* __restrict__ dtot) {
-  cta_exclusive_scan<uint32_t>(dtot + (size_t)blockIdx.x * 256, 256, nullptr);
+// per (frame, pass): exclusive scan of the 256 digit totals -> digit bases
+__global__ void __launch_bounds__(256) dsort_bases_kernel(uint32_t* __restrict__ ghist) {
+  cta_exclusive_scan<uint32_t>(ghist + (size_t)blockIdx.x * 256, 256, nullptr);
 }
 
-// rin/rout (last pass only, else null): the Gaussians' tile rectangles are
-// written in the sorted order as well
+// One pass: tiles are claimed in order through an atomic counter, so a tile
+// only ever waits for tiles that are already running.  rin/rout (last pass
+// only, else null): the Gaussians' tile rectangles are written in the
+// sorted order as well.
 __global__ void __launch_bounds__(kSortThreads)
-    dsort_scatter_kernel(const uint32_t* __restrict__ kin,
-                         const uint32_t* __restrict__ iin,
-                         uint32_t* __restrict__ kout, uint32_t* __restrict__ iout,
-                         int N, int shift, const uint32_t* __restrict__ dh,
-                         const uint32_t* __restrict__ dtot, int n_dblk,
-                         const uint2* __restrict__ rin, uint2* __restrict__ rout) {
+    dsort_pass_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ iin,
+                      uint32_t* __restrict__ kout, uint32_t* __restrict__ iout, int N, int B,
+                      int pass, int n_dblk, const uint32_t* __restrict__ gbase,
+                      uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
+                      Header* __restrict__ hdr, const uint2* __restrict__ rin,
+                      uint2* __restrict__ rout) {
   __shared__ uint32_t wc[kSortWarps][256];
-  const int blk = blockIdx.x, b = blockIdx.y;
+  __shared__ uint32_t s_tile;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int shift = 8 * pass;
+  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
   for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&wc[0][0])[i] = 0;
   __syncthreads();
+  const uint32_t L = s_tile;
+  const int b = (int)(L / (uint32_t)n_dblk), blk = (int)(L - (uint32_t)b * n_dblk);
   const size_t fb = (size_t)b * N;
   const int start = blk * kSortTile + w * (kSortTile / kSortWarps);
   uint32_t key[kSortItems], id[kSortItems], loc[kSortItems];
@@ -263,30 +254,65 @@ __global__ void __launch_bounds__(kSortThreads)
     key[it] = valid ? kin[fb + pos] : 0u;
     id[it] = valid ? (iin ? iin[fb + pos] : (uint32_t)pos) : 0u;
   }
+  // rank within the warp (lanes in order, items in order): stable.  The
+  // lanes sharing a digit in each item first (independent of one another),
+  // then the warp's running digit counts item after item.
+  uint32_t peers[kSortItems];
+  const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    const int pos = start + it * 32 + lane;
-    const bool valid = pos < N;
-    const uint32_t k = key[it];
-    const uint32_t d = valid ? (k >> shift) & 255u : 256u + lane;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t rank = __popc(peers & lanemask_lt());
+    const bool valid = start + it * 32 + lane < N;
+    const uint32_t d = valid ? (key[it] >> shift) & 255u : 256u + lane;
+    peers[it] = __match_any_sync(0xffffffffu, d);
+  }
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const bool valid = start + it * 32 + lane < N;
+    const uint32_t d = (key[it] >> shift) & 255u;
+    const uint32_t rank = __popc(peers[it] & lt);
     const uint32_t before = valid ? wc[w][d] : 0u;
     __syncwarp();
-    if (valid && rank == 0) wc[w][d] = before + __popc(peers);
+    if (valid && rank == 0) wc[w][d] = before + __popc(peers[it]);
     __syncwarp();
     loc[it] = before + rank;
   }
   __syncthreads();
   {
     const int d = tid;  // 256 threads, one digit each
-    uint32_t run = dtot[(size_t)b * 256 + d] + dh[((size_t)b * 256 + d) * n_dblk + blk];
+    uint32_t cnt = 0;
 #pragma unroll
     for (int ww = 0; ww < kSortWarps; ++ww) {
       const uint32_t t = wc[ww][d];
-      wc[ww][d] = run;
-      run += t;
+      wc[ww][d] = cnt;
+      cnt += t;
     }
+    // publish this tile's count, then find the count of the tiles before it
+    volatile uint32_t* st = status + ((size_t)pass * B + b) * (size_t)n_dblk * 256;
+    uint32_t excl = 0;
+    if (blk == 0) {
+      st[d] = kLbPrefix | cnt;
+    } else {
+      st[(size_t)blk * 256 + d] = kLbAggregate | cnt;
+      int j = blk - 1, spins = 0;
+      for (;;) {
+        const uint32_t v = st[(size_t)j * 256 + d];
+        if (v == 0u) {
+          if (++spins > kLbSpinLimit) {  // never expected: tiles before are running
+            set_status(hdr, GFTORF_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += v & kLbCount;
+        if ((v & kLbPrefix) || j == 0) break;
+        --j;
+      }
+      st[(size_t)blk * 256 + d] = kLbPrefix | (excl + cnt);
+    }
+    const uint32_t base = gbase[((size_t)b * 4 + pass) * 256 + d] + excl;
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ++ww) wc[ww][d] += base;
   }
   __syncthreads();
 #pragma unroll
@@ -295,9 +321,11 @@ __global__ void __launch_bounds__(kSortThreads)
     if (pos < N) {
       const uint32_t d = (key[it] >> shift) & 255u;
       const uint32_t dst = wc[w][d] + loc[it];
-      kout[fb + dst] = key[it];
-      iout[fb + dst] = id[it];
-      if (rout) rout[fb + dst] = rin[fb + id[it]];
+      if (dst < (uint32_t)N) {  // always (a timed-out wait leaves garbage, not a fault)
+        kout[fb + dst] = key[it];
+        iout[fb + dst] = id[it];
+        if (rout) rout[fb + dst] = rin[fb + id[it]];
+      }
     }
   }
 }
@@ -580,18 +608,24 @@ __global__ void __launch_bounds__(256)
   // phase 3: Gaussians one at a time, lanes over its tiles
   __shared__ int4 s_g[8][32];  // per warp and Gaussian of the batch: lo, n, width, index
   __shared__ float s_inv[8][32];  // 1 / width
+  // the next batch's offsets, indices and rectangles are loaded while the
+  // current one is written
+  uint32_t eo_n = 0, g_n = 0;
+  uint2 pr_n = make_uint2(0, 0);
+  if (rw + lane < vis) {
+    eo_n = eb[rw + lane];
+    g_n = ids[rw + lane];
+    pr_n = rc[rw + lane];
+  }
   for (int rb = rw;; rb += 32) {
     const int r = rb + lane;
-    uint32_t eo = 0, g = 0;
-    uint2 pr = make_uint2(0, 0);
-    bool ok = false;
-    if (r < vis) {
-      eo = eb[r];
-      ok = eo < ew;
-      if (ok) {
-        g = ids[r];
-        pr = rc[r];
-      }
+    const uint32_t eo = eo_n, g = g_n;
+    const uint2 pr = pr_n;
+    const bool ok = r < vis && eo < ew;
+    if (r + 32 < vis) {
+      eo_n = eb[r + 32];
+      g_n = ids[r + 32];
+      pr_n = rc[r + 32];
     }
     const unsigned take = __ballot_sync(0xffffffffu, ok);
     if (!take) break;
@@ -647,6 +681,13 @@ __global__ void export_keys_kernel(const uint2* __restrict__ ranges,
 
 }  // namespace
 
+// look-back region: 64 words of per-pass tile counters, then one status word
+// per (pass, frame, tile, digit)
+constexpr size_t kLbCounters = 64;
+size_t lb_bytes(const Layout& L) {
+  return (kLbCounters + (size_t)4 * L.B * (L.n_dblk > 0 ? L.n_dblk : 1) * 256) * 4;
+}
+
 void launch_footprints(const Layout& L, const float* u, const float* v,
                        const int32_t* radius, const float* z,
                        unsigned char* ws, cudaStream_t st) {
@@ -673,8 +714,8 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   auto* k1 = k0 + (size_t)L.B * L.N;
   auto* i0 = at<uint32_t>(ws, L.off_ids);
   auto* i1 = at<uint32_t>(ws, L.off_ids2);
-  auto* dh = at<uint32_t>(ws, L.off_dhist);
-  auto* dtot = at<uint32_t>(ws, L.off_dtot);
+  auto* lb = at<uint32_t>(ws, L.off_dhist);     // pass tile counters, then status words
+  auto* ghist = at<uint32_t>(ws, L.off_dtot);   // [frame][pass][digit] totals -> bases
   auto* rect = at<const uint2>(ws, L.off_rect);
   auto* srect = at<uint2>(ws, L.off_srect);
   auto* ecnt = at<uint32_t>(ws, L.off_ecnt);
@@ -688,21 +729,21 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
     cudaMemsetAsync(ranges, 0, (size_t)L.B * L.NT * sizeof(uint2), st);
     return;
   }
-  // 1. depth sort: zkey -> (k0,i0) -> (k1,i1) -> (k0,i0) -> (k1,i1)
+  // 1. depth sort: zkey -> (k0,i0) -> (k1,i1) -> (k0,i0) -> (k1,i1); the
+  // digit totals of all passes, then one look-back kernel per pass
   const uint32_t* kin = zkey;
   const uint32_t* iin = nullptr;
   uint32_t* kout[2] = {k0, k1};
   uint32_t* iout[2] = {i0, i1};
-  dim3 g(L.n_dblk, L.B);
+  cudaMemsetAsync(ghist, 0, (size_t)L.B * 1024 * 4, st);
+  cudaMemsetAsync(lb, 0, lb_bytes(L), st);
+  dsort_hist_kernel<<<dim3(L.n_dblk, L.B), kSortThreads, 0, st>>>(zkey, L.N, ghist);
+  dsort_bases_kernel<<<L.B * 4, 256, 0, st>>>(ghist);
   for (int pass = 0; pass < 4; ++pass) {
-    const int shift = 8 * pass;
-    dsort_hist_kernel<<<g, kSortThreads, 0, st>>>(kin, L.N, shift, dh, L.n_dblk);
-    dsort_scan_rows_kernel<<<(L.B * 256 + 7) / 8, 256, 0, st>>>(dh, dtot, L.B * 256, L.n_dblk);
-    dsort_scan_digits_kernel<<<L.B, 256, 0, st>>>(dtot);
-    dsort_scatter_kernel<<<g, kSortThreads, 0, st>>>(kin, iin, kout[pass & 1], iout[pass & 1],
-                                                     L.N, shift, dh, dtot, L.n_dblk,
-                                                     pass == 3 ? rect : nullptr,
-                                                     pass == 3 ? srect : nullptr);
+    dsort_pass_kernel<<<L.B * L.n_dblk, kSortThreads, 0, st>>>(
+        kin, iin, kout[pass & 1], iout[pass & 1], L.N, L.B, pass, L.n_dblk, ghist,
+        lb + kLbCounters, lb + pass, hdr, pass == 3 ? rect : nullptr,
+        pass == 3 ? srect : nullptr);
     kin = kout[pass & 1];
     iin = iout[pass & 1];
   }
@@ -724,7 +765,7 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   tile_scatter_kernel<<<L.n_chunk, nw * 32, (size_t)nw * corners, st>>>(
       sorted, srect, hdr, ecnt, tcnt, ttot, values, L.N, L.NT, L.tiles_x, L.tiles_y, L.B,
       L.cap);
-  count_launches(16 + 9);
+  count_launches(6 + 9);
 }
 
 void launch_export_keys(const Layout& L, uint64_t* keys, unsigned char* ws,

@@ -163,6 +163,7 @@ void launch_footprints(const Layout& L, const float* u, const float* v,
                        const int32_t* radius, const float* z,
                        unsigned char* ws, cudaStream_t st);
 void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st);
+size_t lb_bytes(const Layout& L);  // depth-sort look-back region
 void launch_export_keys(const Layout& L, uint64_t* keys, unsigned char* ws,
                         cudaStream_t st);
 template <typename Real, bool DEPTH>
