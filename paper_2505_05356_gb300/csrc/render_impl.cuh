@@ -223,6 +223,57 @@ __device__ __forceinline__ Real log2_oG(const Real* r, const Column<Real>& c, Re
   return fma_rn(fma_rn(r[4], dy, c.cb_dx), dy, c.a_lo);
 }
 
+// Two FP32 values in one 64-bit register pair, for the packed FP32x2
+// instructions of this architecture: each lane is the IEEE round-to-nearest
+// result of the scalar operation, so packed and scalar code agree bit for
+// bit, while one instruction issue does the work of two.
+struct F2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ F2 pack2(float a, float b) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(F2 x, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ F2 sub2_rn(F2 a, F2 b) {
+  F2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 fma2_rn(F2 a, F2 b, F2 c) {
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+
+// log2_oG of the PPT pixels of one column: pairs of pixels in packed FP32x2
+// (the same roundings as log2_oG); the double instantiation stays scalar
+template <int PPT>
+__device__ __forceinline__ void log2_oG_column(const float* r, const Column<float>& c,
+                                               const float* fpy, float* lg) {
+  if constexpr (PPT % 2 == 0) {
+    const F2 r1 = pack2(r[1], r[1]), r4 = pack2(r[4], r[4]);
+    const F2 cb = pack2(c.cb_dx, c.cb_dx), alo = pack2(c.a_lo, c.a_lo);
+#pragma unroll
+    for (int h = 0; h < PPT / 2; ++h) {
+      const F2 dy = sub2_rn(r1, pack2(fpy[2 * h], fpy[2 * h + 1]));
+      unpack2(fma2_rn(fma2_rn(r4, dy, cb), dy, alo), lg[2 * h], lg[2 * h + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) lg[k] = log2_oG(r, c, sub_rn(r[1], fpy[k]));
+  }
+}
+template <int PPT>
+__device__ __forceinline__ void log2_oG_column(const double* r, const Column<double>& c,
+                                               const double* fpy, double* lg) {
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) lg[k] = log2_oG(r, c, sub_rn(r[1], fpy[k]));
+}
+
 // Resident CTAs per SM the compiler is asked to fit (register budget).  Only
 // the 4-pixel variants (128 threads per 16x32 tile) are register limited: the
 // forward keeps 7 CTAs (<= 72 registers), the backward 6 (<= 80).
@@ -331,11 +382,9 @@ __device__ __forceinline__ void render_tile_fwd(
         // the exponents of all PPT pixels first (independent chains), then
         // each pixel's decisions
         Real lg[PPT], oG[PPT];
+        log2_oG_column<PPT>(r, col, fpy, lg);
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          lg[k] = log2_oG(r, col, sub_rn(r[1], fpy[k]));
-          oG[k] = ex2_approx(lg[k]);
-        }
+        for (int k = 0; k < PPT; ++k) oG[k] = ex2_approx(lg[k]);
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (done & (1u << k)) continue;
@@ -620,11 +669,13 @@ __device__ __forceinline__ void render_tile_bwd(
         // moments over this thread's pixels (same column) of dL/dpower:
         // S0 = sum d, S1 = sum d dy, S2 = sum d dy^2; S5 = sum dL/dalpha o G
         Real S0 = 0, S1 = 0, S2 = 0, S5 = 0;
+        Real lgv[PPT];  // exponents of all PPT pixels first (packed pairs)
+        log2_oG_column<PPT>(r, col, fpy, lgv);
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (j >= my_hi[k]) continue;
           const Real dy = sub_rn(r[1], fpy[k]);
-          const Real lg = log2_oG(r, col, dy);
+          const Real lg = lgv[k];
           const Real oG = ex2_approx(lg);
           const Real alpha = oG < amax ? oG : amax;
           if (lg > r[5] || alpha < amin) continue;
