@@ -139,8 +139,9 @@ KERNEL_OF_STAGE = {"composite_bwd": "render_bwd_kernel", "composite_fwd": "rende
 
 def _traffic(stage, frames):
     """DRAM bytes per launch of the stage's kernel from the committed ncu
-    capture (profiles/traffic.json), scaled to `frames`; None when the
-    kernel's source changed since the capture or none exists."""
+    capture (profiles/traffic.json), scaled to `frames` when the capture ran
+    another batch size; None when the kernel's source changed since the
+    capture or none exists."""
     import hashlib
     kern = KERNEL_OF_STAGE.get(stage)
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -153,7 +154,7 @@ def _traffic(stage, frames):
         h = hashlib.sha256(f.read()).hexdigest()[:16]
     if not rec or rec.get("source_sha256_16") != h:
         return None
-    return int(rec["dram_bytes_per_launch_2frames"] * frames / rec["frames_in_capture"])
+    return int(rec["dram_bytes_per_launch"] * frames / rec["frames_in_capture"])
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
