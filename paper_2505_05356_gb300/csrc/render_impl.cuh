@@ -125,6 +125,38 @@ __device__ __forceinline__ TileCtx tile_of(uint32_t item, int NT, int tiles_x) {
   return c;
 }
 
+// The pixels of a thread and the block of its warp, tile-local.  Tiles at
+// most 16 wide: thread t owns column t % TW, rows from (t / TW) PPT, so a warp
+// covers 32 / TW whole rows of PPT-pixel strips.  32-wide tiles: warps cover
+// 16 x 2 PPT blocks, TW / 16 of them across, so that a warp's pixels stay a
+// compact block whatever the tile's width (its record mask tests that block).
+struct ThreadPix {
+  int lx, ly0;             // first pixel of the thread
+  int wx0, wx1, wy0, wy1;  // the warp's block (inclusive)
+};
+template <int PPT>
+__device__ __forceinline__ ThreadPix thread_pixels(int tid, int TW) {
+  ThreadPix t;
+  const int lane = tid & 31, wid = tid >> 5;
+  if (TW <= 16) {
+    t.lx = tid % TW;
+    t.ly0 = (tid / TW) * PPT;
+    t.wx0 = 0;
+    t.wx1 = TW - 1;
+    t.wy0 = ((wid << 5) / TW) * PPT;
+    t.wy1 = (((wid << 5) + 31) / TW) * PPT + PPT - 1;
+  } else {
+    const int across = TW / 16, bx = wid % across, by = wid / across;
+    t.lx = bx * 16 + (lane & 15);
+    t.ly0 = by * 2 * PPT + (lane >> 4) * PPT;
+    t.wx0 = bx * 16;
+    t.wx1 = bx * 16 + 15;
+    t.wy0 = by * 2 * PPT;
+    t.wy1 = t.wy0 + 2 * PPT - 1;
+  }
+  return t;
+}
+
 struct RenderGeom {
   int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B, cull, phasor;
 };
@@ -275,11 +307,16 @@ __device__ __forceinline__ void log2_oG_column(const double* r, const Column<dou
 }
 
 // Resident CTAs per SM the compiler is asked to fit (register budget).  Only
-// the 4-pixel variants (128 threads per 16x32 tile) are register limited: the
-// forward keeps 7 CTAs (<= 72 registers), the backward 6 (<= 80).
-template <int PPT, bool BWD>
+// the 4-pixel variants are register limited: with 128 threads (16x32 tile) the
+// forward keeps 7 CTAs (<= 72 registers), the backward 6 (<= 80); with 256
+// threads (32x32 tile, WIDE) 3 of either (<= 85).
+template <int PPT, bool BWD, bool WIDE>
 struct kMinBlocks {
-  static constexpr int value = PPT == 4 ? (BWD ? 6 : 7) : 0;
+  static constexpr int value = WIDE ? 3 : (PPT == 4 ? (BWD ? 6 : 7) : 0);
+};
+template <int PPT, bool WIDE>
+struct kMaxThreads {
+  static constexpr int value = (WIDE ? 1024 : 512) / PPT;
 };
 
 template <typename Real, int F, int PPT, bool DEPTH, bool COUNT>
@@ -294,7 +331,8 @@ __device__ __forceinline__ void render_tile_fwd(
   constexpr int RS = rec_stride<Real, F>();
   constexpr unsigned ALL = (1u << PPT) - 1u;
   const int nthr = blockDim.x, tid = threadIdx.x;
-  const int lx = tid % rg.TW, ly0 = (tid / rg.TW) * PPT;
+  const ThreadPix tp = thread_pixels<PPT>(tid, rg.TW);
+  const int lx = tp.lx, ly0 = tp.ly0;
   const int px = tc.tx * rg.TW + lx, py0 = tc.ty * rg.TH + ly0;
   const Real fpx = (Real)px + Real(0.5);
   Real fpy[PPT];
@@ -326,10 +364,10 @@ __device__ __forceinline__ void render_tile_fwd(
   const Real cx0 = (Real)(tc.tx * rg.TW) + Real(0.5), cx1 = cx0 + (Real)(rg.TW - 1);
   const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
   const Real log2_amin = log2(amin);
-  // this warp's rows of the tile (it spans whole rows: 32 is a multiple of TW)
+  // this warp's block of the tile (pixel centres)
   const int lane = tid & 31, wid = tid >> 5;
-  const Real wy0 = cy0 + (Real)(((wid << 5) / rg.TW) * PPT);
-  const Real wy1 = cy0 + (Real)(((wid << 5) + 31) / rg.TW * PPT + PPT - 1);
+  const Real wx0 = cx0 + (Real)tp.wx0, wx1 = cx0 + (Real)tp.wx1;
+  const Real wy0 = cy0 + (Real)tp.wy0, wy1 = cy0 + (Real)tp.wy1;
   uint32_t wevals = 0;  // pairs of records that reach the warp's rows (COUNT only)
   for (uint32_t base = range.x; base < range.y; base += nthr) {
     if (__syncthreads_count(done == ALL) == nthr) break;
@@ -354,13 +392,13 @@ __device__ __forceinline__ void render_tile_fwd(
       s_idx[pos] = i;
     }
     __syncthreads();
-    // records that can reach alpha_min at a pixel centre of this warp's rows
+    // records that can reach alpha_min at a pixel centre of this warp's block
     // (the tile test on the warp's rectangle): bit j of word q is record
     // 32 q + j; the others are skipped by every pixel of the warp
     const int nq = (cnt + 31) >> 5;
     for (int q = 0; q < nq; ++q) {
       const int j = (q << 5) + lane;
-      const bool hit = j < cnt && (!rg.cull || tile_hit<Real>(s_rec + j * RS, cx0, cx1, wy0, wy1,
+      const bool hit = j < cnt && (!rg.cull || tile_hit<Real>(s_rec + j * RS, wx0, wx1, wy0, wy1,
                                                                log2_amin));
       const unsigned m = __ballot_sync(0xffffffffu, hit);
       if (lane == 0) s_mask[wid * kMaskWords + q] = m;
@@ -445,8 +483,9 @@ __device__ __forceinline__ void render_tile_fwd(
   }
 }
 
-template <typename Real, int F, int PPT, bool DEPTH, bool COUNT>
-__global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT, false>::value)
+template <typename Real, int F, int PPT, bool DEPTH, bool COUNT, bool WIDE>
+__global__ void __launch_bounds__(kMaxThreads<PPT, WIDE>::value,
+                                  kMinBlocks<PPT, false, WIDE>::value)
     render_fwd_kernel(RenderGeom rg, const TableT<Real>* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
@@ -499,7 +538,8 @@ __device__ __forceinline__ void render_tile_bwd(
   constexpr int RS = rec_stride<Real, F>();
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
-  const int lx = tid % rg.TW, ly0 = (tid / rg.TW) * PPT;
+  const ThreadPix tp = thread_pixels<PPT>(tid, rg.TW);
+  const int lx = tp.lx, ly0 = tp.ly0;
   const int px = tc.tx * rg.TW + lx, py0 = tc.ty * rg.TH + ly0;
   const Real fpx = (Real)px + Real(0.5);
   const Real amax = (Real)tab->alpha_max, amin = (Real)tab->alpha_min;
@@ -600,9 +640,9 @@ __device__ __forceinline__ void render_tile_bwd(
   const Real cx0 = (Real)(tc.tx * rg.TW) + Real(0.5), cx1 = cx0 + (Real)(rg.TW - 1);
   const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
   const Real log2_amin = log2(amin);
-  // this warp's rows of the tile (it spans whole rows: 32 is a multiple of TW)
-  const Real wy0 = cy0 + (Real)(((wid << 5) / rg.TW) * PPT);
-  const Real wy1 = cy0 + (Real)(((wid << 5) + 31) / rg.TW * PPT + PPT - 1);
+  // this warp's block of the tile (pixel centres)
+  const Real wx0 = cx0 + (Real)tp.wx0, wx1 = cx0 + (Real)tp.wx1;
+  const Real wy0 = cy0 + (Real)tp.wy0, wy1 = cy0 + (Real)tp.wy1;
   for (int hi = maxn; hi > 0; hi -= nthr) {
     const int lo = max(0, hi - nthr);
     const int cnt = hi - lo;
@@ -642,12 +682,12 @@ __device__ __forceinline__ void render_tile_bwd(
     int warp_hi = thread_hi;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) warp_hi = max(warp_hi, __shfl_xor_sync(0xffffffffu, warp_hi, o));
-    // records below warp_hi that can reach alpha_min in this warp's rows (the
+    // records below warp_hi that can reach alpha_min in this warp's block (the
     // forward's warp test, so the same records): bit j of word q is 32 q + j
     const int nq = (warp_hi + 31) >> 5;
     for (int q = 0; q < nq; ++q) {
       const int j = (q << 5) + lane;
-      const bool hit = j < warp_hi && (!rg.cull || tile_hit<Real>(s_rec + j * RS, cx0, cx1, wy0,
+      const bool hit = j < warp_hi && (!rg.cull || tile_hit<Real>(s_rec + j * RS, wx0, wx1, wy0,
                                                                    wy1, log2_amin));
       const unsigned m = __ballot_sync(0xffffffffu, hit);
       if (lane == 0) s_mask[wid * kMaskWords + q] = m;
@@ -736,8 +776,9 @@ __device__ __forceinline__ void render_tile_bwd(
   }
 }
 
-template <typename Real, int F, int PPT, bool DEPTH>
-__global__ void __launch_bounds__(512 / PPT, kMinBlocks<PPT, true>::value)
+template <typename Real, int F, int PPT, bool DEPTH, bool WIDE>
+__global__ void __launch_bounds__(kMaxThreads<PPT, WIDE>::value,
+                                  kMinBlocks<PPT, true, WIDE>::value)
     render_bwd_kernel(RenderGeom rg, const TableT<Real>* __restrict__ tab,
                       Header* __restrict__ hdr,
                       const uint2* __restrict__ ranges,
@@ -798,13 +839,13 @@ int persistent_grid(KernelT kernel, int threads, size_t smem) {
   return sm_count() * (per_sm > 0 ? per_sm : 1);
 }
 
-template <typename Real, int F, int PPT, bool DEPTH, bool COUNT>
+template <typename Real, int F, int PPT, bool DEPTH, bool COUNT, bool WIDE>
 void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                 cudaStream_t st) {
   constexpr int RS = rec_stride<Real, F>();
   const int threads = L.TW * L.TH / PPT;
   const size_t smem = (size_t)threads * (2 * RS * sizeof(Real) + sizeof(uint32_t));
-  auto kernel = render_fwd_kernel<Real, F, PPT, DEPTH, COUNT>;
+  auto kernel = render_fwd_kernel<Real, F, PPT, DEPTH, COUNT, WIDE>;
   static PerDeviceOnce attr;
   attr.run([&] {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -825,7 +866,7 @@ void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
   count_launches(1);
 }
 
-template <typename Real, int F, int PPT, bool DEPTH>
+template <typename Real, int F, int PPT, bool DEPTH, bool WIDE>
 void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
                 unsigned char* ws, cudaStream_t st) {
   constexpr int NF = 2 * F + 1;
@@ -834,7 +875,7 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
   const int threads = L.TW * L.TH / PPT;
   const size_t smem = (size_t)threads * (2 * RS + GS) * sizeof(Real) +
                       32 * sizeof(Real) + (size_t)threads * 2 * sizeof(uint32_t);
-  auto kernel = render_bwd_kernel<Real, F, PPT, DEPTH>;
+  auto kernel = render_bwd_kernel<Real, F, PPT, DEPTH, WIDE>;
   static PerDeviceOnce attr;
   attr.run([&] {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -859,28 +900,40 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
 template <typename Real, int F, bool DEPTH>
 void fwd_dispatch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                   cudaStream_t st) {
+  // 32-wide tiles come with 4 pixels per thread (256 threads)
+  if (L.TW > 16) {
+    if (L.count_pairs)
+      fwd_launch<Real, F, 4, DEPTH, true, true>(L, bg, out, ws, st);
+    else
+      fwd_launch<Real, F, 4, DEPTH, false, true>(L, bg, out, ws, st);
+    return;
+  }
   if (L.count_pairs) {
     switch (L.ppt) {
-      case 1: fwd_launch<Real, F, 1, DEPTH, true>(L, bg, out, ws, st); break;
-      case 4: fwd_launch<Real, F, 4, DEPTH, true>(L, bg, out, ws, st); break;
-      default: fwd_launch<Real, F, 2, DEPTH, true>(L, bg, out, ws, st); break;
+      case 1: fwd_launch<Real, F, 1, DEPTH, true, false>(L, bg, out, ws, st); break;
+      case 4: fwd_launch<Real, F, 4, DEPTH, true, false>(L, bg, out, ws, st); break;
+      default: fwd_launch<Real, F, 2, DEPTH, true, false>(L, bg, out, ws, st); break;
     }
     return;
   }
   switch (L.ppt) {
-    case 1: fwd_launch<Real, F, 1, DEPTH, false>(L, bg, out, ws, st); break;
-    case 4: fwd_launch<Real, F, 4, DEPTH, false>(L, bg, out, ws, st); break;
-    default: fwd_launch<Real, F, 2, DEPTH, false>(L, bg, out, ws, st); break;
+    case 1: fwd_launch<Real, F, 1, DEPTH, false, false>(L, bg, out, ws, st); break;
+    case 4: fwd_launch<Real, F, 4, DEPTH, false, false>(L, bg, out, ws, st); break;
+    default: fwd_launch<Real, F, 2, DEPTH, false, false>(L, bg, out, ws, st); break;
   }
 }
 
 template <typename Real, int F, bool DEPTH>
 void bwd_dispatch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
                   unsigned char* ws, cudaStream_t st) {
+  if (L.TW > 16) {
+    bwd_launch<Real, F, 4, DEPTH, true>(L, bg, dout, dbg, ws, st);
+    return;
+  }
   switch (L.ppt) {
-    case 1: bwd_launch<Real, F, 1, DEPTH>(L, bg, dout, dbg, ws, st); break;
-    case 4: bwd_launch<Real, F, 4, DEPTH>(L, bg, dout, dbg, ws, st); break;
-    default: bwd_launch<Real, F, 2, DEPTH>(L, bg, dout, dbg, ws, st); break;
+    case 1: bwd_launch<Real, F, 1, DEPTH, false>(L, bg, dout, dbg, ws, st); break;
+    case 4: bwd_launch<Real, F, 4, DEPTH, false>(L, bg, dout, dbg, ws, st); break;
+    default: bwd_launch<Real, F, 2, DEPTH, false>(L, bg, dout, dbg, ws, st); break;
   }
 }
 

@@ -26,6 +26,7 @@ SMALL = [
     ("static_1k", dict(width=50, height=37)),
     ("static_1k", dict(tile=(8, 8), width=72, height=40)),
     ("static_1k", dict(tile=(16, 32), width=70, height=75)),
+    ("static_1k", dict(tile=(32, 32), width=70, height=75)),
     ("static_1k", dict(freqs_hz=[30e6, 80e6], z_range=(0.5, 6.0))),
     ("static_1k", dict(offsets_rad=[0.1, 0.9, 2.0, 2.5, 3.3, 4.0, 5.1, 6.0])),
     ("dynamic_100k", dict(n=3000, width=96, height=80, frames=3)),
@@ -166,6 +167,28 @@ def test_pixels_per_thread_bit_identical(tile, freqs):
         np.testing.assert_array_equal(res["nlast"], ref["nlast"])
         for k, (nrm, elem) in grads_close(res["grads"], ref["grads"]).items():
             assert nrm <= 1e-5, (ppt, k, nrm)
+
+
+@pytest.mark.parametrize("freqs,extra", [([30e6], False), ([30e6, 80e6], True)])
+def test_tile_shapes_render_identically(freqs, extra):
+    """Every pixel composites the same Gaussians in the same (depth) order
+    whatever the tile shape, so the forward is bit-identical across shapes
+    (and the gradients equal up to atomic summation order); this also checks
+    the 32x32 tile's thread layout (16x8 warp blocks, two across)."""
+    sc = scenes.make_scene("batch_300k", 18, n=5000, width=100, height=70, frames=2,
+                           freqs_hz=freqs, phasor=extra, depth=extra)
+    dout = scenes.random_dout(sc, 7)
+    runs = {}
+    for tile, ppt in (((16, 32), 4), ((32, 32), 4), ((16, 16), 2), ((8, 8), 1)):
+        sc.consts.tile_w, sc.consts.tile_h = tile
+        runs[tile] = run_gpu(sc, dout, pixels_per_thread=ppt)
+    ref = runs[(16, 32)]
+    for tile, res in runs.items():
+        assert res["status"][0] == gftorf.OK
+        np.testing.assert_array_equal(res["out"], ref["out"], err_msg=str(tile))
+        np.testing.assert_array_equal(res["tfinal"], ref["tfinal"], err_msg=str(tile))
+        for k, (nrm, elem) in grads_close(res["grads"], ref["grads"]).items():
+            assert nrm <= 1e-5, (tile, k, nrm)
 
 
 def test_batched_equals_per_frame():

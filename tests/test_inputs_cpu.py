@@ -84,5 +84,8 @@ def test_autotune_candidates_are_accepted_launch_shapes():
         assert (tw, th) in autotune.TILES and c["mode"] in (0, 1)
         assert tw * th // c["ppt"] >= 32  # a full warp per tile
         assert th % c["ppt"] == 0          # whole columns of pixels per thread
-    # the 8x8 tile with 4 pixels per thread (16 threads) is not offered
+    # the 8x8 tile with 4 pixels per thread (16 threads) is not offered, and
+    # 32-wide tiles only with 4 pixels per thread
     assert not any(tuple(c["tile"]) == (8, 8) and c["ppt"] == 4 for c in cands)
+    assert not any(c["tile"][0] == 32 and c["ppt"] != 4 for c in cands)
+    assert any(tuple(c["tile"]) == (32, 32) for c in cands)
