@@ -189,7 +189,11 @@ __global__ void footprint_kernel(const float* __restrict__ u,
 // keys (they do not depend on the order); each pass is then one kernel that
 // ranks a tile of keys in shared memory and finds the tile's offset for each
 // digit from the tiles before it (decoupled look-back: every tile publishes
-// its digit counts, then the running prefix once it knows it).
+// its digit counts, then the running prefix once it knows it).  Culled
+// Gaussians (key 0xFFFFFFFF) are left out: their place in the order is never
+// read (every later kernel stops at the frame's visible count), so the first
+// pass packs the visible keys at the front of the frame and the later passes
+// run only the frame's ceil(visible / 2048) tiles.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kLbPrefix = 0x80000000u;  // status word: inclusive prefix
 constexpr uint32_t kLbAggregate = 0x40000000u;  // status word: this tile's count only
@@ -208,8 +212,10 @@ __global__ void __launch_bounds__(kSortThreads)
     const int pos = blk * kSortTile + it * kSortThreads + tid;
     if (pos < N) {
       const uint32_t key = k[pos];
+      if (key != kCulledKey) {
 #pragma unroll
-      for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
+        for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
+      }
     }
   }
   __syncthreads();
@@ -246,14 +252,22 @@ __global__ void __launch_bounds__(kSortThreads)
   const int b = (int)(L / (uint32_t)n_dblk), blk = (int)(L - (uint32_t)b * n_dblk);
   const size_t fb = (size_t)b * N;
   const int start = blk * kSortTile + w * (kSortTile / kSortWarps);
+  // the first pass reads all N keys of the frame (culled ones skipped), the
+  // later ones the visible keys packed at its front
+  const int vis = (int)hdr->vis[b];
+  const int n_in = pass == 0 ? N : vis;
+  if (blk * kSortTile >= n_in) return;  // no keys: no later tile waits for it
   uint32_t key[kSortItems], id[kSortItems], loc[kSortItems];
+  bool live[kSortItems];
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {  // all loads in flight first
     const int pos = start + it * 32 + lane;
-    const bool valid = pos < N;
-    key[it] = valid ? kin[fb + pos] : 0u;
+    const bool valid = pos < n_in;
+    key[it] = valid ? kin[fb + pos] : kCulledKey;
     id[it] = valid ? (iin ? iin[fb + pos] : (uint32_t)pos) : 0u;
   }
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) live[it] = key[it] != kCulledKey;
   // rank within the warp (lanes in order, items in order): stable.  The
   // lanes sharing a digit in each item first (independent of one another),
   // then the warp's running digit counts item after item.
@@ -261,13 +275,12 @@ __global__ void __launch_bounds__(kSortThreads)
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    const bool valid = start + it * 32 + lane < N;
-    const uint32_t d = valid ? (key[it] >> shift) & 255u : 256u + lane;
+    const uint32_t d = live[it] ? (key[it] >> shift) & 255u : 256u + lane;
     peers[it] = __match_any_sync(0xffffffffu, d);
   }
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    const bool valid = start + it * 32 + lane < N;
+    const bool valid = live[it];
     const uint32_t d = (key[it] >> shift) & 255u;
     const uint32_t rank = __popc(peers[it] & lt);
     const uint32_t before = valid ? wc[w][d] : 0u;
@@ -317,11 +330,10 @@ __global__ void __launch_bounds__(kSortThreads)
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    const int pos = start + it * 32 + lane;
-    if (pos < N) {
+    if (live[it]) {
       const uint32_t d = (key[it] >> shift) & 255u;
       const uint32_t dst = wc[w][d] + loc[it];
-      if (dst < (uint32_t)N) {  // always (a timed-out wait leaves garbage, not a fault)
+      if (dst < (uint32_t)vis) {  // always (a timed-out wait leaves garbage, not a fault)
         kout[fb + dst] = key[it];
         iout[fb + dst] = id[it];
         if (rout) rout[fb + dst] = rin[fb + id[it]];
