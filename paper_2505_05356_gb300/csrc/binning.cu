@@ -555,12 +555,13 @@ __global__ void __launch_bounds__(1024)
 // [s + w kChunk/nw, ...).  Its per-tile counts come from the corners of its
 // Gaussians' parts (as in tile_count); each tile's cursor for warp w starts
 // at tile base + chunk prefix + earlier warps' counts.  Then the warp takes
-// its Gaussians 32 at a time (depth order) and walks them one by one, lanes
-// spread over the Gaussian's tiles of the sub-range (the tiles of one
-// Gaussian are distinct, so the lanes never share a cursor); the row-major
-// index in the rectangle is split into (row, column) with a float reciprocal
-// and an exact one-step correction.
-__global__ void __launch_bounds__(256)
+// its Gaussians 32 at a time (depth order) and their instances in the
+// sub-range 32 at a time, one per lane in list order (a lane finds its
+// Gaussian by counting the Gaussians that start at or before its slot);
+// lanes that share a tile take consecutive places in lane order, ranked by
+// __match_any_sync; the row-major index in the rectangle is split into (row,
+// column) with a float reciprocal and an exact one-step correction.
+__global__ void __launch_bounds__(256, 8)
     tile_scatter_kernel(const uint32_t* __restrict__ sorted_ids,
                         const uint2* __restrict__ srect,
                         const Header* __restrict__ hdr,
@@ -617,9 +618,10 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   if (!active) return;
-  // phase 3: Gaussians one at a time, lanes over its tiles
-  __shared__ int4 s_g[8][32];  // per warp and Gaussian of the batch: lo, n, width, index
+  // phase 3: the batch's instances 32 at a time, one per lane, in list order
+  __shared__ int4 s_g[8][32];     // per warp and non-empty Gaussian: lo - start, width, index, corner
   __shared__ float s_inv[8][32];  // 1 / width
+  const unsigned lt = (1u << lane) - 1u;
   // the next batch's offsets, indices and rectangles are loaded while the
   // current one is written
   uint32_t eo_n = 0, g_n = 0;
@@ -647,32 +649,57 @@ __global__ void __launch_bounds__(256)
     const uint32_t n_all = ok ? (uint32_t)(wd * (y1 - y0)) : 0u;
     const uint32_t lo = ok ? max(sw, eo) - eo : 0u;
     const uint32_t n = ok ? min(ew, eo + n_all) - eo - lo : 0u;
-    s_g[w][lane] = make_int4((int)lo, (int)n, wd, (int)g);
-    s_inv[w][lane] = __frcp_rn((float)wd);
+    // slots [start, start + n) of the batch's instances are this Gaussian's
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t start = incl - n;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const bool ne = n > 0u;
+    const unsigned nem = __ballot_sync(0xffffffffu, ne);
+    if (ne) {  // non-empty Gaussians packed in order: their starts increase strictly
+      const int ci = __popc(nem & lt);
+      s_g[w][ci] = make_int4((int)lo - (int)start, wd, (int)g, x0 | (y0 << 16));
+      s_inv[w][ci] = __frcp_rn((float)wd);
+    }
     __syncwarp();
-    const int cnt = __popc(take);
-    const int xy = x0 | (y0 << 16);  // the rectangle's corner, broadcast by shuffle
-    for (int jj = 0; jj < cnt; ++jj) {
-      const int4 q = s_g[w][jj];
-      const float inv = s_inv[w][jj];
-      const int xyj = __shfl_sync(0xffffffffu, xy, jj);
-      for (int k = lane; k < q.y; k += 32) {
-        const int local = q.x + k;
+    int carry = -1;  // packed index of the Gaussian owning the slot before the window
+    for (uint32_t base = 0; base < total; base += 32) {
+      // bit s: a Gaussian starts at slot base + s
+      const uint32_t rel = start - base;
+      const unsigned sb = __reduce_or_sync(0xffffffffu, ne && rel < 32u ? 1u << rel : 0u);
+      const int jj = carry + __popc(sb & (lt | (1u << lane)));
+      carry = __shfl_sync(0xffffffffu, jj, 31);
+      const uint32_t i = base + (uint32_t)lane;
+      int idx = -1, gj = 0;
+      if (i < total) {
+        const int4 q = s_g[w][jj];
+        const float inv = s_inv[w][jj];
+        const int local = q.x + (int)i;
         int ky = (int)((float)local * inv);
-        int kx = local - ky * q.z;
+        int kx = local - ky * q.y;
         if (kx < 0) {
           --ky;
-          kx += q.z;
-        } else if (kx >= q.z) {
+          kx += q.y;
+        } else if (kx >= q.y) {
           ++ky;
-          kx -= q.z;
+          kx -= q.y;
         }
-        const int idx = ((xyj >> 16) + ky) * cols + (xyj & 0xFFFF) + kx;
-        if ((unsigned)idx < (unsigned)A) {
-          const uint32_t p = D[idx];
-          D[idx] = p + 1;
-          if ((int64_t)p < cap) values[p] = (uint32_t)q.w;
-        }
+        idx = ((q.w >> 16) + ky) * cols + (q.w & 0xFFFF) + kx;
+        gj = q.z;
+      }
+      const bool act = (unsigned)idx < (unsigned)A;
+      const unsigned am = __ballot_sync(0xffffffffu, act);
+      if (act) {
+        // lanes of one tile take consecutive places, in slot (= depth) order
+        const unsigned peers = __match_any_sync(am, idx);
+        const uint32_t p = D[idx] + __popc(peers & lt);
+        __syncwarp(am);
+        if ((peers >> lane) == 1u) D[idx] = p + 1u;
+        if ((int64_t)p < cap) values[p] = (uint32_t)gj;
       }
       __syncwarp();
     }
