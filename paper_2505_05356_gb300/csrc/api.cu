@@ -109,7 +109,7 @@ Layout make_layout(const gftorf_dims* d) {
   L.off_dhist = take(lb_bytes(L));
   L.off_dtot = take((size_t)L.B * 1024 * 4);
   L.off_ecnt = take((size_t)L.B * L.N * 4 + 4);
-  L.off_bsum = take((size_t)(L.n_scan + 1) * 8);
+  L.off_bsum = take((size_t)(L.n_scan + 1) * 8);  // scan status words, 2 counters
   L.off_tcnt = take((size_t)L.n_chunk * L.NT * 4);
   L.off_toff = take((size_t)L.B * L.NT * 4);
   L.off_ranges = take((size_t)L.B * L.NT * sizeof(uint2));
@@ -178,7 +178,7 @@ Layout binning_layout(const gftorf_dims* d) {
   L.off_dhist = take(lb_bytes(L));
   L.off_dtot = take((size_t)L.B * 1024 * 4);
   L.off_ecnt = take(BN * 4 + 4);
-  L.off_bsum = take((size_t)(L.n_scan + 1) * 8);
+  L.off_bsum = take((size_t)(L.n_scan + 1) * 8);  // scan status words, 2 counters
   L.off_tcnt = take((size_t)L.n_chunk * L.NT * 4);
   L.off_toff = take((size_t)L.B * L.NT * 4);
   L.off_ranges = take((size_t)L.B * L.NT * sizeof(uint2));

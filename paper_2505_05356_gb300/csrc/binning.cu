@@ -10,12 +10,14 @@
 //   1. depth sort: 4 passes of 8 bits over the per-frame depth keys
 //      (culled Gaussians carry 0xFFFFFFFF and end up last); the last pass
 //      also writes each Gaussian's tile rectangle in depth order;
-//   2. emission offsets: exclusive scan of the tiles each depth-ordered
-//      Gaussian covers; chunks of kChunk consecutive instances per frame;
+//   2. emission offsets: exclusive scan (one pass, decoupled look-back) of
+//      the tiles each depth-ordered Gaussian covers, counted by the last
+//      depth-sort pass; chunks of kChunk consecutive instances per frame;
 //   3. per chunk, tile counts: every Gaussian (or the part of its rectangle
 //      inside the chunk) adds +-1 at the corners of its tile rectangle in a
-//      difference array, whose 2D prefix sum is the count of each tile;
-//      exclusive scans over chunks and tiles give the tile ranges;
+//      difference array, whose 2D prefix sum is the count of each tile
+//      (also summed into per-tile totals); a scan over each frame's chunks
+//      per tile, and over its tiles, gives the tile ranges;
 //   4. scatter: per warp of a chunk the same corner counts give its cursors;
 //      then the warp walks its Gaussians in depth order, lanes spread over
 //      one Gaussian's tiles, each writing the Gaussian index at its tile's
@@ -225,8 +227,16 @@ __global__ void __launch_bounds__(kSortThreads)
   }
 }
 
-// per (frame, pass): exclusive scan of the 256 digit totals -> digit bases
-__global__ void __launch_bounds__(256) dsort_bases_kernel(uint32_t* __restrict__ ghist) {
+// per (frame, pass): exclusive scan of the 256 digit totals -> digit bases.
+// The same CTAs clear the later stages' per-step words: the per-(frame,
+// tile) instance totals and the emission scan's status words and counters.
+__global__ void __launch_bounds__(256)
+    dsort_bases_kernel(uint32_t* __restrict__ ghist, uint32_t* __restrict__ ttot, int n_ttot,
+                       uint64_t* __restrict__ scan_state, int n_state) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_ttot; i += gridDim.x * blockDim.x)
+    ttot[i] = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_state; i += gridDim.x * blockDim.x)
+    scan_state[i] = 0;
   cta_exclusive_scan<uint32_t>(ghist + (size_t)blockIdx.x * 256, 256, nullptr);
 }
 
@@ -234,13 +244,13 @@ __global__ void __launch_bounds__(256) dsort_bases_kernel(uint32_t* __restrict__
 // only ever waits for tiles that are already running.  rin/rout (last pass
 // only, else null): the Gaussians' tile rectangles are written in the
 // sorted order as well.
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 5)  // <= 48 registers, no spill
     dsort_pass_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ iin,
                       uint32_t* __restrict__ kout, uint32_t* __restrict__ iout, int N, int B,
                       int pass, int n_dblk, const uint32_t* __restrict__ gbase,
                       uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
                       Header* __restrict__ hdr, const uint2* __restrict__ rin,
-                      uint2* __restrict__ rout) {
+                      uint2* __restrict__ rout, uint32_t* __restrict__ ecnt) {
   __shared__ uint32_t wc[kSortWarps][256];
   __shared__ uint32_t s_tile;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -256,6 +266,10 @@ __global__ void __launch_bounds__(kSortThreads)
   // later ones the visible keys packed at its front
   const int vis = (int)hdr->vis[b];
   const int n_in = pass == 0 ? N : vis;
+  if (ecnt) {  // last pass: the tile's places past the visible count cover no tiles
+    const int z0 = max(vis, blk * kSortTile), z1 = min(N, (blk + 1) * kSortTile);
+    for (int p = z0 + tid; p < z1; p += kSortThreads) ecnt[fb + p] = 0u;
+  }
   if (blk * kSortTile >= n_in) return;  // no keys: no later tile waits for it
   uint32_t key[kSortItems], id[kSortItems], loc[kSortItems];
   bool live[kSortItems];
@@ -336,76 +350,62 @@ __global__ void __launch_bounds__(kSortThreads)
       if (dst < (uint32_t)vis) {  // always (a timed-out wait leaves garbage, not a fault)
         kout[fb + dst] = key[it];
         iout[fb + dst] = id[it];
-        if (rout) rout[fb + dst] = rin[fb + id[it]];
+        if (rout) {  // last pass: rectangle and tile count in depth order
+          const uint2 rr = rin[fb + id[it]];
+          rout[fb + dst] = rr;
+          int x0, y0, x1, y1;
+          unpack_rect(rr, x0, y0, x1, y1);
+          ecnt[fb + dst] = (uint32_t)((x1 - x0) * (y1 - y0));
+        }
       }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// emission offsets: tiles covered by each depth-ordered Gaussian, scanned
-// over the whole batch (frame-major), so instance k of the batch is tile
-// (k - e[g]) of Gaussian g's rectangle (row-major) for the g with
-// e[g] <= k < e[g + 1]
+// emission offsets: tiles covered by each depth-ordered Gaussian (written by
+// the last depth-sort pass), scanned over the whole batch (frame-major), so
+// instance k of the batch is tile (k - e[g]) of Gaussian g's rectangle
+// (row-major) for the g with e[g] <= k < e[g + 1].  One pass: tiles of
+// kScanTile counts claimed in order through an atomic counter, each finding
+// the sum of the tiles before it by decoupled look-back on 64-bit status
+// words; the CTA that finishes last writes the chunk table (first instance
+// and first binning chunk of each frame; chunks never straddle frames).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-    inst_count_kernel(const uint2* __restrict__ srect, const Header* __restrict__ hdr,
-                      uint32_t* __restrict__ ecnt, int N) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  if (i >= N) return;
-  uint32_t c = 0;
-  if (i < (int)hdr->vis[b]) {
-    int x0, y0, x1, y1;
-    unpack_rect(srect[(size_t)b * N + i], x0, y0, x1, y1);
-    c = (uint32_t)((x1 - x0) * (y1 - y0));
-  }
-  ecnt[(size_t)b * N + i] = c;
-}
+constexpr uint64_t kScanPrefix = 1ull << 63;     // status word: inclusive prefix
+constexpr uint64_t kScanAggregate = 1ull << 62;  // status word: this tile's sum only
+constexpr uint64_t kScanValue = kScanAggregate - 1;
 
-// device-wide exclusive scan: tile sums, scan of the sums, tile scans
 __global__ void __launch_bounds__(256)
-    scan_reduce_kernel(const uint32_t* __restrict__ a, int64_t S,
-                       uint64_t* __restrict__ bsum) {
+    emission_scan_kernel(uint32_t* __restrict__ a, int64_t S, uint64_t* __restrict__ state,
+                         int nblk, Header* __restrict__ hdr, int B, int N, int64_t cap,
+                         int n_chunk) {
+  constexpr int kItems = kScanTile / 256;  // 16 consecutive counts per thread
   __shared__ uint64_t s_w[8];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  uint64_t sum = 0;
-  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
-    const int64_t i = base + k;
-    if (i < S) sum += a[i];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
-    bsum[blockIdx.x] = t;
-  }
-}
-
-__global__ void __launch_bounds__(1024)
-    scan_top_kernel(uint64_t* __restrict__ bsum, int nblk) {
-  __shared__ uint64_t s_total;
-  cta_exclusive_scan<uint64_t>(bsum, nblk, &s_total);
-  if (threadIdx.x == 0) bsum[nblk] = s_total;
-}
-
-__global__ void __launch_bounds__(256)
-    scan_down_kernel(uint32_t* __restrict__ a, int64_t S,
-                     const uint64_t* __restrict__ bsum) {
-  constexpr int kItems = kScanTile / 256;
-  __shared__ uint64_t s_w[8];
+  __shared__ uint64_t s_excl;
+  __shared__ uint32_t s_tile;
+  __shared__ bool s_last;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kItems;
+  unsigned int* counters = reinterpret_cast<unsigned int*>(state + nblk);  // claim, done
+  if (tid == 0) s_tile = atomicAdd(&counters[0], 1u);
+  __syncthreads();
+  const int tile = (int)s_tile;
+  const int64_t base = (int64_t)tile * kScanTile + (int64_t)tid * kItems;
   uint32_t v[kItems];
+  if (base + kItems <= S) {
+    const uint4* src = reinterpret_cast<const uint4*>(a + base);
+#pragma unroll
+    for (int q = 0; q < kItems / 4; ++q) {
+      const uint4 x = src[q];
+      v[4 * q] = x.x, v[4 * q + 1] = x.y, v[4 * q + 2] = x.z, v[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) v[k] = base + k < S ? a[base + k] : 0u;
+  }
   uint64_t sum = 0;
 #pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    v[k] = base + k < S ? a[base + k] : 0u;
-    sum += v[k];
-  }
+  for (int k = 0; k < kItems; ++k) sum += v[k];
   uint64_t incl = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -414,29 +414,70 @@ __global__ void __launch_bounds__(256)
   }
   if (lane == 31) s_w[wid] = incl;
   __syncthreads();
-  uint64_t run = bsum[blockIdx.x] + incl - sum;
-  for (int w = 0; w < wid; ++w) run += s_w[w];
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    if (base + k < S) a[base + k] = (uint32_t)run;
-    run += v[k];
+  if (tid == 0) {
+    uint64_t agg = 0;
+    for (int w = 0; w < 8; ++w) agg += s_w[w];
+    volatile uint64_t* st = state;
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st[0] = kScanPrefix | agg;
+    } else {
+      st[tile] = kScanAggregate | agg;
+      int j = tile - 1, spins = 0;
+      for (;;) {
+        const uint64_t w = st[j];
+        if (w == 0u) {
+          if (++spins > kLbSpinLimit) {  // never expected: tiles before are running
+            set_status(hdr, GFTORF_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += w & kScanValue;
+        if ((w & kScanPrefix) || j == 0) break;
+        --j;
+      }
+      st[tile] = kScanPrefix | (excl + agg);
+    }
+    s_excl = excl;
   }
-}
-
-// per frame: first instance and first chunk (chunks never straddle frames)
-__global__ void chunk_table_kernel(const uint32_t* __restrict__ eoff,
-                                   const uint64_t* __restrict__ bsum, int nblk,
-                                   Header* __restrict__ hdr, int B, int N,
-                                   int64_t cap, int n_chunk) {
-  if (threadIdx.x != 0) return;
-  const uint64_t total = bsum[nblk];
+  __syncthreads();
+  uint64_t run = s_excl + incl - sum;
+  for (int w = 0; w < wid; ++w) run += s_w[w];
+  if (base + kItems <= S) {
+    uint4* dst = reinterpret_cast<uint4*>(a + base);
+#pragma unroll
+    for (int q = 0; q < kItems / 4; ++q) {
+      uint4 x;
+      x.x = (uint32_t)run; run += v[4 * q];
+      x.y = (uint32_t)run; run += v[4 * q + 1];
+      x.z = (uint32_t)run; run += v[4 * q + 2];
+      x.w = (uint32_t)run; run += v[4 * q + 3];
+      dst[q] = x;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      if (base + k < S) a[base + k] = (uint32_t)run;
+      run += v[k];
+    }
+  }
+  // the last CTA to finish sees every tile's offsets
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&counters[1], 1u) == (unsigned)(nblk - 1);
+  __syncthreads();
+  if (!s_last || tid != 0) return;
+  __threadfence();
+  const uint64_t total = *reinterpret_cast<volatile uint64_t*>(&state[nblk - 1]) & kScanValue;
   const bool over = total > (uint64_t)cap;
   hdr->count = (int64_t)total;
   if (over) set_status(hdr, GFTORF_ERR_CAPACITY);
   uint32_t c = 0;
   for (int b = 0; b < B; ++b) {
-    const uint64_t fs = eoff[(size_t)b * N];
-    const uint64_t fe = b + 1 < B ? (uint64_t)eoff[(size_t)(b + 1) * N] : total;
+    const uint64_t fs = __ldcg(&a[(size_t)b * N]);
+    const uint64_t fe = b + 1 < B ? (uint64_t)__ldcg(&a[(size_t)(b + 1) * N]) : total;
     hdr->fstart[b] = (uint32_t)fs;
     hdr->coff[b] = c;
     if (!over) c += (uint32_t)((fe - fs + kChunk - 1) / kChunk);
@@ -461,11 +502,13 @@ __device__ __forceinline__ ChunkPos chunk_pos(const Header* hdr, int c) {
 }
 
 // count the tiles hit by the instances [s, e) of one chunk: corners of each
-// Gaussian's part of the chunk in a difference array, then its 2D prefix sum
+// Gaussian's part of the chunk in a difference array, then its 2D prefix
+// sum; the counts are also added to the frame's per-tile totals
 __global__ void __launch_bounds__(256)
     tile_count_kernel(const uint2* __restrict__ srect, const Header* __restrict__ hdr,
-                      const uint32_t* __restrict__ eoff, uint32_t* __restrict__ tcnt, int N,
-                      int NT, int tiles_x, int tiles_y, int B) {
+                      const uint32_t* __restrict__ eoff, uint32_t* __restrict__ tcnt,
+                      uint32_t* __restrict__ ttot, int N, int NT, int tiles_x, int tiles_y,
+                      int B) {
   extern __shared__ uint32_t D[];  // (tiles_y + 1) x (tiles_x + 1)
   __shared__ int s_r0;
   const int c = blockIdx.x;
@@ -495,25 +538,40 @@ __global__ void __launch_bounds__(256)
   prefix2d<false>(D, rows, cols, threadIdx.x, blockDim.x);
   __syncthreads();
   uint32_t* out = tcnt + (size_t)c * NT;
+  uint32_t* tot = ttot + (size_t)cp.b * NT;
   for (int t = threadIdx.x; t < NT; t += blockDim.x) {
     const int ty = t / tiles_x, tx = t - ty * tiles_x;
-    out[t] = D[ty * cols + tx];
+    const uint32_t v = D[ty * cols + tx];
+    out[t] = v;
+    if (v) atomicAdd(&tot[t], v);
   }
 }
 
-// per (frame, tile): exclusive prefix over the frame's chunks; tile totals.
-// A CTA covers 32 tiles (lanes, coalesced rows) and splits the frame's chunks
-// into 8 consecutive segments (warps): segment sums, then per-segment rescan.
+// per (frame, tile): exclusive prefix over the frame's chunks, and the tile's
+// range of the batch's list: the frame's first instance, plus the totals of
+// the frame's tiles before it (those of earlier CTAs summed from the
+// per-tile totals, those of this CTA's 32 tiles scanned), plus nothing else
+// (a frame's instances are contiguous).  A CTA covers 32 tiles (lanes,
+// coalesced rows) and splits the frame's chunks into 8 consecutive segments
+// (warps): segment sums, then per-segment rescan.  Lists that overflowed
+// the capacity are left empty.
 __global__ void __launch_bounds__(256)
-    tile_colscan_kernel(uint32_t* __restrict__ tcnt, uint32_t* __restrict__ ttot,
-                        const Header* __restrict__ hdr, int NT) {
+    tile_colscan_kernel(uint32_t* __restrict__ tcnt, const uint32_t* __restrict__ ttot,
+                        uint2* __restrict__ ranges, const Header* __restrict__ hdr, int NT,
+                        int64_t cap) {
   __shared__ uint32_t s_seg[8][32];
+  __shared__ uint32_t s_pre[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int t = blockIdx.x * 32 + lane;
+  const int t0 = blockIdx.x * 32, t = t0 + lane;
   const int b = blockIdx.y;
   const uint32_t c0 = hdr->coff[b], n = hdr->coff[b + 1] - c0;
   const uint32_t seg = (n + 7) / 8;
   const uint32_t s0 = c0 + min(n, (uint32_t)w * seg), s1 = c0 + min(n, (uint32_t)(w + 1) * seg);
+  uint32_t pre = 0;  // instances of the frame's tiles [0, t0)
+  for (int i = threadIdx.x; i < t0; i += blockDim.x) pre += ttot[(size_t)b * NT + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+  if (lane == 0) s_pre[w] = pre;
   uint32_t sum = 0;
   if (t < NT) {
 #pragma unroll 4
@@ -530,25 +588,23 @@ __global__ void __launch_bounds__(256)
       tcnt[(size_t)c * NT + t] = run;
       run += v;
     }
-    if (w == 7) ttot[(size_t)b * NT + t] = run;
   }
-}
-
-// exclusive scan of the tile totals over (frame, tile); ranges; capacity
-__global__ void __launch_bounds__(1024)
-    tile_scan_kernel(uint32_t* __restrict__ ttot, uint2* __restrict__ ranges,
-                     Header* __restrict__ hdr, int64_t S, int64_t cap) {
-  __shared__ uint64_t s_total;
-  for (int64_t i = threadIdx.x; i < S; i += blockDim.x) ranges[i].y = ttot[i];
-  __syncthreads();
-  cta_exclusive_scan<uint32_t>(ttot, S, &s_total);
-  __syncthreads();
-  const uint64_t total = s_total;
-  for (int64_t i = threadIdx.x; i < S; i += blockDim.x) {
-    const uint64_t s = ttot[i], e = s + ranges[i].y;
-    ranges[i] = make_uint2((uint32_t)min(s, (uint64_t)cap), (uint32_t)min(e, (uint64_t)cap));
+  if (w == 7) {  // run: the tile's total
+    uint32_t incl = t < NT ? run : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (t < NT) {
+      uint32_t base = hdr->fstart[b];
+      for (int ww = 0; ww < 8; ++ww) base += s_pre[ww];
+      const uint64_t st = (uint64_t)base + incl - run, en = st + run;
+      const bool over = hdr->count > cap;
+      ranges[(size_t)b * NT + t] = over ? make_uint2(0u, 0u)
+                                        : make_uint2((uint32_t)st, (uint32_t)en);
+    }
   }
-  if (threadIdx.x == 0 && total > (uint64_t)cap) set_status(hdr, GFTORF_ERR_CAPACITY);
 }
 
 // Stable scatter of one chunk.  Warp w owns the instance sub-range
@@ -567,7 +623,7 @@ __global__ void __launch_bounds__(256, 8)
                         const Header* __restrict__ hdr,
                         const uint32_t* __restrict__ eoff,
                         const uint32_t* __restrict__ tcnt,
-                        const uint32_t* __restrict__ toff,
+                        const uint2* __restrict__ ranges,
                         uint32_t* __restrict__ values, int N, int NT,
                         int tiles_x, int tiles_y, int B, int64_t cap) {
   extern __shared__ uint32_t cur[];  // [warps][(tiles_y + 1) x (tiles_x + 1)]
@@ -606,10 +662,10 @@ __global__ void __launch_bounds__(256, 8)
   __syncthreads();
   // phase 2: cursors
   const uint32_t* cc = tcnt + (size_t)c * NT;
-  const uint32_t* to = toff + (size_t)cp.b * NT;
+  const uint2* to = ranges + (size_t)cp.b * NT;
   for (int t = threadIdx.x; t < NT; t += blockDim.x) {
     const int ty = t / tiles_x, idx = t + ty;  // ty * cols + (t - ty * tiles_x)
-    uint32_t run = to[t] + cc[t];
+    uint32_t run = to[t].x + cc[t];
     for (int ww = 0; ww < nw; ++ww) {
       const uint32_t v = cur[(size_t)ww * A + idx];
       cur[(size_t)ww * A + idx] = run;
@@ -774,37 +830,35 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   const uint32_t* iin = nullptr;
   uint32_t* kout[2] = {k0, k1};
   uint32_t* iout[2] = {i0, i1};
-  cudaMemsetAsync(ghist, 0, (size_t)L.B * 1024 * 4, st);
-  cudaMemsetAsync(lb, 0, lb_bytes(L), st);
+  // the look-back words and the digit totals are adjacent: one memset
+  cudaMemsetAsync(lb, 0, L.off_dtot + (size_t)L.B * 1024 * 4 - L.off_dhist, st);
   dsort_hist_kernel<<<dim3(L.n_dblk, L.B), kSortThreads, 0, st>>>(zkey, L.N, ghist);
-  dsort_bases_kernel<<<L.B * 4, 256, 0, st>>>(ghist);
+  dsort_bases_kernel<<<L.B * 4, 256, 0, st>>>(ghist, ttot, L.B * L.NT, bsum, L.n_scan + 1);
   for (int pass = 0; pass < 4; ++pass) {
     dsort_pass_kernel<<<L.B * L.n_dblk, kSortThreads, 0, st>>>(
         kin, iin, kout[pass & 1], iout[pass & 1], L.N, L.B, pass, L.n_dblk, ghist,
         lb + kLbCounters, lb + pass, hdr, pass == 3 ? rect : nullptr,
-        pass == 3 ? srect : nullptr);
+        pass == 3 ? srect : nullptr, pass == 3 ? ecnt : nullptr);
     kin = kout[pass & 1];
     iin = iout[pass & 1];
   }
-  // 2. emission offsets of the depth-ordered Gaussians, chunk table
-  const int64_t S = (int64_t)L.B * L.N;
-  inst_count_kernel<<<dim3((L.N + 255) / 256, L.B), 256, 0, st>>>(srect, hdr, ecnt, L.N);
-  scan_reduce_kernel<<<L.n_scan, 256, 0, st>>>(ecnt, S, bsum);
-  scan_top_kernel<<<1, 1024, 0, st>>>(bsum, L.n_scan);
-  scan_down_kernel<<<L.n_scan, 256, 0, st>>>(ecnt, S, bsum);
-  chunk_table_kernel<<<1, 32, 0, st>>>(ecnt, bsum, L.n_scan, hdr, L.B, L.N, L.cap, L.n_chunk);
-  // 3. per-chunk tile counts, per-frame column scan, tile ranges
+  // 2. emission offsets of the depth-ordered Gaussians (their tile counts
+  // written by the last pass), chunk table
+  emission_scan_kernel<<<L.n_scan, 256, 0, st>>>(ecnt, (int64_t)L.B * L.N, bsum, L.n_scan, hdr,
+                                                 L.B, L.N, L.cap, L.n_chunk);
+  // 3. per-chunk tile counts and per-tile totals; per-frame column scan and
+  // tile ranges
   const size_t corners = (size_t)(L.tiles_x + 1) * (L.tiles_y + 1) * 4;
-  tile_count_kernel<<<L.n_chunk, 256, corners, st>>>(srect, hdr, ecnt, tcnt, L.N, L.NT,
+  tile_count_kernel<<<L.n_chunk, 256, corners, st>>>(srect, hdr, ecnt, tcnt, ttot, L.N, L.NT,
                                                      L.tiles_x, L.tiles_y, L.B);
-  tile_colscan_kernel<<<dim3((L.NT + 31) / 32, L.B), 256, 0, st>>>(tcnt, ttot, hdr, L.NT);
-  tile_scan_kernel<<<1, 1024, 0, st>>>(ttot, ranges, hdr, (int64_t)L.B * L.NT, L.cap);
+  tile_colscan_kernel<<<dim3((L.NT + 31) / 32, L.B), 256, 0, st>>>(tcnt, ttot, ranges, hdr,
+                                                                   L.NT, L.cap);
   // 4. stable scatter
   const int nw = L.scatter_warps;
   tile_scatter_kernel<<<L.n_chunk, nw * 32, (size_t)nw * corners, st>>>(
-      sorted, srect, hdr, ecnt, tcnt, ttot, values, L.N, L.NT, L.tiles_x, L.tiles_y, L.B,
+      sorted, srect, hdr, ecnt, tcnt, ranges, values, L.N, L.NT, L.tiles_x, L.tiles_y, L.B,
       L.cap);
-  count_launches(6 + 9);
+  count_launches(10);
 }
 
 void launch_export_keys(const Layout& L, uint64_t* keys, unsigned char* ws,

@@ -80,7 +80,7 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 // Tile binning: a chunk of kChunk consecutive instances (in emission order:
 // frame, depth rank, tile of the rectangle) per CTA.
-constexpr int kChunk = 16384;
+constexpr int kChunk = 8192;
 // Device-wide scans: elements per CTA.
 constexpr int kScanTile = 4096;
 
