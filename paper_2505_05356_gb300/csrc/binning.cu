@@ -106,10 +106,15 @@ __device__ __forceinline__ void diff_add_rect(uint32_t* D, int cols, int xa, int
 }
 
 // The instances [lo, hi) (row-major indices, hi > lo) of a Gaussian whose
-// tile rectangle is w wide and starts at (x0, y0): at most three rectangles
-// (the tail of a first row, whole rows, the head of a last row).
+// tile rectangle is w x h and starts at (x0, y0): the whole rectangle (the
+// usual case), else at most three rectangles (the tail of a first row, whole
+// rows, the head of a last row).
 __device__ __forceinline__ void diff_add_span(uint32_t* D, int cols, int x0, int y0, int w,
-                                              int lo, int hi) {
+                                              int h, int lo, int hi) {
+  if (lo == 0 && hi == w * h) {
+    diff_add_rect(D, cols, x0, y0, x0 + w, y0 + h);
+    return;
+  }
   const int ky0 = lo / w, kx0 = lo - ky0 * w;
   const int last = hi - 1;
   const int ky1 = last / w, kx1 = last - ky1 * w;
@@ -283,14 +288,23 @@ __global__ void __launch_bounds__(kSortThreads, 5)  // <= 48 registers, no spill
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) live[it] = key[it] != kCulledKey;
   // rank within the warp (lanes in order, items in order): stable.  The
-  // lanes sharing a digit in each item first (independent of one another),
-  // then the warp's running digit counts item after item.
+  // lanes sharing a digit in each item first (independent of one another:
+  // eight ballots, one per digit bit, measured faster than match.any), then
+  // the warp's running digit counts item after item.
   uint32_t peers[kSortItems];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    const uint32_t d = live[it] ? (key[it] >> shift) & 255u : 256u + lane;
-    peers[it] = __match_any_sync(0xffffffffu, d);
+    // lanes with the same digit: one ballot per digit bit (live lanes only)
+    const uint32_t d = (key[it] >> shift) & 255u;
+    unsigned pm = __ballot_sync(0xffffffffu, live[it]);
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+      const bool on = (d >> bit) & 1u;
+      const unsigned bm = __ballot_sync(0xffffffffu, on);
+      pm &= on ? bm : ~bm;
+    }
+    peers[it] = live[it] ? pm : (1u << lane);
   }
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
@@ -414,33 +428,45 @@ __global__ void __launch_bounds__(256)
   }
   if (lane == 31) s_w[wid] = incl;
   __syncthreads();
-  if (tid == 0) {
+  if (wid == 0) {
+    // publish this tile's sum, then the first warp reads the status words of
+    // the 32 tiles before it at once, window after window, until one holds an
+    // inclusive prefix (or tile 0 is reached)
     uint64_t agg = 0;
     for (int w = 0; w < 8; ++w) agg += s_w[w];
     volatile uint64_t* st = state;
+    if (lane == 0) st[tile] = (tile == 0 ? kScanPrefix : kScanAggregate) | agg;
     uint64_t excl = 0;
-    if (tile == 0) {
-      st[0] = kScanPrefix | agg;
-    } else {
-      st[tile] = kScanAggregate | agg;
-      int j = tile - 1, spins = 0;
-      for (;;) {
-        const uint64_t w = st[j];
-        if (w == 0u) {
-          if (++spins > kLbSpinLimit) {  // never expected: tiles before are running
-            set_status(hdr, GFTORF_ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-          continue;
+    int top = tile - 1;  // newest tile not yet summed
+    int spins = 0;
+    while (top >= 0) {
+      const int j = top - lane;
+      uint64_t w = kScanPrefix;  // before tile 0: prefix 0
+      if (j >= 0) w = st[j];
+      // the window is usable up to the first tile still unpublished
+      const unsigned pending = __ballot_sync(0xffffffffu, w == 0u);
+      const unsigned pref = __ballot_sync(0xffffffffu, (w & kScanPrefix) != 0u);
+      const int first_pending = pending ? __ffs(pending) - 1 : 32;
+      const int first_pref = pref ? __ffs(pref) - 1 : 32;
+      const int take = min(first_pending, first_pref + 1);  // lanes [0, take) summed
+      uint64_t v = lane < take ? (w & kScanValue) : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      excl += v;
+      if (first_pref < first_pending) break;  // reached an inclusive prefix
+      top -= take;
+      if (take == 0) {
+        if (++spins > kLbSpinLimit) {  // never expected: tiles before are running
+          if (lane == 0) set_status(hdr, GFTORF_ERR_TIMEOUT);
+          break;
         }
-        excl += w & kScanValue;
-        if ((w & kScanPrefix) || j == 0) break;
-        --j;
+        __nanosleep(32);
       }
-      st[tile] = kScanPrefix | (excl + agg);
     }
-    s_excl = excl;
+    if (lane == 0) {
+      if (tile != 0) st[tile] = kScanPrefix | (excl + agg);
+      s_excl = excl;
+    }
   }
   __syncthreads();
   uint64_t run = s_excl + incl - sum;
@@ -532,7 +558,7 @@ __global__ void __launch_bounds__(256)
     const int w = x1 - x0;
     const uint32_t n = (uint32_t)(w * (y1 - y0));
     const uint32_t lo = max(cp.s, eo) - eo, hi = min(cp.e, eo + n) - eo;
-    diff_add_span(D, cols, x0, y0, w, (int)lo, (int)hi);
+    diff_add_span(D, cols, x0, y0, w, y1 - y0, (int)lo, (int)hi);
   }
   __syncthreads();
   prefix2d<false>(D, rows, cols, threadIdx.x, blockDim.x);
@@ -601,8 +627,9 @@ __global__ void __launch_bounds__(256)
       for (int ww = 0; ww < 8; ++ww) base += s_pre[ww];
       const uint64_t st = (uint64_t)base + incl - run, en = st + run;
       const bool over = hdr->count > cap;
-      ranges[(size_t)b * NT + t] = over ? make_uint2(0u, 0u)
-                                        : make_uint2((uint32_t)st, (uint32_t)en);
+      const uint64_t c = (uint64_t)cap;  // never exceeded when not over
+      ranges[(size_t)b * NT + t] =
+          over ? make_uint2(0u, 0u) : make_uint2((uint32_t)min(st, c), (uint32_t)min(en, c));
     }
   }
 }
@@ -616,7 +643,9 @@ __global__ void __launch_bounds__(256)
 // Gaussian by counting the Gaussians that start at or before its slot);
 // lanes that share a tile take consecutive places in lane order, ranked by
 // __match_any_sync; the row-major index in the rectangle is split into (row,
-// column) with a float reciprocal and an exact one-step correction.
+// column) with an approximate float reciprocal (relative error near 2^-23:
+// for indices below 50000 the quotient is off by far less than one) and an
+// exact one-step correction.
 __global__ void __launch_bounds__(256, 8)
     tile_scatter_kernel(const uint32_t* __restrict__ sorted_ids,
                         const uint2* __restrict__ srect,
@@ -654,7 +683,7 @@ __global__ void __launch_bounds__(256, 8)
       const int wd = x1 - x0;
       const uint32_t n = (uint32_t)(wd * (y1 - y0));
       const uint32_t lo = max(sw, eo) - eo, hi = min(ew, eo + n) - eo;
-      diff_add_span(D, cols, x0, y0, wd, (int)lo, (int)hi);
+      diff_add_span(D, cols, x0, y0, wd, y1 - y0, (int)lo, (int)hi);
     }
     __syncwarp();
     prefix2d<true>(D, rows, cols, lane, 32);
@@ -678,6 +707,7 @@ __global__ void __launch_bounds__(256, 8)
   __shared__ int4 s_g[8][32];     // per warp and non-empty Gaussian: lo - start, width, index, corner
   __shared__ float s_inv[8][32];  // 1 / width
   const unsigned lt = (1u << lane) - 1u;
+  const uint32_t capu = cap < (int64_t)0xFFFFFFFF ? (uint32_t)cap : 0xFFFFFFFFu;
   // the next batch's offsets, indices and rectangles are loaded while the
   // current one is written
   uint32_t eo_n = 0, g_n = 0;
@@ -719,7 +749,7 @@ __global__ void __launch_bounds__(256, 8)
     if (ne) {  // non-empty Gaussians packed in order: their starts increase strictly
       const int ci = __popc(nem & lt);
       s_g[w][ci] = make_int4((int)lo - (int)start, wd, (int)g, x0 | (y0 << 16));
-      s_inv[w][ci] = __frcp_rn((float)wd);
+      s_inv[w][ci] = rcp_approx((float)wd);
     }
     __syncwarp();
     int carry = -1;  // packed index of the Gaussian owning the slot before the window
@@ -728,7 +758,7 @@ __global__ void __launch_bounds__(256, 8)
       const uint32_t rel = start - base;
       const unsigned sb = __reduce_or_sync(0xffffffffu, ne && rel < 32u ? 1u << rel : 0u);
       const int jj = carry + __popc(sb & (lt | (1u << lane)));
-      carry = __shfl_sync(0xffffffffu, jj, 31);
+      carry += __popc(sb);  // lane 31's jj
       const uint32_t i = base + (uint32_t)lane;
       int idx = -1, gj = 0;
       if (i < total) {
@@ -755,7 +785,7 @@ __global__ void __launch_bounds__(256, 8)
         const uint32_t p = D[idx] + __popc(peers & lt);
         __syncwarp(am);
         if ((peers >> lane) == 1u) D[idx] = p + 1u;
-        if ((int64_t)p < cap) values[p] = (uint32_t)gj;
+        if (p < capu) values[p] = (uint32_t)gj;
       }
       __syncwarp();
     }

@@ -218,6 +218,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 __device__ __forceinline__ double ex2_approx(double x) { return exp2(x); }
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Tile rectangle [x0,x1) x [y0,y1) of the disc of radius r around (u, v),
 // every step in single precision with one rounding each (the binning
