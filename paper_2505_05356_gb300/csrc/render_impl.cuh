@@ -57,6 +57,8 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 __device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float rcp_fast(float a) { return rcp_approx(a); }
+__device__ __forceinline__ double rcp_fast(double a) { return 1.0 / a; }
 __device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
 
 template <typename Real>
@@ -423,6 +425,7 @@ __device__ __forceinline__ void render_tile_fwd(
         log2_oG_column<PPT>(r, col, fpy, lg);
 #pragma unroll
         for (int k = 0; k < PPT; ++k) oG[k] = ex2_approx(lg[k]);
+        const uint32_t jn = s_idx[j] + 1;  // list entries up to this one
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (done & (1u << k)) continue;
@@ -432,17 +435,18 @@ __device__ __forceinline__ void render_tile_fwd(
           }
           const Real alpha = oG[k] < amax ? oG[k] : amax;
           if (lg[k] > r[5] || alpha < amin) continue;
-          const Real tn = T[k] * (Real(1) - alpha);
+          const Real aT = alpha * T[k];
+          const Real tn = T[k] - aT;  // T (1 - alpha)
           if (tn < tmin) {
             done |= 1u << k;
             continue;
           }
-          const Real w = alpha * T[k] * T[k];
+          const Real w = aT * T[k];
 #pragma unroll
           for (int f = 0; f < NF; ++f) acc[k][f] += w * r[6 + f];
-          if (DEPTH) accD[k] += alpha * T[k] * r[7 + NF];  // Eq. 5: one-way T
+          if (DEPTH) accD[k] += aT * r[7 + NF];  // Eq. 5: one-way T
           T[k] = tn;
-          last[k] = s_idx[j] + 1;
+          last[k] = jn;
         }
       }
     }
@@ -721,7 +725,7 @@ __device__ __forceinline__ void render_tile_bwd(
           if (lg > r[5] || alpha < amin) continue;
           has = true;
           const Real oma = Real(1) - alpha;
-          const Real rcp = div_fast(Real(1), oma);
+          const Real rcp = rcp_fast(oma);
           const Real Tk = T[k] * rcp;
           const Real T2 = Tk * Tk;
           Real gq = 0;
