@@ -390,12 +390,13 @@ constexpr uint64_t kScanPrefix = 1ull << 63;     // status word: inclusive prefi
 constexpr uint64_t kScanAggregate = 1ull << 62;  // status word: this tile's sum only
 constexpr uint64_t kScanValue = kScanAggregate - 1;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kScanThreads)
     emission_scan_kernel(uint32_t* __restrict__ a, int64_t S, uint64_t* __restrict__ state,
                          int nblk, Header* __restrict__ hdr, int B, int N, int64_t cap,
                          int n_chunk) {
-  constexpr int kItems = kScanTile / 256;  // 16 consecutive counts per thread
-  __shared__ uint64_t s_w[8];
+  constexpr int kItems = kScanTile / kScanThreads;  // consecutive counts per thread
+  constexpr int kWarps = kScanThreads / 32;
+  __shared__ uint64_t s_w[kWarps];
   __shared__ uint64_t s_excl;
   __shared__ uint32_t s_tile;
   __shared__ bool s_last;
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(256)
     // the 32 tiles before it at once, window after window, until one holds an
     // inclusive prefix (or tile 0 is reached)
     uint64_t agg = 0;
-    for (int w = 0; w < 8; ++w) agg += s_w[w];
+    for (int w = 0; w < kWarps; ++w) agg += s_w[w];
     volatile uint64_t* st = state;
     if (lane == 0) st[tile] = (tile == 0 ? kScanPrefix : kScanAggregate) | agg;
     uint64_t excl = 0;
@@ -537,8 +538,8 @@ __global__ void __launch_bounds__(256)
                       int B) {
   extern __shared__ uint32_t D[];  // (tiles_y + 1) x (tiles_x + 1)
   __shared__ int s_r0;
-  const int c = blockIdx.x;
-  if ((uint32_t)c >= hdr->coff[B]) return;
+  const int n_chunks = (int)hdr->coff[B];
+  for (int c = blockIdx.x; c < n_chunks; c += gridDim.x) {
   const ChunkPos cp = chunk_pos(hdr, c);
   const int vis = (int)hdr->vis[cp.b];
   const uint32_t* eb = eoff + (size_t)cp.b * N;
@@ -570,6 +571,8 @@ __global__ void __launch_bounds__(256)
     const uint32_t v = D[ty * cols + tx];
     out[t] = v;
     if (v) atomicAdd(&tot[t], v);
+  }
+  __syncthreads();  // D is cleared for the next chunk
   }
 }
 
@@ -646,18 +649,15 @@ __global__ void __launch_bounds__(256)
 // column) with an approximate float reciprocal (relative error near 2^-23:
 // for indices below 50000 the quotient is off by far less than one) and an
 // exact one-step correction.
-__global__ void __launch_bounds__(256, 8)
-    tile_scatter_kernel(const uint32_t* __restrict__ sorted_ids,
-                        const uint2* __restrict__ srect,
-                        const Header* __restrict__ hdr,
-                        const uint32_t* __restrict__ eoff,
-                        const uint32_t* __restrict__ tcnt,
-                        const uint2* __restrict__ ranges,
-                        uint32_t* __restrict__ values, int N, int NT,
-                        int tiles_x, int tiles_y, int B, int64_t cap) {
+__device__ __forceinline__ void scatter_chunk(int c, const uint32_t* __restrict__ sorted_ids,
+                                              const uint2* __restrict__ srect,
+                                              const Header* __restrict__ hdr,
+                                              const uint32_t* __restrict__ eoff,
+                                              const uint32_t* __restrict__ tcnt,
+                                              const uint2* __restrict__ ranges,
+                                              uint32_t* __restrict__ values, int N, int NT,
+                                              int tiles_x, int tiles_y, int64_t cap) {
   extern __shared__ uint32_t cur[];  // [warps][(tiles_y + 1) x (tiles_x + 1)]
-  const int c = blockIdx.x;
-  if ((uint32_t)c >= hdr->coff[B]) return;
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ChunkPos cp = chunk_pos(hdr, c);
   const int vis = (int)hdr->vis[cp.b];
@@ -793,6 +793,26 @@ __global__ void __launch_bounds__(256, 8)
   }
 }
 
+// CTAs loop over the batch's chunks (the grid is what fits on the GPU at
+// once; the chunk count is known only on the device)
+__global__ void __launch_bounds__(256, 8)
+    tile_scatter_kernel(const uint32_t* __restrict__ sorted_ids,
+                        const uint2* __restrict__ srect,
+                        const Header* __restrict__ hdr,
+                        const uint32_t* __restrict__ eoff,
+                        const uint32_t* __restrict__ tcnt,
+                        const uint2* __restrict__ ranges,
+                        uint32_t* __restrict__ values, int N, int NT,
+                        int tiles_x, int tiles_y, int B, int64_t cap) {
+  const int n_chunks = (int)hdr->coff[B];
+  for (int c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    scatter_chunk(c, sorted_ids, srect, hdr, eoff, tcnt, ranges, values, N, NT, tiles_x,
+                  tiles_y, cap);
+    __syncthreads();  // the cursors are cleared for the next chunk
+  }
+}
+
+
 __global__ void export_keys_kernel(const uint2* __restrict__ ranges,
                                    const uint32_t* __restrict__ values,
                                    const uint32_t* __restrict__ zkey,
@@ -822,6 +842,17 @@ void launch_footprints(const Layout& L, const float* u, const float* v,
       u, v, radius, z, at<Header>(ws, L.off_header), at<uint2>(ws, L.off_rect),
       at<uint32_t>(ws, L.off_zkey), L.N, L.TW, L.TH, L.tiles_x, L.tiles_y);
   count_launches(1);
+}
+
+// CTAs of a kernel that loops over the batch's chunks: as many as are
+// resident at once (at most one per chunk the capacity allows)
+template <typename KernelT>
+int chunk_grid(KernelT kernel, int threads, size_t smem, int n_chunk) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return max(1, min(n_chunk, per_sm * sm_count()));
 }
 
 void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
@@ -874,18 +905,19 @@ void launch_binning(const Layout& L, unsigned char* ws, cudaStream_t st) {
   }
   // 2. emission offsets of the depth-ordered Gaussians (their tile counts
   // written by the last pass), chunk table
-  emission_scan_kernel<<<L.n_scan, 256, 0, st>>>(ecnt, (int64_t)L.B * L.N, bsum, L.n_scan, hdr,
+  emission_scan_kernel<<<L.n_scan, kScanThreads, 0, st>>>(ecnt, (int64_t)L.B * L.N, bsum, L.n_scan, hdr,
                                                  L.B, L.N, L.cap, L.n_chunk);
   // 3. per-chunk tile counts and per-tile totals; per-frame column scan and
   // tile ranges
   const size_t corners = (size_t)(L.tiles_x + 1) * (L.tiles_y + 1) * 4;
-  tile_count_kernel<<<L.n_chunk, 256, corners, st>>>(srect, hdr, ecnt, tcnt, ttot, L.N, L.NT,
+  tile_count_kernel<<<chunk_grid(tile_count_kernel, 256, corners, L.n_chunk), 256, corners, st>>>(srect, hdr, ecnt, tcnt, ttot, L.N, L.NT,
                                                      L.tiles_x, L.tiles_y, L.B);
   tile_colscan_kernel<<<dim3((L.NT + 31) / 32, L.B), 256, 0, st>>>(tcnt, ttot, ranges, hdr,
                                                                    L.NT, L.cap);
   // 4. stable scatter
   const int nw = L.scatter_warps;
-  tile_scatter_kernel<<<L.n_chunk, nw * 32, (size_t)nw * corners, st>>>(
+  tile_scatter_kernel<<<chunk_grid(tile_scatter_kernel, nw * 32, (size_t)nw * corners, L.n_chunk),
+                        nw * 32, (size_t)nw * corners, st>>>(
       sorted, srect, hdr, ecnt, tcnt, ranges, values, L.N, L.NT, L.tiles_x, L.tiles_y, L.B,
       L.cap);
   count_launches(10);

@@ -81,8 +81,10 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // Tile binning: a chunk of kChunk consecutive instances (in emission order:
 // frame, depth rank, tile of the rectangle) per CTA.
 constexpr int kChunk = 8192;
-// Device-wide scans: elements per CTA.
-constexpr int kScanTile = 4096;
+// Device-wide scan: elements per CTA (few enough CTAs that they all fit on
+// the GPU at once, so the look-back chains stay short) and threads per CTA.
+constexpr int kScanTile = 16384;
+constexpr int kScanThreads = 512;
 
 // Per-frame camera in device memory.
 template <typename T>

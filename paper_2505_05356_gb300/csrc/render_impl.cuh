@@ -177,7 +177,7 @@ __device__ __forceinline__ bool tile_hit(const Real* r, Real cx0, Real cx1, Real
   const Real lx = cx0 - r[0], hx = cx1 - r[0], ly = cy0 - r[1], hy = cy1 - r[1];
   if (lx <= Real(0) && hx >= Real(0) && ly <= Real(0) && hy >= Real(0)) return true;
   const Real A = -r[2], B = -r[3], C = -r[4];
-  const Real hA = div_fast(Real(0.5), A), hC = div_fast(Real(0.5), C);
+  const Real hA = Real(0.5) * rcp_fast(A), hC = Real(0.5) * rcp_fast(C);
   Real m = Real(1e30);
   // horizontal edges dy = ly, hy
 #pragma unroll
@@ -753,13 +753,17 @@ __device__ __forceinline__ void render_tile_bwd(
           }
         }
         if (has) {
+          // moments in dx as well: the gradients of u, v, the conic and o are
+          // linear in these sums, so the warp sums them and the flush applies
+          // the record's constants once per CTA
           const Real dx = col.dx;
-          c[5] = S5 * r[6 + NF];  // d alpha / d o = G = alpha / o
-          c[0] = ln2 * (Real(2) * r[2] * dx * S0 + r[3] * S1);
-          c[1] = ln2 * (Real(2) * r[4] * S1 + col.cb_dx * S0);
-          c[2] = Real(-0.5) * dx * dx * S0;
-          c[3] = -dx * S1;
-          c[4] = Real(-0.5) * S2;
+          const Real b = dx * S0;
+          c[0] = b;       // sum dx d
+          c[1] = dx * b;  // sum dx^2 d
+          c[2] = S1;      // sum dy d
+          c[3] = dx * S1; // sum dx dy d
+          c[4] = S2;      // sum dy^2 d
+          c[5] = S5;      // sum dL/dalpha o G
         }
       }
       if (__any_sync(0xffffffffu, has)) {
@@ -769,12 +773,25 @@ __device__ __forceinline__ void render_tile_bwd(
      }
     }
     __syncthreads();
-    for (int k = tid; k < nk * GS; k += nthr) {
-      const Real v = s_grad[k];
-      if (v != Real(0)) {
-        const int j = k / GS, comp = k - j * GS;
-        atomicAdd(&gbase[(size_t)s_id[j] * g2d_stride + comp], v);
-      }
+    // per record: the 2D gradient from the CTA's sums (alpha = 2^(log2 o +
+    // ln2-scaled quadratic), d alpha / d o = alpha / o), one global atomic per
+    // non-zero component
+    for (int jj = tid; jj < nk; jj += nthr) {
+      const Real* rr = s_rec + jj * RS;
+      const Real* sg = s_grad + jj * GS;
+      Real v[GS];
+      v[0] = ln2 * (Real(2) * rr[2] * sg[0] + rr[3] * sg[2]);
+      v[1] = ln2 * (Real(2) * rr[4] * sg[2] + rr[3] * sg[0]);
+      v[2] = Real(-0.5) * sg[1];
+      v[3] = -sg[3];
+      v[4] = Real(-0.5) * sg[4];
+      v[5] = sg[5] * rr[6 + NF];
+#pragma unroll
+      for (int q = 6; q < GS; ++q) v[q] = sg[q];
+      Real* gr = gbase + (size_t)s_id[jj] * g2d_stride;
+#pragma unroll
+      for (int q = 0; q < GS; ++q)
+        if (v[q] != Real(0)) atomicAdd(&gr[q], v[q]);
     }
     __syncthreads();
   }
