@@ -495,22 +495,47 @@ __global__ void __launch_bounds__(kScanThreads)
   __syncthreads();
   if (tid == 0) s_last = atomicAdd(&counters[1], 1u) == (unsigned)(nblk - 1);
   __syncthreads();
-  if (!s_last || tid != 0) return;
+  if (!s_last || wid != 0) return;
   __threadfence();
+  // chunk table by one warp: lane l takes frames l and l + 32 (at most 64)
   const uint64_t total = *reinterpret_cast<volatile uint64_t*>(&state[nblk - 1]) & kScanValue;
   const bool over = total > (uint64_t)cap;
-  hdr->count = (int64_t)total;
-  if (over) set_status(hdr, GFTORF_ERR_CAPACITY);
-  uint32_t c = 0;
-  for (int b = 0; b < B; ++b) {
-    const uint64_t fs = __ldcg(&a[(size_t)b * N]);
-    const uint64_t fe = b + 1 < B ? (uint64_t)__ldcg(&a[(size_t)(b + 1) * N]) : total;
-    hdr->fstart[b] = (uint32_t)fs;
-    hdr->coff[b] = c;
-    if (!over) c += (uint32_t)((fe - fs + kChunk - 1) / kChunk);
+  uint64_t fs[2], n[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int b = lane + 32 * h;
+    fs[h] = b < B ? (uint64_t)__ldcg(&a[(size_t)b * N]) : total;
   }
-  hdr->fstart[B] = (uint32_t)total;
-  hdr->coff[B] = c <= (uint32_t)n_chunk ? c : (uint32_t)n_chunk;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // the next frame's first instance
+    uint64_t fe = __shfl_down_sync(0xffffffffu, fs[h], 1);
+    const uint64_t wrap = __shfl_sync(0xffffffffu, h == 0 ? fs[1] : total, 0);
+    if (lane == 31) fe = wrap;
+    const int b = lane + 32 * h;
+    n[h] = (b < B && !over) ? (fe - fs[h] + kChunk - 1) / kChunk : 0u;
+  }
+  uint64_t nrun = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint64_t incl = n[h];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int b = lane + 32 * h;
+    if (b < B) {
+      hdr->fstart[b] = (uint32_t)fs[h];
+      hdr->coff[b] = (uint32_t)(nrun + incl - n[h]);
+    }
+    nrun += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) {
+    hdr->count = (int64_t)total;
+    if (over) set_status(hdr, GFTORF_ERR_CAPACITY);
+    hdr->fstart[B] = (uint32_t)total;
+    hdr->coff[B] = nrun <= (uint64_t)n_chunk ? (uint32_t)nrun : (uint32_t)n_chunk;
+  }
 }
 
 struct ChunkPos {

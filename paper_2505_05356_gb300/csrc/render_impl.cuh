@@ -711,8 +711,10 @@ __device__ __forceinline__ void render_tile_bwd(
       if (j < thread_hi) {
         const Column<Real> col = column_of(r, fpx);
         // moments over this thread's pixels (same column) of dL/dpower:
-        // S0 = sum d, S1 = sum d dy, S2 = sum d dy^2; S5 = sum dL/dalpha o G
-        Real S0 = 0, S1 = 0, S2 = 0, S5 = 0;
+        // S0 = sum d, S1 = sum d dy, S2 = sum d dy^2 (S0 is also the sum of
+        // dL/dalpha o G: where alpha is not clamped, d = dL/dalpha alpha and
+        // alpha = o G)
+        Real S0 = 0, S1 = 0, S2 = 0;
         Real lgv[PPT];  // exponents of all PPT pixels first (packed pairs)
         log2_oG_column<PPT>(r, col, fpy, lgv);
 #pragma unroll
@@ -731,8 +733,9 @@ __device__ __forceinline__ void render_tile_bwd(
           Real gq = 0;
 #pragma unroll
           for (int f = 0; f < NF; ++f) gq += gacc[k][f] * r[6 + f];
-          Real dLda = T2 * (gq - (oma + oma) * A[k]) - gTf[k] * rcp;
-          A[k] = alpha * gq + oma * oma * A[k];
+          const Real X = oma * A[k];
+          Real dLda = T2 * (gq - Real(2) * X) - gTf[k] * rcp;
+          A[k] = alpha * gq + oma * X;
           if (DEPTH) {
             const Real gDd = gD[k] * r[7 + NF];
             dLda += Tk * (gDd - BD[k]);
@@ -744,7 +747,6 @@ __device__ __forceinline__ void render_tile_bwd(
           for (int f = 0; f < NF; ++f) c[6 + f] += gacc[k][f] * aT2;
           T[k] = Tk;
           if (oG < amax) {  // alpha = o G is not clamped: it depends on o, u, v, conic
-            S5 += dLda * oG;
             const Real d = dLda * alpha;  // d alpha / d power = alpha
             const Real t = d * dy;
             S0 += d;
@@ -763,7 +765,7 @@ __device__ __forceinline__ void render_tile_bwd(
           c[2] = S1;      // sum dy d
           c[3] = dx * S1; // sum dx dy d
           c[4] = S2;      // sum dy^2 d
-          c[5] = S5;      // sum dL/dalpha o G
+          c[5] = S0;      // sum dL/dalpha o G
         }
       }
       if (__any_sync(0xffffffffu, has)) {
