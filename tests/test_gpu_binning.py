@@ -96,16 +96,18 @@ def _oracle_footprints(sc):
     return [np.ascontiguousarray(np.stack(a)) for a in (u, v, r, z)]
 
 
-def test_sort_matches_oracle_bit_exact_at_benchmark_density():
+@pytest.mark.parametrize("tile,least", [((16, 32), 40_000_000), ((32, 32), 25_000_000)])
+def test_sort_matches_oracle_bit_exact_at_benchmark_density(tile, least):
     """The benchmark's density: 300k Gaussians x 16 frames at 640x480 with
-    16x32 tiles (tens of millions of instances, thousands of binning chunks,
-    full-width scans), footprints as the oracle projects them, sorted by
-    gftorf_sort_footprints and by the oracle's (key, index) sort."""
+    16x32 and 32x32 tiles (tens of millions of instances, thousands of
+    binning chunks, full-width scans), footprints as the oracle projects
+    them, sorted by gftorf_sort_footprints and by the oracle's (key, index)
+    sort."""
     from paper_2505_05356_gb300 import scenes
-    sc = scenes.make_scene("batch_300k", 0, tile=(16, 32))
+    sc = scenes.make_scene("batch_300k", 0, tile=tile)
     u, v, r, z = _oracle_footprints(sc)
-    m = _compare(u, v, r, z, sc.width, sc.height, (16, 32))
-    assert m > 40_000_000
+    m = _compare(u, v, r, z, sc.width, sc.height, tile)
+    assert m > least
 
 
 def test_pipeline_lists_match_oracle_rects_full_size():
