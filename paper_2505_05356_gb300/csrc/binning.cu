@@ -258,6 +258,11 @@ __global__ void __launch_bounds__(kSortThreads, 5)  // <= 48 registers, no spill
                       uint2* __restrict__ rout, uint32_t* __restrict__ ecnt) {
   __shared__ uint32_t wc[kSortWarps][256];
   __shared__ uint32_t s_tile;
+  // the tile's keys and indices in digit order (staged, then written out in
+  // runs of consecutive places), each digit's first place in the tile and in
+  // the frame, the warps' digit-count sums
+  __shared__ uint32_t s_key[kSortTile], s_id[kSortTile];
+  __shared__ uint32_t s_tstart[256], s_gbase[256], s_wsum[kSortWarps];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int shift = 8 * pass;
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
@@ -351,26 +356,52 @@ __global__ void __launch_bounds__(kSortThreads, 5)  // <= 48 registers, no spill
       }
       st[(size_t)blk * 256 + d] = kLbPrefix | (excl + cnt);
     }
-    const uint32_t base = gbase[((size_t)b * 4 + pass) * 256 + d] + excl;
+    s_gbase[d] = gbase[((size_t)b * 4 + pass) * 256 + d] + excl;
+    // first place of digit d in the tile: exclusive scan of the counts
+    uint32_t incl = cnt;
 #pragma unroll
-    for (int ww = 0; ww < kSortWarps; ++ww) wc[ww][d] += base;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_wsum[w] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ++ww) before += ww < w ? s_wsum[ww] : 0u;
+    s_tstart[d] = before + incl - cnt;
   }
   __syncthreads();
+  // stage in digit order: place = digit start + earlier warps' count of the
+  // digit + rank in the warp
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
     if (live[it]) {
       const uint32_t d = (key[it] >> shift) & 255u;
-      const uint32_t dst = wc[w][d] + loc[it];
-      if (dst < (uint32_t)vis) {  // always (a timed-out wait leaves garbage, not a fault)
-        kout[fb + dst] = key[it];
-        iout[fb + dst] = id[it];
-        if (rout) {  // last pass: rectangle and tile count in depth order
-          const uint2 rr = rin[fb + id[it]];
-          rout[fb + dst] = rr;
-          int x0, y0, x1, y1;
-          unpack_rect(rr, x0, y0, x1, y1);
-          ecnt[fb + dst] = (uint32_t)((x1 - x0) * (y1 - y0));
-        }
+      const uint32_t tp = s_tstart[d] + wc[w][d] + loc[it];
+      s_key[tp] = key[it];
+      s_id[tp] = id[it];
+    }
+  }
+  __syncthreads();
+  // write out: consecutive threads take consecutive staged places, which lie
+  // in runs of one digit at consecutive places of the frame
+  uint32_t n_live = 0;
+#pragma unroll
+  for (int ww = 0; ww < kSortWarps; ++ww) n_live += s_wsum[ww];
+  for (uint32_t p = tid; p < n_live; p += kSortThreads) {
+    const uint32_t k = s_key[p], g = s_id[p];
+    const uint32_t d = (k >> shift) & 255u;
+    const uint32_t dst = s_gbase[d] + (p - s_tstart[d]);
+    if (dst < (uint32_t)vis) {  // always (a timed-out wait leaves garbage, not a fault)
+      kout[fb + dst] = k;
+      iout[fb + dst] = g;
+      if (rout) {  // last pass: rectangle and tile count in depth order
+        const uint2 rr = rin[fb + g];
+        rout[fb + dst] = rr;
+        int x0, y0, x1, y1;
+        unpack_rect(rr, x0, y0, x1, y1);
+        ecnt[fb + dst] = (uint32_t)((x1 - x0) * (y1 - y0));
       }
     }
   }
