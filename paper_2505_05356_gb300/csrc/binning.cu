@@ -129,6 +129,42 @@ __device__ __forceinline__ void diff_add_span(uint32_t* D, int cols, int x0, int
   }
 }
 
+// Corner counts of the depth-ordered Gaussians r0, r0 + stride, ... (below
+// vis) whose instances meet [s, e): four Gaussians' offsets and rectangles
+// loaded at once per step (emission offsets increase with r, so the first
+// Gaussian starting at or past e ends the walk).
+__device__ __forceinline__ void diff_add_gaussians(uint32_t* D, int cols,
+                                                   const uint32_t* __restrict__ eb,
+                                                   const uint2* __restrict__ rc, int r0,
+                                                   int stride, int vis, uint32_t s, uint32_t e) {
+  constexpr int U = 4;
+  for (int r = r0; r < vis; r += U * stride) {
+    uint32_t eo[U];
+    uint2 rr[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int ri = r + i * stride;
+      eo[i] = ri < vis ? eb[ri] : 0xFFFFFFFFu;
+      rr[i] = ri < vis ? rc[ri] : make_uint2(0u, 0u);
+    }
+    bool stop = false;
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      if (stop || eo[i] >= e) {
+        stop = true;
+      } else {
+        int x0, y0, x1, y1;
+        unpack_rect(rr[i], x0, y0, x1, y1);
+        const int w = x1 - x0;
+        const uint32_t n = (uint32_t)(w * (y1 - y0));
+        const uint32_t lo = max(s, eo[i]) - eo[i], hi = min(e, eo[i] + n) - eo[i];
+        diff_add_span(D, cols, x0, y0, w, y1 - y0, (int)lo, (int)hi);
+      }
+    }
+    if (stop) break;
+  }
+}
+
 // Inclusive 2D prefix sum of D (rows x cols) by threads [0, nthr) of a group
 // (a warp: WARP = true, else the whole CTA): a sequential scan per row, then
 // per column.
@@ -607,16 +643,7 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   const uint2* rc = srect + (size_t)cp.b * N;
-  for (int r = s_r0 + threadIdx.x; r < vis; r += blockDim.x) {
-    const uint32_t eo = eb[r];
-    if (eo >= cp.e) break;
-    int x0, y0, x1, y1;
-    unpack_rect(rc[r], x0, y0, x1, y1);
-    const int w = x1 - x0;
-    const uint32_t n = (uint32_t)(w * (y1 - y0));
-    const uint32_t lo = max(cp.s, eo) - eo, hi = min(cp.e, eo + n) - eo;
-    diff_add_span(D, cols, x0, y0, w, y1 - y0, (int)lo, (int)hi);
-  }
+  diff_add_gaussians(D, cols, eb, rc, s_r0 + threadIdx.x, blockDim.x, vis, cp.s, cp.e);
   __syncthreads();
   prefix2d<false>(D, rows, cols, threadIdx.x, blockDim.x);
   __syncthreads();
@@ -731,16 +758,7 @@ __device__ __forceinline__ void scatter_chunk(int c, const uint32_t* __restrict_
   __syncthreads();
   // phase 1: this warp's tile counts
   if (active) {
-    for (int r = rw + lane; r < vis; r += 32) {
-      const uint32_t eo = eb[r];
-      if (eo >= ew) break;
-      int x0, y0, x1, y1;
-      unpack_rect(rc[r], x0, y0, x1, y1);
-      const int wd = x1 - x0;
-      const uint32_t n = (uint32_t)(wd * (y1 - y0));
-      const uint32_t lo = max(sw, eo) - eo, hi = min(ew, eo + n) - eo;
-      diff_add_span(D, cols, x0, y0, wd, y1 - y0, (int)lo, (int)hi);
-    }
+    diff_add_gaussians(D, cols, eb, rc, rw + lane, 32, vis, sw, ew);
     __syncwarp();
     prefix2d<true>(D, rows, cols, lane, 32);
   }
