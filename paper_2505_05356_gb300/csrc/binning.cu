@@ -425,19 +425,50 @@ __global__ void __launch_bounds__(kSortThreads, 5)  // <= 48 registers, no spill
   uint32_t n_live = 0;
 #pragma unroll
   for (int ww = 0; ww < kSortWarps; ++ww) n_live += s_wsum[ww];
-  for (uint32_t p = tid; p < n_live; p += kSortThreads) {
-    const uint32_t k = s_key[p], g = s_id[p];
-    const uint32_t d = (k >> shift) & 255u;
-    const uint32_t dst = s_gbase[d] + (p - s_tstart[d]);
-    if (dst < (uint32_t)vis) {  // always (a timed-out wait leaves garbage, not a fault)
-      kout[fb + dst] = k;
-      iout[fb + dst] = g;
-      if (rout) {  // last pass: rectangle and tile count in depth order
-        const uint2 rr = rin[fb + g];
-        rout[fb + dst] = rr;
+  if (!rout) {
+    for (uint32_t p = tid; p < n_live; p += kSortThreads) {
+      const uint32_t k = s_key[p], g = s_id[p];
+      const uint32_t d = (k >> shift) & 255u;
+      const uint32_t dst = s_gbase[d] + (p - s_tstart[d]);
+      if (dst < (uint32_t)vis) {  // always (a timed-out wait leaves garbage, not a fault)
+        kout[fb + dst] = k;
+        iout[fb + dst] = g;
+      }
+    }
+    return;
+  }
+  // last pass: indices, rectangles and tile counts in depth order (the keys
+  // are not needed again); the rectangles' gathers of four places at once
+  constexpr int G = 4;
+#pragma unroll 1
+  for (uint32_t p0 = tid; p0 < n_live; p0 += G * kSortThreads) {
+    uint32_t gg[G], dd[G];
+    uint2 rr[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const uint32_t p = p0 + i * kSortThreads;
+      dd[i] = 0xFFFFFFFFu;
+      gg[i] = 0u;
+      rr[i] = make_uint2(0u, 0u);
+      if (p < n_live) {
+        const uint32_t k = s_key[p], g = s_id[p];
+        const uint32_t d = (k >> shift) & 255u;
+        const uint32_t dst = s_gbase[d] + (p - s_tstart[d]);
+        if (dst < (uint32_t)vis) {  // always (a timed-out wait leaves garbage, not a fault)
+          dd[i] = dst;
+          gg[i] = g;
+          rr[i] = rin[fb + g];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      if (dd[i] != 0xFFFFFFFFu) {
+        iout[fb + dd[i]] = gg[i];
+        rout[fb + dd[i]] = rr[i];
         int x0, y0, x1, y1;
-        unpack_rect(rr, x0, y0, x1, y1);
-        ecnt[fb + dst] = (uint32_t)((x1 - x0) * (y1 - y0));
+        unpack_rect(rr[i], x0, y0, x1, y1);
+        ecnt[fb + dd[i]] = (uint32_t)((x1 - x0) * (y1 - y0));
       }
     }
   }
