@@ -98,14 +98,17 @@ typedef struct {
   int32_t n_gaussians;   /* N in [0, 2^30)                                  */
   int32_t n_frames;      /* B in [1, GFTORF_MAX_FRAMES]                     */
   int32_t width, height; /* image size in pixels, >= 1                      */
-  int32_t tile_w, tile_h;/* one of 8x8, 16x16, 16x32, 32x32 (w x h)        */
+  int32_t tile_w, tile_h;/* one of 8x8, 16x16, 16x32, 32x32, 64x32 (w x h):
+                            the binning tile; a 64x32 tile's list is
+                            composited by two CTAs of 32x32 pixels         */
   int32_t n_freq;        /* F in [1, GFTORF_MAX_FREQ]                       */
   int32_t n_offsets;     /* P in [1, GFTORF_MAX_OFFSETS]                    */
   int32_t dtype;         /* gftorf_dtype                                    */
   int32_t render_mode;   /* 0: one CTA per (frame, tile);
                             1: persistent CTAs over a (frame, tile) queue   */
   int32_t pixels_per_thread; /* compositing pixels per thread: 1, 2 or 4
-                            (0: 2, or 4 for 32x32 tiles, which take only 4);
+                            (0: 2, or 4 for 32- and 64-wide tiles, which
+                            take only 4);
                             tile_w * tile_h / it must be >= 32.  Results do
                             not depend on it, nor on the tile shape.        */
   int32_t flags;         /* GFTORF_FLAG_* bits, 0 for the defaults         */

@@ -17,7 +17,7 @@ import torch
 
 from . import gftorf
 
-TILES: Tuple[Tuple[int, int], ...] = ((8, 8), (16, 16), (16, 32), (32, 32))
+TILES: Tuple[Tuple[int, int], ...] = ((8, 8), (16, 16), (16, 32), (32, 32), (64, 32))
 PIXELS_PER_THREAD = (1, 2, 4)
 MODES = (0, 1)
 
@@ -27,7 +27,7 @@ def candidates(tiles=TILES, ppts=PIXELS_PER_THREAD, modes=MODES) -> List[dict]:
     for (tw, th), ppt, mode in itertools.product(tiles, ppts, modes):
         if tw * th // ppt < 32:
             continue
-        if tw == 32 and ppt != 4:  # 32-wide tiles: 4 pixels per thread only
+        if tw >= 32 and ppt != 4:  # 32 wide or more: 4 pixels per thread only
             continue
         out.append(dict(tile=(tw, th), ppt=ppt, mode=mode))
     return out

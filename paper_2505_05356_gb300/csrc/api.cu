@@ -22,7 +22,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool tile_ok(int tw, int th) {
   return (tw == 8 && th == 8) || (tw == 16 && th == 16) || (tw == 16 && th == 32) ||
-         (tw == 32 && th == 32);
+         (tw == 32 && th == 32) || (tw == 64 && th == 32);
 }
 
 bool dims_ok(const gftorf_dims* d) {
@@ -38,7 +38,7 @@ bool dims_ok(const gftorf_dims* d) {
   if (d->render_mode != 0 && d->render_mode != 1) return false;
   const int ppt = d->pixels_per_thread;
   if (ppt != 0 && ppt != 1 && ppt != 2 && ppt != 4) return false;
-  if (d->tile_w == 32 && ppt != 0 && ppt != 4) return false;  // 32x32: 4 pixels per thread
+  if (d->tile_w >= 32 && ppt != 0 && ppt != 4) return false;  // 32 wide or more: 4 per thread
   if (d->tile_w * d->tile_h / (ppt ? ppt : 2) < 32) return false;  // a full warp per tile
   if (d->flags & ~(GFTORF_FLAG_NO_TILE_CULL | GFTORF_FLAG_COUNT_PAIRS | GFTORF_FLAG_PHASOR |
                    GFTORF_FLAG_DEPTH))
@@ -70,7 +70,7 @@ Layout make_layout(const gftorf_dims* d) {
   L.C = L.F * L.P + 1, L.NF = 2 * L.F + 1, L.dtype = d->dtype;
   L.real_size = d->dtype == GFTORF_F64 ? 8 : 4;
   L.mode = d->render_mode;
-  L.ppt = d->pixels_per_thread ? d->pixels_per_thread : (d->tile_w == 32 ? 4 : 2);
+  L.ppt = d->pixels_per_thread ? d->pixels_per_thread : (d->tile_w >= 32 ? 4 : 2);
   L.cull = (d->flags & GFTORF_FLAG_NO_TILE_CULL) ? 0 : 1;
   L.count_pairs = (d->flags & GFTORF_FLAG_COUNT_PAIRS) ? 1 : 0;
   L.phasor = (d->flags & GFTORF_FLAG_PHASOR) ? 1 : 0;

@@ -114,16 +114,30 @@ __device__ __forceinline__ int butterfly_slot(int lane) {
   return start < end ? start : -1;
 }
 
+// One CTA composites CW = min(TW, 32) columns of a binning tile: a 64-wide
+// tile (whose list is shared) is taken by S = 2 CTAs, each testing the
+// records against its own half, so each pixel composites the same records in
+// the same order as with 32-wide tiles.
 struct TileCtx {
   int b, tile, tx, ty;
+  int x0;  // first pixel column of the CTA's part of the tile
 };
 
-__device__ __forceinline__ TileCtx tile_of(uint32_t item, int NT, int tiles_x) {
+struct RenderGeom {
+  int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B, cull, phasor;
+  int CW, S;  // columns per CTA, CTAs per tile
+};
+
+__device__ __forceinline__ TileCtx tile_of(uint32_t item, const RenderGeom& rg) {
   TileCtx c;
-  c.b = item / NT;
-  c.tile = item - c.b * NT;
-  c.ty = c.tile / tiles_x;
-  c.tx = c.tile - c.ty * tiles_x;
+  const uint32_t per_frame = (uint32_t)rg.NT * rg.S;
+  c.b = item / per_frame;
+  const uint32_t sub = item - (uint32_t)c.b * per_frame;
+  c.tile = sub / rg.S;
+  const int part = (int)(sub - (uint32_t)c.tile * rg.S);
+  c.ty = c.tile / rg.tiles_x;
+  c.tx = c.tile - c.ty * rg.tiles_x;
+  c.x0 = c.tx * rg.TW + part * rg.CW;
   return c;
 }
 
@@ -158,10 +172,6 @@ __device__ __forceinline__ ThreadPix thread_pixels(int tid, int TW) {
   }
   return t;
 }
-
-struct RenderGeom {
-  int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B, cull, phasor;
-};
 
 // Can the Gaussian of record r reach alpha_min at some pixel centre of the
 // tile whose centres span [cx0, cx1] x [cy0, cy1]?  With A, B, C the negated
@@ -333,9 +343,9 @@ __device__ __forceinline__ void render_tile_fwd(
   constexpr int RS = rec_stride<Real, F>();
   constexpr unsigned ALL = (1u << PPT) - 1u;
   const int nthr = blockDim.x, tid = threadIdx.x;
-  const ThreadPix tp = thread_pixels<PPT>(tid, rg.TW);
+  const ThreadPix tp = thread_pixels<PPT>(tid, rg.CW);
   const int lx = tp.lx, ly0 = tp.ly0;
-  const int px = tc.tx * rg.TW + lx, py0 = tc.ty * rg.TH + ly0;
+  const int px = tc.x0 + lx, py0 = tc.ty * rg.TH + ly0;
   const Real fpx = (Real)px + Real(0.5);
   Real fpy[PPT];
   unsigned done = 0;
@@ -363,7 +373,7 @@ __device__ __forceinline__ void render_tile_fwd(
   }
 
   constexpr int V4 = RS * (int)sizeof(Real) / 16;
-  const Real cx0 = (Real)(tc.tx * rg.TW) + Real(0.5), cx1 = cx0 + (Real)(rg.TW - 1);
+  const Real cx0 = (Real)tc.x0 + Real(0.5), cx1 = cx0 + (Real)(rg.CW - 1);
   const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
   const Real log2_amin = log2(amin);
   // this warp's block of the tile (pixel centres)
@@ -504,10 +514,10 @@ __global__ void __launch_bounds__(kMaxThreads<PPT, WIDE>::value,
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_stage + (size_t)blockDim.x * RS);
   __shared__ int s_cnt[32];
   __shared__ unsigned s_mask[kMaskWords * kMaskWords];  // [warp][word]
-  const uint32_t items = (uint32_t)rg.B * rg.NT;
+  const uint32_t items = (uint32_t)rg.B * rg.NT * rg.S;
   if (!persistent) {
-    const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
-    render_tile_fwd<Real, F, PPT, DEPTH, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+    const uint32_t item = blockIdx.y * rg.NT * rg.S + blockIdx.x;
+    render_tile_fwd<Real, F, PPT, DEPTH, COUNT>(tile_of(item, rg), rg, tab, ranges,
                                          values, rec, bg, out, tfinal, nlast, s_rec, s_stage,
                                          s_idx, s_cnt, s_mask, hdr);
     return;
@@ -519,7 +529,7 @@ __global__ void __launch_bounds__(kMaxThreads<PPT, WIDE>::value,
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= items) break;
-    render_tile_fwd<Real, F, PPT, DEPTH, COUNT>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+    render_tile_fwd<Real, F, PPT, DEPTH, COUNT>(tile_of(item, rg), rg, tab, ranges,
                                          values, rec, bg, out, tfinal, nlast, s_rec, s_stage,
                                          s_idx, s_cnt, s_mask, hdr);
   }
@@ -542,9 +552,9 @@ __device__ __forceinline__ void render_tile_bwd(
   constexpr int RS = rec_stride<Real, F>();
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
-  const ThreadPix tp = thread_pixels<PPT>(tid, rg.TW);
+  const ThreadPix tp = thread_pixels<PPT>(tid, rg.CW);
   const int lx = tp.lx, ly0 = tp.ly0;
-  const int px = tc.tx * rg.TW + lx, py0 = tc.ty * rg.TH + ly0;
+  const int px = tc.x0 + lx, py0 = tc.ty * rg.TH + ly0;
   const Real fpx = (Real)px + Real(0.5);
   const Real amax = (Real)tab->alpha_max, amin = (Real)tab->alpha_min;
   const uint2 range = ranges[(size_t)tc.b * rg.NT + tc.tile];
@@ -641,7 +651,7 @@ __device__ __forceinline__ void render_tile_bwd(
   Real* gbase = g2d + (size_t)tc.b * rg.N * g2d_stride;
 
   constexpr int V4 = RS * (int)sizeof(Real) / 16;
-  const Real cx0 = (Real)(tc.tx * rg.TW) + Real(0.5), cx1 = cx0 + (Real)(rg.TW - 1);
+  const Real cx0 = (Real)tc.x0 + Real(0.5), cx1 = cx0 + (Real)(rg.CW - 1);
   const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
   const Real log2_amin = log2(amin);
   // this warp's block of the tile (pixel centres)
@@ -824,10 +834,10 @@ __global__ void __launch_bounds__(kMaxThreads<PPT, WIDE>::value,
   Real* s_stage = reinterpret_cast<Real*>(s_idx + nthr);
   __shared__ int s_cnt[32];
   __shared__ unsigned s_mask[kMaskWords * kMaskWords];  // [warp][word]
-  const uint32_t items = (uint32_t)rg.B * rg.NT;
+  const uint32_t items = (uint32_t)rg.B * rg.NT * rg.S;
   if (!persistent) {
-    const uint32_t item = blockIdx.y * rg.NT + blockIdx.x;
-    render_tile_bwd<Real, F, PPT, DEPTH>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+    const uint32_t item = blockIdx.y * rg.NT * rg.S + blockIdx.x;
+    render_tile_bwd<Real, F, PPT, DEPTH>(tile_of(item, rg), rg, tab, ranges,
                                   values, rec, bg, dout, tfinal, nlast, g2d,
                                   g2d_stride, dbg, s_rec, s_grad, s_id, s_red, s_idx, s_cnt,
                                   s_stage, s_mask);
@@ -840,7 +850,7 @@ __global__ void __launch_bounds__(kMaxThreads<PPT, WIDE>::value,
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= items) break;
-    render_tile_bwd<Real, F, PPT, DEPTH>(tile_of(item, rg.NT, rg.tiles_x), rg, tab, ranges,
+    render_tile_bwd<Real, F, PPT, DEPTH>(tile_of(item, rg), rg, tab, ranges,
                                   values, rec, bg, dout, tfinal, nlast, g2d,
                                   g2d_stride, dbg, s_rec, s_grad, s_id, s_red, s_idx, s_cnt,
                                   s_stage, s_mask);
@@ -852,6 +862,8 @@ RenderGeom geom_of(const Layout& L) {
   g.N = L.N, g.W = L.W, g.H = L.H, g.TW = L.TW, g.TH = L.TH;
   g.tiles_x = L.tiles_x, g.NT = L.NT, g.P = L.P, g.C = L.C;
   g.rec_stride = L.rec_stride, g.B = L.B, g.cull = L.cull, g.phasor = L.phasor;
+  g.CW = L.TW < 32 ? L.TW : 32;
+  g.S = L.TW / g.CW;
   return g;
 }
 
@@ -866,7 +878,8 @@ template <typename Real, int F, int PPT, bool DEPTH, bool COUNT, bool WIDE>
 void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                 cudaStream_t st) {
   constexpr int RS = rec_stride<Real, F>();
-  const int threads = L.TW * L.TH / PPT;
+  const RenderGeom rg = geom_of(L);
+  const int threads = rg.CW * L.TH / PPT;
   const size_t smem = (size_t)threads * (2 * RS * sizeof(Real) + sizeof(uint32_t));
   auto kernel = render_fwd_kernel<Real, F, PPT, DEPTH, COUNT, WIDE>;
   static PerDeviceOnce attr;
@@ -875,14 +888,14 @@ void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                                 96 * 1024) == cudaSuccess;
   });
   auto* hdr = at<Header>(ws, L.off_header);
-  dim3 grid(L.NT, L.B);
+  dim3 grid(L.NT * rg.S, L.B);
   if (L.mode == 1) {
     const int n = persistent_grid(kernel, threads, smem);
-    grid = dim3(min(n, L.B * L.NT), 1);
+    grid = dim3(min(n, L.B * L.NT * rg.S), 1);
     cudaMemsetAsync(&hdr->queue[0], 0, sizeof(uint32_t), st);
   }
   kernel<<<grid, threads, smem, st>>>(
-      geom_of(L), table_of<Real>(ws, L.off_table), hdr,
+      rg, table_of<Real>(ws, L.off_table), hdr,
       at<const uint2>(ws, L.off_ranges), at<const uint32_t>(ws, L.off_values),
       at<const Real>(ws, L.off_rec), bg, out, at<Real>(ws, L.off_tfinal),
       at<uint32_t>(ws, L.off_nlast), L.mode == 1);
@@ -895,7 +908,8 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
   constexpr int NF = 2 * F + 1;
   constexpr int GS = 6 + NF + (DEPTH ? 1 : 0);
   constexpr int RS = rec_stride<Real, F>();
-  const int threads = L.TW * L.TH / PPT;
+  const RenderGeom rg = geom_of(L);
+  const int threads = rg.CW * L.TH / PPT;
   const size_t smem = (size_t)threads * (2 * RS + GS) * sizeof(Real) +
                       32 * sizeof(Real) + (size_t)threads * 2 * sizeof(uint32_t);
   auto kernel = render_bwd_kernel<Real, F, PPT, DEPTH, WIDE>;
@@ -905,14 +919,14 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
                                 96 * 1024) == cudaSuccess;
   });
   auto* hdr = at<Header>(ws, L.off_header);
-  dim3 grid(L.NT, L.B);
+  dim3 grid(L.NT * rg.S, L.B);
   if (L.mode == 1) {
     const int n = persistent_grid(kernel, threads, smem);
-    grid = dim3(min(n, L.B * L.NT), 1);
+    grid = dim3(min(n, L.B * L.NT * rg.S), 1);
     cudaMemsetAsync(&hdr->queue[1], 0, sizeof(uint32_t), st);
   }
   kernel<<<grid, threads, smem, st>>>(
-      geom_of(L), table_of<Real>(ws, L.off_table), hdr,
+      rg, table_of<Real>(ws, L.off_table), hdr,
       at<const uint2>(ws, L.off_ranges), at<const uint32_t>(ws, L.off_values),
       at<const Real>(ws, L.off_rec), bg, dout, at<const Real>(ws, L.off_tfinal),
       at<const uint32_t>(ws, L.off_nlast), at<Real>(ws, L.off_g2d),

@@ -96,10 +96,11 @@ def _oracle_footprints(sc):
     return [np.ascontiguousarray(np.stack(a)) for a in (u, v, r, z)]
 
 
-@pytest.mark.parametrize("tile,least", [((16, 32), 40_000_000), ((32, 32), 25_000_000)])
+@pytest.mark.parametrize("tile,least", [((16, 32), 40_000_000), ((32, 32), 25_000_000),
+                                        ((64, 32), 14_000_000)])
 def test_sort_matches_oracle_bit_exact_at_benchmark_density(tile, least):
     """The benchmark's density: 300k Gaussians x 16 frames at 640x480 with
-    16x32 and 32x32 tiles (tens of millions of instances, thousands of
+    16x32, 32x32 and 64x32 tiles (tens of millions of instances, thousands of
     binning chunks, full-width scans), footprints as the oracle projects
     them, sorted by gftorf_sort_footprints and by the oracle's (key, index)
     sort."""

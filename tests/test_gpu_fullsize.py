@@ -47,6 +47,8 @@ FULL = [  # (workload, expected (n, frames, width, height), tile, ppt, mode, gra
     ("batch_300k", (300_000, 16, 640, 480), (16, 32), 4, 0, False),
     ("batch_300k", (300_000, 16, 640, 480), (16, 32), 4, 1, True),
     ("batch_300k", (300_000, 16, 640, 480), (32, 32), 4, 0, True),
+    ("batch_300k", (300_000, 16, 640, 480), (64, 32), 4, 0, True),
+    ("twofreq_500k", (500_000, 8, 640, 576), (64, 32), 4, 1, False),
     ("dynamic_100k", (100_000, 1, 640, 480), (16, 32), 4, 1, True),
     ("twofreq_500k", (500_000, 8, 640, 576), (16, 32), 4, 1, True),
 ]
