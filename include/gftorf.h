@@ -98,9 +98,10 @@ typedef struct {
   int32_t n_gaussians;   /* N in [0, 2^30)                                  */
   int32_t n_frames;      /* B in [1, GFTORF_MAX_FRAMES]                     */
   int32_t width, height; /* image size in pixels, >= 1                      */
-  int32_t tile_w, tile_h;/* one of 8x8, 16x16, 16x32, 32x32, 64x32 (w x h):
-                            the binning tile; a 64x32 tile's list is
-                            composited by two CTAs of 32x32 pixels         */
+  int32_t tile_w, tile_h;/* one of 8x8, 16x16, 16x32, 32x32, 64x32, 64x64
+                            (w x h): the binning tile; a 64x32 or 64x64
+                            tile's list is composited by two or four CTAs
+                            of 32x32 pixels                               */
   int32_t n_freq;        /* F in [1, GFTORF_MAX_FREQ]                       */
   int32_t n_offsets;     /* P in [1, GFTORF_MAX_OFFSETS]                    */
   int32_t dtype;         /* gftorf_dtype                                    */

@@ -17,7 +17,7 @@ import torch
 
 from . import gftorf
 
-TILES: Tuple[Tuple[int, int], ...] = ((8, 8), (16, 16), (16, 32), (32, 32), (64, 32))
+TILES: Tuple[Tuple[int, int], ...] = ((8, 8), (16, 16), (16, 32), (32, 32), (64, 32), (64, 64))
 PIXELS_PER_THREAD = (1, 2, 4)
 MODES = (0, 1)
 

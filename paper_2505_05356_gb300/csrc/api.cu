@@ -22,7 +22,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool tile_ok(int tw, int th) {
   return (tw == 8 && th == 8) || (tw == 16 && th == 16) || (tw == 16 && th == 32) ||
-         (tw == 32 && th == 32) || (tw == 64 && th == 32);
+         (tw == 32 && th == 32) || (tw == 64 && th == 32) || (tw == 64 && th == 64);
 }
 
 bool dims_ok(const gftorf_dims* d) {

@@ -114,18 +114,19 @@ __device__ __forceinline__ int butterfly_slot(int lane) {
   return start < end ? start : -1;
 }
 
-// One CTA composites CW = min(TW, 32) columns of a binning tile: a 64-wide
-// tile (whose list is shared) is taken by S = 2 CTAs, each testing the
-// records against its own half, so each pixel composites the same records in
-// the same order as with 32-wide tiles.
+// One CTA composites a CW x CH part of a binning tile (CW = min(TW, 32); CH =
+// 32 for tiles 32 or more wide, else TH): a 64x32 tile (whose list is shared)
+// is taken by S = 2 CTAs, a 64x64 one by 4, each testing the records against
+// its own part, so each pixel composites the same records in the same order
+// as with 32x32 tiles.
 struct TileCtx {
   int b, tile, tx, ty;
-  int x0;  // first pixel column of the CTA's part of the tile
+  int x0, y0;  // first pixel column and row of the CTA's part of the tile
 };
 
 struct RenderGeom {
   int N, W, H, TW, TH, tiles_x, NT, P, C, rec_stride, B, cull, phasor;
-  int CW, S;  // columns per CTA, CTAs per tile
+  int CW, CH, SX, S;  // columns and rows per CTA, CTAs across and per tile
 };
 
 __device__ __forceinline__ TileCtx tile_of(uint32_t item, const RenderGeom& rg) {
@@ -137,7 +138,9 @@ __device__ __forceinline__ TileCtx tile_of(uint32_t item, const RenderGeom& rg) 
   const int part = (int)(sub - (uint32_t)c.tile * rg.S);
   c.ty = c.tile / rg.tiles_x;
   c.tx = c.tile - c.ty * rg.tiles_x;
-  c.x0 = c.tx * rg.TW + part * rg.CW;
+  const int py = part / rg.SX, pxp = part - py * rg.SX;
+  c.x0 = c.tx * rg.TW + pxp * rg.CW;
+  c.y0 = c.ty * rg.TH + py * rg.CH;
   return c;
 }
 
@@ -345,7 +348,7 @@ __device__ __forceinline__ void render_tile_fwd(
   const int nthr = blockDim.x, tid = threadIdx.x;
   const ThreadPix tp = thread_pixels<PPT>(tid, rg.CW);
   const int lx = tp.lx, ly0 = tp.ly0;
-  const int px = tc.x0 + lx, py0 = tc.ty * rg.TH + ly0;
+  const int px = tc.x0 + lx, py0 = tc.y0 + ly0;
   const Real fpx = (Real)px + Real(0.5);
   Real fpy[PPT];
   unsigned done = 0;
@@ -374,7 +377,7 @@ __device__ __forceinline__ void render_tile_fwd(
 
   constexpr int V4 = RS * (int)sizeof(Real) / 16;
   const Real cx0 = (Real)tc.x0 + Real(0.5), cx1 = cx0 + (Real)(rg.CW - 1);
-  const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
+  const Real cy0 = (Real)tc.y0 + Real(0.5), cy1 = cy0 + (Real)(rg.CH - 1);
   const Real log2_amin = log2(amin);
   // this warp's block of the tile (pixel centres)
   const int lane = tid & 31, wid = tid >> 5;
@@ -554,7 +557,7 @@ __device__ __forceinline__ void render_tile_bwd(
   const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
   const ThreadPix tp = thread_pixels<PPT>(tid, rg.CW);
   const int lx = tp.lx, ly0 = tp.ly0;
-  const int px = tc.x0 + lx, py0 = tc.ty * rg.TH + ly0;
+  const int px = tc.x0 + lx, py0 = tc.y0 + ly0;
   const Real fpx = (Real)px + Real(0.5);
   const Real amax = (Real)tab->alpha_max, amin = (Real)tab->alpha_min;
   const uint2 range = ranges[(size_t)tc.b * rg.NT + tc.tile];
@@ -652,7 +655,7 @@ __device__ __forceinline__ void render_tile_bwd(
 
   constexpr int V4 = RS * (int)sizeof(Real) / 16;
   const Real cx0 = (Real)tc.x0 + Real(0.5), cx1 = cx0 + (Real)(rg.CW - 1);
-  const Real cy0 = (Real)(tc.ty * rg.TH) + Real(0.5), cy1 = cy0 + (Real)(rg.TH - 1);
+  const Real cy0 = (Real)tc.y0 + Real(0.5), cy1 = cy0 + (Real)(rg.CH - 1);
   const Real log2_amin = log2(amin);
   // this warp's block of the tile (pixel centres)
   const Real wx0 = cx0 + (Real)tp.wx0, wx1 = cx0 + (Real)tp.wx1;
@@ -863,7 +866,9 @@ RenderGeom geom_of(const Layout& L) {
   g.tiles_x = L.tiles_x, g.NT = L.NT, g.P = L.P, g.C = L.C;
   g.rec_stride = L.rec_stride, g.B = L.B, g.cull = L.cull, g.phasor = L.phasor;
   g.CW = L.TW < 32 ? L.TW : 32;
-  g.S = L.TW / g.CW;
+  g.CH = L.TW < 32 ? L.TH : 32;
+  g.SX = L.TW / g.CW;
+  g.S = g.SX * (L.TH / g.CH);
   return g;
 }
 
@@ -879,7 +884,7 @@ void fwd_launch(const Layout& L, const Real* bg, Real* out, unsigned char* ws,
                 cudaStream_t st) {
   constexpr int RS = rec_stride<Real, F>();
   const RenderGeom rg = geom_of(L);
-  const int threads = rg.CW * L.TH / PPT;
+  const int threads = rg.CW * rg.CH / PPT;
   const size_t smem = (size_t)threads * (2 * RS * sizeof(Real) + sizeof(uint32_t));
   auto kernel = render_fwd_kernel<Real, F, PPT, DEPTH, COUNT, WIDE>;
   static PerDeviceOnce attr;
@@ -909,7 +914,7 @@ void bwd_launch(const Layout& L, const Real* bg, const Real* dout, Real* dbg,
   constexpr int GS = 6 + NF + (DEPTH ? 1 : 0);
   constexpr int RS = rec_stride<Real, F>();
   const RenderGeom rg = geom_of(L);
-  const int threads = rg.CW * L.TH / PPT;
+  const int threads = rg.CW * rg.CH / PPT;
   const size_t smem = (size_t)threads * (2 * RS + GS) * sizeof(Real) +
                       32 * sizeof(Real) + (size_t)threads * 2 * sizeof(uint32_t);
   auto kernel = render_bwd_kernel<Real, F, PPT, DEPTH, WIDE>;

@@ -48,6 +48,7 @@ FULL = [  # (workload, expected (n, frames, width, height), tile, ppt, mode, gra
     ("batch_300k", (300_000, 16, 640, 480), (16, 32), 4, 1, True),
     ("batch_300k", (300_000, 16, 640, 480), (32, 32), 4, 0, True),
     ("batch_300k", (300_000, 16, 640, 480), (64, 32), 4, 0, True),
+    ("batch_300k", (300_000, 16, 640, 480), (64, 64), 4, 1, True),
     ("twofreq_500k", (500_000, 8, 640, 576), (64, 32), 4, 1, False),
     ("dynamic_100k", (100_000, 1, 640, 480), (16, 32), 4, 1, True),
     ("twofreq_500k", (500_000, 8, 640, 576), (16, 32), 4, 1, True),
@@ -88,7 +89,11 @@ def test_full_size_sampled_tiles(name, size, tile, ppt, mode, full_grad):
         worst = max(worst, float(err[~flag].max()))
         for i in np.flatnonzero(flag):
             worst_alt = max(worst_alt, match_alternatives(got[i], r["alts"][int(i)], sigma))
-    assert npix == sc.frames * K_TILES * tile[0] * tile[1]  # the grids tile these images exactly
+    # every pixel of the sampled tiles that lies in the image (64-high tiles
+    # overhang 480-row images)
+    inside = sum(min(tile[0], sc.width - tx * tile[0]) * min(tile[1], sc.height - ty * tile[1])
+                 for b in range(sc.frames) for tx, ty in tiles[b])
+    assert npix == inside
     # every sampled pixel equals a valid oracle result: the nominal walk, or
     # (near-threshold decisions) the walk that decided them the same way
     assert worst <= 1e-5, worst
