@@ -8,8 +8,10 @@
 // BEFORE duplication -- they are a per-Gaussian key -- and whose high digit
 // (frame, tile) is one stable counting pass over the duplicated instances:
 //   1. depth sort: 4 passes of 8 bits over the per-frame depth keys
-//      (culled Gaussians carry 0xFFFFFFFF and end up last); the last pass
-//      also writes each Gaussian's tile rectangle in depth order;
+//      (culled Gaussians carry 0xFFFFFFFF and are left out), each tile of
+//      keys ranked in shared memory and written out in digit order; the last
+//      pass also writes each Gaussian's tile rectangle and tile count in
+//      depth order;
 //   2. emission offsets: exclusive scan (one pass, decoupled look-back) of
 //      the tiles each depth-ordered Gaussian covers, counted by the last
 //      depth-sort pass; chunks of kChunk consecutive instances per frame;
@@ -19,9 +21,9 @@
 //      (also summed into per-tile totals); a scan over each frame's chunks
 //      per tile, and over its tiles, gives the tile ranges;
 //   4. scatter: per warp of a chunk the same corner counts give its cursors;
-//      then the warp walks its Gaussians in depth order, lanes spread over
-//      one Gaussian's tiles, each writing the Gaussian index at its tile's
-//      running cursor (stable by construction).
+//      then the warp deals its instances out 32 at a time in emission order,
+//      each lane writing its Gaussian's index at its tile's running cursor
+//      (lanes of one tile in lane order: stable by construction).
 // The 64-bit keys themselves are never needed by the compositing kernels;
 // gftorf_export_tile_lists materialises them from the ranges.
 #include "gftorf_internal.cuh"

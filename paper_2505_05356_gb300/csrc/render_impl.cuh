@@ -2,7 +2,8 @@
 // backward re-walk (Eq. S3).  A thread owns PPT (1, 2 or 4) vertically
 // adjacent pixels of a tile, so each staged Gaussian record, its column
 // offset and (backward) its warp reduction serve PPT pixels; one CTA per
-// (frame, tile) or persistent CTAs pulling (frame, tile) items from a queue.
+// (frame, tile part) or persistent CTAs pulling such items from a queue (a
+// tile 64 wide is composited in 32x32 parts, one CTA each).
 //
 // Forward, per pixel, front to back over the tile's depth-ordered list:
 //   alpha = min(alpha_max, 2^(power2 + log2 o)), power2 = log2(e) * power
@@ -56,10 +57,10 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
-__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+// 1/a: one rcp.approx in single precision (the backward's T recovery and the
+// tile test's half-reciprocals tolerate its ~1 ulp), exact in double
 __device__ __forceinline__ float rcp_fast(float a) { return rcp_approx(a); }
 __device__ __forceinline__ double rcp_fast(double a) { return 1.0 / a; }
-__device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
 
 template <typename Real>
 __device__ __forceinline__ Real warp_sum(Real v) {
