@@ -58,8 +58,19 @@ def test_workspace_size_validates_dims(lib):
                 dict(tile_w=8, tile_h=8, pixels_per_thread=4), dict(flags=16),
                 dict(n_gaussians=-1), dict(max_instances=-1), dict(n_sh=2),
                 dict(n_sh=25), dict(reserved=1),
-                dict(max_instances=1 << 33)):
+                dict(max_instances=1 << 33),
+                # tiles 32 or more wide take 4 pixels per thread only; no other
+                # 64-wide or taller shapes
+                dict(tile_w=64, tile_h=32, pixels_per_thread=2),
+                dict(tile_w=64, tile_h=64, pixels_per_thread=1),
+                dict(tile_w=64, tile_h=16), dict(tile_w=128, tile_h=64),
+                dict(tile_w=32, tile_h=64)):
         assert lib.gftorf_workspace_size(ctypes.byref(_dims(**bad))) == 0, bad
+    # every binning tile shape, with its pixels per thread
+    for tw, th, ppt in ((8, 8, 1), (16, 16, 2), (16, 32, 4), (32, 32, 4), (64, 32, 4),
+                        (64, 64, 4), (64, 64, 0)):
+        d = _dims(tile_w=tw, tile_h=th, pixels_per_thread=ppt)
+        assert lib.gftorf_workspace_size(ctypes.byref(d)) > 0, (tw, th, ppt)
     assert lib.gftorf_workspace_size(None) == 0
     # the empty scene is a valid problem
     assert lib.gftorf_workspace_size(ctypes.byref(_dims(n_gaussians=0))) > 0
